@@ -1,0 +1,350 @@
+"""Benchmark: embeddings/s and queries/s of the GPU subgraph matcher.
+
+Workload (the power-law labelled configuration): an R-MAT scale-16 graph
+(65,536 vertices, edge factor 16, a=.57 b=.19 c=.19, symmetrised, deduplicated,
+self-loops removed) with 8 Zipf(1.0) vertex labels, and 20 random-walk
+queries of 4-8 vertices (induced edges, inherited labels).  Each query is
+restricted to a prefix [0, hi) of the image of query vertex 0 because the full
+results of these queries reach 10^10-10^17 rows; hi and the expected count and
+row digest of every slice were written by the CPU oracle
+(tests/golden/make_workloads.py).
+
+A step = all 20 query slices through the whole path (filter, order, every
+verification level with its count and write passes, sorting into canonical
+order), enumerating the sorted rows into a device buffer.  The graph is
+resident; L2 is flushed before each timed step (the graph is smaller than L2).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+One JSON line on rank 0.  `--impl reference` times the CPU oracle on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+GOLDEN = os.path.join(ROOT, "tests", "golden", "rmat16_labelled_slices.json")
+METRIC = "embeddings/sec & queries/sec at 1 GB300 (batched vs plain, bit-exact); p50/p99"
+UNIT = "embeddings/s"
+WORKLOAD = ("R-MAT scale 16 (65,536 vertices, edge factor 16), 8 Zipf(1.0) labels, "
+            "20 random-walk queries of 4-8 vertices, each on an oracle-sized root slice")
+
+
+def load_workload():
+    from paper_2003_01527_gb300 import inputs as I
+    with open(GOLDEN) as f:
+        gold = json.load(f)
+    g, _ = I.rmat_labelled_workload(scale=16, num_labels=8, zipf_s=1.0, num_queries=0, seed=2)
+    h = hashlib.sha256()
+    for a in (g.row_ptr, g.col, g.labels):
+        h.update(np.ascontiguousarray(a, dtype="<i4").tobytes())
+    if h.hexdigest() != gold["graph"]["sha256"]:
+        raise SystemExit("generated graph differs from the stored workload")
+    return g, gold["queries"]
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def rank_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# --------------------------------------------------------------- GPU arm
+
+
+def run_gpu(args):
+    import torch
+    rank, world, local = rank_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2003_01527_gb300 import build
+    build.build()
+    from paper_2003_01527_gb300 import gsm
+
+    g, queries = load_workload()
+    M = gsm.Matcher(device=local, time_kernels=True)
+    M.load_graph(g.row_ptr, g.col, g.labels, validate=True)
+    Qs = [M.query(q["k"], q["edges"], q["labels"]).restrict(0, 0, q["root_hi"]) for q in queries]
+    outs = [torch.empty(max(q["count"], 1) * q["k"], dtype=torch.int32, device="cuda")
+            for q in queries]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
+    stream = M.stream  # the library issues every kernel on this stream
+
+    def step():
+        total, launches = 0, 0
+        for Q, out in zip(Qs, outs):
+            _, c = M.enumerate(Q, out=out)
+            total += c
+            launches += M.last_run_stats()["kernel_launches"]
+        return total, launches
+
+    # warm-up, and bit-exact check against the stored oracle digests
+    for _ in range(max(args.warmup, 3)):
+        step()
+    for q, Q, out in zip(queries, Qs, outs):
+        _, c = M.enumerate(Q, out=out)
+        rows = out[:c * q["k"]].cpu().numpy().astype("<i4")
+        if c != q["count"] or hashlib.sha256(rows.tobytes()).hexdigest() != q["rows_sha256"]:
+            raise SystemExit(f"result mismatch on a query slice (count {c} vs {q['count']})")
+    M.kernel_stats(reset=True)
+
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms_total, embeddings, launches = 0.0, 0, 0
+    for _ in range(args.steps):
+        flush.fill_(1)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        e, l = step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms_total += ev0.elapsed_time(ev1)
+        embeddings += e
+        launches += l
+    clocks = sampler.stop()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    kstats = M.kernel_stats(reset=True)
+
+    ms_per_step = ms_total / args.steps
+    if dist:
+        t = torch.tensor([ms_per_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_per_step = float(t.item())
+    per_step = embeddings / args.steps
+    value = per_step * world / (ms_per_step / 1e3)
+    qps = len(queries) * world / (ms_per_step / 1e3)
+
+    # dominant kernel and its roofline
+    dom = max(kstats, key=lambda s: s["total_ms"])
+    peak, peak_kind = peaks()
+    achieved = dom["algo_bytes"] / (dom["total_ms"] / 1e3) / 1e9 if dom["total_ms"] else 0.0
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        try:
+            with open(prof) as f:
+                tr = json.load(f)
+            traffic = tr.get(dom["name"])
+        except Exception:
+            traffic = None
+
+    # end to end through the public API with host buffers: graph upload from
+    # pinned host memory, every query, rows read back to pinned host memory
+    pin = {k: torch.from_numpy(getattr(g, k)).pin_memory() for k in ("row_ptr", "col", "labels")}
+    host_out = [torch.empty(max(q["count"], 1) * q["k"], dtype=torch.int32).pin_memory()
+                for q in queries]
+    h2d = sum(t.numel() * 4 for t in pin.values())
+    d2h = sum(q["count"] * q["k"] * 4 for q in queries)
+    e2e_ms = []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        M.load_graph(pin["row_ptr"].numpy(), pin["col"].numpy(), pin["labels"].numpy())
+        for Q, out in zip(Qs, host_out):
+            M.enumerate(Q, out=out)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_value = per_step * world / (statistics.median(e2e_ms) / 1e3)
+
+    cpu = cpu_baseline(g, queries) if (rank == 0 and world == 1 and not args.no_cpu) else None
+
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic (seeded R-MAT + random-walk queries)",
+        "config": {"workload": WORKLOAD, "queries": len(queries),
+                   "embeddings_per_step": per_step, "mode": "enumerate, sorted rows on device",
+                   "l2": "flushed (512 MB write) before every timed step",
+                   "parallelism": f"replicas x{world}"},
+        "queries_per_sec": round(qps, 2),
+        "roofline": {"bound": "hbm", "kernel": dom["name"], "achieved": round(achieved, 1),
+                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": traffic, "peak_source": peak_kind},
+        "kernels": {s["name"]: {"launches": s["launches"], "ms": round(s["total_ms"], 3),
+                                "algo_GB": round(s["algo_bytes"] / 1e9, 4)}
+                    for s in kstats if s["launches"]},
+        "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": round(statistics.median(e2e_ms), 3)},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    M.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------------- CPU oracle
+
+
+def oracle_sample(g, queries, budget_s=20.0):
+    """The oracle on a bounded sample: the non-empty query slices in order,
+    each over a sub-range of its roots, until about budget_s seconds of work."""
+    import oracle
+    from paper_2003_01527_gb300 import inputs as I
+    t_total, emb, used = 0.0, 0, []
+    for i, q in enumerate(queries):
+        if q["count"] == 0:
+            continue
+        qq = I.query_from_edges(q["k"], q["edges"], q["labels"])
+        hi = max(1, q["root_hi"] // 4)
+        t0 = time.perf_counter()
+        c, _, rc = oracle.match(g, qq, enumerate=True, root_range=(0, hi))
+        dt = time.perf_counter() - t0
+        t_total += dt
+        emb += c
+        used.append(f"q{i}[0,{hi})")
+        if t_total > budget_s:
+            break
+    return emb, t_total, used
+
+
+def cpu_baseline(g, queries):
+    import oracle
+    emb, secs, used = oracle_sample(g, queries)
+    return {"value": round(emb / secs, 1), "unit": UNIT, "cores": oracle.max_threads(),
+            "kind": "oracle",
+            "sample": f"{len(used)} query slices, first quarter of each root range "
+                      f"({', '.join(used)}): {emb} embeddings enumerated and sorted in "
+                      f"{secs:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = rank_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    g, queries = load_workload()
+    for _ in range(args.warmup):
+        oracle_sample(g, queries, budget_s=2.0)
+    emb, secs = 0, 0.0
+    samples = []
+    for _ in range(args.steps):
+        e, s, used = oracle_sample(g, queries, budget_s=10.0)
+        emb += e
+        secs += s
+        samples = used
+    value = emb / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(secs / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic (seeded R-MAT + random-walk queries)",
+        "config": {"workload": WORKLOAD, "sample": ", ".join(samples)},
+        "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": oracle.max_threads(),
+                         "kind": "oracle", "sample": ", ".join(samples)},
+        "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gsm", choices=["gsm", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

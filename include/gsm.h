@@ -1,0 +1,210 @@
+/*
+ * gsm.h -- C ABI of libgsm, a GB300 (sm_103a) subgraph matcher.
+ *
+ * Problem (paper Sec. 1 and Sec. 3.2, "Our proposed algorithm: GSM"): given an
+ * undirected, vertex-labelled data graph G stored as CSR and a small connected
+ * labelled query graph Q, count or list every subgraph isomorphism of Q into G.
+ * An embedding is an injective map f : V(Q) -> V(G) with lab(f(u)) = qlab(u)
+ * for every query vertex u and {f(u), f(u')} in E(G) for every query edge
+ * {u, u'} (non-induced).  Embeddings are ordered maps: automorphic images are
+ * distinct results.  A result row is (f(q_0), ..., f(q_{k-1})) in query-vertex
+ * id order; rows are returned sorted lexicographically.
+ *
+ * Method (Sec. 3.2, Algorithm 1): per-query-vertex candidate filtering from
+ * label, degree and neighbourhood signatures; a host-side matching order along
+ * a query spanning tree; then one breadth-first verification level per query
+ * vertex, each checking label, injectivity and every non-tree query edge of a
+ * candidate in one step, with compaction of the survivors (Sec. 3.3), and
+ * intermediate results held under a fixed device-memory budget.
+ *
+ * Conventions
+ *  - Every call returns a gsm_status: GSM_OK (0), GSM_PENDING (1), or a
+ *    negative error.  No C++ exception crosses this boundary.  After an error
+ *    gsm_last_error(ctx) describes it.
+ *  - A gsm_ctx is used by one host thread at a time.
+ *  - Pointers are host pointers unless a flag says they are device pointers
+ *    (device pointers must belong to the context's device).
+ *  - Sizes are element counts unless named *_bytes.
+ */
+#ifndef GSM_H_
+#define GSM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t gsm_status;
+
+#define GSM_OK 0
+#define GSM_PENDING 1
+#define GSM_ERR_INVALID_ARG (-1)   /* a null pointer, a size out of range, a bad flag */
+#define GSM_ERR_INVALID_GRAPH (-2) /* CSR not sorted/symmetric, self-loop, duplicate */
+#define GSM_ERR_INVALID_QUERY (-3) /* k outside 1..16, bad edge, duplicate, disconnected */
+#define GSM_ERR_NO_GRAPH (-4)      /* matching before gsm_load_graph */
+#define GSM_ERR_OOM (-5)           /* the device allocator failed */
+#define GSM_ERR_BUDGET (-6)        /* one unit of work does not fit the memory budget */
+#define GSM_ERR_OVERFLOW (-7)      /* the count exceeds 2^64 - 1 */
+#define GSM_ERR_TRUNCATED (-8)     /* more rows than the caller's capacity */
+#define GSM_ERR_TIMEOUT (-9)       /* a bounded device wait gave up */
+#define GSM_ERR_CUDA (-10)         /* a CUDA runtime call failed */
+#define GSM_ERR_TOO_LARGE (-11)    /* nnz >= 2^31 or n >= 2^31 - 1 */
+
+typedef struct gsm_ctx gsm_ctx;
+typedef struct gsm_query gsm_query;
+
+/* Device memory hooks.  alloc returns a device pointer aligned to 256 bytes
+ * (or NULL on failure); free releases it.  `stream` is the context's stream. */
+typedef void *(*gsm_alloc_fn)(void *alloc_ctx, size_t bytes, void *stream);
+typedef void (*gsm_free_fn)(void *alloc_ctx, void *ptr, size_t bytes, void *stream);
+
+#define GSM_OPT_TIME_KERNELS 1 /* record per-kernel CUDA-event times (gsm_kernel_stats) */
+
+typedef struct gsm_options {
+  /* Cap on device memory for intermediate frontiers and scratch, in bytes.
+   * 0 = 90% of the device memory free at gsm_create.  The graph, candidate
+   * bitmaps and final result buffers are not counted. */
+  size_t mem_budget_bytes;
+  /* cudaStream_t every kernel and copy is issued on; NULL = a stream the
+   * library creates and owns. */
+  void *stream;
+  gsm_alloc_fn alloc; /* NULL = cudaMalloc */
+  gsm_free_fn free;   /* NULL = cudaFree */
+  void *alloc_ctx;
+  int32_t block_size;     /* threads per CTA of the extend kernels; 0 = 256; 128..1024, x32 */
+  int64_t chunk_rows;     /* max frontier rows per extend launch; 0 = from the budget */
+  int32_t filter_rounds;  /* extra candidate-refinement rounds (Sec. 3.2); 0 = one pass */
+  int32_t flags;          /* GSM_OPT_* */
+} gsm_options;
+
+/* Fills *opt with the defaults described above. */
+void gsm_default_options(gsm_options *opt);
+
+/* Creates a context on CUDA device `device`.  opt may be NULL (defaults).
+ * Errors: GSM_ERR_INVALID_ARG, GSM_ERR_CUDA. */
+gsm_status gsm_create(gsm_ctx **out, int32_t device, const gsm_options *opt);
+
+/* Releases every resource of the context (queries must be destroyed first). */
+void gsm_destroy(gsm_ctx *ctx);
+
+/* Message of the last error on this context ("" if none).  Owned by ctx. */
+const char *gsm_last_error(const gsm_ctx *ctx);
+
+/* Static name of a status code. */
+const char *gsm_status_string(gsm_status s);
+
+#define GSM_DEVICE_PTRS 1 /* row_ptr/col/labels are device pointers */
+#define GSM_VALIDATE 2    /* check sortedness, symmetry, self-loops, duplicates */
+
+/* Loads the data graph G (paper Sec. 3.3: CSR, no preprocessing).
+ *   n        vertices, 0 <= n < 2^31 - 1
+ *   nnz      directed CSR entries (= 2|E|), < 2^31
+ *   row_ptr  int32[n+1], row_ptr[0] = 0, row_ptr[n] = nnz, non-decreasing
+ *   col      int32[nnz], row v = col[row_ptr[v] .. row_ptr[v+1]), strictly
+ *            ascending, no v in its own row, and w in row v <=> v in row w
+ *   labels   int32[n] vertex labels (any int32 values), or NULL for all-zero
+ * The library copies the arrays (caller may free them on return) and keeps the
+ * copy resident; a second call replaces the graph.  row_ptr is always checked
+ * (GSM_ERR_INVALID_GRAPH); the rules on col are checked on the device with
+ * GSM_VALIDATE and are otherwise the caller's guarantee.  Errors:
+ * GSM_ERR_INVALID_ARG, GSM_ERR_TOO_LARGE, GSM_ERR_INVALID_GRAPH, GSM_ERR_OOM,
+ * GSM_ERR_CUDA. */
+gsm_status gsm_load_graph(gsm_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr,
+                          const int32_t *col, const int32_t *labels, int32_t flags);
+
+/* Creates a query graph Q (host memory only).
+ *   k       query vertices, 1..16
+ *   m       undirected edges
+ *   edges   int32[2m]: edge e joins edges[2e] and edges[2e+1]; no self-loop,
+ *           no edge listed twice (in either direction); Q must be connected
+ *   labels  int32[k] query labels, or NULL for all-zero labels
+ * Errors: GSM_ERR_INVALID_ARG, GSM_ERR_INVALID_QUERY. */
+gsm_status gsm_query_create(gsm_ctx *ctx, int32_t k, int32_t m, const int32_t *edges,
+                            const int32_t *labels, gsm_query **out);
+
+void gsm_query_destroy(gsm_query *q);
+
+/* Restricts the results of q to embeddings with lo <= f(u) < hi (a root-range
+ * slice; with u = 0 the slice is a contiguous block of the sorted result).
+ * Calling it again for the same u replaces the range.
+ * Errors: GSM_ERR_INVALID_ARG (u out of range, lo > hi, negative bound). */
+gsm_status gsm_query_restrict(gsm_query *q, int32_t u, int32_t lo, int32_t hi);
+
+/* Counts the embeddings of q in the loaded graph.
+ * Errors: GSM_ERR_NO_GRAPH, GSM_ERR_BUDGET, GSM_ERR_OOM, GSM_ERR_OVERFLOW,
+ * GSM_ERR_CUDA. */
+gsm_status gsm_count(gsm_ctx *ctx, const gsm_query *q, uint64_t *count);
+
+#define GSM_OUT_DEVICE 1 /* `out` is a device pointer */
+
+/* Lists the embeddings of q: out is int32[cap_rows * k], row-major, rows in
+ * ascending lexicographic order, column j = f(q_j).  *count receives the total
+ * number of embeddings.  If it exceeds cap_rows the first cap_rows rows are
+ * written and GSM_ERR_TRUNCATED is returned.  out may be NULL iff cap_rows = 0.
+ * Final rows are staged in library-owned device buffers (2 x count x k x 4
+ * bytes, outside the budget).  Errors: as gsm_count, plus GSM_ERR_TRUNCATED. */
+gsm_status gsm_enumerate(gsm_ctx *ctx, const gsm_query *q, int32_t *out, uint64_t cap_rows,
+                         uint64_t *count, int32_t flags);
+
+/* Copies rows [first, first + nrows) of the last gsm_enumerate result on this
+ * context (kept in library buffers until the next gsm_count / gsm_enumerate /
+ * gsm_candidates call) into out (host, or device with GSM_OUT_DEVICE).
+ * Errors: GSM_ERR_INVALID_ARG (range outside the last result), GSM_ERR_CUDA. */
+gsm_status gsm_last_rows(gsm_ctx *ctx, int32_t *out, uint64_t first, uint64_t nrows,
+                         int32_t flags);
+
+/* Candidate sets of the filtering step (paper Sec. 3.2, Algorithm 1
+ * Filter_candidate_set): bit v of bitmap u (word v/32, bit v%32) is set iff
+ * lab(v) = qlab(u), deg(v) >= deg_Q(u), for every label l the number of
+ * neighbours of v with label l is at least the number of query neighbours of u
+ * with label l, and v lies in u's restriction range (if any).
+ *   bitmaps  host uint32[k * ceil(n/32)] (may be NULL)
+ *   sizes    host uint64[k]: |C(u)| (may be NULL) */
+gsm_status gsm_candidates(gsm_ctx *ctx, const gsm_query *q, uint32_t *bitmaps, uint64_t *sizes);
+
+/* The matching order of Sec. 3.2 (host only, no device work): order[i] is the
+ * i-th query vertex placed, parent[i] the position (< i) of its spanning-tree
+ * parent (-1 for i = 0).  The first vertex minimises the candidate count
+ * (ties: larger query degree, then lower id); every later one maximises the
+ * number of edges to placed vertices, then minimises the candidate count, then
+ * maximises the query degree, then takes the lower id.  The parent is the
+ * earliest-placed neighbour.  cand_sizes = uint64[k] (NULL = all equal).
+ * Errors: GSM_ERR_INVALID_QUERY. */
+gsm_status gsm_plan_order(int32_t k, int32_t m, const int32_t *edges, const uint64_t *cand_sizes,
+                          int32_t *order, int32_t *parent);
+
+/* Per-kernel measurements, collected while GSM_OPT_TIME_KERNELS is set. */
+typedef struct gsm_kernel_stat {
+  char name[32];
+  uint64_t launches;
+  double total_ms;       /* sum of CUDA-event durations on the context's stream */
+  double algo_bytes;     /* algorithmic bytes moved by those launches */
+  uint64_t items;        /* work items (candidates checked, rows written, ...) */
+} gsm_kernel_stat;
+
+/* Copies up to max entries into out, returns the number of kernels tracked
+ * through *n.  reset != 0 clears the counters afterwards. */
+gsm_status gsm_kernel_stats(gsm_ctx *ctx, gsm_kernel_stat *out, int32_t max, int32_t *n,
+                            int32_t reset);
+
+/* Work counters of the last gsm_count / gsm_enumerate call. */
+typedef struct gsm_run_stats {
+  int32_t k;
+  int32_t order[16];
+  uint64_t cand_size[16];    /* |C(u)| per query vertex id */
+  uint64_t frontier[16];     /* rows at level i (i = 1..k; [0] unused) */
+  uint64_t candidates[16];   /* candidates checked while extending level i -> i+1 */
+  uint64_t chunks;           /* extend sub-chunks launched */
+  uint64_t peak_bytes;       /* high-water mark of budgeted device memory */
+  uint64_t kernel_launches;  /* kernels launched by the call */
+} gsm_run_stats;
+
+gsm_status gsm_last_run_stats(gsm_ctx *ctx, gsm_run_stats *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSM_H_ */

@@ -1,0 +1,1086 @@
+// libgsm host side: the C ABI of include/gsm.h, device-memory management, the
+// matching-order planner, and the level driver that runs one verification
+// level per query vertex (paper Sec. 3.2, Algorithm 1) depth-first over
+// frontier chunks so intermediate results stay inside a fixed budget.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gsm.h"
+#include "kernels.cuh"
+
+using namespace gsm;
+
+// ------------------------------------------------------------------ context
+
+namespace {
+
+struct KStat {
+  const char *name;
+  uint64_t launches = 0;
+  double total_ms = 0, algo_bytes = 0;
+  uint64_t items = 0;
+};
+
+enum KernelId { K_FILTER, K_LIST, K_PIVOT, K_COUNT, K_WRITE, K_SORT, K_NUM };
+const char *kKernelNames[K_NUM] = {"filter", "bitmap_to_list", "pivot_scan",
+                                   "extend_count", "extend_write", "sort_rows"};
+
+struct Pending {
+  int kid;
+  cudaEvent_t a, b;
+  double bytes;
+  uint64_t items;
+};
+
+struct Block {
+  char *ptr;
+  size_t cap;
+};
+
+}  // namespace
+
+struct gsm_query {
+  int32_t k = 0, m = 0;
+  std::vector<int32_t> edges;
+  int32_t labels[kMaxK] = {};
+  uint32_t adj[kMaxK] = {};
+  int32_t lo[kMaxK], hi[kMaxK];
+};
+
+struct gsm_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  gsm_options opt{};
+  size_t budget = 0;
+  std::string err;
+
+  // graph
+  bool has_graph = false;
+  int32_t n = 0;
+  int64_t nnz = 0;
+  int32_t max_deg = 0;
+  int32_t *d_rp = nullptr, *d_col = nullptr, *d_lab = nullptr;
+  std::vector<int32_t> label_values;  // sorted distinct labels; dense id = index
+
+  // query-lifetime buffers (outside the budget)
+  void *bitmaps = nullptr;
+  size_t bitmaps_cap = 0;
+  unsigned long long *d_small = nullptr;  // [0..15] sizes, [16] total, [17] err
+  void *acc[2] = {nullptr, nullptr};
+  size_t acc_cap[2] = {0, 0};
+  const int32_t *last_rows = nullptr;  // sorted rows of the last gsm_enumerate
+  uint64_t last_count = 0;
+  int32_t last_k = 0;
+
+  // budgeted memory: frontier stack (segmented) and scratch
+  std::vector<Block> blocks;
+  size_t top_block = 0, top_used = 0;  // stack pointer
+  size_t budget_used = 0;              // bytes allocated for blocks + scratch
+  size_t live_bytes = 0, peak_bytes = 0;
+  void *scratch = nullptr;
+  size_t scratch_cap = 0;
+
+  int64_t *h_stage = nullptr;  // pinned staging for small device->host reads
+
+  // stats
+  KStat kstats[K_NUM];
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> event_pool;
+  gsm_run_stats run{};
+};
+
+namespace {
+
+struct Fail {
+  gsm_status code;
+};
+
+void set_err(gsm_ctx *c, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  c->err = buf;
+}
+
+#define CU(call)                                                                     \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess) {                                                         \
+      set_err(ctx, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+              __LINE__);                                                             \
+      throw Fail{GSM_ERR_CUDA};                                                      \
+    }                                                                                \
+  } while (0)
+
+#define FAIL(code, ...)        \
+  do {                         \
+    set_err(ctx, __VA_ARGS__); \
+    throw Fail{code};          \
+  } while (0)
+
+void *dev_alloc(gsm_ctx *ctx, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  void *p = nullptr;
+  if (ctx->opt.alloc) {
+    p = ctx->opt.alloc(ctx->opt.alloc_ctx, bytes, ctx->stream);
+    if (!p) FAIL(GSM_ERR_OOM, "device allocation of %zu bytes failed", bytes);
+  } else {
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      FAIL(GSM_ERR_OOM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+  }
+  return p;
+}
+
+void dev_free(gsm_ctx *ctx, void *p, size_t bytes) {
+  if (!p) return;
+  if (ctx->opt.free)
+    ctx->opt.free(ctx->opt.alloc_ctx, p, bytes, ctx->stream);
+  else
+    cudaFree(p);
+}
+
+// Grows a buffer that is outside the budget; keeps the contents if asked.
+void ensure_buf(gsm_ctx *ctx, void **p, size_t *cap, size_t bytes, bool keep, size_t keep_bytes) {
+  if (*cap >= bytes && *p) return;
+  size_t want = std::max(bytes, *cap + *cap / 2);
+  void *q = dev_alloc(ctx, want);
+  if (keep && keep_bytes) CU(cudaMemcpyAsync(q, *p, keep_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  dev_free(ctx, *p, *cap);
+  *p = q;
+  *cap = want;
+}
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+// ---- budgeted stack ----
+
+struct Mark {
+  size_t block, used, live;
+};
+
+Mark stack_mark(gsm_ctx *c) { return {c->top_block, c->top_used, c->live_bytes}; }
+void stack_release(gsm_ctx *c, Mark m) {
+  c->top_block = m.block;
+  c->top_used = m.used;
+  c->live_bytes = m.live;
+}
+
+// First block index a push may use when the top block is full: the top
+// block itself if nothing live is in it, else the one above.
+size_t stack_start(const gsm_ctx *c) {
+  if (c->blocks.empty()) return 0;
+  return c->top_used == 0 ? c->top_block : c->top_block + 1;
+}
+
+// Can `bytes` be pushed without exceeding the budget?
+bool stack_fits(gsm_ctx *c, size_t bytes) {
+  bytes = align_up(bytes);
+  const auto &B = c->blocks;
+  if (c->top_block < B.size() && B[c->top_block].cap - c->top_used >= bytes) return true;
+  const size_t start = stack_start(c);
+  size_t free_above = 0;
+  for (size_t b = start; b < B.size(); ++b) {
+    if (B[b].cap >= bytes) return true;
+    free_above += B[b].cap;
+  }
+  return c->budget_used - free_above + bytes <= c->budget;
+}
+
+void *stack_push(gsm_ctx *ctx, size_t bytes) {
+  bytes = align_up(bytes);
+  auto &B = ctx->blocks;
+  char *p = nullptr;
+  if (ctx->top_block < B.size() && B[ctx->top_block].cap - ctx->top_used >= bytes) {
+    p = B[ctx->top_block].ptr + ctx->top_used;
+    ctx->top_used += bytes;
+  } else {
+    const size_t start = stack_start(ctx);
+    for (size_t b = start; b < B.size() && !p; ++b) {
+      if (B[b].cap >= bytes) {
+        std::swap(B[b], B[start]);  // blocks at or above start hold nothing live
+        p = B[start].ptr;
+      }
+    }
+    if (!p) {
+      // drop the cached blocks at or above start, then allocate a new one
+      while (B.size() > start) {
+        dev_free(ctx, B.back().ptr, B.back().cap);
+        ctx->budget_used -= B.back().cap;
+        B.pop_back();
+      }
+      const size_t last = B.empty() ? 0 : B.back().cap;
+      size_t want = std::max(bytes, std::max<size_t>(last * 2, size_t(64) << 20));
+      if (ctx->budget_used + want > ctx->budget) want = bytes;
+      if (ctx->budget_used + want > ctx->budget)
+        FAIL(GSM_ERR_BUDGET,
+             "frontier chunk of %zu bytes exceeds the memory budget (%zu of %zu in use)", bytes,
+             ctx->budget_used, ctx->budget);
+      B.push_back(Block{(char *)dev_alloc(ctx, want), want});
+      ctx->budget_used += want;
+      p = B[start].ptr;
+    }
+    ctx->top_block = start;
+    ctx->top_used = bytes;
+  }
+  ctx->live_bytes += bytes;
+  ctx->peak_bytes = std::max(ctx->peak_bytes, ctx->live_bytes + ctx->scratch_cap);
+  return p;
+}
+
+// Scratch: reused by every step, contents dead between steps.
+void *scratch_get(gsm_ctx *ctx, size_t bytes) {
+  bytes = align_up(bytes);
+  if (ctx->scratch_cap >= bytes) return ctx->scratch;
+  size_t want = std::max(bytes, ctx->scratch_cap * 2);
+  if (ctx->budget_used - ctx->scratch_cap + want > ctx->budget) want = bytes;
+  if (ctx->budget_used - ctx->scratch_cap + want > ctx->budget)
+    FAIL(GSM_ERR_BUDGET, "scratch of %zu bytes exceeds the memory budget", bytes);
+  if (ctx->scratch) {
+    CU(cudaStreamSynchronize(ctx->stream));
+    dev_free(ctx, ctx->scratch, ctx->scratch_cap);
+    ctx->budget_used -= ctx->scratch_cap;
+  }
+  ctx->scratch = dev_alloc(ctx, want);
+  ctx->scratch_cap = want;
+  ctx->budget_used += want;
+  ctx->peak_bytes = std::max(ctx->peak_bytes, ctx->live_bytes + ctx->scratch_cap);
+  return ctx->scratch;
+}
+
+// Carves consecutive aligned pieces out of one scratch request.
+struct Carve {
+  size_t off = 0;
+  template <typename T>
+  size_t add(int64_t elems) {
+    size_t o = off;
+    off = align_up(off + sizeof(T) * (size_t)std::max<int64_t>(elems, 1));
+    return o;
+  }
+};
+
+int64_t read_i64(gsm_ctx *ctx, const int64_t *dptr) {
+  CU(cudaMemcpyAsync(ctx->h_stage, dptr, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  return ctx->h_stage[0];
+}
+
+// ---- kernel timing ----
+
+cudaEvent_t get_event(gsm_ctx *ctx) {
+  if (!ctx->event_pool.empty()) {
+    cudaEvent_t e = ctx->event_pool.back();
+    ctx->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  CU(cudaEventCreate(&e));
+  return e;
+}
+
+template <typename F>
+void timed(gsm_ctx *ctx, int kid, double bytes, uint64_t items, int launches, F &&launch) {
+  const bool on = ctx->opt.flags & GSM_OPT_TIME_KERNELS;
+  Pending p{kid, nullptr, nullptr, bytes, items};
+  if (on) {
+    p.a = get_event(ctx);
+    p.b = get_event(ctx);
+    CU(cudaEventRecord(p.a, ctx->stream));
+  }
+  launch();
+  CU(cudaGetLastError());
+  ctx->run.kernel_launches += launches;
+  if (on) {
+    CU(cudaEventRecord(p.b, ctx->stream));
+    ctx->pending.push_back(p);
+  } else {
+    KStat &s = ctx->kstats[kid];
+    s.launches += 1;
+    s.algo_bytes += bytes;
+    s.items += items;
+  }
+}
+
+void resolve_timings(gsm_ctx *ctx) {
+  if (ctx->pending.empty()) return;
+  CU(cudaStreamSynchronize(ctx->stream));
+  for (auto &p : ctx->pending) {
+    float ms = 0;
+    CU(cudaEventElapsedTime(&ms, p.a, p.b));
+    KStat &s = ctx->kstats[p.kid];
+    s.launches += 1;
+    s.total_ms += ms;
+    s.algo_bytes += p.bytes;
+    s.items += p.items;
+    ctx->event_pool.push_back(p.a);
+    ctx->event_pool.push_back(p.b);
+  }
+  ctx->pending.clear();
+}
+
+// ------------------------------------------------------------------ planner
+
+int popc(uint32_t x) { return __builtin_popcount(x); }
+
+// Matching order of Sec. 3.2 (after VF3): first the vertex with the fewest
+// candidates (ties: larger degree, lower id); then repeatedly the unplaced
+// vertex with the most edges to placed vertices (d_M), then fewest candidates
+// (the P_f estimate), then larger degree, then lower id.  Since Q is
+// connected the chosen vertex always has a placed neighbour, so the order
+// follows a spanning tree; each vertex's parent is its earliest-placed
+// neighbour.
+void plan(int32_t k, const uint32_t *adj, const uint64_t *sizes, int32_t *order,
+          int32_t *parent) {
+  uint32_t placed = 0;
+  for (int32_t i = 0; i < k; ++i) {
+    int32_t best = -1;
+    for (int32_t u = 0; u < k; ++u) {
+      if (placed >> u & 1u) continue;
+      const int dm = popc(adj[u] & placed);
+      if (i > 0 && dm == 0) continue;
+      if (best < 0) {
+        best = u;
+        continue;
+      }
+      const int dmb = popc(adj[best] & placed);
+      const uint64_t su = sizes ? sizes[u] : 0, sb = sizes ? sizes[best] : 0;
+      const int du = popc(adj[u]), db = popc(adj[best]);
+      bool better;
+      if (dm != dmb) better = dm > dmb;
+      else if (su != sb) better = su < sb;
+      else if (du != db) better = du > db;
+      else better = u < best;
+      if (better) best = u;
+    }
+    order[i] = best;
+    placed |= 1u << best;
+    parent[i] = -1;
+    for (int32_t j = 0; j < i; ++j)
+      if (adj[best] >> order[j] & 1u) {
+        parent[i] = j;
+        break;
+      }
+  }
+}
+
+gsm_status validate_query_edges(int32_t k, int32_t m, const int32_t *edges, uint32_t *adj) {
+  if (k < 1 || k > kMaxK) return GSM_ERR_INVALID_QUERY;
+  if (m < 0 || m > k * (k - 1) / 2) return GSM_ERR_INVALID_QUERY;
+  if (m > 0 && !edges) return GSM_ERR_INVALID_ARG;
+  for (int32_t u = 0; u < k; ++u) adj[u] = 0;
+  for (int32_t e = 0; e < m; ++e) {
+    int32_t a = edges[2 * e], b = edges[2 * e + 1];
+    if (a < 0 || a >= k || b < 0 || b >= k || a == b) return GSM_ERR_INVALID_QUERY;
+    if (adj[a] >> b & 1u) return GSM_ERR_INVALID_QUERY;
+    adj[a] |= 1u << b;
+    adj[b] |= 1u << a;
+  }
+  uint32_t seen = 1u, frontier = 1u;
+  while (frontier) {
+    uint32_t next = 0;
+    for (int32_t u = 0; u < k; ++u)
+      if (frontier >> u & 1u) next |= adj[u];
+    frontier = next & ~seen;
+    seen |= next;
+  }
+  return seen == ((k == 32) ? 0xffffffffu : ((1u << k) - 1u)) ? GSM_OK : GSM_ERR_INVALID_QUERY;
+}
+
+// ------------------------------------------------------------------ driver
+
+struct Run {
+  gsm_ctx *ctx;
+  const gsm_query *q;
+  bool enumerate;
+  int32_t k;
+  int32_t order[kMaxK], parent[kMaxK];
+  LevelDesc lv[kMaxK];
+  GraphDev g;
+  int32_t block;
+  int64_t wcap;        // max candidates per extend launch
+  int64_t chunk_rows;  // max rows per extend launch (0 = unbounded)
+  uint64_t acc_rows = 0;
+  unsigned __int128 count = 0;
+  unsigned long long *d_total;
+};
+
+void recurse(Run &R, int32_t i, const int32_t *F, int64_t rows);
+
+void process_sub(Run &R, int32_t i, const int32_t *F, const int32_t *pstart, const uint8_t *pslot,
+                 const int64_t *woff, int64_t ra, int64_t rb, int64_t wa, int64_t wb) {
+  gsm_ctx *ctx = R.ctx;
+  const LevelDesc &d = R.lv[i];
+  const bool last = i == R.k - 1;
+  const int64_t W = wb - wa, nrows = rb - ra;
+  if (W <= 0) return;
+  const int64_t tile_items = (int64_t)R.block * kItemsPerThread;
+  const int64_t tiles = (W + tile_items - 1) / tile_items;
+  const double read_bytes = (double)nrows * (4.0 * i + 13.0) + 4.0 * (double)W;
+  ctx->run.chunks += 1;
+  if (last && !R.enumerate) {
+    timed(ctx, K_COUNT, read_bytes, (uint64_t)W, 1, [&] {
+      launch_extend_count(R.g, d, F, pstart, pslot, woff, ra, rb, wa, wb, R.block, nullptr,
+                          nullptr, R.d_total, ctx->stream);
+    });
+    return;
+  }
+  Carve cv;
+  const size_t o_mask = cv.add<uint32_t>(tiles * (tile_items / 32));
+  const size_t o_cnt = cv.add<int32_t>(tiles);
+  const size_t o_off = cv.add<int64_t>(tiles + 1);
+  const size_t o_tmp = cv.add<int64_t>(scan_tmp_elems(tiles));
+  char *sc = (char *)scratch_get(ctx, cv.off);
+  uint32_t *masks = (uint32_t *)(sc + o_mask);
+  int32_t *tile_cnt = (int32_t *)(sc + o_cnt);
+  int64_t *tile_off = (int64_t *)(sc + o_off);
+  int64_t *tmp = (int64_t *)(sc + o_tmp);
+  timed(ctx, K_COUNT, read_bytes + W / 8.0, (uint64_t)W, 1, [&] {
+    launch_extend_count(R.g, d, F, pstart, pslot, woff, ra, rb, wa, wb, R.block, masks, tile_cnt,
+                        nullptr, ctx->stream);
+  });
+  timed(ctx, K_PIVOT, 12.0 * tiles, (uint64_t)tiles, 3,
+        [&] { launch_scan_i32(tile_cnt, tile_off, tiles, tmp, ctx->stream); });
+  const int64_t S = read_i64(ctx, tile_off + tiles);
+  if (S == 0) return;
+  const int32_t w_out = i + 1;
+  if (last) {
+    const size_t need = (size_t)(R.acc_rows + S) * R.k * sizeof(int32_t);
+    ensure_buf(ctx, &ctx->acc[0], &ctx->acc_cap[0], need, true,
+               (size_t)R.acc_rows * R.k * sizeof(int32_t));
+    int32_t *out = (int32_t *)ctx->acc[0] + (size_t)R.acc_rows * R.k;
+    timed(ctx, K_WRITE, 4.0 * S * w_out, (uint64_t)S, 1, [&] {
+      launch_extend_write(R.g, d, F, pstart, woff, ra, rb, wa, wb, R.block, masks, tile_off, out,
+                          ctx->stream);
+    });
+    R.acc_rows += (uint64_t)S;
+    return;
+  }
+  const size_t bytes = (size_t)S * w_out * sizeof(int32_t);
+  if (!stack_fits(ctx, bytes)) {
+    if (nrows <= 1)
+      FAIL(GSM_ERR_BUDGET, "the %lld partial results of one row need %zu bytes, over the budget",
+           (long long)S, bytes);
+    const int64_t mid = ra + nrows / 2;
+    const int64_t wmid = read_i64(ctx, woff + mid);
+    process_sub(R, i, F, pstart, pslot, woff, ra, mid, wa, wmid);
+    process_sub(R, i, F, pstart, pslot, woff, mid, rb, wmid, wb);
+    return;
+  }
+  const Mark mk = stack_mark(ctx);
+  int32_t *Fn = (int32_t *)stack_push(ctx, bytes);
+  timed(ctx, K_WRITE, 4.0 * S * w_out, (uint64_t)S, 1, [&] {
+    launch_extend_write(R.g, d, F, pstart, woff, ra, rb, wa, wb, R.block, masks, tile_off, Fn,
+                        ctx->stream);
+  });
+  recurse(R, i + 1, Fn, S);
+  stack_release(ctx, mk);
+}
+
+// Extends rows of width i (F, `rows` of them) through the remaining levels.
+void recurse(Run &R, int32_t i, const int32_t *F, int64_t rows) {
+  gsm_ctx *ctx = R.ctx;
+  if (rows <= 0) return;
+  const LevelDesc &d = R.lv[i];
+  const Mark mk = stack_mark(ctx);
+  int32_t *pstart = (int32_t *)stack_push(ctx, sizeof(int32_t) * rows);
+  uint8_t *pslot = (uint8_t *)stack_push(ctx, rows);
+  int64_t *woff = (int64_t *)stack_push(ctx, sizeof(int64_t) * (rows + 1));
+  int64_t *tmp = (int64_t *)scratch_get(ctx, sizeof(int64_t) * scan_tmp_elems(rows));
+  timed(ctx, K_PIVOT, (double)rows * (4.0 * d.nb + 8.0 * d.nb + 13.0 + 16.0), (uint64_t)rows, 4, [&] {
+    launch_pivot(R.g, d, F, rows, pstart, pslot, woff, ctx->stream);
+    launch_scan_i64(woff, woff, rows, tmp, ctx->stream);
+  });
+  const int64_t W = read_i64(ctx, woff + rows);
+  ctx->run.frontier[i] += (uint64_t)rows;
+  ctx->run.candidates[i] += (uint64_t)W;
+  const bool split_w = W > R.wcap;
+  const bool split_r = R.chunk_rows > 0 && rows > R.chunk_rows;
+  if (!split_w && !split_r) {
+    process_sub(R, i, F, pstart, pslot, woff, 0, rows, 0, W);
+  } else {
+    // row boundaries: work targets (each piece <= wcap) merged with multiples of chunk_rows
+    std::vector<int64_t> bnd, bw;
+    if (split_w) {
+      const int64_t step = std::max<int64_t>(1, R.wcap - ctx->max_deg);
+      const int64_t J = (W + step - 1) / step;
+      Carve cv;
+      const size_t o_b = cv.add<int64_t>(J + 1), o_w = cv.add<int64_t>(J + 1);
+      char *sc = (char *)scratch_get(ctx, cv.off);
+      launch_split_points(woff, rows, step, J, (int64_t *)(sc + o_b), (int64_t *)(sc + o_w),
+                          ctx->stream);
+      CU(cudaGetLastError());
+      bnd.resize(J + 1);
+      CU(cudaMemcpyAsync(bnd.data(), sc + o_b, sizeof(int64_t) * (J + 1), cudaMemcpyDeviceToHost,
+                         ctx->stream));
+      CU(cudaStreamSynchronize(ctx->stream));
+      bnd[0] = 0;
+    } else {
+      bnd = {0, rows};
+    }
+    if (split_r) {
+      std::vector<int64_t> extra;
+      for (int64_t r = R.chunk_rows; r < rows; r += R.chunk_rows) extra.push_back(r);
+      bnd.insert(bnd.end(), extra.begin(), extra.end());
+    }
+    std::sort(bnd.begin(), bnd.end());
+    bnd.erase(std::unique(bnd.begin(), bnd.end()), bnd.end());
+    // work offset at every boundary
+    bw.resize(bnd.size());
+    for (size_t j = 0; j < bnd.size(); ++j) {
+      CU(cudaMemcpyAsync(&bw[j], woff + bnd[j], sizeof(int64_t), cudaMemcpyDeviceToHost,
+                         ctx->stream));
+    }
+    CU(cudaStreamSynchronize(ctx->stream));
+    for (size_t j = 0; j + 1 < bnd.size(); ++j)
+      process_sub(R, i, F, pstart, pslot, woff, bnd[j], bnd[j + 1], bw[j], bw[j + 1]);
+  }
+  stack_release(ctx, mk);
+}
+
+void fill_filter(gsm_ctx *ctx, const gsm_query *q, const int32_t *dense, FilterDesc &fd) {
+  std::memset(&fd, 0, sizeof(fd));
+  fd.k = q->k;
+  fd.n_words = (ctx->n + 31) / 32;
+  for (int32_t u = 0; u < q->k; ++u) {
+    fd.qlab[u] = dense[u];
+    fd.qdeg[u] = popc(q->adj[u]);
+    fd.lo[u] = std::max<int32_t>(0, q->lo[u]);
+    fd.hi[u] = std::min<int32_t>(ctx->n, q->hi[u]);
+  }
+  if (ctx->label_values.size() <= 1) return;  // one label: counts equal degrees
+  for (int32_t u = 0; u < q->k; ++u) {
+    int32_t lab_of[kMaxK], cnt_of[kMaxK], nl = 0;
+    for (int32_t w = 0; w < q->k; ++w) {
+      if (!(q->adj[u] >> w & 1u)) continue;
+      int32_t j = 0;
+      while (j < nl && lab_of[j] != dense[w]) ++j;
+      if (j == nl) {
+        lab_of[nl] = dense[w];
+        cnt_of[nl++] = 0;
+      }
+      cnt_of[j]++;
+    }
+    for (int32_t j = 0; j < nl; ++j) {
+      int32_t s = 0;
+      while (s < fd.nslots && fd.slot_label[s] != lab_of[j]) ++s;
+      if (s == fd.nslots) fd.slot_label[fd.nslots++] = lab_of[j];
+      fd.req_slot[u][fd.nreq[u]] = s;
+      fd.req_cnt[u][fd.nreq[u]++] = cnt_of[j];
+    }
+  }
+}
+
+// Maps query labels to the graph's dense label ids; false if one is absent.
+bool dense_labels(gsm_ctx *ctx, const gsm_query *q, int32_t *dense) {
+  for (int32_t u = 0; u < q->k; ++u) {
+    auto it = std::lower_bound(ctx->label_values.begin(), ctx->label_values.end(), q->labels[u]);
+    if (it == ctx->label_values.end() || *it != q->labels[u]) return false;
+    dense[u] = (int32_t)(it - ctx->label_values.begin());
+  }
+  return true;
+}
+
+// Filtering step: fills the k candidate bitmaps and returns |C(u)|.
+void run_filter(gsm_ctx *ctx, const gsm_query *q, const int32_t *dense, uint64_t *sizes) {
+  FilterDesc fd;
+  fill_filter(ctx, q, dense, fd);
+  const size_t bytes = (size_t)q->k * fd.n_words * sizeof(uint32_t);
+  ensure_buf(ctx, &ctx->bitmaps, &ctx->bitmaps_cap, bytes, false, 0);
+  CU(cudaMemsetAsync(ctx->d_small, 0, sizeof(unsigned long long) * kMaxK, ctx->stream));
+  GraphDev g{ctx->n, ctx->nnz, ctx->d_rp, ctx->d_col, ctx->d_lab};
+  timed(ctx, K_FILTER, 12.0 * ctx->n + bytes, (uint64_t)ctx->n, 1, [&] {
+    launch_filter(g, fd, (uint32_t *)ctx->bitmaps, ctx->d_small, ctx->stream);
+  });
+  CU(cudaMemcpyAsync(ctx->h_stage, ctx->d_small, sizeof(uint64_t) * q->k, cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  std::memcpy(sizes, ctx->h_stage, sizeof(uint64_t) * q->k);
+}
+
+// The whole matcher for one query.  out == nullptr and !enumerate: count only.
+void run_query(gsm_ctx *ctx, const gsm_query *q, bool enumerate, int32_t *out, uint64_t cap_rows,
+               int32_t flags, uint64_t *count_out, bool *truncated) {
+  if (!ctx->has_graph) FAIL(GSM_ERR_NO_GRAPH, "no data graph loaded");
+  std::memset(&ctx->run, 0, sizeof(ctx->run));
+  // nothing is live between calls (an earlier call may have failed mid-way)
+  ctx->top_block = 0;
+  ctx->top_used = 0;
+  ctx->live_bytes = 0;
+  ctx->last_rows = nullptr;
+  ctx->last_count = 0;
+  ctx->last_k = q->k;
+  ctx->peak_bytes = 0;
+  Run R;
+  R.ctx = ctx;
+  R.q = q;
+  R.enumerate = enumerate;
+  R.k = q->k;
+  R.g = GraphDev{ctx->n, ctx->nnz, ctx->d_rp, ctx->d_col, ctx->d_lab};
+  R.block = ctx->opt.block_size > 0 ? ctx->opt.block_size : 256;
+  R.chunk_rows = ctx->opt.chunk_rows;
+  R.wcap = std::max<int64_t>((int64_t)ctx->max_deg + 1,
+                             std::min<int64_t>(int64_t(1) << 30, (int64_t)(ctx->budget / 2)));
+  R.d_total = ctx->d_small + kMaxK;
+  ctx->run.k = q->k;
+  *truncated = false;
+  *count_out = 0;
+
+  int32_t dense[kMaxK];
+  uint64_t sizes[kMaxK] = {};
+  if (!dense_labels(ctx, q, dense)) return;  // a query label absent from G: no embedding
+  run_filter(ctx, q, dense, sizes);
+  for (int32_t u = 0; u < q->k; ++u) ctx->run.cand_size[u] = sizes[u];
+  for (int32_t u = 0; u < q->k; ++u)
+    if (sizes[u] == 0) return;
+  plan(q->k, q->adj, sizes, R.order, R.parent);
+  for (int32_t i = 0; i < q->k; ++i) ctx->run.order[i] = R.order[i];
+
+  const int32_t nw = (ctx->n + 31) / 32;
+  const uint32_t *bm = (const uint32_t *)ctx->bitmaps;
+  for (int32_t i = 1; i < q->k; ++i) {
+    LevelDesc &d = R.lv[i];
+    std::memset(&d, 0, sizeof(d));
+    const int32_t u = R.order[i];
+    d.i = i;
+    for (int32_t j = 0; j < i; ++j) {
+      const int32_t uj = R.order[j];
+      if (q->adj[u] >> uj & 1u)
+        d.bpos[d.nb++] = j;  // ascending position: the first is the tree parent
+      else if (dense[uj] == dense[u])
+        d.inj[d.ninj++] = j;
+    }
+    for (int32_t j = 0; j <= i; ++j) d.out_col[j] = (i == q->k - 1) ? R.order[j] : j;
+    d.bitmap = bm + (size_t)u * nw;
+  }
+
+  CU(cudaMemsetAsync(R.d_total, 0, sizeof(unsigned long long), ctx->stream));
+  const Mark mk = stack_mark(ctx);
+  const int64_t R1 = (int64_t)sizes[R.order[0]];
+  int32_t *F1 = (int32_t *)stack_push(ctx, sizeof(int32_t) * R1);
+  {
+    Carve cv;
+    const size_t o_cnt = cv.add<int32_t>(nw), o_off = cv.add<int64_t>(nw + 1),
+                 o_tmp = cv.add<int64_t>(scan_tmp_elems(nw));
+    char *sc = (char *)scratch_get(ctx, cv.off);
+    timed(ctx, K_LIST, nw * 4.0 + 4.0 * R1, (uint64_t)R1, 5, [&] {
+      launch_bitmap_to_list(bm + (size_t)R.order[0] * nw, nw, (int32_t *)(sc + o_cnt),
+                            (int64_t *)(sc + o_off), (int64_t *)(sc + o_tmp), F1, ctx->stream);
+    });
+  }
+  ctx->run.frontier[1] = (uint64_t)R1;
+  if (q->k == 1) {
+    if (enumerate) {
+      ensure_buf(ctx, &ctx->acc[0], &ctx->acc_cap[0], sizeof(int32_t) * R1, false, 0);
+      CU(cudaMemcpyAsync(ctx->acc[0], F1, sizeof(int32_t) * R1, cudaMemcpyDeviceToDevice,
+                         ctx->stream));
+    }
+    R.acc_rows = (uint64_t)R1;
+  } else {
+    recurse(R, 1, F1, R1);
+  }
+  stack_release(ctx, mk);
+
+  uint64_t total;
+  if (enumerate || q->k == 1) {
+    total = R.acc_rows;
+  } else {
+    CU(cudaMemcpyAsync(ctx->h_stage, R.d_total, sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    total = (uint64_t)ctx->h_stage[0];
+  }
+  ctx->run.frontier[q->k] = total;
+  *count_out = total;
+  if (!enumerate) return;
+
+  // canonical order: rows are already sorted when the matching order is the
+  // identity (levels emit rows in lexicographic order of the matching order)
+  int32_t *rows = (int32_t *)ctx->acc[0];
+  bool identity = true;
+  for (int32_t j = 0; j < q->k; ++j) identity = identity && R.order[j] == j;
+  if (!identity && total > 1) {
+    const size_t bytes = (size_t)total * q->k * sizeof(int32_t);
+    ensure_buf(ctx, &ctx->acc[1], &ctx->acc_cap[1], bytes, false, 0);
+    const int64_t H = sort_hist_elems((int64_t)total);
+    Carve cv;
+    const size_t o_h = cv.add<int32_t>(H), o_ho = cv.add<int64_t>(H + 1),
+                 o_t = cv.add<int64_t>(scan_tmp_elems(H));
+    char *sc = (char *)scratch_get(ctx, cv.off);
+    int bits = 1;
+    while (bits < 31 && (int64_t(1) << bits) < ctx->n) ++bits;
+    int which = 0;
+    int launches = 0;
+    timed(ctx, K_SORT, 2.0 * bytes * q->k * ((bits + 7) / 8), total, 0, [&] {
+      which = launch_sort_rows((int32_t *)ctx->acc[0], (int32_t *)ctx->acc[1], (int64_t)total,
+                               q->k, bits, (int32_t *)(sc + o_h), (int64_t *)(sc + o_ho),
+                               (int64_t *)(sc + o_t), ctx->stream, &launches);
+    });
+    ctx->run.kernel_launches += launches;
+    rows = (int32_t *)ctx->acc[which];
+  }
+  ctx->last_rows = rows;
+  ctx->last_count = total;
+  const uint64_t ncopy = std::min<uint64_t>(total, cap_rows);
+  if (ncopy) {
+    CU(cudaMemcpyAsync(out, rows, (size_t)ncopy * q->k * sizeof(int32_t),
+                       (flags & GSM_OUT_DEVICE) ? cudaMemcpyDeviceToDevice
+                                                : cudaMemcpyDeviceToHost,
+                       ctx->stream));
+  }
+  CU(cudaStreamSynchronize(ctx->stream));
+  *truncated = total > cap_rows;
+}
+
+template <typename F>
+gsm_status guarded(gsm_ctx *ctx, F &&f) {
+  try {
+    f();
+    return GSM_OK;
+  } catch (const Fail &e) {
+    return e.code;
+  } catch (const std::exception &e) {
+    set_err(ctx, "internal error: %s", e.what());
+    return GSM_ERR_OOM;
+  }
+}
+
+void free_graph(gsm_ctx *ctx) {
+  if (ctx->d_rp) dev_free(ctx, ctx->d_rp, sizeof(int32_t) * (ctx->n + 1));
+  if (ctx->d_col) dev_free(ctx, ctx->d_col, sizeof(int32_t) * std::max<int64_t>(ctx->nnz, 1));
+  if (ctx->d_lab) dev_free(ctx, ctx->d_lab, sizeof(int32_t) * std::max<int32_t>(ctx->n, 1));
+  ctx->d_rp = ctx->d_col = ctx->d_lab = nullptr;
+  ctx->has_graph = false;
+  ctx->label_values.clear();
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" {
+
+void gsm_default_options(gsm_options *opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+}
+
+const char *gsm_status_string(gsm_status s) {
+  switch (s) {
+    case GSM_OK: return "GSM_OK";
+    case GSM_PENDING: return "GSM_PENDING";
+    case GSM_ERR_INVALID_ARG: return "GSM_ERR_INVALID_ARG";
+    case GSM_ERR_INVALID_GRAPH: return "GSM_ERR_INVALID_GRAPH";
+    case GSM_ERR_INVALID_QUERY: return "GSM_ERR_INVALID_QUERY";
+    case GSM_ERR_NO_GRAPH: return "GSM_ERR_NO_GRAPH";
+    case GSM_ERR_OOM: return "GSM_ERR_OOM";
+    case GSM_ERR_BUDGET: return "GSM_ERR_BUDGET";
+    case GSM_ERR_OVERFLOW: return "GSM_ERR_OVERFLOW";
+    case GSM_ERR_TRUNCATED: return "GSM_ERR_TRUNCATED";
+    case GSM_ERR_TIMEOUT: return "GSM_ERR_TIMEOUT";
+    case GSM_ERR_CUDA: return "GSM_ERR_CUDA";
+    case GSM_ERR_TOO_LARGE: return "GSM_ERR_TOO_LARGE";
+    default: return "GSM_ERR_UNKNOWN";
+  }
+}
+
+gsm_status gsm_create(gsm_ctx **out, int32_t device, const gsm_options *opt) {
+  if (!out) return GSM_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (opt && opt->block_size != 0 &&
+      (opt->block_size < 128 || opt->block_size > 1024 || opt->block_size % 32))
+    return GSM_ERR_INVALID_ARG;
+  if (opt && opt->chunk_rows < 0) return GSM_ERR_INVALID_ARG;
+  gsm_ctx *ctx = new gsm_ctx();
+  if (opt) ctx->opt = *opt;
+  ctx->device = device;
+  for (int i = 0; i < K_NUM; ++i) ctx->kstats[i].name = kKernelNames[i];
+  gsm_status st = guarded(ctx, [&] {
+    CU(cudaSetDevice(device));
+    if (ctx->opt.stream) {
+      ctx->stream = (cudaStream_t)ctx->opt.stream;
+    } else {
+      CU(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+      ctx->own_stream = true;
+    }
+    size_t free_b = 0, total_b = 0;
+    CU(cudaMemGetInfo(&free_b, &total_b));
+    ctx->budget = ctx->opt.mem_budget_bytes ? ctx->opt.mem_budget_bytes : free_b / 10 * 9;
+    CU(cudaMallocHost(&ctx->h_stage, 4096));
+    ctx->d_small = (unsigned long long *)dev_alloc(ctx, 256);
+  });
+  if (st != GSM_OK) {
+    gsm_destroy(ctx);
+    return st;
+  }
+  *out = ctx;
+  return GSM_OK;
+}
+
+void gsm_destroy(gsm_ctx *ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  try {
+    free_graph(ctx);
+    for (auto &b : ctx->blocks) dev_free(ctx, b.ptr, b.cap);
+    dev_free(ctx, ctx->scratch, ctx->scratch_cap);
+    dev_free(ctx, ctx->bitmaps, ctx->bitmaps_cap);
+    dev_free(ctx, ctx->acc[0], ctx->acc_cap[0]);
+    dev_free(ctx, ctx->acc[1], ctx->acc_cap[1]);
+    dev_free(ctx, ctx->d_small, 256);
+  } catch (...) {
+  }
+  for (auto e : ctx->event_pool) cudaEventDestroy(e);
+  for (auto &p : ctx->pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+const char *gsm_last_error(const gsm_ctx *ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+gsm_status gsm_load_graph(gsm_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr,
+                          const int32_t *col, const int32_t *labels, int32_t flags) {
+  if (!ctx) return GSM_ERR_INVALID_ARG;
+  if (n < 0 || nnz < 0 || !row_ptr || (nnz > 0 && !col) ||
+      (flags & ~(GSM_DEVICE_PTRS | GSM_VALIDATE))) {
+    set_err(ctx, "invalid graph arguments");
+    return GSM_ERR_INVALID_ARG;
+  }
+  if (n >= 0x7fffffff || nnz >= (int64_t(1) << 31)) {
+    set_err(ctx, "graph too large for int32 CSR (n=%d nnz=%lld)", n, (long long)nnz);
+    return GSM_ERR_TOO_LARGE;
+  }
+  return guarded(ctx, [&] {
+    CU(cudaSetDevice(ctx->device));
+    CU(cudaStreamSynchronize(ctx->stream));
+    free_graph(ctx);
+    const bool dev = flags & GSM_DEVICE_PTRS;
+    const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    std::vector<int32_t> h_rp(n + 1), h_lab(n);
+    if (dev) {
+      CU(cudaMemcpy(h_rp.data(), row_ptr, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost));
+      if (labels)
+        CU(cudaMemcpy(h_lab.data(), labels, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+    } else {
+      std::memcpy(h_rp.data(), row_ptr, sizeof(int32_t) * (n + 1));
+      if (labels && n) std::memcpy(h_lab.data(), labels, sizeof(int32_t) * n);
+    }
+    ctx->n = n;
+    ctx->nnz = nnz;
+    ctx->d_rp = (int32_t *)dev_alloc(ctx, sizeof(int32_t) * (n + 1));
+    ctx->d_col = (int32_t *)dev_alloc(ctx, sizeof(int32_t) * std::max<int64_t>(nnz, 1));
+    ctx->d_lab = (int32_t *)dev_alloc(ctx, sizeof(int32_t) * std::max<int32_t>(n, 1));
+    CU(cudaMemcpyAsync(ctx->d_rp, h_rp.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    if (nnz)
+      CU(cudaMemcpyAsync(ctx->d_col, col, sizeof(int32_t) * nnz, kind, ctx->stream));
+    // dense label ids: index into the sorted distinct label values
+    std::vector<int32_t> vals(h_lab);
+    std::sort(vals.begin(), vals.end());
+    vals.erase(std::unique(vals.begin(), vals.end()), vals.end());
+    if (vals.empty()) vals.push_back(0);
+    std::vector<int32_t> dense(n);
+    for (int32_t v = 0; v < n; ++v)
+      dense[v] = (int32_t)(std::lower_bound(vals.begin(), vals.end(), h_lab[v]) - vals.begin());
+    ctx->label_values = vals;
+    if (n)
+      CU(cudaMemcpyAsync(ctx->d_lab, dense.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice,
+                         ctx->stream));
+    int32_t md = 0;
+    bool rp_ok = h_rp[0] == 0 && (int64_t)h_rp[n] == nnz;
+    for (int32_t v = 0; v < n; ++v) {
+      const int32_t dv = h_rp[v + 1] - h_rp[v];
+      if (dv < 0) rp_ok = false;
+      md = std::max(md, dv);
+    }
+    ctx->max_deg = md;
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (flags & GSM_VALIDATE) {
+      if (!rp_ok) {
+        free_graph(ctx);
+        FAIL(GSM_ERR_INVALID_GRAPH, "row_ptr is not a valid CSR offset array");
+      }
+      GraphDev g{n, nnz, ctx->d_rp, ctx->d_col, ctx->d_lab};
+      int32_t *err = (int32_t *)(ctx->d_small + kMaxK + 1);
+      CU(cudaMemsetAsync(err, 0, sizeof(int32_t), ctx->stream));
+      launch_validate(g, err, ctx->stream);
+      launch_validate_rows(g, err, ctx->stream);
+      CU(cudaGetLastError());
+      int32_t h_err = 0;
+      CU(cudaMemcpyAsync(ctx->h_stage, err, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+      CU(cudaStreamSynchronize(ctx->stream));
+      std::memcpy(&h_err, ctx->h_stage, sizeof(int32_t));
+      if (h_err) {
+        free_graph(ctx);
+        FAIL(GSM_ERR_INVALID_GRAPH,
+             "invalid data graph (%s%s%s)", (h_err & 1) ? "unsorted/duplicate/self-loop/range " : "",
+             (h_err & 2) ? "asymmetric " : "", (h_err & 4) ? "row_ptr" : "");
+      }
+    } else if (!rp_ok) {
+      free_graph(ctx);
+      FAIL(GSM_ERR_INVALID_GRAPH, "row_ptr is not a valid CSR offset array");
+    }
+    ctx->has_graph = true;
+  });
+}
+
+gsm_status gsm_query_create(gsm_ctx *ctx, int32_t k, int32_t m, const int32_t *edges,
+                            const int32_t *labels, gsm_query **out) {
+  if (!out) return GSM_ERR_INVALID_ARG;
+  *out = nullptr;
+  uint32_t adj[kMaxK];
+  gsm_status st = validate_query_edges(k, m, edges, adj);
+  if (st != GSM_OK) {
+    if (ctx) set_err(ctx, "invalid query graph");
+    return st;
+  }
+  gsm_query *q = new gsm_query();
+  q->k = k;
+  q->m = m;
+  q->edges.assign(edges, edges + 2 * m);
+  for (int32_t u = 0; u < k; ++u) {
+    q->labels[u] = labels ? labels[u] : 0;
+    q->adj[u] = adj[u];
+    q->lo[u] = 0;
+    q->hi[u] = 0x7fffffff;
+  }
+  *out = q;
+  return GSM_OK;
+}
+
+void gsm_query_destroy(gsm_query *q) { delete q; }
+
+gsm_status gsm_query_restrict(gsm_query *q, int32_t u, int32_t lo, int32_t hi) {
+  if (!q || u < 0 || u >= q->k || lo < 0 || hi < lo) return GSM_ERR_INVALID_ARG;
+  q->lo[u] = lo;
+  q->hi[u] = hi;
+  return GSM_OK;
+}
+
+gsm_status gsm_count(gsm_ctx *ctx, const gsm_query *q, uint64_t *count) {
+  if (!ctx || !q || !count) return GSM_ERR_INVALID_ARG;
+  bool trunc = false;
+  gsm_status st = guarded(ctx, [&] {
+    CU(cudaSetDevice(ctx->device));
+    run_query(ctx, q, false, nullptr, 0, 0, count, &trunc);
+    resolve_timings(ctx);
+    ctx->run.peak_bytes = ctx->peak_bytes;
+  });
+  return st;
+}
+
+gsm_status gsm_enumerate(gsm_ctx *ctx, const gsm_query *q, int32_t *out, uint64_t cap_rows,
+                         uint64_t *count, int32_t flags) {
+  if (!ctx || !q || !count || (cap_rows > 0 && !out) || (flags & ~GSM_OUT_DEVICE))
+    return GSM_ERR_INVALID_ARG;
+  bool trunc = false;
+  gsm_status st = guarded(ctx, [&] {
+    CU(cudaSetDevice(ctx->device));
+    run_query(ctx, q, true, out, cap_rows, flags, count, &trunc);
+    resolve_timings(ctx);
+    ctx->run.peak_bytes = ctx->peak_bytes;
+  });
+  if (st == GSM_OK && trunc) {
+    set_err(ctx, "%llu embeddings, capacity %llu rows", (unsigned long long)*count,
+            (unsigned long long)cap_rows);
+    return GSM_ERR_TRUNCATED;
+  }
+  return st;
+}
+
+gsm_status gsm_last_rows(gsm_ctx *ctx, int32_t *out, uint64_t first, uint64_t nrows,
+                         int32_t flags) {
+  if (!ctx || (nrows > 0 && !out) || (flags & ~GSM_OUT_DEVICE)) return GSM_ERR_INVALID_ARG;
+  if (first > ctx->last_count || nrows > ctx->last_count - first) {
+    set_err(ctx, "rows [%llu, %llu) outside the last result of %llu rows",
+            (unsigned long long)first, (unsigned long long)(first + nrows),
+            (unsigned long long)ctx->last_count);
+    return GSM_ERR_INVALID_ARG;
+  }
+  if (nrows == 0) return GSM_OK;
+  return guarded(ctx, [&] {
+    CU(cudaSetDevice(ctx->device));
+    CU(cudaMemcpyAsync(out, ctx->last_rows + first * ctx->last_k,
+                       (size_t)nrows * ctx->last_k * sizeof(int32_t),
+                       (flags & GSM_OUT_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+  });
+}
+
+gsm_status gsm_candidates(gsm_ctx *ctx, const gsm_query *q, uint32_t *bitmaps, uint64_t *sizes) {
+  if (!ctx || !q) return GSM_ERR_INVALID_ARG;
+  return guarded(ctx, [&] {
+    if (!ctx->has_graph) FAIL(GSM_ERR_NO_GRAPH, "no data graph loaded");
+    CU(cudaSetDevice(ctx->device));
+    int32_t dense[kMaxK];
+    uint64_t sz[kMaxK] = {};
+    const size_t nw = (ctx->n + 31) / 32;
+    if (!dense_labels(ctx, q, dense)) {
+      if (bitmaps) std::memset(bitmaps, 0, sizeof(uint32_t) * nw * q->k);
+      if (sizes) std::memset(sizes, 0, sizeof(uint64_t) * q->k);
+      return;
+    }
+    run_filter(ctx, q, dense, sz);
+    if (sizes) std::memcpy(sizes, sz, sizeof(uint64_t) * q->k);
+    if (bitmaps) {
+      CU(cudaMemcpyAsync(bitmaps, ctx->bitmaps, sizeof(uint32_t) * nw * q->k,
+                         cudaMemcpyDeviceToHost, ctx->stream));
+      CU(cudaStreamSynchronize(ctx->stream));
+    }
+    resolve_timings(ctx);
+  });
+}
+
+gsm_status gsm_plan_order(int32_t k, int32_t m, const int32_t *edges, const uint64_t *cand_sizes,
+                          int32_t *order, int32_t *parent) {
+  if (!order || !parent) return GSM_ERR_INVALID_ARG;
+  uint32_t adj[kMaxK];
+  gsm_status st = validate_query_edges(k, m, edges, adj);
+  if (st != GSM_OK) return st;
+  plan(k, adj, cand_sizes, order, parent);
+  return GSM_OK;
+}
+
+gsm_status gsm_kernel_stats(gsm_ctx *ctx, gsm_kernel_stat *out, int32_t max, int32_t *n,
+                            int32_t reset) {
+  if (!ctx || (max > 0 && !out)) return GSM_ERR_INVALID_ARG;
+  for (int32_t i = 0; i < K_NUM && i < max; ++i) {
+    std::memset(&out[i], 0, sizeof(out[i]));
+    std::snprintf(out[i].name, sizeof(out[i].name), "%s", ctx->kstats[i].name);
+    out[i].launches = ctx->kstats[i].launches;
+    out[i].total_ms = ctx->kstats[i].total_ms;
+    out[i].algo_bytes = ctx->kstats[i].algo_bytes;
+    out[i].items = ctx->kstats[i].items;
+  }
+  if (n) *n = K_NUM;
+  if (reset)
+    for (int32_t i = 0; i < K_NUM; ++i) {
+      const char *nm = ctx->kstats[i].name;
+      ctx->kstats[i] = KStat();
+      ctx->kstats[i].name = nm;
+    }
+  return GSM_OK;
+}
+
+gsm_status gsm_last_run_stats(gsm_ctx *ctx, gsm_run_stats *out) {
+  if (!ctx || !out) return GSM_ERR_INVALID_ARG;
+  *out = ctx->run;
+  return GSM_OK;
+}
+
+}  // extern "C"

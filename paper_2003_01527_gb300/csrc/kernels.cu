@@ -1,0 +1,598 @@
+// Device kernels of the matcher: graph validation, candidate filtering,
+// candidate-list compaction, scans, and the two passes of one verification
+// level (count/verify with survivor bitmask, then write).
+//
+// Paper mapping (Sec. 3.2, Algorithm 1; Sec. 3.3):
+//   k_filter            Filter_candidate_set (label / degree / neighbourhood)
+//   k_bitmap_*          the first frontier: compaction of C(pi_0)
+//   k_pivot             Advance setup: which mapped neighbour's row to traverse
+//   k_extend_count      Advance + Compute: check label, injectivity and every
+//                       non-tree edge of each traversed candidate in one step
+//   k_scan_*            the compaction scan
+//   k_extend_write      Write_to_Partial: survivors to consecutive rows
+#include <cstdio>
+
+#include "kernels.cuh"
+
+namespace gsm {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kScanThreads = 256;
+constexpr int kScanIpt = 8;
+constexpr int kScanTile = kScanThreads * kScanIpt;
+
+__device__ __forceinline__ bool bitmap_has(const uint32_t *__restrict__ bm, int32_t v) {
+  return (__ldg(bm + (v >> 5)) >> (v & 31)) & 1u;
+}
+
+// Binary search of key in the ascending slice col[beg, end).
+__device__ __forceinline__ bool row_contains(const int32_t *__restrict__ col, int32_t beg,
+                                             int32_t end, int32_t key) {
+  int32_t lo = beg, len = end - beg;
+  while (len > 0) {
+    int32_t half = len >> 1;
+    if (__ldg(col + lo + half) < key) {
+      lo += half + 1;
+      len -= half + 1;
+    } else {
+      len = half;
+    }
+  }
+  return lo < end && __ldg(col + lo) == key;
+}
+
+// First index in [lo, hi) with a[idx] > key, or hi.
+__device__ __forceinline__ int64_t upper_bound_i64(const int64_t *__restrict__ a, int64_t lo,
+                                                   int64_t hi, int64_t key) {
+  int64_t len = hi - lo;
+  while (len > 0) {
+    int64_t half = len >> 1;
+    if (a[lo + half] <= key) {
+      lo += half + 1;
+      len -= half + 1;
+    } else {
+      len = half;
+    }
+  }
+  return lo;
+}
+
+// ------------------------------------------------------------ validation
+
+__global__ void k_validate_rp(int32_t n, int64_t nnz, const int32_t *__restrict__ rp,
+                              int32_t *err) {
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= n; v += stride) {
+    int32_t x = rp[v];
+    bool bad = x < 0 || x > nnz;
+    if (v == 0 && x != 0) bad = true;
+    if (v == n && (int64_t)x != nnz) bad = true;
+    if (v < n && rp[v + 1] < x) bad = true;
+    if (bad) atomicOr(err, 4);
+  }
+}
+
+__global__ void k_validate_rows(int32_t n, const int32_t *__restrict__ rp,
+                                const int32_t *__restrict__ col, int32_t *err) {
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    int32_t b = rp[v], e = rp[v + 1];
+    int32_t flags = 0;
+    for (int32_t idx = b; idx < e; ++idx) {
+      int32_t w = col[idx];
+      if (w < 0 || w >= n || w == (int32_t)v || (idx > b && col[idx - 1] >= w)) {
+        flags |= 1;
+        break;
+      }
+      if (!row_contains(col, rp[w], rp[w + 1], (int32_t)v)) {
+        flags |= 2;
+        break;
+      }
+    }
+    if (flags) atomicOr(err, flags);
+  }
+}
+
+// ------------------------------------------------------------ filter
+
+// One warp handles 32 consecutive data vertices.  Each lane first applies the
+// label / degree / range test for its own vertex; vertices that also need
+// per-label neighbour counts are then scanned one at a time by the whole warp
+// (coalesced reads of the CSR row, labels gathered through L2), and the k
+// bitmap words of the group are formed by ballots.
+__global__ void __launch_bounds__(256) k_filter(GraphDev g, FilterDesc d,
+                                                uint32_t *__restrict__ bitmaps,
+                                                unsigned long long *__restrict__ sizes) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp_id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long my_size = 0;  // lane u accumulates |C(u)|
+  for (int64_t grp = warp_id; grp < d.n_words; grp += n_warps) {
+    const int64_t v64 = grp * 32 + lane;
+    const bool valid = v64 < g.n;
+    const int32_t v = (int32_t)v64;
+    int32_t lv = -1, deg = -1;
+    if (valid) {
+      lv = g.lab[v];
+      deg = g.rp[v + 1] - g.rp[v];
+    }
+    uint32_t pre = 0, need = 0;
+#pragma unroll
+    for (int u = 0; u < kMaxK; ++u) {
+      if (u < d.k && valid && lv == d.qlab[u] && deg >= d.qdeg[u] && v >= d.lo[u] &&
+          v < d.hi[u]) {
+        pre |= 1u << u;
+        if (d.nreq[u] > 0) need |= 1u << u;
+      }
+    }
+    uint32_t result = pre & ~need;
+    uint32_t todo = __ballot_sync(kFull, need != 0);
+    while (todo) {
+      const int src = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const int32_t vv = (int32_t)(grp * 32 + src);
+      const uint32_t vneed = __shfl_sync(kFull, need, src);
+      const int32_t b = g.rp[vv], e = g.rp[vv + 1];
+      int32_t cnt[kMaxK];
+#pragma unroll
+      for (int s = 0; s < kMaxK; ++s) cnt[s] = 0;
+      for (int32_t idx = b + lane; idx < e; idx += 32) {
+        const int32_t lw = __ldg(g.lab + __ldg(g.col + idx));
+#pragma unroll
+        for (int s = 0; s < kMaxK; ++s)
+          if (s < d.nslots && lw == d.slot_label[s]) ++cnt[s];
+      }
+#pragma unroll
+      for (int s = 0; s < kMaxK; ++s)
+        if (s < d.nslots) cnt[s] = __reduce_add_sync(kFull, cnt[s]);
+      uint32_t pass = 0;
+      for (int u = 0; u < d.k; ++u) {
+        if (!((vneed >> u) & 1u)) continue;
+        bool ok = true;
+        for (int r = 0; r < d.nreq[u]; ++r) {
+          const int slot = d.req_slot[u][r];
+          int32_t c = 0;
+#pragma unroll
+          for (int s = 0; s < kMaxK; ++s) c = (s == slot) ? cnt[s] : c;
+          ok = ok && c >= d.req_cnt[u][r];
+        }
+        if (ok) pass |= 1u << u;
+      }
+      if (lane == src) result |= pass;
+    }
+#pragma unroll
+    for (int u = 0; u < kMaxK; ++u) {
+      if (u < d.k) {
+        const uint32_t word = __ballot_sync(kFull, (result >> u) & 1u);
+        if (lane == u) {
+          bitmaps[(int64_t)u * d.n_words + grp] = word;
+          my_size += __popc(word);
+        }
+      }
+    }
+  }
+  if (lane < d.k && my_size) atomicAdd(sizes + lane, my_size);
+}
+
+// ------------------------------------------------------------ scans
+
+__device__ __forceinline__ int64_t warp_incl_scan(int64_t x, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int64_t y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+// Exclusive block scan of one value per thread (blockDim.x <= 1024); returns
+// the exclusive prefix and writes the block total to *total.
+__device__ int64_t block_excl_scan(int64_t x, int64_t *s_warp, int64_t *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  int64_t incl = warp_incl_scan(x, lane);
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int64_t t = lane < nw ? s_warp[lane] : 0;
+    int64_t ti = warp_incl_scan(t, lane);
+    if (lane < nw) s_warp[lane] = ti - t;
+    if (lane == 31) s_warp[32] = ti;
+  }
+  __syncthreads();
+  int64_t r = incl - x + s_warp[warp];
+  *total = s_warp[32];
+  __syncthreads();
+  return r;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const T *in, int64_t n,
+                                                              int64_t *partial) {
+  __shared__ int64_t s_warp[33];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  int64_t sum = 0;
+#pragma unroll
+  for (int j = 0; j < kScanIpt; ++j) {
+    int64_t idx = base + j * kScanThreads + threadIdx.x;
+    if (idx < n) sum += in[idx];
+  }
+  int64_t total;
+  block_excl_scan(sum, s_warp, &total);
+  if (threadIdx.x == 0) partial[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_partials(int64_t *partial, int64_t nb) {
+  __shared__ int64_t s_warp[33];
+  int64_t carry = 0;
+  for (int64_t base = 0; base < nb; base += blockDim.x) {
+    int64_t idx = base + threadIdx.x;
+    int64_t x = idx < nb ? partial[idx] : 0;
+    int64_t total;
+    int64_t ex = block_excl_scan(x, s_warp, &total);
+    if (idx < nb) partial[idx] = ex + carry;
+    carry += total;
+  }
+  if (threadIdx.x == 0) partial[nb] = carry;
+}
+
+// In-place safe: a CTA reads its whole tile before writing it, and out[n]
+// lies past the input.
+template <typename T>
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(const T *in, int64_t n,
+                                                            const int64_t *__restrict__ partial,
+                                                            int64_t nb, int64_t *out) {
+  __shared__ int64_t s_val[kScanTile];
+  __shared__ int64_t s_warp[33];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+#pragma unroll
+  for (int j = 0; j < kScanIpt; ++j) {
+    int64_t idx = base + j * kScanThreads + threadIdx.x;
+    s_val[j * kScanThreads + threadIdx.x] = idx < n ? (int64_t)in[idx] : 0;
+  }
+  __syncthreads();
+  int64_t loc[kScanIpt];
+  int64_t sum = 0;
+#pragma unroll
+  for (int j = 0; j < kScanIpt; ++j) {
+    loc[j] = sum;
+    sum += s_val[threadIdx.x * kScanIpt + j];
+  }
+  int64_t total;
+  int64_t ex = block_excl_scan(sum, s_warp, &total);
+  const int64_t off = partial[blockIdx.x] + ex;
+#pragma unroll
+  for (int j = 0; j < kScanIpt; ++j) s_val[threadIdx.x * kScanIpt + j] = off + loc[j];
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < kScanIpt; ++j) {
+    int64_t idx = base + j * kScanThreads + threadIdx.x;
+    if (idx < n) out[idx] = s_val[j * kScanThreads + threadIdx.x];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = partial[nb];
+}
+
+// ------------------------------------------------------------ bitmap -> list
+
+__global__ void k_bitmap_popc(const uint32_t *__restrict__ bm, int32_t n_words,
+                              int32_t *__restrict__ cnt) {
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n_words; w += stride)
+    cnt[w] = __popc(bm[w]);
+}
+
+__global__ void k_bitmap_emit(const uint32_t *__restrict__ bm, int32_t n_words,
+                              const int64_t *__restrict__ off, int32_t *__restrict__ out) {
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n_words; w += stride) {
+    uint32_t word = bm[w];
+    int64_t pos = off[w];
+    while (word) {
+      int b = __ffs(word) - 1;
+      word &= word - 1;
+      out[pos++] = (int32_t)(w * 32 + b);
+    }
+  }
+}
+
+// ------------------------------------------------------------ extend
+
+__global__ void k_pivot(GraphDev g, LevelDesc d, const int32_t *__restrict__ F, int64_t R,
+                        int32_t *__restrict__ pstart, uint8_t *__restrict__ pslot,
+                        int64_t *__restrict__ work) {
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R; r += stride) {
+    const int32_t *row = F + r * d.i;
+    int32_t best = 0x7fffffff, best_start = 0, best_slot = 0;
+    for (int b = 0; b < d.nb; ++b) {
+      const int32_t x = row[d.bpos[b]];
+      const int32_t s = __ldg(g.rp + x), e = __ldg(g.rp + x + 1);
+      if (e - s < best) {
+        best = e - s;
+        best_start = s;
+        best_slot = b;
+      }
+    }
+    pstart[r] = best_start;
+    pslot[r] = (uint8_t)best_slot;
+    work[r] = best;
+  }
+}
+
+// Shared tile set-up of both extend passes: finds the rows [r0, r0+span) whose
+// candidates overlap items [e0, e1) and stages their work offsets in shared
+// memory when they fit.
+struct TileRows {
+  int64_t r0;
+  int32_t span;
+  bool staged;
+};
+
+__device__ __forceinline__ TileRows tile_rows(const int64_t *__restrict__ woff, int64_t ra,
+                                              int64_t rb, int64_t e0, int64_t e1,
+                                              int64_t *s_woff, int32_t cap, int64_t *s_meta) {
+  if (threadIdx.x == 0) {
+    const int64_t r0 = upper_bound_i64(woff, ra, rb + 1, e0) - 1;
+    const int64_t r1 = upper_bound_i64(woff, r0, rb + 1, e1 - 1) - 1;
+    s_meta[0] = r0;
+    s_meta[1] = r1 - r0 + 1;
+  }
+  __syncthreads();
+  TileRows t;
+  t.r0 = s_meta[0];
+  t.span = (int32_t)s_meta[1];
+  t.staged = t.span + 1 <= cap;
+  if (t.staged)
+    for (int32_t j = threadIdx.x; j <= t.span; j += blockDim.x) s_woff[j] = woff[t.r0 + j];
+  __syncthreads();
+  return t;
+}
+
+// Row of item e: the largest r in [r0, r0+span) with woff[r] <= e.
+__device__ __forceinline__ int64_t find_row(const TileRows &t, const int64_t *s_woff,
+                                            const int64_t *__restrict__ woff, int64_t e,
+                                            int64_t *row_start) {
+  int32_t lo = 0, hi = t.span;
+  if (t.staged) {
+    while (hi - lo > 1) {
+      int32_t mid = (lo + hi) >> 1;
+      if (s_woff[mid] <= e) lo = mid; else hi = mid;
+    }
+    *row_start = s_woff[lo];
+  } else {
+    while (hi - lo > 1) {
+      int32_t mid = (lo + hi) >> 1;
+      if (woff[t.r0 + mid] <= e) lo = mid; else hi = mid;
+    }
+    *row_start = woff[t.r0 + lo];
+  }
+  return t.r0 + lo;
+}
+
+// The one-step check of Sec. 3.2 verification for candidate w of row `row`:
+// label + signature (bitmap of C(pi_i)), injectivity against same-label,
+// non-adjacent positions, and presence of every query edge to a mapped
+// neighbour other than the pivot (binary search in that neighbour's row).
+__device__ __forceinline__ bool check_candidate(const GraphDev &g, const LevelDesc &d,
+                                                const int32_t *__restrict__ row, int32_t w,
+                                                int slot) {
+  if (!bitmap_has(d.bitmap, w)) return false;
+  for (int t = 0; t < d.ninj; ++t)
+    if (row[d.inj[t]] == w) return false;
+  for (int b = 0; b < d.nb; ++b) {
+    if (b == slot) continue;
+    const int32_t x = row[d.bpos[b]];
+    if (!row_contains(g.col, __ldg(g.rp + x), __ldg(g.rp + x + 1), w)) return false;
+  }
+  return true;
+}
+
+template <bool kMasks>
+__global__ void __launch_bounds__(1024) k_extend_count(
+    GraphDev g, LevelDesc d, const int32_t *__restrict__ F, const int32_t *__restrict__ pstart,
+    const uint8_t *__restrict__ pslot, const int64_t *__restrict__ woff, int64_t ra, int64_t rb,
+    int64_t wa, int64_t wb, uint32_t *__restrict__ masks, int32_t *__restrict__ tile_cnt,
+    unsigned long long *__restrict__ total) {
+  extern __shared__ int64_t s_woff[];
+  __shared__ int64_t s_meta[2];
+  __shared__ int32_t s_count;
+  const int64_t B = blockDim.x;
+  const int64_t tile_items = B * kItemsPerThread;
+  const int64_t e0 = wa + (int64_t)blockIdx.x * tile_items;
+  const int64_t e1 = min(e0 + tile_items, wb);
+  if (threadIdx.x == 0) s_count = 0;
+  const TileRows t = tile_rows(woff, ra, rb, e0, e1, s_woff, (int32_t)tile_items + 1, s_meta);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t cnt = 0;
+#pragma unroll
+  for (int j = 0; j < kItemsPerThread; ++j) {
+    const int64_t e = e0 + j * B + threadIdx.x;
+    bool ok = false;
+    if (e < e1) {
+      int64_t rs;
+      const int64_t r = find_row(t, s_woff, woff, e, &rs);
+      const int32_t w = __ldg(g.col + pstart[r] + (e - rs));
+      ok = check_candidate(g, d, F + r * d.i, w, pslot[r]);
+    }
+    const uint32_t m = __ballot_sync(kFull, ok);
+    if (lane == 0) {
+      if (kMasks) masks[((e0 - wa) + j * B) / 32 + warp] = m;
+      cnt += __popc(m);
+    }
+  }
+  if (lane == 0 && cnt) atomicAdd(&s_count, cnt);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (tile_cnt) tile_cnt[blockIdx.x] = s_count;
+    if (total && s_count) atomicAdd(total, (unsigned long long)s_count);
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_extend_write(
+    GraphDev g, LevelDesc d, const int32_t *__restrict__ F, const int32_t *__restrict__ pstart,
+    const int64_t *__restrict__ woff, int64_t ra, int64_t rb, int64_t wa, int64_t wb,
+    const uint32_t *__restrict__ masks, const int64_t *__restrict__ tile_off,
+    int32_t *__restrict__ out) {
+  extern __shared__ int64_t s_woff[];
+  __shared__ int64_t s_meta[2];
+  __shared__ uint32_t s_mask[kItemsPerThread * 1024 / 32];
+  __shared__ int32_t s_wpre[kItemsPerThread * 1024 / 32];
+  const int64_t base = tile_off[blockIdx.x];
+  if (tile_off[blockIdx.x + 1] == base) return;  // uniform across the block
+  const int64_t B = blockDim.x;
+  const int64_t tile_items = B * kItemsPerThread;
+  const int32_t tile_words = (int32_t)(tile_items / 32);
+  const int64_t e0 = wa + (int64_t)blockIdx.x * tile_items;
+  const int64_t e1 = min(e0 + tile_items, wb);
+  for (int32_t w = threadIdx.x; w < tile_words; w += blockDim.x)
+    s_mask[w] = masks[(int64_t)blockIdx.x * tile_words + w];
+  const TileRows t = tile_rows(woff, ra, rb, e0, e1, s_woff, (int32_t)tile_items + 1, s_meta);
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x < 32) {
+    int32_t carry = 0;
+    for (int32_t c = 0; c < tile_words; c += 32) {
+      const int32_t idx = c + lane;
+      const int32_t x = idx < tile_words ? __popc(s_mask[idx]) : 0;
+      int32_t incl = x;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+      }
+      if (idx < tile_words) s_wpre[idx] = carry + incl - x;
+      carry += __shfl_sync(kFull, incl, 31);
+    }
+  }
+  __syncthreads();
+  const uint32_t lt = (1u << lane) - 1u;
+  const int32_t i = d.i;
+#pragma unroll
+  for (int j = 0; j < kItemsPerThread; ++j) {
+    const int32_t widx = (int32_t)((j * B + threadIdx.x) >> 5);
+    const uint32_t m = s_mask[widx];
+    if (!((m >> lane) & 1u)) continue;
+    const int64_t e = e0 + j * B + threadIdx.x;
+    const int64_t pos = base + s_wpre[widx] + __popc(m & lt);
+    int64_t rs;
+    const int64_t r = find_row(t, s_woff, woff, e, &rs);
+    const int32_t w = __ldg(g.col + pstart[r] + (e - rs));
+    const int32_t *row = F + r * i;
+    int32_t *o = out + pos * (i + 1);
+    for (int c = 0; c < i; ++c) o[d.out_col[c]] = row[c];
+    o[d.out_col[i]] = w;
+  }
+}
+
+__global__ void k_split_points(const int64_t *__restrict__ woff, int64_t R, int64_t step,
+                               int64_t J, int64_t *bounds, int64_t *bound_w) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j > J) return;
+  int64_t r;
+  if (j == J) {
+    r = R;
+  } else {
+    r = upper_bound_i64(woff, 0, R + 1, j * step) - 1;
+    if (r < 0) r = 0;
+    if (r > R) r = R;
+  }
+  bounds[j] = r;
+  bound_w[j] = woff[r];
+}
+
+inline int grid_for(int64_t n, int threads, int cap = 152 * 32) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (int)b;
+}
+
+}  // namespace
+
+void launch_validate(const GraphDev &g, int32_t *err, cudaStream_t s) {
+  k_validate_rp<<<grid_for((int64_t)g.n + 1, 256), 256, 0, s>>>(g.n, g.nnz, g.rp, err);
+  // rows are only read if row_ptr is sane; the host checks err in between
+}
+
+void launch_validate_rows(const GraphDev &g, int32_t *err, cudaStream_t s) {
+  k_validate_rows<<<grid_for(g.n, 128), 128, 0, s>>>(g.n, g.rp, g.col, err);
+}
+
+void launch_filter(const GraphDev &g, const FilterDesc &d, uint32_t *bitmaps,
+                   unsigned long long *sizes, cudaStream_t s) {
+  const int threads = 256;
+  int64_t warps_needed = d.n_words;
+  int blocks = grid_for(warps_needed * 32, threads, 152 * 16);
+  k_filter<<<blocks, threads, 0, s>>>(g, d, bitmaps, sizes);
+}
+
+int64_t scan_tmp_elems(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
+
+template <typename T>
+void scan_impl(const T *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t s) {
+  const int64_t nb = (n + kScanTile - 1) / kScanTile;
+  if (nb == 0) {
+    cudaMemsetAsync(out, 0, sizeof(int64_t), s);
+    return;
+  }
+  k_scan_reduce<T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, tmp);
+  k_scan_partials<<<1, 1024, 0, s>>>(tmp, nb);
+  k_scan_down<T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, tmp, nb, out);
+}
+
+void launch_scan_i32(const int32_t *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t s) {
+  scan_impl<int32_t>(in, out, n, tmp, s);
+}
+
+void launch_scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t s) {
+  scan_impl<int64_t>(in, out, n, tmp, s);
+}
+
+void launch_bitmap_to_list(const uint32_t *bitmap, int32_t n_words, int32_t *cnt, int64_t *off,
+                           int64_t *tmp, int32_t *out, cudaStream_t s) {
+  k_bitmap_popc<<<grid_for(n_words, 256), 256, 0, s>>>(bitmap, n_words, cnt);
+  launch_scan_i32(cnt, off, n_words, tmp, s);
+  k_bitmap_emit<<<grid_for(n_words, 256), 256, 0, s>>>(bitmap, n_words, off, out);
+}
+
+void launch_pivot(const GraphDev &g, const LevelDesc &d, const int32_t *F, int64_t R,
+                  int32_t *pstart, uint8_t *pslot, int64_t *work, cudaStream_t s) {
+  k_pivot<<<grid_for(R, 256, 152 * 64), 256, 0, s>>>(g, d, F, R, pstart, pslot, work);
+}
+
+void launch_extend_count(const GraphDev &g, const LevelDesc &d, const int32_t *F,
+                         const int32_t *pstart, const uint8_t *pslot, const int64_t *woff,
+                         int64_t ra, int64_t rb, int64_t wa, int64_t wb, int32_t block,
+                         uint32_t *masks, int32_t *tile_cnt, unsigned long long *total,
+                         cudaStream_t s) {
+  const int64_t tile_items = (int64_t)block * kItemsPerThread;
+  const int64_t tiles = (wb - wa + tile_items - 1) / tile_items;
+  if (tiles <= 0) return;
+  const size_t smem = (size_t)(tile_items + 1) * sizeof(int64_t);
+  if (masks)
+    k_extend_count<true><<<(unsigned)tiles, block, smem, s>>>(g, d, F, pstart, pslot, woff, ra,
+                                                               rb, wa, wb, masks, tile_cnt, total);
+  else
+    k_extend_count<false><<<(unsigned)tiles, block, smem, s>>>(g, d, F, pstart, pslot, woff, ra,
+                                                                rb, wa, wb, masks, tile_cnt, total);
+}
+
+void launch_extend_write(const GraphDev &g, const LevelDesc &d, const int32_t *F,
+                         const int32_t *pstart, const int64_t *woff, int64_t ra, int64_t rb,
+                         int64_t wa, int64_t wb, int32_t block, const uint32_t *masks,
+                         const int64_t *tile_off, int32_t *out, cudaStream_t s) {
+  const int64_t tile_items = (int64_t)block * kItemsPerThread;
+  const int64_t tiles = (wb - wa + tile_items - 1) / tile_items;
+  if (tiles <= 0) return;
+  const size_t smem = (size_t)(tile_items + 1) * sizeof(int64_t);
+  k_extend_write<<<(unsigned)tiles, block, smem, s>>>(g, d, F, pstart, woff, ra, rb, wa, wb,
+                                                      masks, tile_off, out);
+}
+
+void launch_split_points(const int64_t *woff, int64_t R, int64_t step, int64_t J,
+                         int64_t *bounds, int64_t *bound_w, cudaStream_t s) {
+  k_split_points<<<(unsigned)((J + 1 + 255) / 256), 256, 0, s>>>(woff, R, step, J, bounds,
+                                                                  bound_w);
+}
+
+}  // namespace gsm

@@ -1,0 +1,110 @@
+// Internal interface between the host driver (api.cu) and the device kernels
+// (kernels.cu, sort.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gsm {
+
+constexpr int kMaxK = 16;
+
+// Items (candidate edges) one CTA of the extend kernels covers: blockDim.x
+// threads x kItemsPerThread, item j of thread t is tile_base + j*blockDim + t,
+// so a warp touches 32 consecutive candidates of (usually) one CSR row.
+constexpr int kItemsPerThread = 4;
+
+// Filter description of one query (Sec. 3.2 filtering: label, degree and the
+// per-label neighbour counts that refine the paper's neighbourhood encoding).
+struct FilterDesc {
+  int32_t k;
+  int32_t n_words;                 // ceil(n/32): stride between bitmaps
+  int32_t qlab[kMaxK];             // dense label id of query vertex u
+  int32_t qdeg[kMaxK];             // deg_Q(u)
+  int32_t lo[kMaxK], hi[kMaxK];    // restriction of f(u) to [lo, hi)
+  int32_t nreq[kMaxK];             // number of (slot, count) requirements of u
+  int32_t req_slot[kMaxK][kMaxK];  // label slot of requirement r of u
+  int32_t req_cnt[kMaxK][kMaxK];   // neighbours needed with that label
+  int32_t nslots;                  // distinct labels used by requirements
+  int32_t slot_label[kMaxK];       // dense label id of each slot
+};
+
+// One verification level: extends rows of width i (positions 0..i-1 hold the
+// images of pi_0..pi_{i-1}) by a vertex for pi_i.
+struct LevelDesc {
+  int32_t i;                  // input row width
+  int32_t nb;                 // mapped query neighbours of pi_i (tree parent + non-tree)
+  int32_t bpos[kMaxK];        // their row positions
+  int32_t ninj;               // positions that need an explicit injectivity test
+  int32_t inj[kMaxK];
+  int32_t out_col[kMaxK + 1]; // output column of position j (0..i); identity except last level
+  const uint32_t *bitmap;     // C(pi_i)
+};
+
+struct GraphDev {
+  int32_t n;
+  int64_t nnz;
+  const int32_t *rp;
+  const int32_t *col;
+  const int32_t *lab;  // dense label ids
+};
+
+// ---- launchers (all asynchronous on `s`) ----
+
+// err[0] |= 1 on a malformed row (unsorted/duplicate/self-loop/out of range),
+// |= 2 on an asymmetric entry, |= 4 on a bad row_ptr.
+void launch_validate(const GraphDev &g, int32_t *err, cudaStream_t s);
+// Row checks; only valid to run once launch_validate reported a sane row_ptr.
+void launch_validate_rows(const GraphDev &g, int32_t *err, cudaStream_t s);
+
+// Writes k bitmaps of n_words words and adds |C(u)| into sizes[u].
+void launch_filter(const GraphDev &g, const FilterDesc &d, uint32_t *bitmaps,
+                   unsigned long long *sizes, cudaStream_t s);
+
+// Exclusive scan: out[0..n] with out[n] = total.  tmp needs scan_tmp_elems(n)
+// int64 elements.  The int64 form may run in place (in == out).
+int64_t scan_tmp_elems(int64_t n);
+void launch_scan_i32(const int32_t *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t s);
+void launch_scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t s);
+
+// Bitmap -> ascending vertex list.  cnt: int32[n_words], off: int64[n_words+1]
+// (scratch), tmp: scan_tmp_elems(n_words).
+void launch_bitmap_to_list(const uint32_t *bitmap, int32_t n_words, int32_t *cnt, int64_t *off,
+                           int64_t *tmp, int32_t *out, cudaStream_t s);
+
+// Per row: pick the mapped neighbour of pi_i with the fewest neighbours (the
+// pivot) and record its CSR start, its slot in bpos, and its degree as work
+// (int64, so the work array can be scanned in place into offsets).
+void launch_pivot(const GraphDev &g, const LevelDesc &d, const int32_t *F, int64_t R,
+                  int32_t *pstart, uint8_t *pslot, int64_t *work, cudaStream_t s);
+
+// Verification pass over candidates [wa, wb) of rows [ra, rb): writes one
+// survivor bit per candidate into masks (if non-null), one survivor count per
+// tile into tile_cnt (if non-null), and adds the total into *total (if non-null).
+void launch_extend_count(const GraphDev &g, const LevelDesc &d, const int32_t *F,
+                         const int32_t *pstart, const uint8_t *pslot, const int64_t *woff,
+                         int64_t ra, int64_t rb, int64_t wa, int64_t wb, int32_t block,
+                         uint32_t *masks, int32_t *tile_cnt, unsigned long long *total,
+                         cudaStream_t s);
+
+// Write pass: survivor q of tile t goes to row tile_off[t] + rank of out.
+void launch_extend_write(const GraphDev &g, const LevelDesc &d, const int32_t *F,
+                         const int32_t *pstart, const int64_t *woff, int64_t ra, int64_t rb,
+                         int64_t wa, int64_t wb, int32_t block, const uint32_t *masks,
+                         const int64_t *tile_off, int32_t *out, cudaStream_t s);
+
+// Row boundaries for work-bounded sub-chunks: bounds[j] = the row r with
+// woff[r] <= j*step < woff[r+1] (clamped to [0, R]); bounds[J] = R.
+void launch_split_points(const int64_t *woff, int64_t R, int64_t step, int64_t J,
+                         int64_t *bounds, int64_t *bound_w, cudaStream_t s);
+
+// Lexicographic sort of N rows of k int32 (LSD radix, 8-bit digits).
+// `bits` = significant bits per column (values < 2^bits).  Result lands in
+// `a` or `b`; the function returns which (0 = a, 1 = b).  hist needs
+// sort_hist_elems(N) int32, hist_off sort_hist_elems(N)+1 int64, tmp
+// scan_tmp_elems(sort_hist_elems(N)) int64.
+int64_t sort_hist_elems(int64_t N);
+int launch_sort_rows(int32_t *a, int32_t *b, int64_t N, int32_t k, int32_t bits, int32_t *hist,
+                     int64_t *hist_off, int64_t *tmp, cudaStream_t s, int *launches);
+
+}  // namespace gsm

@@ -1,0 +1,373 @@
+"""Python binding of libgsm (include/gsm.h): argument marshalling only.
+
+Every function named ``gsm_*`` here is the C entry point of the same name;
+the ``Matcher`` class is a convenience wrapper over them.  All matching work
+runs in the library's CUDA kernels; this module never computes a result
+itself, and importing it fails loudly when libgsm.so is missing.
+
+PyTorch supplies device memory (the caching allocator, through the library's
+alloc/free hooks) and streams (the context runs on the caller's current torch
+stream unless told otherwise).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgsm.so")
+
+GSM_OK = 0
+GSM_PENDING = 1
+GSM_ERR_INVALID_ARG = -1
+GSM_ERR_INVALID_GRAPH = -2
+GSM_ERR_INVALID_QUERY = -3
+GSM_ERR_NO_GRAPH = -4
+GSM_ERR_OOM = -5
+GSM_ERR_BUDGET = -6
+GSM_ERR_OVERFLOW = -7
+GSM_ERR_TRUNCATED = -8
+GSM_ERR_TIMEOUT = -9
+GSM_ERR_CUDA = -10
+GSM_ERR_TOO_LARGE = -11
+
+GSM_DEVICE_PTRS = 1
+GSM_VALIDATE = 2
+GSM_OUT_DEVICE = 1
+GSM_OPT_TIME_KERNELS = 1
+
+MAX_K = 16
+
+# The public names of the C ABI (include/gsm.h); tests check the library
+# exports each of them.
+EXPORTED = [
+    "gsm_default_options", "gsm_create", "gsm_destroy", "gsm_last_error", "gsm_status_string",
+    "gsm_load_graph", "gsm_query_create", "gsm_query_destroy", "gsm_query_restrict", "gsm_count",
+    "gsm_enumerate", "gsm_last_rows", "gsm_candidates", "gsm_plan_order", "gsm_kernel_stats",
+    "gsm_last_run_stats",
+]
+
+_alloc_fn = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_free_fn = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                            ctypes.c_void_p)
+
+
+class gsm_options(ctypes.Structure):
+    _fields_ = [("mem_budget_bytes", ctypes.c_size_t), ("stream", ctypes.c_void_p),
+                ("alloc", _alloc_fn), ("free", _free_fn), ("alloc_ctx", ctypes.c_void_p),
+                ("block_size", ctypes.c_int32), ("chunk_rows", ctypes.c_int64),
+                ("filter_rounds", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+class gsm_kernel_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint64),
+                ("total_ms", ctypes.c_double), ("algo_bytes", ctypes.c_double),
+                ("items", ctypes.c_uint64)]
+
+
+class gsm_run_stats(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("order", ctypes.c_int32 * 16),
+                ("cand_size", ctypes.c_uint64 * 16), ("frontier", ctypes.c_uint64 * 16),
+                ("candidates", ctypes.c_uint64 * 16), ("chunks", ctypes.c_uint64),
+                ("peak_bytes", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libgsm.so not built ({LIB_PATH}); run "
+                          "python -m paper_2003_01527_gb300.build")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+    sig = {
+        "gsm_default_options": (None, [ctypes.POINTER(gsm_options)]),
+        "gsm_create": (i32, [ctypes.POINTER(vp), i32, ctypes.POINTER(gsm_options)]),
+        "gsm_destroy": (None, [vp]),
+        "gsm_last_error": (ctypes.c_char_p, [vp]),
+        "gsm_status_string": (ctypes.c_char_p, [i32]),
+        "gsm_load_graph": (i32, [vp, i32, i64, vp, vp, vp, i32]),
+        "gsm_query_create": (i32, [vp, i32, i32, vp, vp, ctypes.POINTER(vp)]),
+        "gsm_query_destroy": (None, [vp]),
+        "gsm_query_restrict": (i32, [vp, i32, i32, i32]),
+        "gsm_count": (i32, [vp, vp, ctypes.POINTER(u64)]),
+        "gsm_enumerate": (i32, [vp, vp, vp, u64, ctypes.POINTER(u64), i32]),
+        "gsm_last_rows": (i32, [vp, vp, u64, u64, i32]),
+        "gsm_candidates": (i32, [vp, vp, vp, vp]),
+        "gsm_plan_order": (i32, [i32, i32, vp, vp, vp, vp]),
+        "gsm_kernel_stats": (i32, [vp, ctypes.POINTER(gsm_kernel_stat), i32,
+                                   ctypes.POINTER(i32), i32]),
+        "gsm_last_run_stats": (i32, [vp, ctypes.POINTER(gsm_run_stats)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+class GsmError(RuntimeError):
+    def __init__(self, status: int, message: str = ""):
+        self.status = status
+        name = _lib.gsm_status_string(status).decode()
+        super().__init__(f"{name}: {message}" if message else name)
+
+
+def _ptr(a) -> int:
+    """Raw address of a numpy array or torch tensor (contiguous)."""
+    if a is None:
+        return 0
+    if hasattr(a, "data_ptr"):
+        return int(a.data_ptr())
+    return int(a.ctypes.data)
+
+
+def _is_cuda(a) -> bool:
+    return hasattr(a, "is_cuda") and bool(a.is_cuda)
+
+
+# ----------------------------------------------------------- C-name wrappers
+
+def gsm_status_string(status: int) -> str:
+    return _lib.gsm_status_string(status).decode()
+
+
+def gsm_default_options() -> gsm_options:
+    opt = gsm_options()
+    _lib.gsm_default_options(ctypes.byref(opt))
+    return opt
+
+
+def gsm_create(device: int, opt: gsm_options | None) -> int:
+    h = ctypes.c_void_p()
+    st = _lib.gsm_create(ctypes.byref(h), device, ctypes.byref(opt) if opt is not None else None)
+    if st != GSM_OK:
+        raise GsmError(st, "gsm_create")
+    return h.value
+
+
+def gsm_destroy(ctx: int) -> None:
+    _lib.gsm_destroy(ctx)
+
+
+def gsm_last_error(ctx: int) -> str:
+    return _lib.gsm_last_error(ctx).decode()
+
+
+def _check(ctx, st, ok=(GSM_OK,)):
+    if st not in ok:
+        raise GsmError(st, gsm_last_error(ctx) if ctx else "")
+    return st
+
+
+def gsm_load_graph(ctx: int, n: int, nnz: int, row_ptr, col, labels, flags: int) -> None:
+    _check(ctx, _lib.gsm_load_graph(ctx, n, nnz, _ptr(row_ptr), _ptr(col), _ptr(labels), flags))
+
+
+def gsm_query_create(ctx: int, k: int, m: int, edges, labels) -> int:
+    h = ctypes.c_void_p()
+    _check(ctx, _lib.gsm_query_create(ctx, k, m, _ptr(edges), _ptr(labels), ctypes.byref(h)))
+    return h.value
+
+
+def gsm_query_destroy(q: int) -> None:
+    _lib.gsm_query_destroy(q)
+
+
+def gsm_query_restrict(q: int, u: int, lo: int, hi: int) -> None:
+    st = _lib.gsm_query_restrict(q, u, lo, hi)
+    if st != GSM_OK:
+        raise GsmError(st, "gsm_query_restrict")
+
+
+def gsm_count(ctx: int, q: int) -> int:
+    c = ctypes.c_uint64()
+    _check(ctx, _lib.gsm_count(ctx, q, ctypes.byref(c)))
+    return c.value
+
+
+def gsm_enumerate(ctx: int, q: int, out, cap_rows: int, flags: int) -> tuple[int, int]:
+    """Returns (count, status); status is GSM_OK or GSM_ERR_TRUNCATED."""
+    c = ctypes.c_uint64()
+    st = _lib.gsm_enumerate(ctx, q, _ptr(out), cap_rows, ctypes.byref(c), flags)
+    _check(ctx, st, (GSM_OK, GSM_ERR_TRUNCATED))
+    return c.value, st
+
+
+def gsm_last_rows(ctx: int, out, first: int, nrows: int, flags: int) -> None:
+    _check(ctx, _lib.gsm_last_rows(ctx, _ptr(out), first, nrows, flags))
+
+
+def gsm_candidates(ctx: int, q: int, bitmaps, sizes) -> None:
+    _check(ctx, _lib.gsm_candidates(ctx, q, _ptr(bitmaps), _ptr(sizes)))
+
+
+def gsm_plan_order(k: int, edges, cand_sizes=None) -> tuple[np.ndarray, np.ndarray]:
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1))
+    order = np.zeros(k, dtype=np.int32)
+    parent = np.zeros(k, dtype=np.int32)
+    cs = None if cand_sizes is None else np.ascontiguousarray(cand_sizes, dtype=np.uint64)
+    st = _lib.gsm_plan_order(k, e.size // 2, _ptr(e) if e.size else None, _ptr(cs),
+                             _ptr(order), _ptr(parent))
+    if st != GSM_OK:
+        raise GsmError(st, "gsm_plan_order")
+    return order, parent
+
+
+def gsm_kernel_stats(ctx: int, reset: bool = False) -> list[dict]:
+    arr = (gsm_kernel_stat * 16)()
+    n = ctypes.c_int32()
+    _check(ctx, _lib.gsm_kernel_stats(ctx, arr, 16, ctypes.byref(n), int(reset)))
+    return [{"name": arr[i].name.decode(), "launches": arr[i].launches,
+             "total_ms": arr[i].total_ms, "algo_bytes": arr[i].algo_bytes,
+             "items": arr[i].items} for i in range(min(n.value, 16))]
+
+
+def gsm_last_run_stats(ctx: int) -> dict:
+    s = gsm_run_stats()
+    _check(ctx, _lib.gsm_last_run_stats(ctx, ctypes.byref(s)))
+    k = s.k
+    return {"k": k, "order": list(s.order[:k]), "cand_size": list(s.cand_size[:k]),
+            "frontier": list(s.frontier[:k + 1]), "candidates": list(s.candidates[:k]),
+            "chunks": s.chunks, "peak_bytes": s.peak_bytes,
+            "kernel_launches": s.kernel_launches}
+
+
+# ----------------------------------------------------------- convenience
+
+
+class Query:
+    def __init__(self, matcher: "Matcher", k: int, edges, labels=None):
+        e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1))
+        lab = None if labels is None else np.ascontiguousarray(labels, dtype=np.int32)
+        self.k = int(k)
+        self.m = e.size // 2
+        self._e, self._lab = e, lab
+        self.handle = gsm_query_create(matcher.ctx, k, self.m, e if e.size else None, lab)
+
+    def restrict(self, u: int, lo: int, hi: int) -> "Query":
+        gsm_query_restrict(self.handle, u, lo, hi)
+        return self
+
+    def close(self):
+        if self.handle:
+            gsm_query_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Matcher:
+    """One libgsm context on one CUDA device, fed by torch's allocator.
+
+    stream: a torch.cuda.Stream (or raw cudaStream_t) the context issues all
+    work on; None creates a dedicated stream (self.stream)."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0, stream=None,
+                 block_size: int = 0, chunk_rows: int = 0, time_kernels: bool = False,
+                 torch_allocator: bool = True):
+        import torch
+        self.device = device
+        opt = gsm_default_options()
+        opt.mem_budget_bytes = mem_budget_bytes
+        if stream is None:
+            # a dedicated torch stream: every library kernel and copy runs on
+            # it, so events recorded on self.stream bracket the library's work
+            stream = torch.cuda.Stream(device=device)
+        self.stream = stream
+        opt.stream = ctypes.c_void_p(int(stream.cuda_stream) if hasattr(stream, "cuda_stream")
+                                     else int(stream))
+        opt.block_size = block_size
+        opt.chunk_rows = chunk_rows
+        opt.flags = GSM_OPT_TIME_KERNELS if time_kernels else 0
+        if torch_allocator:
+            dev = device
+
+            def _alloc(_ctx, nbytes, stream_ptr):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream_ptr)
+                except Exception:
+                    return None
+
+            def _free(_ctx, ptr, _nbytes, _stream):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            self._cb = (_alloc_fn(_alloc), _free_fn(_free))
+            opt.alloc, opt.free = self._cb
+        self.ctx = gsm_create(device, opt)
+        self.n = 0
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            gsm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load_graph(self, row_ptr, col, labels=None, validate: bool = False):
+        """row_ptr/col/labels: numpy arrays (host) or CUDA torch tensors."""
+        dev = _is_cuda(row_ptr)
+        if not dev:
+            row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+            col = np.ascontiguousarray(col, dtype=np.int32)
+            if labels is not None:
+                labels = np.ascontiguousarray(labels, dtype=np.int32)
+        n = int(row_ptr.shape[0]) - 1
+        nnz = int(col.shape[0])
+        flags = (GSM_DEVICE_PTRS if dev else 0) | (GSM_VALIDATE if validate else 0)
+        gsm_load_graph(self.ctx, n, nnz, row_ptr, col if nnz else None, labels, flags)
+        self.n = n
+
+    def query(self, k: int, edges, labels=None) -> Query:
+        return Query(self, k, edges, labels)
+
+    def count(self, q: Query) -> int:
+        return gsm_count(self.ctx, q.handle)
+
+    def enumerate(self, q: Query, cap_rows: int | None = None, out=None):
+        """Returns (rows, count).  With out=None the rows come back as a numpy
+        array of min(count, cap_rows) x k; out may be a CUDA int32 tensor of
+        cap_rows*k elements (rows stay on the device)."""
+        if out is not None:
+            cap = int(out.numel()) // q.k if cap_rows is None else cap_rows
+            flags = GSM_OUT_DEVICE if _is_cuda(out) else 0
+            count, _ = gsm_enumerate(self.ctx, q.handle, out, cap, flags)
+            return out, count
+        if cap_rows is None:
+            count, _ = gsm_enumerate(self.ctx, q.handle, None, 0, 0)
+            buf = np.empty((max(count, 1), q.k), dtype=np.int32)
+            gsm_last_rows(self.ctx, buf, 0, count, 0)
+            return buf[:count], count
+        buf = np.empty((max(cap_rows, 1), q.k), dtype=np.int32)
+        count, _ = gsm_enumerate(self.ctx, q.handle, buf if cap_rows else None, cap_rows, 0)
+        return buf[:min(count, cap_rows)], count
+
+    def candidates(self, q: Query):
+        nw = (self.n + 31) // 32
+        bm = np.zeros((q.k, max(nw, 1)), dtype=np.uint32)
+        sizes = np.zeros(q.k, dtype=np.uint64)
+        gsm_candidates(self.ctx, q.handle, bm, sizes)
+        return bm[:, :nw], sizes
+
+    def kernel_stats(self, reset: bool = False):
+        return gsm_kernel_stats(self.ctx, reset)
+
+    def last_run_stats(self):
+        return gsm_last_run_stats(self.ctx)
+
+
+def unpack_bitmaps(bm: np.ndarray, n: int) -> np.ndarray:
+    """uint32 bitmaps [k, words] -> uint8 [k, n] (bit v%32 of word v/32)."""
+    bits = np.unpackbits(bm.view(np.uint8).reshape(bm.shape[0], -1), axis=1, bitorder="little")
+    return bits[:, :n]
