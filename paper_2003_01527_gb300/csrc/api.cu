@@ -77,10 +77,12 @@ struct gsm_ctx {
   uint64_t last_count = 0;
   int32_t last_k = 0;
 
-  // budgeted memory: frontier stack (segmented) and scratch
+  // budgeted memory: frontier stack (segmented) and scratch; the scratch
+  // area may take up to a quarter of the budget, the stack the rest
   std::vector<Block> blocks;
   size_t top_block = 0, top_used = 0;  // stack pointer
-  size_t budget_used = 0;              // bytes allocated for blocks + scratch
+  size_t stack_alloc = 0;              // bytes allocated for stack blocks
+  size_t stack_limit = 0, scratch_limit = 0;
   size_t live_bytes = 0, peak_bytes = 0;
   void *scratch = nullptr;
   size_t scratch_cap = 0;
@@ -183,9 +185,10 @@ size_t stack_start(const gsm_ctx *c) {
   return c->top_used == 0 ? c->top_block : c->top_block + 1;
 }
 
-// Can `bytes` be pushed without exceeding the budget?
+// Can pushes totalling `bytes` (each already aligned) be made without
+// exceeding the stack's share of the budget?  Either they all fit in what is
+// left of the top block, or one block (cached or new) can hold all of them.
 bool stack_fits(gsm_ctx *c, size_t bytes) {
-  bytes = align_up(bytes);
   const auto &B = c->blocks;
   if (c->top_block < B.size() && B[c->top_block].cap - c->top_used >= bytes) return true;
   const size_t start = stack_start(c);
@@ -194,7 +197,7 @@ bool stack_fits(gsm_ctx *c, size_t bytes) {
     if (B[b].cap >= bytes) return true;
     free_above += B[b].cap;
   }
-  return c->budget_used - free_above + bytes <= c->budget;
+  return c->stack_alloc - free_above + bytes <= c->stack_limit;
 }
 
 void *stack_push(gsm_ctx *ctx, size_t bytes) {
@@ -216,18 +219,19 @@ void *stack_push(gsm_ctx *ctx, size_t bytes) {
       // drop the cached blocks at or above start, then allocate a new one
       while (B.size() > start) {
         dev_free(ctx, B.back().ptr, B.back().cap);
-        ctx->budget_used -= B.back().cap;
+        ctx->stack_alloc -= B.back().cap;
         B.pop_back();
       }
-      const size_t last = B.empty() ? 0 : B.back().cap;
-      size_t want = std::max(bytes, std::max<size_t>(last * 2, size_t(64) << 20));
-      if (ctx->budget_used + want > ctx->budget) want = bytes;
-      if (ctx->budget_used + want > ctx->budget)
+      const size_t avail = ctx->stack_limit - std::min(ctx->stack_limit, ctx->stack_alloc);
+      if (bytes > avail)
         FAIL(GSM_ERR_BUDGET,
-             "frontier chunk of %zu bytes exceeds the memory budget (%zu of %zu in use)", bytes,
-             ctx->budget_used, ctx->budget);
+             "frontier chunk of %zu bytes exceeds the memory budget (%zu of %zu bytes of stack "
+             "in use)", bytes, ctx->stack_alloc, ctx->stack_limit);
+      const size_t last = B.empty() ? 0 : B.back().cap;
+      const size_t want =
+          std::max(bytes, std::min(avail, std::max<size_t>(last * 2, size_t(64) << 20)));
       B.push_back(Block{(char *)dev_alloc(ctx, want), want});
-      ctx->budget_used += want;
+      ctx->stack_alloc += want;
       p = B[start].ptr;
     }
     ctx->top_block = start;
@@ -242,18 +246,18 @@ void *stack_push(gsm_ctx *ctx, size_t bytes) {
 void *scratch_get(gsm_ctx *ctx, size_t bytes) {
   bytes = align_up(bytes);
   if (ctx->scratch_cap >= bytes) return ctx->scratch;
-  size_t want = std::max(bytes, ctx->scratch_cap * 2);
-  if (ctx->budget_used - ctx->scratch_cap + want > ctx->budget) want = bytes;
-  if (ctx->budget_used - ctx->scratch_cap + want > ctx->budget)
-    FAIL(GSM_ERR_BUDGET, "scratch of %zu bytes exceeds the memory budget", bytes);
+  if (bytes > ctx->scratch_limit)
+    FAIL(GSM_ERR_BUDGET, "scratch of %zu bytes exceeds its share of the budget (%zu)", bytes,
+         ctx->scratch_limit);
+  const size_t want = std::min(ctx->scratch_limit, std::max(bytes, ctx->scratch_cap * 2));
   if (ctx->scratch) {
     CU(cudaStreamSynchronize(ctx->stream));
     dev_free(ctx, ctx->scratch, ctx->scratch_cap);
-    ctx->budget_used -= ctx->scratch_cap;
   }
+  ctx->scratch = nullptr;
+  ctx->scratch_cap = 0;
   ctx->scratch = dev_alloc(ctx, want);
   ctx->scratch_cap = want;
-  ctx->budget_used += want;
   ctx->peak_bytes = std::max(ctx->peak_bytes, ctx->live_bytes + ctx->scratch_cap);
   return ctx->scratch;
 }
@@ -466,7 +470,10 @@ void process_sub(Run &R, int32_t i, const int32_t *F, const int32_t *pstart, con
     return;
   }
   const size_t bytes = (size_t)S * w_out * sizeof(int32_t);
-  if (!stack_fits(ctx, bytes)) {
+  // the next level also pushes pivot start, pivot slot and work offsets
+  const size_t need = align_up(bytes) + align_up(4 * (size_t)S) + align_up((size_t)S) +
+                      align_up(8 * ((size_t)S + 1));
+  if (!stack_fits(ctx, need)) {
     if (nrows <= 1)
       FAIL(GSM_ERR_BUDGET, "the %lld partial results of one row need %zu bytes, over the budget",
            (long long)S, bytes);
@@ -628,8 +635,10 @@ void run_query(gsm_ctx *ctx, const gsm_query *q, bool enumerate, int32_t *out, u
   R.g = GraphDev{ctx->n, ctx->nnz, ctx->d_rp, ctx->d_col, ctx->d_lab};
   R.block = ctx->opt.block_size > 0 ? ctx->opt.block_size : 256;
   R.chunk_rows = ctx->opt.chunk_rows;
+  // masks take W/8 bytes and tile arrays 12 bytes per tile of scratch
   R.wcap = std::max<int64_t>((int64_t)ctx->max_deg + 1,
-                             std::min<int64_t>(int64_t(1) << 30, (int64_t)(ctx->budget / 2)));
+                             std::min<int64_t>(int64_t(1) << 30,
+                                               (int64_t)(ctx->scratch_limit / 2) * 7));
   R.d_total = ctx->d_small + kMaxK;
   ctx->run.k = q->k;
   *truncated = false;
@@ -815,6 +824,8 @@ gsm_status gsm_create(gsm_ctx **out, int32_t device, const gsm_options *opt) {
     size_t free_b = 0, total_b = 0;
     CU(cudaMemGetInfo(&free_b, &total_b));
     ctx->budget = ctx->opt.mem_budget_bytes ? ctx->opt.mem_budget_bytes : free_b / 10 * 9;
+    ctx->scratch_limit = ctx->budget / 4;
+    ctx->stack_limit = ctx->budget - ctx->scratch_limit;
     CU(cudaMallocHost(&ctx->h_stage, 4096));
     ctx->d_small = (unsigned long long *)dev_alloc(ctx, 256);
   });
