@@ -164,6 +164,45 @@ gsm_status gsm_last_rows(gsm_ctx *ctx, int32_t *out, uint64_t first, uint64_t nr
  *   sizes    host uint64[k]: |C(u)| (may be NULL) */
 gsm_status gsm_candidates(gsm_ctx *ctx, const gsm_query *q, uint32_t *bitmaps, uint64_t *sizes);
 
+/* Size of the fixed device array behind gsm_candidates_static: bitmap words of
+ * one call, k * ceil(n/32) * 4 bytes, must fit in it (e.g. n <= 4,194,304 at
+ * k = 16).  A further 256 bytes hold the counters. */
+#define GSM_STATIC_SCRATCH_BITMAP_BYTES (8u << 20)
+
+/* gsm_candidates without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory -- a process whose device memory is already claimed by
+ * another allocator (a serving process whose caching allocator reserved the
+ * free HBM up front, where cudaMalloc would fail or fragment that pool), or
+ * code in a latency-critical loop that cannot afford the device-wide
+ * synchronisation cudaMalloc/cudaFree may perform.
+ *
+ * It computes the same bitmaps and sizes as gsm_candidates, from a graph the
+ * caller keeps in device memory, and needs no context:
+ *   n, nnz, row_ptr, col, labels   the data graph on the current device, in
+ *            the layout of gsm_load_graph (labels required, raw values; the
+ *            caller guarantees the CSR rules -- nothing is validated)
+ *   q        the query (its restrictions apply)
+ *   bitmaps  uint32[k * ceil(n/32)] and sizes uint64[k] (either may be NULL),
+ *            host memory, or device memory with flags = GSM_OUT_DEVICE
+ *   stream   cudaStream_t to run on (NULL = the legacy default stream); the
+ *            call returns after the stream has finished the work
+ * Working memory is one fixed file-scope device array
+ * (GSM_STATIC_SCRATCH_BITMAP_BYTES + 256 bytes) that every GPU which loads the
+ * library holds until the process exits.  The library allocates nothing: no
+ * cudaMalloc, no cudaFree, no allocator hook.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents
+ * (the counters are cleared at the start of every call), so calls whose work
+ * overlaps on the GPU -- from two streams or two host threads -- race and give
+ * wrong results.
+ * Errors: GSM_ERR_INVALID_ARG, GSM_ERR_TOO_LARGE (k * ceil(n/32) * 4 bytes over
+ * the array, or the graph over the int32 CSR limits), GSM_ERR_CUDA. */
+gsm_status gsm_candidates_static(int32_t n, int64_t nnz, const int32_t *row_ptr,
+                                 const int32_t *col, const int32_t *labels, const gsm_query *q,
+                                 uint32_t *bitmaps, uint64_t *sizes, int32_t flags, void *stream);
+
 /* The matching order of Sec. 3.2 (host only, no device work): order[i] is the
  * i-th query vertex placed, parent[i] the position (< i) of its spanning-tree
  * parent (-1 for i = 0).  The first vertex minimises the candidate count

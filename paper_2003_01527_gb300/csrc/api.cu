@@ -11,6 +11,7 @@
 
 #include "gsm.h"
 #include "kernels.cuh"
+#include "query_access.h"
 
 using namespace gsm;
 
@@ -773,6 +774,22 @@ void free_graph(gsm_ctx *ctx) {
 }
 
 }  // namespace
+
+namespace gsm {
+
+int32_t query_k(const gsm_query *q) { return q->k; }
+
+void query_describe(const gsm_query *q, int32_t *labels, uint32_t *adj, int32_t *lo,
+                    int32_t *hi) {
+  for (int32_t u = 0; u < q->k; ++u) {
+    labels[u] = q->labels[u];
+    adj[u] = q->adj[u];
+    lo[u] = q->lo[u];
+    hi[u] = q->hi[u];
+  }
+}
+
+}  // namespace gsm
 
 // ------------------------------------------------------------------ C ABI
 

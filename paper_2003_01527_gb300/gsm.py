@@ -46,8 +46,9 @@ EXPORTED = [
     "gsm_default_options", "gsm_create", "gsm_destroy", "gsm_last_error", "gsm_status_string",
     "gsm_load_graph", "gsm_query_create", "gsm_query_destroy", "gsm_query_restrict", "gsm_count",
     "gsm_enumerate", "gsm_last_rows", "gsm_candidates", "gsm_plan_order", "gsm_kernel_stats",
-    "gsm_last_run_stats",
+    "gsm_last_run_stats", "gsm_candidates_static",
 ]
+GSM_STATIC_SCRATCH_BITMAP_BYTES = 8 << 20
 
 _alloc_fn = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 _free_fn = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
@@ -95,6 +96,7 @@ def _load():
         "gsm_last_rows": (i32, [vp, vp, u64, u64, i32]),
         "gsm_candidates": (i32, [vp, vp, vp, vp]),
         "gsm_plan_order": (i32, [i32, i32, vp, vp, vp, vp]),
+        "gsm_candidates_static": (i32, [i32, i64, vp, vp, vp, vp, vp, vp, i32, vp]),
         "gsm_kernel_stats": (i32, [vp, ctypes.POINTER(gsm_kernel_stat), i32,
                                    ctypes.POINTER(i32), i32]),
         "gsm_last_run_stats": (i32, [vp, ctypes.POINTER(gsm_run_stats)]),
@@ -203,6 +205,18 @@ def gsm_last_rows(ctx: int, out, first: int, nrows: int, flags: int) -> None:
 
 def gsm_candidates(ctx: int, q: int, bitmaps, sizes) -> None:
     _check(ctx, _lib.gsm_candidates(ctx, q, _ptr(bitmaps), _ptr(sizes)))
+
+
+def gsm_candidates_static(n: int, nnz: int, row_ptr, col, labels, q: int, bitmaps, sizes,
+                          flags: int = 0, stream=None) -> None:
+    """The allocation-free candidate filter (see include/gsm.h): the graph is
+    device memory the caller owns; bitmaps/sizes are host arrays, or device
+    tensors with flags=GSM_OUT_DEVICE."""
+    st = _lib.gsm_candidates_static(n, nnz, _ptr(row_ptr), _ptr(col), _ptr(labels), q,
+                                    _ptr(bitmaps), _ptr(sizes), flags,
+                                    int(getattr(stream, "cuda_stream", stream or 0)))
+    if st != GSM_OK:
+        raise GsmError(st, "gsm_candidates_static")
 
 
 def gsm_plan_order(k: int, edges, cand_sizes=None) -> tuple[np.ndarray, np.ndarray]:
