@@ -142,6 +142,9 @@ def run_gpu(args):
     from paper_2003_01527_gb300 import gsm
 
     g, queries = load_workload()
+    if args.queries:
+        keep = [int(x) for x in args.queries.split(",")]
+        queries = [queries[i] for i in keep]
     M = gsm.Matcher(device=local, time_kernels=True)
     M.load_graph(g.row_ptr, g.col, g.labels, validate=True)
     Qs = [M.query(q["k"], q["edges"], q["labels"]).restrict(0, 0, q["root_hi"]) for q in queries]
@@ -339,6 +342,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gsm", choices=["gsm", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--queries", default="",
+                    help="comma-separated query indices (a smaller case for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

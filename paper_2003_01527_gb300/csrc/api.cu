@@ -74,6 +74,8 @@ struct gsm_ctx {
   unsigned long long *d_small = nullptr;  // [0..15] sizes, [16] total, [17] err
   void *acc[2] = {nullptr, nullptr};
   size_t acc_cap[2] = {0, 0};
+  void *sort_tmp = nullptr;  // radix-sort histograms (scale with the result)
+  size_t sort_tmp_cap = 0;
   const int32_t *last_rows = nullptr;  // sorted rows of the last gsm_enumerate
   uint64_t last_count = 0;
   int32_t last_k = 0;
@@ -414,44 +416,70 @@ struct Run {
   int32_t block;
   int64_t wcap;        // max candidates per extend launch
   int64_t chunk_rows;  // max rows per extend launch (0 = unbounded)
-  uint64_t acc_rows = 0;
+  uint64_t acc_rows = 0;  // final rows so far (column-major in ctx->acc[0])
+  int64_t acc_ld = 0;     // rows per column of ctx->acc[0]
   unsigned __int128 count = 0;
   unsigned long long *d_total;
 };
 
 void recurse(Run &R, int32_t i, const int32_t *F, int64_t rows);
 
-void process_sub(Run &R, int32_t i, const int32_t *F, const int32_t *pstart, const uint8_t *pslot,
-                 const int64_t *woff, int64_t ra, int64_t rb, int64_t wa, int64_t wb) {
+// Grows the column-major final-row accumulator to hold `rows` rows, keeping
+// the R.acc_rows rows already written.
+void ensure_acc(Run &R, uint64_t rows) {
+  gsm_ctx *ctx = R.ctx;
+  if ((int64_t)rows <= R.acc_ld) return;
+  const int64_t ld = std::max<int64_t>((int64_t)rows, R.acc_ld + R.acc_ld / 2);
+  const size_t bytes = (size_t)ld * R.k * sizeof(int32_t);
+  void *q = dev_alloc(ctx, bytes);
+  if (R.acc_rows)
+    CU(cudaMemcpy2DAsync(q, ld * sizeof(int32_t), ctx->acc[0], R.acc_ld * sizeof(int32_t),
+                         R.acc_rows * sizeof(int32_t), R.k, cudaMemcpyDeviceToDevice,
+                         ctx->stream));
+  dev_free(ctx, ctx->acc[0], ctx->acc_cap[0]);
+  ctx->acc[0] = q;
+  ctx->acc_cap[0] = bytes;
+  R.acc_ld = ld;
+}
+
+void process_sub(Run &R, int32_t i, const int32_t *F, int64_t ld, const int32_t *pstart,
+                 const uint8_t *pslot, const int64_t *woff, int64_t ra, int64_t rb, int64_t wa,
+                 int64_t wb) {
   gsm_ctx *ctx = R.ctx;
   const LevelDesc &d = R.lv[i];
   const bool last = i == R.k - 1;
   const int64_t W = wb - wa, nrows = rb - ra;
   if (W <= 0) return;
   const int64_t tile_items = (int64_t)R.block * kItemsPerThread;
-  const int64_t tiles = (W + tile_items - 1) / tile_items;
+  const int64_t tiles = extend_tiles(wa, wb, R.block);
   const double read_bytes = (double)nrows * (4.0 * i + 13.0) + 4.0 * (double)W;
   ctx->run.chunks += 1;
-  if (last && !R.enumerate) {
+  const bool count_only = last && !R.enumerate;
+  Carve cv;
+  const size_t o_row = cv.add<int32_t>(tiles + 1);
+  const size_t o_mask = count_only ? 0 : cv.add<uint32_t>(tiles * (tile_items / 32));
+  const size_t o_cnt = count_only ? 0 : cv.add<int32_t>(tiles);
+  const size_t o_off = count_only ? 0 : cv.add<int64_t>(tiles + 1);
+  const size_t o_tmp = count_only ? 0 : cv.add<int64_t>(scan_tmp_elems(tiles));
+  char *sc = (char *)scratch_get(ctx, cv.off);
+  int32_t *tile_row = (int32_t *)(sc + o_row);
+  timed(ctx, K_PIVOT, 8.0 * (nrows + tiles), (uint64_t)tiles, 1, [&] {
+    launch_tile_rows(woff, ra, rb, wa, wb, R.block, tile_row, ctx->stream);
+  });
+  if (count_only) {
     timed(ctx, K_COUNT, read_bytes, (uint64_t)W, 1, [&] {
-      launch_extend_count(R.g, d, F, pstart, pslot, woff, ra, rb, wa, wb, R.block, nullptr,
+      launch_extend_count(R.g, d, F, ld, pstart, pslot, woff, tile_row, wa, wb, R.block, nullptr,
                           nullptr, R.d_total, ctx->stream);
     });
     return;
   }
-  Carve cv;
-  const size_t o_mask = cv.add<uint32_t>(tiles * (tile_items / 32));
-  const size_t o_cnt = cv.add<int32_t>(tiles);
-  const size_t o_off = cv.add<int64_t>(tiles + 1);
-  const size_t o_tmp = cv.add<int64_t>(scan_tmp_elems(tiles));
-  char *sc = (char *)scratch_get(ctx, cv.off);
   uint32_t *masks = (uint32_t *)(sc + o_mask);
   int32_t *tile_cnt = (int32_t *)(sc + o_cnt);
   int64_t *tile_off = (int64_t *)(sc + o_off);
   int64_t *tmp = (int64_t *)(sc + o_tmp);
   timed(ctx, K_COUNT, read_bytes + W / 8.0, (uint64_t)W, 1, [&] {
-    launch_extend_count(R.g, d, F, pstart, pslot, woff, ra, rb, wa, wb, R.block, masks, tile_cnt,
-                        nullptr, ctx->stream);
+    launch_extend_count(R.g, d, F, ld, pstart, pslot, woff, tile_row, wa, wb, R.block, masks,
+                        tile_cnt, nullptr, ctx->stream);
   });
   timed(ctx, K_PIVOT, 12.0 * tiles, (uint64_t)tiles, 3,
         [&] { launch_scan_i32(tile_cnt, tile_off, tiles, tmp, ctx->stream); });
@@ -459,13 +487,11 @@ void process_sub(Run &R, int32_t i, const int32_t *F, const int32_t *pstart, con
   if (S == 0) return;
   const int32_t w_out = i + 1;
   if (last) {
-    const size_t need = (size_t)(R.acc_rows + S) * R.k * sizeof(int32_t);
-    ensure_buf(ctx, &ctx->acc[0], &ctx->acc_cap[0], need, true,
-               (size_t)R.acc_rows * R.k * sizeof(int32_t));
-    int32_t *out = (int32_t *)ctx->acc[0] + (size_t)R.acc_rows * R.k;
+    ensure_acc(R, R.acc_rows + (uint64_t)S);
+    int32_t *out = (int32_t *)ctx->acc[0] + R.acc_rows;
     timed(ctx, K_WRITE, 4.0 * S * w_out, (uint64_t)S, 1, [&] {
-      launch_extend_write(R.g, d, F, pstart, woff, ra, rb, wa, wb, R.block, masks, tile_off, out,
-                          ctx->stream);
+      launch_extend_write(R.g, d, F, ld, pstart, woff, tile_row, wa, wb, R.block, masks,
+                          tile_off, out, R.acc_ld, ctx->stream);
     });
     R.acc_rows += (uint64_t)S;
     return;
@@ -474,21 +500,23 @@ void process_sub(Run &R, int32_t i, const int32_t *F, const int32_t *pstart, con
   // the next level also pushes pivot start, pivot slot and work offsets
   const size_t need = align_up(bytes) + align_up(4 * (size_t)S) + align_up((size_t)S) +
                       align_up(8 * ((size_t)S + 1));
-  if (!stack_fits(ctx, need)) {
+  // elements of a frontier are indexed with 32 bits inside the kernels
+  const bool too_many = (int64_t)S * w_out >= (int64_t(1) << 31) - 1;
+  if (too_many || !stack_fits(ctx, need)) {
     if (nrows <= 1)
       FAIL(GSM_ERR_BUDGET, "the %lld partial results of one row need %zu bytes, over the budget",
            (long long)S, bytes);
     const int64_t mid = ra + nrows / 2;
     const int64_t wmid = read_i64(ctx, woff + mid);
-    process_sub(R, i, F, pstart, pslot, woff, ra, mid, wa, wmid);
-    process_sub(R, i, F, pstart, pslot, woff, mid, rb, wmid, wb);
+    process_sub(R, i, F, ld, pstart, pslot, woff, ra, mid, wa, wmid);
+    process_sub(R, i, F, ld, pstart, pslot, woff, mid, rb, wmid, wb);
     return;
   }
   const Mark mk = stack_mark(ctx);
   int32_t *Fn = (int32_t *)stack_push(ctx, bytes);
   timed(ctx, K_WRITE, 4.0 * S * w_out, (uint64_t)S, 1, [&] {
-    launch_extend_write(R.g, d, F, pstart, woff, ra, rb, wa, wb, R.block, masks, tile_off, Fn,
-                        ctx->stream);
+    launch_extend_write(R.g, d, F, ld, pstart, woff, tile_row, wa, wb, R.block, masks, tile_off,
+                        Fn, S, ctx->stream);
   });
   recurse(R, i + 1, Fn, S);
   stack_release(ctx, mk);
@@ -514,7 +542,7 @@ void recurse(Run &R, int32_t i, const int32_t *F, int64_t rows) {
   const bool split_w = W > R.wcap;
   const bool split_r = R.chunk_rows > 0 && rows > R.chunk_rows;
   if (!split_w && !split_r) {
-    process_sub(R, i, F, pstart, pslot, woff, 0, rows, 0, W);
+    process_sub(R, i, F, rows, pstart, pslot, woff, 0, rows, 0, W);
   } else {
     // row boundaries: work targets (each piece <= wcap) merged with multiples of chunk_rows
     std::vector<int64_t> bnd, bw;
@@ -550,7 +578,7 @@ void recurse(Run &R, int32_t i, const int32_t *F, int64_t rows) {
     }
     CU(cudaStreamSynchronize(ctx->stream));
     for (size_t j = 0; j + 1 < bnd.size(); ++j)
-      process_sub(R, i, F, pstart, pslot, woff, bnd[j], bnd[j + 1], bw[j], bw[j + 1]);
+      process_sub(R, i, F, rows, pstart, pslot, woff, bnd[j], bnd[j + 1], bw[j], bw[j + 1]);
   }
   stack_release(ctx, mk);
 }
@@ -638,7 +666,7 @@ void run_query(gsm_ctx *ctx, const gsm_query *q, bool enumerate, int32_t *out, u
   R.chunk_rows = ctx->opt.chunk_rows;
   // masks take W/8 bytes and tile arrays 12 bytes per tile of scratch
   R.wcap = std::max<int64_t>((int64_t)ctx->max_deg + 1,
-                             std::min<int64_t>(int64_t(1) << 30,
+                             std::min<int64_t>((int64_t(1) << 30) - 4096,
                                                (int64_t)(ctx->scratch_limit / 2) * 7));
   R.d_total = ctx->d_small + kMaxK;
   ctx->run.k = q->k;
@@ -688,9 +716,10 @@ void run_query(gsm_ctx *ctx, const gsm_query *q, bool enumerate, int32_t *out, u
     });
   }
   ctx->run.frontier[1] = (uint64_t)R1;
+  R.acc_ld = (int64_t)(ctx->acc_cap[0] / (sizeof(int32_t) * q->k));
   if (q->k == 1) {
     if (enumerate) {
-      ensure_buf(ctx, &ctx->acc[0], &ctx->acc_cap[0], sizeof(int32_t) * R1, false, 0);
+      ensure_acc(R, (uint64_t)R1);
       CU(cudaMemcpyAsync(ctx->acc[0], F1, sizeof(int32_t) * R1, cudaMemcpyDeviceToDevice,
                          ctx->stream));
     }
@@ -714,25 +743,30 @@ void run_query(gsm_ctx *ctx, const gsm_query *q, bool enumerate, int32_t *out, u
   if (!enumerate) return;
 
   // canonical order: rows are already sorted when the matching order is the
-  // identity (levels emit rows in lexicographic order of the matching order)
+  // identity (levels emit rows in lexicographic order of the matching order);
+  // either way the column-major rows end up row-major in one of the buffers
   int32_t *rows = (int32_t *)ctx->acc[0];
-  bool identity = true;
-  for (int32_t j = 0; j < q->k; ++j) identity = identity && R.order[j] == j;
-  if (!identity && total > 1) {
+  if (q->k > 1 && total > 0) {
+    bool identity = true;
+    for (int32_t j = 0; j < q->k; ++j) identity = identity && R.order[j] == j;
     const size_t bytes = (size_t)total * q->k * sizeof(int32_t);
     ensure_buf(ctx, &ctx->acc[1], &ctx->acc_cap[1], bytes, false, 0);
-    const int64_t H = sort_hist_elems((int64_t)total);
+    const int64_t H = identity ? 0 : sort_hist_elems((int64_t)total);
     Carve cv;
     const size_t o_h = cv.add<int32_t>(H), o_ho = cv.add<int64_t>(H + 1),
                  o_t = cv.add<int64_t>(scan_tmp_elems(H));
-    char *sc = (char *)scratch_get(ctx, cv.off);
+    // outside the budget, like the result buffers it serves
+    ensure_buf(ctx, &ctx->sort_tmp, &ctx->sort_tmp_cap, cv.off, false, 0);
+    char *sc = (char *)ctx->sort_tmp;
     int bits = 1;
     while (bits < 31 && (int64_t(1) << bits) < ctx->n) ++bits;
     int which = 0;
     int launches = 0;
-    timed(ctx, K_SORT, 2.0 * bytes * q->k * ((bits + 7) / 8), total, 0, [&] {
-      which = launch_sort_rows((int32_t *)ctx->acc[0], (int32_t *)ctx->acc[1], (int64_t)total,
-                               q->k, bits, (int32_t *)(sc + o_h), (int64_t *)(sc + o_ho),
+    const double passes = identity ? 0.5 : q->k * ((bits + 7) / 8);
+    timed(ctx, K_SORT, 2.0 * bytes * passes, total, 0, [&] {
+      which = launch_sort_rows((int32_t *)ctx->acc[0], R.acc_ld, (int32_t *)ctx->acc[1],
+                               (int64_t)total, (int64_t)total, q->k, bits, identity,
+                               (int32_t *)(sc + o_h), (int64_t *)(sc + o_ho),
                                (int64_t *)(sc + o_t), ctx->stream, &launches);
     });
     ctx->run.kernel_launches += launches;
@@ -865,6 +899,7 @@ void gsm_destroy(gsm_ctx *ctx) {
     dev_free(ctx, ctx->bitmaps, ctx->bitmaps_cap);
     dev_free(ctx, ctx->acc[0], ctx->acc_cap[0]);
     dev_free(ctx, ctx->acc[1], ctx->acc_cap[1]);
+    dev_free(ctx, ctx->sort_tmp, ctx->sort_tmp_cap);
     dev_free(ctx, ctx->d_small, 256);
   } catch (...) {
   }

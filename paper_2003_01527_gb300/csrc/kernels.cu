@@ -134,30 +134,40 @@ __global__ void __launch_bounds__(256) k_filter(GraphDev g, FilterDesc d,
       const int32_t vv = (int32_t)(grp * 32 + src);
       const uint32_t vneed = __shfl_sync(kFull, need, src);
       const int32_t b = g.rp[vv], e = g.rp[vv + 1];
-      int32_t cnt[kMaxK];
+      int32_t cnt[kMaxK], tot[kMaxK];
 #pragma unroll
-      for (int s = 0; s < kMaxK; ++s) cnt[s] = 0;
-      for (int32_t idx = b + lane; idx < e; idx += 32) {
-        const int32_t lw = __ldg(g.lab + __ldg(g.col + idx));
+      for (int s = 0; s < kMaxK; ++s) cnt[s] = tot[s] = 0;
+      uint32_t pass = 0;
+      // Scan the row 256 neighbours at a time and stop as soon as every
+      // requirement holds (counts only grow), so hubs end after one chunk.
+      for (int32_t base = b; base < e; base += 256) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int32_t idx = base + j * 32 + lane;
+          if (idx < e) {
+            const int32_t lw = __ldg(g.lab + __ldg(g.col + idx));
+#pragma unroll
+            for (int s = 0; s < kMaxK; ++s)
+              if (s < d.nslots && lw == d.slot_label[s]) ++cnt[s];
+          }
+        }
 #pragma unroll
         for (int s = 0; s < kMaxK; ++s)
-          if (s < d.nslots && lw == d.slot_label[s]) ++cnt[s];
-      }
+          if (s < d.nslots) tot[s] = __reduce_add_sync(kFull, cnt[s]);
+        pass = 0;
+        for (int u = 0; u < d.k; ++u) {
+          if (!((vneed >> u) & 1u)) continue;
+          bool ok = true;
+          for (int r = 0; r < d.nreq[u]; ++r) {
+            const int slot = d.req_slot[u][r];
+            int32_t c = 0;
 #pragma unroll
-      for (int s = 0; s < kMaxK; ++s)
-        if (s < d.nslots) cnt[s] = __reduce_add_sync(kFull, cnt[s]);
-      uint32_t pass = 0;
-      for (int u = 0; u < d.k; ++u) {
-        if (!((vneed >> u) & 1u)) continue;
-        bool ok = true;
-        for (int r = 0; r < d.nreq[u]; ++r) {
-          const int slot = d.req_slot[u][r];
-          int32_t c = 0;
-#pragma unroll
-          for (int s = 0; s < kMaxK; ++s) c = (s == slot) ? cnt[s] : c;
-          ok = ok && c >= d.req_cnt[u][r];
+            for (int s = 0; s < kMaxK; ++s) c = (s == slot) ? tot[s] : c;
+            ok = ok && c >= d.req_cnt[u][r];
+          }
+          if (ok) pass |= 1u << u;
         }
-        if (ok) pass |= 1u << u;
+        if (pass == vneed) break;  // warp-uniform: tot is the same in every lane
       }
       if (lane == src) result |= pass;
     }
@@ -297,16 +307,20 @@ __global__ void k_bitmap_emit(const uint32_t *__restrict__ bm, int32_t n_words,
 }
 
 // ------------------------------------------------------------ extend
+//
+// Frontiers are column-major (SoA): position c of row r of a frontier with
+// leading dimension ld is F[c*ld + r], so a warp reading one position of 32
+// consecutive rows, or writing one position of 32 consecutive survivors,
+// touches 128 contiguous bytes.
 
 __global__ void k_pivot(GraphDev g, LevelDesc d, const int32_t *__restrict__ F, int64_t R,
                         int32_t *__restrict__ pstart, uint8_t *__restrict__ pslot,
                         int64_t *__restrict__ work) {
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R; r += stride) {
-    const int32_t *row = F + r * d.i;
     int32_t best = 0x7fffffff, best_start = 0, best_slot = 0;
     for (int b = 0; b < d.nb; ++b) {
-      const int32_t x = row[d.bpos[b]];
+      const int32_t x = F[(int64_t)d.bpos[b] * R + r];
       const int32_t s = __ldg(g.rp + x), e = __ldg(g.rp + x + 1);
       if (e - s < best) {
         best = e - s;
@@ -320,69 +334,84 @@ __global__ void k_pivot(GraphDev g, LevelDesc d, const int32_t *__restrict__ F, 
   }
 }
 
-// Shared tile set-up of both extend passes: finds the rows [r0, r0+span) whose
-// candidates overlap items [e0, e1) and stages their work offsets in shared
-// memory when they fit.
+// tile_row[t] = the row whose candidates include local item t*tile_items
+// (rows partition the items, so exactly one row writes each entry);
+// tile_row[tiles] = rb - 1.  Rows < 2^31.
+__global__ void k_tile_rows(const int64_t *__restrict__ woff, int64_t ra, int64_t rb, int64_t wa,
+                            int64_t tile_items, int64_t tiles, int32_t *__restrict__ tile_row) {
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = ra + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rb; r += stride) {
+    const int64_t s = woff[r] - wa, e = woff[r + 1] - wa;
+    if (e <= s) continue;
+    for (int64_t t = (s + tile_items - 1) / tile_items; t * tile_items < e; ++t)
+      tile_row[t] = (int32_t)r;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) tile_row[tiles] = (int32_t)(rb - 1);
+}
+
+// Inside one launch every index is 32-bit: candidates are numbered locally
+// from wa (a launch covers fewer than 2^30), rows and frontier elements stay
+// below 2^31 (the driver chunks frontiers to that), only output addresses of
+// the final rows are 64-bit.
+//
+// A tile's rows [r0, r0+span): their work offsets, relative to wa, are staged
+// in shared memory when they fit (span <= tile items: always, unless rows
+// without work pile up); items then find their row by binary search there,
+// otherwise in the global offsets.
 struct TileRows {
-  int64_t r0;
+  int32_t r0;
   int32_t span;
   bool staged;
 };
 
-__device__ __forceinline__ TileRows tile_rows(const int64_t *__restrict__ woff, int64_t ra,
-                                              int64_t rb, int64_t e0, int64_t e1,
-                                              int64_t *s_woff, int32_t cap, int64_t *s_meta) {
-  if (threadIdx.x == 0) {
-    const int64_t r0 = upper_bound_i64(woff, ra, rb + 1, e0) - 1;
-    const int64_t r1 = upper_bound_i64(woff, r0, rb + 1, e1 - 1) - 1;
-    s_meta[0] = r0;
-    s_meta[1] = r1 - r0 + 1;
-  }
-  __syncthreads();
+__device__ __forceinline__ TileRows stage_rows(const int64_t *__restrict__ woff,
+                                               const int32_t *__restrict__ tile_row, int64_t wa,
+                                               int32_t tile_items, int32_t *s_woff) {
   TileRows t;
-  t.r0 = s_meta[0];
-  t.span = (int32_t)s_meta[1];
-  t.staged = t.span + 1 <= cap;
+  t.r0 = tile_row[blockIdx.x];
+  t.span = tile_row[blockIdx.x + 1] + 1 - t.r0;
+  t.staged = t.span <= tile_items;
   if (t.staged)
-    for (int32_t j = threadIdx.x; j <= t.span; j += blockDim.x) s_woff[j] = woff[t.r0 + j];
+    for (int32_t j = threadIdx.x; j <= t.span; j += blockDim.x)
+      s_woff[j] = (int32_t)(woff[t.r0 + j] - wa);
   __syncthreads();
   return t;
 }
 
-// Row of item e: the largest r in [r0, r0+span) with woff[r] <= e.
-__device__ __forceinline__ int64_t find_row(const TileRows &t, const int64_t *s_woff,
-                                            const int64_t *__restrict__ woff, int64_t e,
-                                            int64_t *row_start) {
-  int32_t lo = 0, hi = t.span;
+// Row of local item x and the local offset where that row's candidates start.
+__device__ __forceinline__ int32_t item_row(const TileRows &t, const int32_t *s_woff,
+                                            const int64_t *__restrict__ woff, int64_t wa,
+                                            int32_t x, int32_t *row_start) {
+  int32_t lo = 0, hi = t.span;  // largest j in [0, span) with offset(r0+j) <= x
   if (t.staged) {
     while (hi - lo > 1) {
-      int32_t mid = (lo + hi) >> 1;
-      if (s_woff[mid] <= e) lo = mid; else hi = mid;
+      const int32_t mid = (lo + hi) >> 1;
+      if (s_woff[mid] <= x) lo = mid; else hi = mid;
     }
     *row_start = s_woff[lo];
   } else {
     while (hi - lo > 1) {
-      int32_t mid = (lo + hi) >> 1;
-      if (woff[t.r0 + mid] <= e) lo = mid; else hi = mid;
+      const int32_t mid = (lo + hi) >> 1;
+      if (woff[t.r0 + mid] - wa <= x) lo = mid; else hi = mid;
     }
-    *row_start = woff[t.r0 + lo];
+    *row_start = (int32_t)(woff[t.r0 + lo] - wa);
   }
   return t.r0 + lo;
 }
 
-// The one-step check of Sec. 3.2 verification for candidate w of row `row`:
+// The one-step check of Sec. 3.2 verification for candidate w of row r:
 // label + signature (bitmap of C(pi_i)), injectivity against same-label,
 // non-adjacent positions, and presence of every query edge to a mapped
 // neighbour other than the pivot (binary search in that neighbour's row).
 __device__ __forceinline__ bool check_candidate(const GraphDev &g, const LevelDesc &d,
-                                                const int32_t *__restrict__ row, int32_t w,
-                                                int slot) {
+                                                const int32_t *__restrict__ F, int32_t ld,
+                                                int32_t r, int32_t w, int slot) {
   if (!bitmap_has(d.bitmap, w)) return false;
   for (int t = 0; t < d.ninj; ++t)
-    if (row[d.inj[t]] == w) return false;
+    if (F[d.inj[t] * ld + r] == w) return false;
   for (int b = 0; b < d.nb; ++b) {
     if (b == slot) continue;
-    const int32_t x = row[d.bpos[b]];
+    const int32_t x = F[d.bpos[b] * ld + r];
     if (!row_contains(g.col, __ldg(g.rp + x), __ldg(g.rp + x + 1), w)) return false;
   }
   return true;
@@ -390,34 +419,34 @@ __device__ __forceinline__ bool check_candidate(const GraphDev &g, const LevelDe
 
 template <bool kMasks>
 __global__ void __launch_bounds__(1024) k_extend_count(
-    GraphDev g, LevelDesc d, const int32_t *__restrict__ F, const int32_t *__restrict__ pstart,
-    const uint8_t *__restrict__ pslot, const int64_t *__restrict__ woff, int64_t ra, int64_t rb,
-    int64_t wa, int64_t wb, uint32_t *__restrict__ masks, int32_t *__restrict__ tile_cnt,
+    GraphDev g, LevelDesc d, const int32_t *__restrict__ F, int32_t ld,
+    const int32_t *__restrict__ pstart, const uint8_t *__restrict__ pslot,
+    const int64_t *__restrict__ woff, const int32_t *__restrict__ tile_row, int64_t wa,
+    int32_t W, uint32_t *__restrict__ masks, int32_t *__restrict__ tile_cnt,
     unsigned long long *__restrict__ total) {
-  extern __shared__ int64_t s_woff[];
-  __shared__ int64_t s_meta[2];
+  extern __shared__ int32_t s_woff[];
   __shared__ int32_t s_count;
-  const int64_t B = blockDim.x;
-  const int64_t tile_items = B * kItemsPerThread;
-  const int64_t e0 = wa + (int64_t)blockIdx.x * tile_items;
-  const int64_t e1 = min(e0 + tile_items, wb);
+  const int32_t B = blockDim.x;
+  const int32_t tile_items = B * kItemsPerThread;
+  const int32_t x0 = blockIdx.x * tile_items;
+  const int32_t x1 = min(x0 + tile_items, W);
   if (threadIdx.x == 0) s_count = 0;
-  const TileRows t = tile_rows(woff, ra, rb, e0, e1, s_woff, (int32_t)tile_items + 1, s_meta);
+  const TileRows t = stage_rows(woff, tile_row, wa, tile_items, s_woff);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int32_t cnt = 0;
 #pragma unroll
   for (int j = 0; j < kItemsPerThread; ++j) {
-    const int64_t e = e0 + j * B + threadIdx.x;
+    const int32_t x = x0 + j * B + threadIdx.x;
     bool ok = false;
-    if (e < e1) {
-      int64_t rs;
-      const int64_t r = find_row(t, s_woff, woff, e, &rs);
-      const int32_t w = __ldg(g.col + pstart[r] + (e - rs));
-      ok = check_candidate(g, d, F + r * d.i, w, pslot[r]);
+    if (x < x1) {
+      int32_t rs;
+      const int32_t r = item_row(t, s_woff, woff, wa, x, &rs);
+      const int32_t w = __ldg(g.col + pstart[r] + (x - rs));
+      ok = check_candidate(g, d, F, ld, r, w, pslot[r]);
     }
     const uint32_t m = __ballot_sync(kFull, ok);
     if (lane == 0) {
-      if (kMasks) masks[((e0 - wa) + j * B) / 32 + warp] = m;
+      if (kMasks) masks[(x0 + j * B) / 32 + warp] = m;
       cnt += __popc(m);
     }
   }
@@ -429,58 +458,81 @@ __global__ void __launch_bounds__(1024) k_extend_count(
   }
 }
 
+// Position (0..31) of the n-th (0-based) set bit of m; m has more than n.
+__device__ __forceinline__ int nth_set_bit(uint32_t m, int n) {
+  int pos = 0;
+#pragma unroll
+  for (int w = 16; w; w >>= 1) {
+    const uint32_t lo = m & ((1u << w) - 1u);
+    const int c = __popc(lo);
+    if (n >= c) {
+      n -= c;
+      m >>= w;
+      pos += w;
+    } else {
+      m = lo;
+    }
+  }
+  return pos;
+}
+
+// Write pass: survivor q of tile t becomes output row out_base + tile_off[t] +
+// q; thread q of the CTA handles it (survivors are dense over the threads,
+// whatever the survival rate), so each column store of a warp covers 32
+// consecutive rows.  Position c of the input row goes to column out_col[c] of
+// the column-major output (leading dimension out_ld), the new vertex to
+// column out_col[i].
 __global__ void __launch_bounds__(1024) k_extend_write(
-    GraphDev g, LevelDesc d, const int32_t *__restrict__ F, const int32_t *__restrict__ pstart,
-    const int64_t *__restrict__ woff, int64_t ra, int64_t rb, int64_t wa, int64_t wb,
+    GraphDev g, LevelDesc d, const int32_t *__restrict__ F, int32_t ld,
+    const int32_t *__restrict__ pstart, const int64_t *__restrict__ woff,
+    const int32_t *__restrict__ tile_row, int64_t wa, int32_t W,
     const uint32_t *__restrict__ masks, const int64_t *__restrict__ tile_off,
-    int32_t *__restrict__ out) {
-  extern __shared__ int64_t s_woff[];
-  __shared__ int64_t s_meta[2];
+    int32_t *__restrict__ out, int64_t out_ld) {
+  extern __shared__ int32_t s_woff[];
   __shared__ uint32_t s_mask[kItemsPerThread * 1024 / 32];
   __shared__ int32_t s_wpre[kItemsPerThread * 1024 / 32];
   const int64_t base = tile_off[blockIdx.x];
-  if (tile_off[blockIdx.x + 1] == base) return;  // uniform across the block
-  const int64_t B = blockDim.x;
-  const int64_t tile_items = B * kItemsPerThread;
-  const int32_t tile_words = (int32_t)(tile_items / 32);
-  const int64_t e0 = wa + (int64_t)blockIdx.x * tile_items;
-  const int64_t e1 = min(e0 + tile_items, wb);
-  for (int32_t w = threadIdx.x; w < tile_words; w += blockDim.x)
-    s_mask[w] = masks[(int64_t)blockIdx.x * tile_words + w];
-  const TileRows t = tile_rows(woff, ra, rb, e0, e1, s_woff, (int32_t)tile_items + 1, s_meta);
+  const int32_t cnt = (int32_t)(tile_off[blockIdx.x + 1] - base);
+  if (cnt == 0) return;  // uniform across the block
+  const int32_t B = blockDim.x;
+  const int32_t tile_items = B * kItemsPerThread;
+  const int32_t tile_words = tile_items / 32;
+  const int32_t x0 = blockIdx.x * tile_items;
+  for (int32_t w = threadIdx.x; w < tile_words; w += B)
+    s_mask[w] = masks[blockIdx.x * tile_words + w];
+  const TileRows t = stage_rows(woff, tile_row, wa, tile_items, s_woff);
   const int lane = threadIdx.x & 31;
   if (threadIdx.x < 32) {
     int32_t carry = 0;
     for (int32_t c = 0; c < tile_words; c += 32) {
       const int32_t idx = c + lane;
-      const int32_t x = idx < tile_words ? __popc(s_mask[idx]) : 0;
-      int32_t incl = x;
+      const int32_t v = idx < tile_words ? __popc(s_mask[idx]) : 0;
+      int32_t incl = v;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         int32_t y = __shfl_up_sync(kFull, incl, o);
         if (lane >= o) incl += y;
       }
-      if (idx < tile_words) s_wpre[idx] = carry + incl - x;
+      if (idx < tile_words) s_wpre[idx] = carry + incl - v;
       carry += __shfl_sync(kFull, incl, 31);
     }
   }
   __syncthreads();
-  const uint32_t lt = (1u << lane) - 1u;
   const int32_t i = d.i;
-#pragma unroll
-  for (int j = 0; j < kItemsPerThread; ++j) {
-    const int32_t widx = (int32_t)((j * B + threadIdx.x) >> 5);
-    const uint32_t m = s_mask[widx];
-    if (!((m >> lane) & 1u)) continue;
-    const int64_t e = e0 + j * B + threadIdx.x;
-    const int64_t pos = base + s_wpre[widx] + __popc(m & lt);
-    int64_t rs;
-    const int64_t r = find_row(t, s_woff, woff, e, &rs);
-    const int32_t w = __ldg(g.col + pstart[r] + (e - rs));
-    const int32_t *row = F + r * i;
-    int32_t *o = out + pos * (i + 1);
-    for (int c = 0; c < i; ++c) o[d.out_col[c]] = row[c];
-    o[d.out_col[i]] = w;
+  for (int32_t q = threadIdx.x; q < cnt; q += B) {
+    // word holding survivor q: the last word whose prefix count is <= q
+    int32_t lo = 0, hi = tile_words;
+    while (hi - lo > 1) {
+      const int32_t mid = (lo + hi) >> 1;
+      if (s_wpre[mid] <= q) lo = mid; else hi = mid;
+    }
+    const int32_t x = x0 + lo * 32 + nth_set_bit(s_mask[lo], q - s_wpre[lo]);
+    int32_t rs;
+    const int32_t r = item_row(t, s_woff, woff, wa, x, &rs);
+    const int32_t w = __ldg(g.col + pstart[r] + (x - rs));
+    int32_t *o = out + base + q;
+    for (int c = 0; c < i; ++c) o[d.out_col[c] * out_ld] = F[c * ld + r];
+    o[d.out_col[i] * out_ld] = w;
   }
 }
 
@@ -560,33 +612,47 @@ void launch_pivot(const GraphDev &g, const LevelDesc &d, const int32_t *F, int64
   k_pivot<<<grid_for(R, 256, 152 * 64), 256, 0, s>>>(g, d, F, R, pstart, pslot, work);
 }
 
-void launch_extend_count(const GraphDev &g, const LevelDesc &d, const int32_t *F,
-                         const int32_t *pstart, const uint8_t *pslot, const int64_t *woff,
-                         int64_t ra, int64_t rb, int64_t wa, int64_t wb, int32_t block,
-                         uint32_t *masks, int32_t *tile_cnt, unsigned long long *total,
-                         cudaStream_t s) {
+int64_t extend_tiles(int64_t wa, int64_t wb, int32_t block) {
   const int64_t tile_items = (int64_t)block * kItemsPerThread;
-  const int64_t tiles = (wb - wa + tile_items - 1) / tile_items;
-  if (tiles <= 0) return;
-  const size_t smem = (size_t)(tile_items + 1) * sizeof(int64_t);
-  if (masks)
-    k_extend_count<true><<<(unsigned)tiles, block, smem, s>>>(g, d, F, pstart, pslot, woff, ra,
-                                                               rb, wa, wb, masks, tile_cnt, total);
-  else
-    k_extend_count<false><<<(unsigned)tiles, block, smem, s>>>(g, d, F, pstart, pslot, woff, ra,
-                                                                rb, wa, wb, masks, tile_cnt, total);
+  return (wb - wa + tile_items - 1) / tile_items;
 }
 
-void launch_extend_write(const GraphDev &g, const LevelDesc &d, const int32_t *F,
-                         const int32_t *pstart, const int64_t *woff, int64_t ra, int64_t rb,
-                         int64_t wa, int64_t wb, int32_t block, const uint32_t *masks,
-                         const int64_t *tile_off, int32_t *out, cudaStream_t s) {
-  const int64_t tile_items = (int64_t)block * kItemsPerThread;
-  const int64_t tiles = (wb - wa + tile_items - 1) / tile_items;
+void launch_tile_rows(const int64_t *woff, int64_t ra, int64_t rb, int64_t wa, int64_t wb,
+                      int32_t block, int32_t *tile_row, cudaStream_t s) {
+  const int64_t tiles = extend_tiles(wa, wb, block);
   if (tiles <= 0) return;
-  const size_t smem = (size_t)(tile_items + 1) * sizeof(int64_t);
-  k_extend_write<<<(unsigned)tiles, block, smem, s>>>(g, d, F, pstart, woff, ra, rb, wa, wb,
-                                                      masks, tile_off, out);
+  k_tile_rows<<<grid_for(rb - ra, 256, 152 * 64), 256, 0, s>>>(
+      woff, ra, rb, wa, (int64_t)block * kItemsPerThread, tiles, tile_row);
+}
+
+void launch_extend_count(const GraphDev &g, const LevelDesc &d, const int32_t *F, int64_t ld,
+                         const int32_t *pstart, const uint8_t *pslot, const int64_t *woff,
+                         const int32_t *tile_row, int64_t wa, int64_t wb, int32_t block,
+                         uint32_t *masks, int32_t *tile_cnt, unsigned long long *total,
+                         cudaStream_t s) {
+  const int64_t tiles = extend_tiles(wa, wb, block);
+  if (tiles <= 0) return;
+  const size_t smem = (size_t)((int64_t)block * kItemsPerThread + 1) * sizeof(int32_t);
+  if (masks)
+    k_extend_count<true><<<(unsigned)tiles, block, smem, s>>>(
+        g, d, F, (int32_t)ld, pstart, pslot, woff, tile_row, wa, (int32_t)(wb - wa), masks,
+        tile_cnt, total);
+  else
+    k_extend_count<false><<<(unsigned)tiles, block, smem, s>>>(
+        g, d, F, (int32_t)ld, pstart, pslot, woff, tile_row, wa, (int32_t)(wb - wa), masks,
+        tile_cnt, total);
+}
+
+void launch_extend_write(const GraphDev &g, const LevelDesc &d, const int32_t *F, int64_t ld,
+                         const int32_t *pstart, const int64_t *woff, const int32_t *tile_row,
+                         int64_t wa, int64_t wb, int32_t block, const uint32_t *masks,
+                         const int64_t *tile_off, int32_t *out, int64_t out_ld, cudaStream_t s) {
+  const int64_t tiles = extend_tiles(wa, wb, block);
+  if (tiles <= 0) return;
+  const size_t smem = (size_t)((int64_t)block * kItemsPerThread + 1) * sizeof(int32_t);
+  k_extend_write<<<(unsigned)tiles, block, smem, s>>>(g, d, F, (int32_t)ld, pstart, woff,
+                                                      tile_row, wa, (int32_t)(wb - wa), masks,
+                                                      tile_off, out, out_ld);
 }
 
 void launch_split_points(const int64_t *woff, int64_t R, int64_t step, int64_t J,

@@ -72,39 +72,57 @@ void launch_scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *tmp, c
 void launch_bitmap_to_list(const uint32_t *bitmap, int32_t n_words, int32_t *cnt, int64_t *off,
                            int64_t *tmp, int32_t *out, cudaStream_t s);
 
+// Frontiers are column-major: position c of row r is F[c*ld + r].
+
 // Per row: pick the mapped neighbour of pi_i with the fewest neighbours (the
 // pivot) and record its CSR start, its slot in bpos, and its degree as work
-// (int64, so the work array can be scanned in place into offsets).
+// (int64, so the work array can be scanned in place into offsets).  F has
+// leading dimension R.
 void launch_pivot(const GraphDev &g, const LevelDesc &d, const int32_t *F, int64_t R,
                   int32_t *pstart, uint8_t *pslot, int64_t *work, cudaStream_t s);
 
-// Verification pass over candidates [wa, wb) of rows [ra, rb): writes one
-// survivor bit per candidate into masks (if non-null), one survivor count per
-// tile into tile_cnt (if non-null), and adds the total into *total (if non-null).
-void launch_extend_count(const GraphDev &g, const LevelDesc &d, const int32_t *F,
+// Number of extend tiles for candidates [wa, wb).
+int64_t extend_tiles(int64_t wa, int64_t wb, int32_t block);
+
+// tile_row[0..tiles]: first row of every tile of candidates [wa, wb) of rows
+// [ra, rb) (woff = exclusive work offsets of the level).
+// Limits of one extend launch: wb - wa < 2^30, rows < 2^31, ld * (i+1) < 2^31.
+void launch_tile_rows(const int64_t *woff, int64_t ra, int64_t rb, int64_t wa, int64_t wb,
+                      int32_t block, int32_t *tile_row, cudaStream_t s);
+
+// Verification pass over candidates [wa, wb): writes one survivor bit per
+// candidate into masks (if non-null), one survivor count per tile into
+// tile_cnt (if non-null), and adds the total into *total (if non-null).
+void launch_extend_count(const GraphDev &g, const LevelDesc &d, const int32_t *F, int64_t ld,
                          const int32_t *pstart, const uint8_t *pslot, const int64_t *woff,
-                         int64_t ra, int64_t rb, int64_t wa, int64_t wb, int32_t block,
+                         const int32_t *tile_row, int64_t wa, int64_t wb, int32_t block,
                          uint32_t *masks, int32_t *tile_cnt, unsigned long long *total,
                          cudaStream_t s);
 
-// Write pass: survivor q of tile t goes to row tile_off[t] + rank of out.
-void launch_extend_write(const GraphDev &g, const LevelDesc &d, const int32_t *F,
-                         const int32_t *pstart, const int64_t *woff, int64_t ra, int64_t rb,
+// Write pass: survivor q of tile t goes to row tile_off[t] + rank of the
+// column-major output (leading dimension out_ld); input position c goes to
+// column d.out_col[c], the new vertex to column d.out_col[d.i].
+void launch_extend_write(const GraphDev &g, const LevelDesc &d, const int32_t *F, int64_t ld,
+                         const int32_t *pstart, const int64_t *woff, const int32_t *tile_row,
                          int64_t wa, int64_t wb, int32_t block, const uint32_t *masks,
-                         const int64_t *tile_off, int32_t *out, cudaStream_t s);
+                         const int64_t *tile_off, int32_t *out, int64_t out_ld, cudaStream_t s);
 
 // Row boundaries for work-bounded sub-chunks: bounds[j] = the row r with
 // woff[r] <= j*step < woff[r+1] (clamped to [0, R]); bounds[J] = R.
 void launch_split_points(const int64_t *woff, int64_t R, int64_t step, int64_t J,
                          int64_t *bounds, int64_t *bound_w, cudaStream_t s);
 
-// Lexicographic sort of N rows of k int32 (LSD radix, 8-bit digits).
-// `bits` = significant bits per column (values < 2^bits).  Result lands in
-// `a` or `b`; the function returns which (0 = a, 1 = b).  hist needs
+// Lexicographic sort of N rows of k int32 held column-major in `a` (leading
+// dimension lda), by column 0, then 1, ... (LSD radix, 8-bit digits, values
+// < 2^bits).  `b` is column-major scratch (leading dimension ldb >= N).  The
+// sorted rows are written ROW-major into whichever of a / b the last pass does
+// not read; the function returns which (0 = a, 1 = b).  presorted: the rows
+// are already in order and are only transposed into b.  hist needs
 // sort_hist_elems(N) int32, hist_off sort_hist_elems(N)+1 int64, tmp
 // scan_tmp_elems(sort_hist_elems(N)) int64.
 int64_t sort_hist_elems(int64_t N);
-int launch_sort_rows(int32_t *a, int32_t *b, int64_t N, int32_t k, int32_t bits, int32_t *hist,
-                     int64_t *hist_off, int64_t *tmp, cudaStream_t s, int *launches);
+int launch_sort_rows(int32_t *a, int64_t lda, int32_t *b, int64_t ldb, int64_t N, int32_t k,
+                     int32_t bits, bool presorted, int32_t *hist, int64_t *hist_off, int64_t *tmp,
+                     cudaStream_t s, int *launches);
 
 }  // namespace gsm

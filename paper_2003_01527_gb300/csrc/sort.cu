@@ -6,7 +6,11 @@
 // digit radix sort over 8-bit digits that moves whole rows (k int32 each):
 // columns are processed from the last to the first, low digit to high digit,
 // and every pass is stable, so after the last pass the rows are ordered by
-// column 0, then column 1, and so on.
+// column 0, then column 1, and so on.  Rows arrive column-major (the layout
+// of the frontiers); intermediate passes keep that layout, the last pass
+// writes row-major, the layout of the result.
+#include <utility>
+
 #include "kernels.cuh"
 
 namespace gsm {
@@ -18,8 +22,8 @@ constexpr int kSortChunks = 8;  // rows per CTA = 256 * 8
 constexpr int kSortTile = kSortThreads * kSortChunks;
 constexpr int kBins = 256;
 
-__global__ void __launch_bounds__(kSortThreads) k_sort_hist(const int32_t *__restrict__ rows,
-                                                            int64_t N, int32_t k, int32_t col,
+__global__ void __launch_bounds__(kSortThreads) k_sort_hist(const int32_t *__restrict__ col_in,
+                                                            int64_t N,
                                                             int32_t shift,
                                                             int32_t *__restrict__ hist,
                                                             int64_t nblocks) {
@@ -31,7 +35,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const int32_t *__res
   for (int c = 0; c < kSortChunks; ++c) {
     const int64_t idx = base + c * kSortThreads + threadIdx.x;
     if (idx < N) {
-      const uint32_t dgt = ((uint32_t)rows[idx * k + col] >> shift) & 0xffu;
+      const uint32_t dgt = ((uint32_t)col_in[idx] >> shift) & 0xffu;
       atomicAdd(&s_hist[dgt], 1);
     }
   }
@@ -41,9 +45,14 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const int32_t *__res
   hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = s_hist[threadIdx.x];
 }
 
+// One stable pass: row idx moves to hist_off[digit][block] + (rank among the
+// block's earlier rows with that digit).  Input column-major (ld_in); output
+// column-major (ld_out) or, for the last pass, row-major.
+template <bool kRowOut>
 __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
-    const int32_t *__restrict__ in, int32_t *__restrict__ out, int64_t N, int32_t k, int32_t col,
-    int32_t shift, const int64_t *__restrict__ hist_off, int64_t nblocks) {
+    const int32_t *__restrict__ in, int64_t ld_in, int32_t *__restrict__ out, int64_t ld_out,
+    int64_t N, int32_t k, int32_t col, int32_t shift, const int64_t *__restrict__ hist_off,
+    int64_t nblocks) {
   __shared__ int64_t s_base[kBins];
   __shared__ int32_t s_wcnt[kSortThreads / 32][kBins + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -55,7 +64,8 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
     __syncthreads();
     const int64_t idx = base + c * kSortThreads + threadIdx.x;
     const bool valid = idx < N;
-    const uint32_t dgt = valid ? ((uint32_t)in[idx * k + col] >> shift) & 0xffu : kBins;
+    const uint32_t dgt =
+        valid ? ((uint32_t)in[(int64_t)col * ld_in + idx] >> shift) & 0xffu : kBins;
     const uint32_t peers = __match_any_sync(kFull, dgt);
     const int rank = __popc(peers & lt);
     if (valid && rank == 0) s_wcnt[warp][dgt] = __popc(peers);
@@ -63,15 +73,38 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
     if (valid) {
       int64_t pos = s_base[dgt] + rank;
       for (int w = 0; w < warp; ++w) pos += s_wcnt[w][dgt];
-      const int32_t *src = in + idx * k;
-      int32_t *dst = out + pos * k;
-      for (int j = 0; j < k; ++j) dst[j] = src[j];
+      for (int j = 0; j < k; ++j) {
+        const int32_t v = in[(int64_t)j * ld_in + idx];
+        if (kRowOut)
+          out[pos * k + j] = v;
+        else
+          out[(int64_t)j * ld_out + pos] = v;
+      }
     }
     __syncthreads();
     int32_t add = 0;
     for (int w = 0; w < kSortThreads / 32; ++w) add += s_wcnt[w][threadIdx.x];
     s_base[threadIdx.x] += add;
     __syncthreads();
+  }
+}
+
+// Column-major -> row-major through a shared-memory tile: 32 rows per block,
+// reads and writes both contiguous.
+__global__ void __launch_bounds__(256) k_transpose_rows(const int32_t *__restrict__ in,
+                                                        int64_t ld, int32_t *__restrict__ out,
+                                                        int64_t N, int32_t k) {
+  __shared__ int32_t s_tile[32 * 17];
+  const int64_t r0 = (int64_t)blockIdx.x * 32;
+  for (int t = threadIdx.x; t < 32 * k; t += blockDim.x) {
+    const int j = t / 32, rr = t % 32;
+    if (r0 + rr < N) s_tile[rr * 17 + j] = in[(int64_t)j * ld + r0 + rr];
+  }
+  __syncthreads();
+  const int64_t rows = min((int64_t)32, N - r0);
+  for (int t = threadIdx.x; t < rows * k; t += blockDim.x) {
+    const int rr = t / k, j = t % k;
+    out[(r0 + rr) * k + j] = s_tile[rr * 17 + j];
   }
 }
 
@@ -82,22 +115,37 @@ int64_t sort_hist_elems(int64_t N) {
   return nb * kBins;
 }
 
-int launch_sort_rows(int32_t *a, int32_t *b, int64_t N, int32_t k, int32_t bits, int32_t *hist,
-                     int64_t *hist_off, int64_t *tmp, cudaStream_t s, int *launches) {
-  if (N <= 1) return 0;
+int launch_sort_rows(int32_t *a, int64_t lda, int32_t *b, int64_t ldb, int64_t N, int32_t k,
+                     int32_t bits, bool presorted, int32_t *hist, int64_t *hist_off, int64_t *tmp,
+                     cudaStream_t s, int *launches) {
+  if (N <= 0) return 0;
+  if (presorted || N == 1) {
+    k_transpose_rows<<<(unsigned)((N + 31) / 32), 256, 0, s>>>(a, lda, b, N, k);
+    if (launches) *launches += 1;
+    return 1;
+  }
   const int64_t nb = (N + kSortTile - 1) / kSortTile;
+  const int passes_per_col = (bits + 7) / 8;
+  const int total = k * passes_per_col;
   int32_t *src = a, *dst = b;
+  int64_t ld_src = lda, ld_dst = ldb;
   int which = 0;
+  int pass = 0;
   for (int32_t col = k - 1; col >= 0; --col) {
     for (int32_t shift = 0; shift < bits; shift += 8) {
-      k_sort_hist<<<(unsigned)nb, kSortThreads, 0, s>>>(src, N, k, col, shift, hist, nb);
+      ++pass;
+      k_sort_hist<<<(unsigned)nb, kSortThreads, 0, s>>>(src + (int64_t)col * ld_src, N, shift,
+                                                        hist, nb);
       launch_scan_i32(hist, hist_off, nb * kBins, tmp, s);
-      k_sort_scatter<<<(unsigned)nb, kSortThreads, 0, s>>>(src, dst, N, k, col, shift, hist_off,
-                                                           nb);
+      if (pass == total)
+        k_sort_scatter<true><<<(unsigned)nb, kSortThreads, 0, s>>>(
+            src, ld_src, dst, ld_dst, N, k, col, shift, hist_off, nb);
+      else
+        k_sort_scatter<false><<<(unsigned)nb, kSortThreads, 0, s>>>(
+            src, ld_src, dst, ld_dst, N, k, col, shift, hist_off, nb);
       if (launches) *launches += 5;
-      int32_t *t = src;
-      src = dst;
-      dst = t;
+      std::swap(src, dst);
+      std::swap(ld_src, ld_dst);
       which ^= 1;
     }
   }
