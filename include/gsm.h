@@ -164,6 +164,55 @@ gsm_status gsm_last_rows(gsm_ctx *ctx, int32_t *out, uint64_t first, uint64_t nr
  *   sizes    host uint64[k]: |C(u)| (may be NULL) */
 gsm_status gsm_candidates(gsm_ctx *ctx, const gsm_query *q, uint32_t *bitmaps, uint64_t *sizes);
 
+/* ---- Batched form: many queries against the resident graph at once ----
+ *
+ * The paper runs one query at a time; this form runs a whole batch of
+ * queries (uneven sizes, 1..16 vertices) as one CUDA graph: a batched
+ * candidate filter, then every verification level of every query over one
+ * concatenated frontier (Algorithm 1's levels, all queries in lock step),
+ * with no host synchronisation until the counts come back.  The matching
+ * order of each query uses label/degree histograms of G as its P_f estimate
+ * (the VF3 estimate the paper cites in Sec. 3.2) instead of the candidate
+ * counts, so the order is known before the filter runs.  Results equal
+ * gsm_count's for every query.  The batch works in a fixed-capacity
+ * workspace (about 1.4 GB, allocated on first use, outside the memory budget:
+ * 2^24 frontier rows, 2^27 frontier elements, 2^28 candidates per level); a
+ * batch that would exceed it is rerun query by query on the gsm_count path.
+ */
+typedef struct gsm_batch_stats {
+  int32_t block_size;        /* threads per CTA used by the last batch */
+  int32_t grid;              /* persistent CTAs used by the last batch */
+  int32_t tuned;             /* 1 if the autotuner chose them */
+  int32_t overflowed;        /* 1 if the last batch fell back to gsm_count */
+  uint64_t batches;          /* batches run */
+  uint64_t graph_launches;   /* CUDA graph launches */
+  uint64_t graphs_built;     /* graphs captured and instantiated */
+  uint64_t fallbacks;        /* batches rerun on the single-query path */
+  uint64_t kernels_per_graph;
+  double last_ms;            /* host wall time of the last gsm_run_batch */
+} gsm_batch_stats;
+
+#define GSM_BATCH_AUTOTUNE 1 /* time candidate (block size, grid) pairs for new batch shapes */
+
+/* Counts the embeddings of qs[0..nq) (counts[j] as gsm_count would return
+ * for qs[j]).  Shapes (number of queries, largest query) seen before reuse
+ * their captured graph.  With GSM_BATCH_AUTOTUNE, the first batch of a shape
+ * is run once per candidate configuration (every run gives the same counts)
+ * and the fastest is kept for that shape.  nq <= 65535.
+ * Errors: GSM_ERR_INVALID_ARG, GSM_ERR_NO_GRAPH, GSM_ERR_OOM, GSM_ERR_CUDA, and
+ * the errors of gsm_count on the fallback path. */
+gsm_status gsm_run_batch(gsm_ctx *ctx, const gsm_query *const *qs, int32_t nq, uint64_t *counts,
+                         int32_t flags);
+
+gsm_status gsm_batch_get_stats(gsm_ctx *ctx, gsm_batch_stats *out);
+
+/* Sets the batch workspace capacities (0 keeps the default): frontier rows
+ * (< 2^31), frontier elements (rows x width, < 2^31) and candidates per level
+ * (< 2^30).  Frees the current workspace; the next batch allocates the new one.
+ * Errors: GSM_ERR_INVALID_ARG. */
+gsm_status gsm_batch_configure(gsm_ctx *ctx, uint64_t cap_rows, uint64_t cap_elems,
+                               uint64_t cap_items);
+
 /* Size of the fixed device array behind gsm_candidates_static: bitmap words of
  * one call, k * ceil(n/32) * 4 bytes, must fit in it (e.g. n <= 4,194,304 at
  * k = 16).  A further 256 bytes hold the counters. */

@@ -3,12 +3,18 @@
 // level per query vertex (paper Sec. 3.2, Algorithm 1) depth-first over
 // frontier chunks so intermediate results stay inside a fixed budget.
 #include <algorithm>
+#include <array>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
 
+#include <chrono>
+#include <map>
+#include <tuple>
+
+#include "batch.h"
 #include "gsm.h"
 #include "kernels.cuh"
 #include "query_access.h"
@@ -91,6 +97,28 @@ struct gsm_ctx {
   size_t scratch_cap = 0;
 
   int64_t *h_stage = nullptr;  // pinned staging for small device->host reads
+  int32_t num_sms = 0;
+
+  // batched form: per-label sorted degrees (order estimates without the
+  // filter's results), a fixed-capacity workspace, captured graphs
+  std::vector<std::vector<int32_t>> deg_by_label;
+  int64_t batch_caps[3] = {0, 0, 0};  // rows, elements, candidates (0 = default)
+  struct BatchWs {
+    bool ready = false;
+    int64_t cap_rows = 0, cap_elems = 0, cap_items = 0;
+    int32_t max_nq = 0, max_words_total = 0;
+    std::vector<std::pair<void *, size_t>> allocs;
+    gsm::BatchArgs a{};
+    void *bitmaps = nullptr;
+    size_t bitmaps_cap = 0;
+    FilterDesc *h_fds = nullptr;
+    BatchQuery *h_qs = nullptr;
+    uint32_t **h_bm = nullptr;
+    unsigned long long *h_counts = nullptr;
+  } bw;
+  std::map<std::tuple<int32_t, int32_t, int32_t, int32_t, int32_t>, cudaGraphExec_t> graphs;
+  std::map<std::pair<int32_t, int32_t>, std::pair<int32_t, int32_t>> tuned;  // bucket -> (block, grid)
+  gsm_batch_stats bstats{};
 
   // stats
   KStat kstats[K_NUM];
@@ -798,13 +826,317 @@ gsm_status guarded(gsm_ctx *ctx, F &&f) {
   }
 }
 
+void clear_graphs(gsm_ctx *ctx) {
+  for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+  ctx->graphs.clear();
+}
+
 void free_graph(gsm_ctx *ctx) {
+  clear_graphs(ctx);
   if (ctx->d_rp) dev_free(ctx, ctx->d_rp, sizeof(int32_t) * (ctx->n + 1));
   if (ctx->d_col) dev_free(ctx, ctx->d_col, sizeof(int32_t) * std::max<int64_t>(ctx->nnz, 1));
   if (ctx->d_lab) dev_free(ctx, ctx->d_lab, sizeof(int32_t) * std::max<int32_t>(ctx->n, 1));
   ctx->d_rp = ctx->d_col = ctx->d_lab = nullptr;
   ctx->has_graph = false;
   ctx->label_values.clear();
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ batched form
+
+namespace {
+
+constexpr int64_t kBatchCapRows = int64_t(1) << 24;
+constexpr int64_t kBatchCapElems = int64_t(1) << 27;
+constexpr int64_t kBatchCapItems = int64_t(1) << 28;
+
+template <typename T>
+T *bw_alloc(gsm_ctx *ctx, int64_t elems) {
+  const size_t bytes = sizeof(T) * (size_t)std::max<int64_t>(elems, 1);
+  void *p = dev_alloc(ctx, bytes);
+  ctx->bw.allocs.push_back({p, bytes});
+  return (T *)p;
+}
+
+void bw_free_one(gsm_ctx *ctx, void *p) {
+  for (auto it = ctx->bw.allocs.begin(); it != ctx->bw.allocs.end(); ++it)
+    if (it->first == p) {
+      dev_free(ctx, it->first, it->second);
+      ctx->bw.allocs.erase(it);
+      return;
+    }
+}
+
+// Fixed-capacity buffers (once), per-query arrays (grown with the batch).
+void batch_workspace(gsm_ctx *ctx, int32_t nq, int64_t words_total) {
+  auto &W = ctx->bw;
+  BatchArgs &a = W.a;
+  if (!W.ready) {
+    W.cap_rows = ctx->batch_caps[0] ? ctx->batch_caps[0] : kBatchCapRows;
+    W.cap_elems = ctx->batch_caps[1] ? ctx->batch_caps[1] : kBatchCapElems;
+    W.cap_items = ctx->batch_caps[2] ? ctx->batch_caps[2] : kBatchCapItems;
+    a.cap_rows = W.cap_rows;
+    a.cap_elems = W.cap_elems;
+    a.cap_items = W.cap_items;
+    for (int j = 0; j < 2; ++j) {
+      a.F[j] = bw_alloc<int32_t>(ctx, W.cap_elems);
+      a.rseg[j] = bw_alloc<int32_t>(ctx, W.cap_rows);
+    }
+    a.pstart = bw_alloc<int32_t>(ctx, W.cap_rows);
+    a.pslot = bw_alloc<uint8_t>(ctx, W.cap_rows);
+    a.woff = bw_alloc<int64_t>(ctx, W.cap_rows + 1);
+    const int64_t tiles = W.cap_items / 128 + 3;
+    a.tile_row = bw_alloc<int32_t>(ctx, tiles);
+    a.tile_cnt = bw_alloc<int32_t>(ctx, tiles);
+    a.tile_off = bw_alloc<int64_t>(ctx, tiles);
+    a.masks = bw_alloc<uint32_t>(ctx, W.cap_items / 32 + 256);  // + one tile of the largest block
+    a.state = bw_alloc<BatchStep>(ctx, kMaxK + 1);
+    a.overflow = bw_alloc<int32_t>(ctx, 1);
+    a.partials = bw_alloc<int64_t>(ctx, (int64_t)ctx->num_sms * 32 + 1);
+    W.ready = true;
+  }
+  bool moved = false;
+  if (nq > W.max_nq) {
+    if (W.max_nq) {
+      bw_free_one(ctx, (void *)a.fds);
+      bw_free_one(ctx, (void *)a.bm_out);
+      bw_free_one(ctx, (void *)a.qs);
+      bw_free_one(ctx, a.counts);
+      bw_free_one(ctx, a.sizes);
+      cudaFreeHost(W.h_fds);
+      cudaFreeHost(W.h_qs);
+      cudaFreeHost(W.h_bm);
+      cudaFreeHost(W.h_counts);
+    }
+    const int32_t cap = std::max(nq, 2 * W.max_nq);
+    a.fds = bw_alloc<FilterDesc>(ctx, cap);
+    a.bm_out = bw_alloc<uint32_t *>(ctx, cap);
+    a.qs = bw_alloc<BatchQuery>(ctx, cap);
+    a.counts = bw_alloc<unsigned long long>(ctx, cap);
+    a.sizes = bw_alloc<unsigned long long>(ctx, (int64_t)cap * kMaxK);
+    CU(cudaMallocHost(&W.h_fds, sizeof(FilterDesc) * cap));
+    CU(cudaMallocHost(&W.h_qs, sizeof(BatchQuery) * cap));
+    CU(cudaMallocHost(&W.h_bm, sizeof(uint32_t *) * cap));
+    CU(cudaMallocHost(&W.h_counts, sizeof(unsigned long long) * cap));
+    W.max_nq = cap;
+    moved = true;
+  }
+  if (words_total > W.max_words_total) {
+    if (W.max_words_total) {
+      bw_free_one(ctx, a.wcnt);
+      bw_free_one(ctx, a.woffs);
+    }
+    const int64_t cap = std::max<int64_t>(words_total, 2 * (int64_t)W.max_words_total);
+    a.wcnt = bw_alloc<int32_t>(ctx, cap);
+    a.woffs = bw_alloc<int64_t>(ctx, cap + 1);
+    W.max_words_total = (int32_t)std::min<int64_t>(cap, 0x7fffffff);
+    moved = true;
+  }
+  if (moved) clear_graphs(ctx);  // captured graphs hold the old pointers
+}
+
+void batch_free(gsm_ctx *ctx) {
+  clear_graphs(ctx);
+  for (auto &pa : ctx->bw.allocs) dev_free(ctx, pa.first, pa.second);
+  ctx->bw.allocs.clear();
+  if (ctx->bw.h_fds) cudaFreeHost(ctx->bw.h_fds);
+  if (ctx->bw.h_qs) cudaFreeHost(ctx->bw.h_qs);
+  if (ctx->bw.h_bm) cudaFreeHost(ctx->bw.h_bm);
+  if (ctx->bw.h_counts) cudaFreeHost(ctx->bw.h_counts);
+  if (ctx->bw.bitmaps) dev_free(ctx, ctx->bw.bitmaps, ctx->bw.bitmaps_cap);
+  ctx->bw = gsm_ctx::BatchWs();
+}
+
+// Estimated |C(u)|: vertices with u's label and at least u's degree (the
+// label / degree probability the paper borrows from VF3), scaled by u's
+// restriction range.
+uint64_t estimate_candidates(gsm_ctx *ctx, const gsm_query *q, int32_t u, int32_t dense_label) {
+  const auto &d = ctx->deg_by_label[dense_label];
+  const int32_t qdeg = popc(q->adj[u]);
+  uint64_t c = (uint64_t)(d.end() - std::lower_bound(d.begin(), d.end(), qdeg));
+  const int64_t lo = std::max<int64_t>(0, q->lo[u]), hi = std::min<int64_t>(ctx->n, q->hi[u]);
+  if (hi - lo < ctx->n && ctx->n > 0) {
+    const double f = hi > lo ? (double)(hi - lo) / ctx->n : 0.0;
+    c = c ? std::max<uint64_t>(1, (uint64_t)(c * f)) : 0;
+  }
+  return c;
+}
+
+cudaGraphExec_t batch_graph(gsm_ctx *ctx, int32_t m, int32_t kmax, int32_t n_words,
+                            int32_t block, int32_t grid) {
+  const auto key = std::make_tuple(m, kmax, n_words, block, grid);
+  auto it = ctx->graphs.find(key);
+  if (it != ctx->graphs.end()) return it->second;
+  BatchArgs a = ctx->bw.a;
+  a.nq = m;
+  a.kmax = kmax;
+  a.n_words = n_words;
+  a.block = block;
+  a.grid = grid;
+  GraphDev g{ctx->n, ctx->nnz, ctx->d_rp, ctx->d_col, ctx->d_lab};
+  cudaGraph_t graph = nullptr;
+  CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+  const int launches = batch_enqueue(g, a, ctx->stream);
+  cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+  if (e != cudaSuccess) {
+    set_err(ctx, "capturing the batch graph failed: %s", cudaGetErrorString(e));
+    throw Fail{GSM_ERR_CUDA};
+  }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    set_err(ctx, "instantiating the batch graph failed: %s", cudaGetErrorString(e));
+    throw Fail{GSM_ERR_CUDA};
+  }
+  ctx->graphs[key] = exec;
+  ctx->bstats.graphs_built += 1;
+  ctx->bstats.kernels_per_graph = (uint64_t)launches;
+  return exec;
+}
+
+// Launches the batch graph; returns the overflow flag (counts land in
+// ctx->bw.h_counts).
+bool batch_launch(gsm_ctx *ctx, int32_t m, int32_t kmax, int32_t n_words, int32_t block,
+                  int32_t grid, float *ms) {
+  cudaGraphExec_t exec = batch_graph(ctx, m, kmax, n_words, block, grid);
+  cudaEvent_t e0 = get_event(ctx), e1 = get_event(ctx);
+  CU(cudaEventRecord(e0, ctx->stream));
+  CU(cudaGraphLaunch(exec, ctx->stream));
+  CU(cudaEventRecord(e1, ctx->stream));
+  CU(cudaMemcpyAsync(ctx->bw.h_counts, ctx->bw.a.counts, sizeof(unsigned long long) * m,
+                     cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaMemcpyAsync(ctx->h_stage, ctx->bw.a.overflow, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  CU(cudaEventElapsedTime(ms, e0, e1));
+  ctx->event_pool.push_back(e0);
+  ctx->event_pool.push_back(e1);
+  ctx->bstats.graph_launches += 1;
+  int32_t of = 0;
+  std::memcpy(&of, ctx->h_stage, sizeof(int32_t));
+  return of != 0;
+}
+
+void run_batch(gsm_ctx *ctx, const gsm_query *const *qs, int32_t nq, uint64_t *counts,
+               int32_t flags) {
+  if (!ctx->has_graph) FAIL(GSM_ERR_NO_GRAPH, "no data graph loaded");
+  const auto t0 = std::chrono::steady_clock::now();
+  const int32_t n_words = (ctx->n + 31) / 32;
+  std::vector<int32_t> sel;
+  std::vector<std::array<int32_t, kMaxK>> dense_of;
+  int64_t total_k = 0;
+  for (int32_t j = 0; j < nq; ++j) {
+    counts[j] = 0;
+    std::array<int32_t, kMaxK> dn{};
+    if (!dense_labels(ctx, qs[j], dn.data())) continue;  // a label absent from G
+    sel.push_back(j);
+    dense_of.push_back(dn);
+    total_k += qs[j]->k;
+  }
+  const int32_t m = (int32_t)sel.size();
+  ctx->bstats.batches += 1;
+  ctx->bstats.overflowed = 0;
+  if (m == 0) return;
+  const size_t bm_bytes = (size_t)total_k * n_words * sizeof(uint32_t);
+  if (ctx->bw.bitmaps_cap < bm_bytes) {
+    clear_graphs(ctx);
+    ensure_buf(ctx, &ctx->bw.bitmaps, &ctx->bw.bitmaps_cap, bm_bytes, false, 0);
+  }
+  batch_workspace(ctx, m, (int64_t)m * n_words);
+  auto &W = ctx->bw;
+  uint32_t *bm = (uint32_t *)W.bitmaps;
+  int32_t kmax = 1;
+  int64_t off = 0;
+  for (int32_t t = 0; t < m; ++t) {
+    const gsm_query *q = qs[sel[t]];
+    const int32_t *dense = dense_of[t].data();
+    fill_filter(ctx, q, dense, W.h_fds[t]);
+    uint64_t est[kMaxK];
+    for (int32_t u = 0; u < q->k; ++u) est[u] = estimate_candidates(ctx, q, u, dense[u]);
+    int32_t order[kMaxK], parent[kMaxK];
+    plan(q->k, q->adj, est, order, parent);
+    uint32_t *base = bm + off;
+    off += (int64_t)q->k * n_words;
+    W.h_bm[t] = base;
+    BatchQuery &bq = W.h_qs[t];
+    std::memset(&bq, 0, sizeof(bq));
+    bq.k = q->k;
+    bq.root_bitmap = base + (size_t)order[0] * n_words;
+    for (int32_t i = 1; i < q->k; ++i) {
+      BatchLevel &L = bq.lv[i];
+      const int32_t u = order[i];
+      for (int32_t j = 0; j < i; ++j) {
+        const int32_t uj = order[j];
+        if (q->adj[u] >> uj & 1u)
+          L.bpos[L.nb++] = j;
+        else if (dense[uj] == dense[u])
+          L.inj[L.ninj++] = j;
+      }
+      L.last = i == q->k - 1;
+      L.bitmap = base + (size_t)u * n_words;
+    }
+    kmax = std::max(kmax, q->k);
+  }
+  CU(cudaMemcpyAsync((void *)W.a.fds, W.h_fds, sizeof(FilterDesc) * m, cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CU(cudaMemcpyAsync((void *)W.a.bm_out, W.h_bm, sizeof(uint32_t *) * m, cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CU(cudaMemcpyAsync((void *)W.a.qs, W.h_qs, sizeof(BatchQuery) * m, cudaMemcpyHostToDevice,
+                     ctx->stream));
+  // launch configuration: tuned for this shape, else the default
+  int32_t mb = 1;
+  while (mb < m) mb <<= 1;
+  const auto bucket = std::make_pair(mb, kmax);
+  int32_t block = 256, grid = ctx->num_sms * 4;
+  ctx->bstats.tuned = 0;
+  auto tn = ctx->tuned.find(bucket);
+  bool overflow = false;
+  float ms = 0;
+  if (tn != ctx->tuned.end()) {
+    block = tn->second.first;
+    grid = tn->second.second;
+    ctx->bstats.tuned = 1;
+    overflow = batch_launch(ctx, m, kmax, n_words, block, grid, &ms);
+  } else if (flags & GSM_BATCH_AUTOTUNE) {
+    const int32_t cand[][2] = {{128, 8}, {256, 4}, {256, 8}, {512, 2}, {512, 4}, {1024, 2}};
+    float best = 1e30f;
+    for (const auto &c : cand) {
+      float t = 0;
+      overflow = batch_launch(ctx, m, kmax, n_words, c[0], ctx->num_sms * c[1], &t);
+      if (overflow) break;  // same counts for every configuration
+      if (t < best) {
+        best = t;
+        block = c[0];
+        grid = ctx->num_sms * c[1];
+      }
+    }
+    ms = best;
+    if (!overflow) {
+      ctx->tuned[bucket] = {block, grid};
+      ctx->bstats.tuned = 1;
+    }
+  } else {
+    overflow = batch_launch(ctx, m, kmax, n_words, block, grid, &ms);
+  }
+  ctx->bstats.block_size = block;
+  ctx->bstats.grid = grid;
+  if (overflow) {
+    // the workspace was too small for this batch: run it query by query
+    ctx->bstats.overflowed = 1;
+    ctx->bstats.fallbacks += 1;
+    for (int32_t t = 0; t < m; ++t) {
+      uint64_t c = 0;
+      bool trunc = false;
+      run_query(ctx, qs[sel[t]], false, nullptr, 0, 0, &c, &trunc);
+      counts[sel[t]] = c;
+    }
+  } else {
+    for (int32_t t = 0; t < m; ++t) counts[sel[t]] = W.h_counts[t];
+  }
+  ctx->bstats.last_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
 
 }  // namespace
@@ -878,6 +1210,7 @@ gsm_status gsm_create(gsm_ctx **out, int32_t device, const gsm_options *opt) {
     ctx->scratch_limit = ctx->budget / 4;
     ctx->stack_limit = ctx->budget - ctx->scratch_limit;
     CU(cudaMallocHost(&ctx->h_stage, 4096));
+    CU(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device));
     ctx->d_small = (unsigned long long *)dev_alloc(ctx, 256);
   });
   if (st != GSM_OK) {
@@ -893,6 +1226,7 @@ void gsm_destroy(gsm_ctx *ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   try {
+    batch_free(ctx);
     free_graph(ctx);
     for (auto &b : ctx->blocks) dev_free(ctx, b.ptr, b.cap);
     dev_free(ctx, ctx->scratch, ctx->scratch_cap);
@@ -971,6 +1305,9 @@ gsm_status gsm_load_graph(gsm_ctx *ctx, int32_t n, int64_t nnz, const int32_t *r
       md = std::max(md, dv);
     }
     ctx->max_deg = md;
+    ctx->deg_by_label.assign(vals.size(), {});
+    for (int32_t v = 0; v < n; ++v) ctx->deg_by_label[dense[v]].push_back(h_rp[v + 1] - h_rp[v]);
+    for (auto &d : ctx->deg_by_label) std::sort(d.begin(), d.end());
     CU(cudaStreamSynchronize(ctx->stream));
     if (flags & GSM_VALIDATE) {
       if (!rp_ok) {
@@ -1107,6 +1444,41 @@ gsm_status gsm_candidates(gsm_ctx *ctx, const gsm_query *q, uint32_t *bitmaps, u
     }
     resolve_timings(ctx);
   });
+}
+
+gsm_status gsm_run_batch(gsm_ctx *ctx, const gsm_query *const *qs, int32_t nq, uint64_t *counts,
+                         int32_t flags) {
+  if (!ctx || nq < 0 || nq > 65535 || (nq > 0 && (!qs || !counts)) ||
+      (flags & ~GSM_BATCH_AUTOTUNE))
+    return GSM_ERR_INVALID_ARG;
+  for (int32_t j = 0; j < nq; ++j)
+    if (!qs[j]) return GSM_ERR_INVALID_ARG;
+  return guarded(ctx, [&] {
+    CU(cudaSetDevice(ctx->device));
+    run_batch(ctx, qs, nq, counts, flags);
+    resolve_timings(ctx);
+  });
+}
+
+gsm_status gsm_batch_configure(gsm_ctx *ctx, uint64_t cap_rows, uint64_t cap_elems,
+                               uint64_t cap_items) {
+  if (!ctx || cap_rows >= (uint64_t(1) << 31) || cap_elems >= (uint64_t(1) << 31) ||
+      cap_items >= (uint64_t(1) << 30))
+    return GSM_ERR_INVALID_ARG;
+  return guarded(ctx, [&] {
+    CU(cudaSetDevice(ctx->device));
+    CU(cudaStreamSynchronize(ctx->stream));
+    batch_free(ctx);
+    ctx->batch_caps[0] = (int64_t)cap_rows;
+    ctx->batch_caps[1] = (int64_t)cap_elems;
+    ctx->batch_caps[2] = (int64_t)cap_items;
+  });
+}
+
+gsm_status gsm_batch_get_stats(gsm_ctx *ctx, gsm_batch_stats *out) {
+  if (!ctx || !out) return GSM_ERR_INVALID_ARG;
+  *out = ctx->bstats;
+  return GSM_OK;
 }
 
 gsm_status gsm_plan_order(int32_t k, int32_t m, const int32_t *edges, const uint64_t *cand_sizes,

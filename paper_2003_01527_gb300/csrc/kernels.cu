@@ -12,6 +12,7 @@
 //   k_extend_write      Write_to_Partial: survivors to consecutive rows
 #include <cstdio>
 
+#include "filter_body.cuh"
 #include "kernels.cuh"
 
 namespace gsm {
@@ -96,93 +97,11 @@ __global__ void k_validate_rows(int32_t n, const int32_t *__restrict__ rp,
 
 // ------------------------------------------------------------ filter
 
-// One warp handles 32 consecutive data vertices.  Each lane first applies the
-// label / degree / range test for its own vertex; vertices that also need
-// per-label neighbour counts are then scanned one at a time by the whole warp
-// (coalesced reads of the CSR row, labels gathered through L2), and the k
-// bitmap words of the group are formed by ballots.
 __global__ void __launch_bounds__(256) k_filter(GraphDev g, FilterDesc d,
                                                 uint32_t *__restrict__ bitmaps,
                                                 unsigned long long *__restrict__ sizes) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp_id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  unsigned long long my_size = 0;  // lane u accumulates |C(u)|
-  for (int64_t grp = warp_id; grp < d.n_words; grp += n_warps) {
-    const int64_t v64 = grp * 32 + lane;
-    const bool valid = v64 < g.n;
-    const int32_t v = (int32_t)v64;
-    int32_t lv = -1, deg = -1;
-    if (valid) {
-      lv = g.lab[v];
-      deg = g.rp[v + 1] - g.rp[v];
-    }
-    uint32_t pre = 0, need = 0;
-#pragma unroll
-    for (int u = 0; u < kMaxK; ++u) {
-      if (u < d.k && valid && lv == d.qlab[u] && deg >= d.qdeg[u] && v >= d.lo[u] &&
-          v < d.hi[u]) {
-        pre |= 1u << u;
-        if (d.nreq[u] > 0) need |= 1u << u;
-      }
-    }
-    uint32_t result = pre & ~need;
-    uint32_t todo = __ballot_sync(kFull, need != 0);
-    while (todo) {
-      const int src = __ffs(todo) - 1;
-      todo &= todo - 1;
-      const int32_t vv = (int32_t)(grp * 32 + src);
-      const uint32_t vneed = __shfl_sync(kFull, need, src);
-      const int32_t b = g.rp[vv], e = g.rp[vv + 1];
-      int32_t cnt[kMaxK], tot[kMaxK];
-#pragma unroll
-      for (int s = 0; s < kMaxK; ++s) cnt[s] = tot[s] = 0;
-      uint32_t pass = 0;
-      // Scan the row 256 neighbours at a time and stop as soon as every
-      // requirement holds (counts only grow), so hubs end after one chunk.
-      for (int32_t base = b; base < e; base += 256) {
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int32_t idx = base + j * 32 + lane;
-          if (idx < e) {
-            const int32_t lw = __ldg(g.lab + __ldg(g.col + idx));
-#pragma unroll
-            for (int s = 0; s < kMaxK; ++s)
-              if (s < d.nslots && lw == d.slot_label[s]) ++cnt[s];
-          }
-        }
-#pragma unroll
-        for (int s = 0; s < kMaxK; ++s)
-          if (s < d.nslots) tot[s] = __reduce_add_sync(kFull, cnt[s]);
-        pass = 0;
-        for (int u = 0; u < d.k; ++u) {
-          if (!((vneed >> u) & 1u)) continue;
-          bool ok = true;
-          for (int r = 0; r < d.nreq[u]; ++r) {
-            const int slot = d.req_slot[u][r];
-            int32_t c = 0;
-#pragma unroll
-            for (int s = 0; s < kMaxK; ++s) c = (s == slot) ? tot[s] : c;
-            ok = ok && c >= d.req_cnt[u][r];
-          }
-          if (ok) pass |= 1u << u;
-        }
-        if (pass == vneed) break;  // warp-uniform: tot is the same in every lane
-      }
-      if (lane == src) result |= pass;
-    }
-#pragma unroll
-    for (int u = 0; u < kMaxK; ++u) {
-      if (u < d.k) {
-        const uint32_t word = __ballot_sync(kFull, (result >> u) & 1u);
-        if (lane == u) {
-          bitmaps[(int64_t)u * d.n_words + grp] = word;
-          my_size += __popc(word);
-        }
-      }
-    }
-  }
-  if (lane < d.k && my_size) atomicAdd(sizes + lane, my_size);
+  filter_warps(g, d, bitmaps, sizes, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+               ((int64_t)gridDim.x * blockDim.x) >> 5);
 }
 
 // ------------------------------------------------------------ scans

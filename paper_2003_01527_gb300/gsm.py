@@ -46,8 +46,10 @@ EXPORTED = [
     "gsm_default_options", "gsm_create", "gsm_destroy", "gsm_last_error", "gsm_status_string",
     "gsm_load_graph", "gsm_query_create", "gsm_query_destroy", "gsm_query_restrict", "gsm_count",
     "gsm_enumerate", "gsm_last_rows", "gsm_candidates", "gsm_plan_order", "gsm_kernel_stats",
-    "gsm_last_run_stats", "gsm_candidates_static",
+    "gsm_last_run_stats", "gsm_candidates_static", "gsm_run_batch", "gsm_batch_get_stats",
+    "gsm_batch_configure",
 ]
+GSM_BATCH_AUTOTUNE = 1
 GSM_STATIC_SCRATCH_BITMAP_BYTES = 8 << 20
 
 _alloc_fn = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -66,6 +68,14 @@ class gsm_kernel_stat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint64),
                 ("total_ms", ctypes.c_double), ("algo_bytes", ctypes.c_double),
                 ("items", ctypes.c_uint64)]
+
+
+class gsm_batch_stats(ctypes.Structure):
+    _fields_ = [("block_size", ctypes.c_int32), ("grid", ctypes.c_int32),
+                ("tuned", ctypes.c_int32), ("overflowed", ctypes.c_int32),
+                ("batches", ctypes.c_uint64), ("graph_launches", ctypes.c_uint64),
+                ("graphs_built", ctypes.c_uint64), ("fallbacks", ctypes.c_uint64),
+                ("kernels_per_graph", ctypes.c_uint64), ("last_ms", ctypes.c_double)]
 
 
 class gsm_run_stats(ctypes.Structure):
@@ -97,6 +107,9 @@ def _load():
         "gsm_candidates": (i32, [vp, vp, vp, vp]),
         "gsm_plan_order": (i32, [i32, i32, vp, vp, vp, vp]),
         "gsm_candidates_static": (i32, [i32, i64, vp, vp, vp, vp, vp, vp, i32, vp]),
+        "gsm_run_batch": (i32, [vp, vp, i32, vp, i32]),
+        "gsm_batch_get_stats": (i32, [vp, ctypes.POINTER(gsm_batch_stats)]),
+        "gsm_batch_configure": (i32, [vp, u64, u64, u64]),
         "gsm_kernel_stats": (i32, [vp, ctypes.POINTER(gsm_kernel_stat), i32,
                                    ctypes.POINTER(i32), i32]),
         "gsm_last_run_stats": (i32, [vp, ctypes.POINTER(gsm_run_stats)]),
@@ -217,6 +230,25 @@ def gsm_candidates_static(n: int, nnz: int, row_ptr, col, labels, q: int, bitmap
                                     int(getattr(stream, "cuda_stream", stream or 0)))
     if st != GSM_OK:
         raise GsmError(st, "gsm_candidates_static")
+
+
+def gsm_run_batch(ctx: int, queries, flags: int = 0) -> np.ndarray:
+    """queries: sequence of gsm_query handles; returns uint64 counts."""
+    nq = len(queries)
+    arr = (ctypes.c_void_p * max(nq, 1))(*queries)
+    counts = np.zeros(max(nq, 1), dtype=np.uint64)
+    _check(ctx, _lib.gsm_run_batch(ctx, arr, nq, _ptr(counts), flags))
+    return counts[:nq]
+
+
+def gsm_batch_get_stats(ctx: int) -> dict:
+    s = gsm_batch_stats()
+    _check(ctx, _lib.gsm_batch_get_stats(ctx, ctypes.byref(s)))
+    return {name: getattr(s, name) for name, _ in gsm_batch_stats._fields_}
+
+
+def gsm_batch_configure(ctx: int, cap_rows: int = 0, cap_elems: int = 0, cap_items: int = 0):
+    _check(ctx, _lib.gsm_batch_configure(ctx, cap_rows, cap_elems, cap_items))
 
 
 def gsm_plan_order(k: int, edges, cand_sizes=None) -> tuple[np.ndarray, np.ndarray]:
@@ -373,6 +405,14 @@ class Matcher:
         sizes = np.zeros(q.k, dtype=np.uint64)
         gsm_candidates(self.ctx, q.handle, bm, sizes)
         return bm[:, :nw], sizes
+
+    def run_batch(self, queries, autotune: bool = False) -> list[int]:
+        """Counts of every Query in `queries`, computed as one batch."""
+        flags = GSM_BATCH_AUTOTUNE if autotune else 0
+        return [int(c) for c in gsm_run_batch(self.ctx, [q.handle for q in queries], flags)]
+
+    def batch_stats(self) -> dict:
+        return gsm_batch_get_stats(self.ctx)
 
     def kernel_stats(self, reset: bool = False):
         return gsm_kernel_stats(self.ctx, reset)

@@ -108,7 +108,7 @@ def main(which):
         g, qs = inputs.rmat_labelled_workload(scale=18, num_labels=16, zipf_s=1.2,
                                               num_queries=256, kmin=3, kmax=10,
                                               non_tree=(2, 4), seed=4)
-        make("rmat18_batched_slices", g, qs, cap=1 << 18, budget=1 << 26,
+        make("rmat18_batched_slices", g, qs, cap=1 << 18, budget=1 << 25,
              meta={"generator": "inputs.rmat_labelled_workload(scale=18, num_labels=16, "
                                 "zipf_s=1.2, num_queries=256, kmin=3, kmax=10, "
                                 "non_tree=(2, 4), seed=4)"})
