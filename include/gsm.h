@@ -213,6 +213,45 @@ gsm_status gsm_batch_get_stats(gsm_ctx *ctx, gsm_batch_stats *out);
 gsm_status gsm_batch_configure(gsm_ctx *ctx, uint64_t cap_rows, uint64_t cap_elems,
                                uint64_t cap_items);
 
+/* ---- Served form: a request loop with continuous batching ----
+ *
+ * gsm_server_start starts a thread that owns the context until
+ * gsm_server_stop: meanwhile only gsm_submit, gsm_poll and gsm_server_stop may
+ * be called on the context (from any threads).  Submitted queries wait in
+ * arrival order; whenever one of `lanes` batch lanes (a stream with its own
+ * batch workspace) is free, the waiting queries are admitted into a new batch
+ * while the sum of their estimated peak frontier sizes (from label/degree
+ * histograms, Sec. 3.2's P_f) stays within half a lane's frontier capacity --
+ * at least one query per batch, at most max_batch.  Queries that arrive while
+ * batches run are admitted as soon as a lane frees, so their work overlaps the
+ * running batches on the device.  A batch that overflows its workspace is
+ * recounted query by query.  Every result equals gsm_count's for that query.
+ */
+typedef struct gsm_result {
+  uint64_t count;
+  gsm_status status;     /* GSM_OK or the error that ended the query */
+  int64_t t_submit_ns;   /* steady-clock timestamps (same clock for all) */
+  int64_t t_admit_ns;
+  int64_t t_done_ns;
+} gsm_result;
+
+/* lanes 1..8, max_batch 1..65535.  Errors: GSM_ERR_INVALID_ARG (also if a
+ * server already runs), GSM_ERR_NO_GRAPH, GSM_ERR_CUDA. */
+gsm_status gsm_server_start(gsm_ctx *ctx, int32_t lanes, int32_t max_batch);
+
+/* Queues q; *ticket identifies it.  q must stay alive until its result has
+ * been polled.  Thread-safe.  Errors: GSM_ERR_INVALID_ARG (no server). */
+gsm_status gsm_submit(gsm_ctx *ctx, const gsm_query *q, uint64_t *ticket);
+
+/* GSM_PENDING while the query waits or runs; once done, fills *out, forgets
+ * the ticket and returns GSM_OK (out->status holds the query's own status).
+ * Thread-safe.  Errors: GSM_ERR_INVALID_ARG (unknown ticket, no server). */
+gsm_status gsm_poll(gsm_ctx *ctx, uint64_t ticket, gsm_result *out);
+
+/* Finishes every submitted query, stops the thread and frees the lanes
+ * (results not yet polled are dropped). */
+gsm_status gsm_server_stop(gsm_ctx *ctx);
+
 /* Size of the fixed device array behind gsm_candidates_static: bitmap words of
  * one call, k * ceil(n/32) * 4 bytes, must fit in it (e.g. n <= 4,194,304 at
  * k = 16).  A further 256 bytes hold the counters. */

@@ -11,8 +11,14 @@
 #include <vector>
 
 #include <chrono>
+#include <condition_variable>
+#include <deque>
 #include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
 #include <tuple>
+#include <unordered_map>
 
 #include "batch.h"
 #include "gsm.h"
@@ -100,13 +106,16 @@ struct gsm_ctx {
   int32_t num_sms = 0;
 
   // batched form: per-label sorted degrees (order estimates without the
-  // filter's results), a fixed-capacity workspace, captured graphs
+  // filter's results); lanes = stream + fixed-capacity workspace + graphs
   std::vector<std::vector<int32_t>> deg_by_label;
   int64_t batch_caps[3] = {0, 0, 0};  // rows, elements, candidates (0 = default)
-  struct BatchWs {
+  struct BatchLane {
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
     bool ready = false;
     int64_t cap_rows = 0, cap_elems = 0, cap_items = 0;
-    int32_t max_nq = 0, max_words_total = 0;
+    int32_t max_nq = 0;
+    int64_t max_words_total = 0;
     std::vector<std::pair<void *, size_t>> allocs;
     gsm::BatchArgs a{};
     void *bitmaps = nullptr;
@@ -115,9 +124,19 @@ struct gsm_ctx {
     BatchQuery *h_qs = nullptr;
     uint32_t **h_bm = nullptr;
     unsigned long long *h_counts = nullptr;
-  } bw;
-  std::map<std::tuple<int32_t, int32_t, int32_t, int32_t, int32_t>, cudaGraphExec_t> graphs;
+    int32_t *h_overflow = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_done = nullptr;
+    std::map<std::tuple<int32_t, int32_t, int32_t, int32_t, int32_t>, cudaGraphExec_t> graphs;
+    // a batch in flight (server): which requests, how many queries
+    std::vector<uint64_t> tickets;
+    std::vector<int32_t> sel;
+    int32_t m = 0;
+    bool busy = false;
+  };
+  BatchLane lane0;  // gsm_run_batch, on the context's stream
   std::map<std::pair<int32_t, int32_t>, std::pair<int32_t, int32_t>> tuned;  // bucket -> (block, grid)
+  struct Server;
+  Server *server = nullptr;
   gsm_batch_stats bstats{};
 
   // stats
@@ -826,13 +845,10 @@ gsm_status guarded(gsm_ctx *ctx, F &&f) {
   }
 }
 
-void clear_graphs(gsm_ctx *ctx) {
-  for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
-  ctx->graphs.clear();
-}
+void clear_all_graphs(gsm_ctx *ctx);
 
 void free_graph(gsm_ctx *ctx) {
-  clear_graphs(ctx);
+  clear_all_graphs(ctx);
   if (ctx->d_rp) dev_free(ctx, ctx->d_rp, sizeof(int32_t) * (ctx->n + 1));
   if (ctx->d_col) dev_free(ctx, ctx->d_col, sizeof(int32_t) * std::max<int64_t>(ctx->nnz, 1));
   if (ctx->d_lab) dev_free(ctx, ctx->d_lab, sizeof(int32_t) * std::max<int32_t>(ctx->n, 1));
@@ -847,105 +863,123 @@ void free_graph(gsm_ctx *ctx) {
 
 namespace {
 
+using Lane = gsm_ctx::BatchLane;
+
 constexpr int64_t kBatchCapRows = int64_t(1) << 24;
 constexpr int64_t kBatchCapElems = int64_t(1) << 27;
 constexpr int64_t kBatchCapItems = int64_t(1) << 28;
 
 template <typename T>
-T *bw_alloc(gsm_ctx *ctx, int64_t elems) {
+T *lane_alloc(gsm_ctx *ctx, Lane &L, int64_t elems) {
   const size_t bytes = sizeof(T) * (size_t)std::max<int64_t>(elems, 1);
   void *p = dev_alloc(ctx, bytes);
-  ctx->bw.allocs.push_back({p, bytes});
+  L.allocs.push_back({p, bytes});
   return (T *)p;
 }
 
-void bw_free_one(gsm_ctx *ctx, void *p) {
-  for (auto it = ctx->bw.allocs.begin(); it != ctx->bw.allocs.end(); ++it)
+void lane_free_one(gsm_ctx *ctx, Lane &L, const void *p) {
+  for (auto it = L.allocs.begin(); it != L.allocs.end(); ++it)
     if (it->first == p) {
       dev_free(ctx, it->first, it->second);
-      ctx->bw.allocs.erase(it);
+      L.allocs.erase(it);
       return;
     }
 }
 
-// Fixed-capacity buffers (once), per-query arrays (grown with the batch).
-void batch_workspace(gsm_ctx *ctx, int32_t nq, int64_t words_total) {
-  auto &W = ctx->bw;
-  BatchArgs &a = W.a;
-  if (!W.ready) {
-    W.cap_rows = ctx->batch_caps[0] ? ctx->batch_caps[0] : kBatchCapRows;
-    W.cap_elems = ctx->batch_caps[1] ? ctx->batch_caps[1] : kBatchCapElems;
-    W.cap_items = ctx->batch_caps[2] ? ctx->batch_caps[2] : kBatchCapItems;
-    a.cap_rows = W.cap_rows;
-    a.cap_elems = W.cap_elems;
-    a.cap_items = W.cap_items;
-    for (int j = 0; j < 2; ++j) {
-      a.F[j] = bw_alloc<int32_t>(ctx, W.cap_elems);
-      a.rseg[j] = bw_alloc<int32_t>(ctx, W.cap_rows);
-    }
-    a.pstart = bw_alloc<int32_t>(ctx, W.cap_rows);
-    a.pslot = bw_alloc<uint8_t>(ctx, W.cap_rows);
-    a.woff = bw_alloc<int64_t>(ctx, W.cap_rows + 1);
-    const int64_t tiles = W.cap_items / 128 + 3;
-    a.tile_row = bw_alloc<int32_t>(ctx, tiles);
-    a.tile_cnt = bw_alloc<int32_t>(ctx, tiles);
-    a.tile_off = bw_alloc<int64_t>(ctx, tiles);
-    a.masks = bw_alloc<uint32_t>(ctx, W.cap_items / 32 + 256);  // + one tile of the largest block
-    a.state = bw_alloc<BatchStep>(ctx, kMaxK + 1);
-    a.overflow = bw_alloc<int32_t>(ctx, 1);
-    a.partials = bw_alloc<int64_t>(ctx, (int64_t)ctx->num_sms * 32 + 1);
-    W.ready = true;
-  }
-  bool moved = false;
-  if (nq > W.max_nq) {
-    if (W.max_nq) {
-      bw_free_one(ctx, (void *)a.fds);
-      bw_free_one(ctx, (void *)a.bm_out);
-      bw_free_one(ctx, (void *)a.qs);
-      bw_free_one(ctx, a.counts);
-      bw_free_one(ctx, a.sizes);
-      cudaFreeHost(W.h_fds);
-      cudaFreeHost(W.h_qs);
-      cudaFreeHost(W.h_bm);
-      cudaFreeHost(W.h_counts);
-    }
-    const int32_t cap = std::max(nq, 2 * W.max_nq);
-    a.fds = bw_alloc<FilterDesc>(ctx, cap);
-    a.bm_out = bw_alloc<uint32_t *>(ctx, cap);
-    a.qs = bw_alloc<BatchQuery>(ctx, cap);
-    a.counts = bw_alloc<unsigned long long>(ctx, cap);
-    a.sizes = bw_alloc<unsigned long long>(ctx, (int64_t)cap * kMaxK);
-    CU(cudaMallocHost(&W.h_fds, sizeof(FilterDesc) * cap));
-    CU(cudaMallocHost(&W.h_qs, sizeof(BatchQuery) * cap));
-    CU(cudaMallocHost(&W.h_bm, sizeof(uint32_t *) * cap));
-    CU(cudaMallocHost(&W.h_counts, sizeof(unsigned long long) * cap));
-    W.max_nq = cap;
-    moved = true;
-  }
-  if (words_total > W.max_words_total) {
-    if (W.max_words_total) {
-      bw_free_one(ctx, a.wcnt);
-      bw_free_one(ctx, a.woffs);
-    }
-    const int64_t cap = std::max<int64_t>(words_total, 2 * (int64_t)W.max_words_total);
-    a.wcnt = bw_alloc<int32_t>(ctx, cap);
-    a.woffs = bw_alloc<int64_t>(ctx, cap + 1);
-    W.max_words_total = (int32_t)std::min<int64_t>(cap, 0x7fffffff);
-    moved = true;
-  }
-  if (moved) clear_graphs(ctx);  // captured graphs hold the old pointers
+void lane_clear_graphs(Lane &L) {
+  for (auto &kv : L.graphs) cudaGraphExecDestroy(kv.second);
+  L.graphs.clear();
 }
 
-void batch_free(gsm_ctx *ctx) {
-  clear_graphs(ctx);
-  for (auto &pa : ctx->bw.allocs) dev_free(ctx, pa.first, pa.second);
-  ctx->bw.allocs.clear();
-  if (ctx->bw.h_fds) cudaFreeHost(ctx->bw.h_fds);
-  if (ctx->bw.h_qs) cudaFreeHost(ctx->bw.h_qs);
-  if (ctx->bw.h_bm) cudaFreeHost(ctx->bw.h_bm);
-  if (ctx->bw.h_counts) cudaFreeHost(ctx->bw.h_counts);
-  if (ctx->bw.bitmaps) dev_free(ctx, ctx->bw.bitmaps, ctx->bw.bitmaps_cap);
-  ctx->bw = gsm_ctx::BatchWs();
+// Releases a lane's device memory, pinned buffers and graphs (not its stream).
+void lane_release(gsm_ctx *ctx, Lane &L) {
+  lane_clear_graphs(L);
+  for (auto &pa : L.allocs) dev_free(ctx, pa.first, pa.second);
+  L.allocs.clear();
+  if (L.h_fds) cudaFreeHost(L.h_fds);
+  if (L.h_qs) cudaFreeHost(L.h_qs);
+  if (L.h_bm) cudaFreeHost(L.h_bm);
+  if (L.h_counts) cudaFreeHost(L.h_counts);
+  if (L.h_overflow) cudaFreeHost(L.h_overflow);
+  if (L.bitmaps) dev_free(ctx, L.bitmaps, L.bitmaps_cap);
+  for (cudaEvent_t e : {L.ev0, L.ev1, L.ev_done})
+    if (e) cudaEventDestroy(e);
+  cudaStream_t st = L.stream;
+  const bool own = L.own_stream;
+  L = Lane();
+  L.stream = st;
+  L.own_stream = own;
+}
+
+// Fixed-capacity buffers (once), per-query arrays (grown with the batch).
+void lane_workspace(gsm_ctx *ctx, Lane &L, int32_t nq, int64_t words_total) {
+  BatchArgs &a = L.a;
+  if (!L.ready) {
+    L.cap_rows = ctx->batch_caps[0] ? ctx->batch_caps[0] : kBatchCapRows;
+    L.cap_elems = ctx->batch_caps[1] ? ctx->batch_caps[1] : kBatchCapElems;
+    L.cap_items = ctx->batch_caps[2] ? ctx->batch_caps[2] : kBatchCapItems;
+    a.cap_rows = L.cap_rows;
+    a.cap_elems = L.cap_elems;
+    a.cap_items = L.cap_items;
+    for (int j = 0; j < 2; ++j) {
+      a.F[j] = lane_alloc<int32_t>(ctx, L, L.cap_elems);
+      a.rseg[j] = lane_alloc<int32_t>(ctx, L, L.cap_rows);
+    }
+    a.pstart = lane_alloc<int32_t>(ctx, L, L.cap_rows);
+    a.pslot = lane_alloc<uint8_t>(ctx, L, L.cap_rows);
+    a.woff = lane_alloc<int64_t>(ctx, L, L.cap_rows + 1);
+    const int64_t tiles = L.cap_items / 128 + 3;
+    a.tile_row = lane_alloc<int32_t>(ctx, L, tiles);
+    a.tile_cnt = lane_alloc<int32_t>(ctx, L, tiles);
+    a.tile_off = lane_alloc<int64_t>(ctx, L, tiles);
+    a.masks = lane_alloc<uint32_t>(ctx, L, L.cap_items / 32 + 256);  // + a tile of the largest block
+    a.state = lane_alloc<BatchStep>(ctx, L, kMaxK + 1);
+    a.overflow = lane_alloc<int32_t>(ctx, L, 1);
+    a.partials = lane_alloc<int64_t>(ctx, L, (int64_t)ctx->num_sms * 32 + 1);
+    CU(cudaMallocHost(&L.h_overflow, sizeof(int32_t)));
+    CU(cudaEventCreate(&L.ev0));
+    CU(cudaEventCreate(&L.ev1));
+    CU(cudaEventCreateWithFlags(&L.ev_done, cudaEventDisableTiming));
+    L.ready = true;
+  }
+  bool moved = false;
+  if (nq > L.max_nq) {
+    if (L.max_nq) {
+      lane_free_one(ctx, L, a.fds);
+      lane_free_one(ctx, L, a.bm_out);
+      lane_free_one(ctx, L, a.qs);
+      lane_free_one(ctx, L, a.counts);
+      lane_free_one(ctx, L, a.sizes);
+      cudaFreeHost(L.h_fds);
+      cudaFreeHost(L.h_qs);
+      cudaFreeHost(L.h_bm);
+      cudaFreeHost(L.h_counts);
+    }
+    const int32_t cap = std::max(nq, 2 * L.max_nq);
+    a.fds = lane_alloc<FilterDesc>(ctx, L, cap);
+    a.bm_out = lane_alloc<uint32_t *>(ctx, L, cap);
+    a.qs = lane_alloc<BatchQuery>(ctx, L, cap);
+    a.counts = lane_alloc<unsigned long long>(ctx, L, cap);
+    a.sizes = lane_alloc<unsigned long long>(ctx, L, (int64_t)cap * kMaxK);
+    CU(cudaMallocHost(&L.h_fds, sizeof(FilterDesc) * cap));
+    CU(cudaMallocHost(&L.h_qs, sizeof(BatchQuery) * cap));
+    CU(cudaMallocHost(&L.h_bm, sizeof(uint32_t *) * cap));
+    CU(cudaMallocHost(&L.h_counts, sizeof(unsigned long long) * cap));
+    L.max_nq = cap;
+    moved = true;
+  }
+  if (words_total > L.max_words_total) {
+    if (L.max_words_total) {
+      lane_free_one(ctx, L, a.wcnt);
+      lane_free_one(ctx, L, a.woffs);
+    }
+    const int64_t cap = std::max<int64_t>(words_total, 2 * L.max_words_total);
+    a.wcnt = lane_alloc<int32_t>(ctx, L, cap);
+    a.woffs = lane_alloc<int64_t>(ctx, L, cap + 1);
+    L.max_words_total = cap;
+    moved = true;
+  }
+  if (moved) lane_clear_graphs(L);  // captured graphs hold the old pointers
 }
 
 // Estimated |C(u)|: vertices with u's label and at least u's degree (the
@@ -963,12 +997,36 @@ uint64_t estimate_candidates(gsm_ctx *ctx, const gsm_query *q, int32_t u, int32_
   return c;
 }
 
-cudaGraphExec_t batch_graph(gsm_ctx *ctx, int32_t m, int32_t kmax, int32_t n_words,
-                            int32_t block, int32_t grid) {
+// Plans q with the histogram estimates; returns the largest estimated
+// frontier (rows) over its levels: est_1 = |C(pi_0)|, and each level
+// multiplies by the mean degree, the fraction of vertices in C(pi_i), and
+// (mean degree / n) per non-tree edge.
+double plan_estimated(gsm_ctx *ctx, const gsm_query *q, const int32_t *dense, int32_t *order) {
+  uint64_t est[kMaxK];
+  for (int32_t u = 0; u < q->k; ++u) est[u] = estimate_candidates(ctx, q, u, dense[u]);
+  int32_t parent[kMaxK];
+  plan(q->k, q->adj, est, order, parent);
+  const double n = std::max<double>(1.0, ctx->n);
+  const double dbar = ctx->nnz / n;
+  double rows = (double)est[order[0]], peak = rows;
+  uint32_t placed = 1u << order[0];
+  for (int32_t i = 1; i < q->k; ++i) {
+    const int32_t u = order[i];
+    const int nb = popc(q->adj[u] & placed);
+    rows *= dbar * ((double)est[u] / n);
+    for (int j = 1; j < nb; ++j) rows *= dbar / n;
+    peak = std::max(peak, rows);
+    placed |= 1u << u;
+  }
+  return peak;
+}
+
+cudaGraphExec_t lane_graph(gsm_ctx *ctx, Lane &L, int32_t m, int32_t kmax, int32_t n_words,
+                           int32_t block, int32_t grid) {
   const auto key = std::make_tuple(m, kmax, n_words, block, grid);
-  auto it = ctx->graphs.find(key);
-  if (it != ctx->graphs.end()) return it->second;
-  BatchArgs a = ctx->bw.a;
+  auto it = L.graphs.find(key);
+  if (it != L.graphs.end()) return it->second;
+  BatchArgs a = L.a;
   a.nq = m;
   a.kmax = kmax;
   a.n_words = n_words;
@@ -976,9 +1034,9 @@ cudaGraphExec_t batch_graph(gsm_ctx *ctx, int32_t m, int32_t kmax, int32_t n_wor
   a.grid = grid;
   GraphDev g{ctx->n, ctx->nnz, ctx->d_rp, ctx->d_col, ctx->d_lab};
   cudaGraph_t graph = nullptr;
-  CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-  const int launches = batch_enqueue(g, a, ctx->stream);
-  cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+  CU(cudaStreamBeginCapture(L.stream, cudaStreamCaptureModeThreadLocal));
+  const int launches = batch_enqueue(g, a, L.stream);
+  cudaError_t e = cudaStreamEndCapture(L.stream, &graph);
   if (e != cudaSuccess) {
     set_err(ctx, "capturing the batch graph failed: %s", cudaGetErrorString(e));
     throw Fail{GSM_ERR_CUDA};
@@ -990,153 +1048,332 @@ cudaGraphExec_t batch_graph(gsm_ctx *ctx, int32_t m, int32_t kmax, int32_t n_wor
     set_err(ctx, "instantiating the batch graph failed: %s", cudaGetErrorString(e));
     throw Fail{GSM_ERR_CUDA};
   }
-  ctx->graphs[key] = exec;
+  L.graphs[key] = exec;
   ctx->bstats.graphs_built += 1;
   ctx->bstats.kernels_per_graph = (uint64_t)launches;
   return exec;
 }
 
-// Launches the batch graph; returns the overflow flag (counts land in
-// ctx->bw.h_counts).
-bool batch_launch(gsm_ctx *ctx, int32_t m, int32_t kmax, int32_t n_words, int32_t block,
-                  int32_t grid, float *ms) {
-  cudaGraphExec_t exec = batch_graph(ctx, m, kmax, n_words, block, grid);
-  cudaEvent_t e0 = get_event(ctx), e1 = get_event(ctx);
-  CU(cudaEventRecord(e0, ctx->stream));
-  CU(cudaGraphLaunch(exec, ctx->stream));
-  CU(cudaEventRecord(e1, ctx->stream));
-  CU(cudaMemcpyAsync(ctx->bw.h_counts, ctx->bw.a.counts, sizeof(unsigned long long) * m,
-                     cudaMemcpyDeviceToHost, ctx->stream));
-  CU(cudaMemcpyAsync(ctx->h_stage, ctx->bw.a.overflow, sizeof(int32_t), cudaMemcpyDeviceToHost,
-                     ctx->stream));
-  CU(cudaStreamSynchronize(ctx->stream));
-  CU(cudaEventElapsedTime(ms, e0, e1));
-  ctx->event_pool.push_back(e0);
-  ctx->event_pool.push_back(e1);
+// Host part of a batch: labels, filter descriptions, orders, level
+// descriptions, uploaded (asynchronously) to the lane.  L.sel = indices of
+// the queries that can match (a label absent from G means 0).  Returns the
+// largest query size.
+int32_t lane_prepare(gsm_ctx *ctx, Lane &L, const gsm_query *const *qs, int32_t nq) {
+  const int32_t n_words = (ctx->n + 31) / 32;
+  L.sel.clear();
+  std::vector<std::array<int32_t, kMaxK>> dense_of;
+  int64_t total_k = 0;
+  for (int32_t j = 0; j < nq; ++j) {
+    std::array<int32_t, kMaxK> dn{};
+    if (!dense_labels(ctx, qs[j], dn.data())) continue;
+    L.sel.push_back(j);
+    dense_of.push_back(dn);
+    total_k += qs[j]->k;
+  }
+  L.m = (int32_t)L.sel.size();
+  if (L.m == 0) return 0;
+  const size_t bm_bytes = (size_t)total_k * n_words * sizeof(uint32_t);
+  if (L.bitmaps_cap < bm_bytes) {
+    lane_clear_graphs(L);
+    CU(cudaStreamSynchronize(L.stream));
+    ensure_buf(ctx, &L.bitmaps, &L.bitmaps_cap, bm_bytes, false, 0);
+  }
+  lane_workspace(ctx, L, L.m, (int64_t)L.m * n_words);
+  uint32_t *bm = (uint32_t *)L.bitmaps;
+  int32_t kmax = 1;
+  int64_t off = 0;
+  for (int32_t t = 0; t < L.m; ++t) {
+    const gsm_query *q = qs[L.sel[t]];
+    const int32_t *dense = dense_of[t].data();
+    fill_filter(ctx, q, dense, L.h_fds[t]);
+    int32_t order[kMaxK];
+    plan_estimated(ctx, q, dense, order);
+    uint32_t *base = bm + off;
+    off += (int64_t)q->k * n_words;
+    L.h_bm[t] = base;
+    BatchQuery &bq = L.h_qs[t];
+    std::memset(&bq, 0, sizeof(bq));
+    bq.k = q->k;
+    bq.root_bitmap = base + (size_t)order[0] * n_words;
+    for (int32_t i = 1; i < q->k; ++i) {
+      BatchLevel &lv = bq.lv[i];
+      const int32_t u = order[i];
+      for (int32_t j = 0; j < i; ++j) {
+        const int32_t uj = order[j];
+        if (q->adj[u] >> uj & 1u)
+          lv.bpos[lv.nb++] = j;
+        else if (dense[uj] == dense[u])
+          lv.inj[lv.ninj++] = j;
+      }
+      lv.last = i == q->k - 1;
+      lv.bitmap = base + (size_t)u * n_words;
+    }
+    kmax = std::max(kmax, q->k);
+  }
+  CU(cudaMemcpyAsync((void *)L.a.fds, L.h_fds, sizeof(FilterDesc) * L.m, cudaMemcpyHostToDevice,
+                     L.stream));
+  CU(cudaMemcpyAsync((void *)L.a.bm_out, L.h_bm, sizeof(uint32_t *) * L.m,
+                     cudaMemcpyHostToDevice, L.stream));
+  CU(cudaMemcpyAsync((void *)L.a.qs, L.h_qs, sizeof(BatchQuery) * L.m, cudaMemcpyHostToDevice,
+                     L.stream));
+  return kmax;
+}
+
+// Issues the prepared batch: graph launch, then the counts and the overflow
+// flag back to pinned memory, then ev_done (all asynchronous).
+void lane_issue(gsm_ctx *ctx, Lane &L, int32_t kmax, int32_t block, int32_t grid) {
+  const int32_t n_words = (ctx->n + 31) / 32;
+  cudaGraphExec_t exec = lane_graph(ctx, L, L.m, kmax, n_words, block, grid);
+  CU(cudaEventRecord(L.ev0, L.stream));
+  CU(cudaGraphLaunch(exec, L.stream));
+  CU(cudaEventRecord(L.ev1, L.stream));
+  CU(cudaMemcpyAsync(L.h_counts, L.a.counts, sizeof(unsigned long long) * L.m,
+                     cudaMemcpyDeviceToHost, L.stream));
+  CU(cudaMemcpyAsync(L.h_overflow, L.a.overflow, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                     L.stream));
+  CU(cudaEventRecord(L.ev_done, L.stream));
   ctx->bstats.graph_launches += 1;
-  int32_t of = 0;
-  std::memcpy(&of, ctx->h_stage, sizeof(int32_t));
-  return of != 0;
+  ctx->bstats.block_size = block;
+  ctx->bstats.grid = grid;
+}
+
+// Waits for the issued batch; returns the overflow flag, *ms = graph time.
+bool lane_wait(gsm_ctx *ctx, Lane &L, float *ms) {
+  CU(cudaEventSynchronize(L.ev_done));
+  if (ms) CU(cudaEventElapsedTime(ms, L.ev0, L.ev1));
+  return *L.h_overflow != 0;
+}
+
+std::pair<int32_t, int32_t> batch_config(gsm_ctx *ctx, int32_t m, int32_t kmax, bool *tuned) {
+  int32_t mb = 1;
+  while (mb < m) mb <<= 1;
+  auto it = ctx->tuned.find({mb, kmax});
+  *tuned = it != ctx->tuned.end();
+  if (*tuned) return it->second;
+  return {256, ctx->num_sms * 4};
 }
 
 void run_batch(gsm_ctx *ctx, const gsm_query *const *qs, int32_t nq, uint64_t *counts,
                int32_t flags) {
   if (!ctx->has_graph) FAIL(GSM_ERR_NO_GRAPH, "no data graph loaded");
   const auto t0 = std::chrono::steady_clock::now();
-  const int32_t n_words = (ctx->n + 31) / 32;
-  std::vector<int32_t> sel;
-  std::vector<std::array<int32_t, kMaxK>> dense_of;
-  int64_t total_k = 0;
-  for (int32_t j = 0; j < nq; ++j) {
-    counts[j] = 0;
-    std::array<int32_t, kMaxK> dn{};
-    if (!dense_labels(ctx, qs[j], dn.data())) continue;  // a label absent from G
-    sel.push_back(j);
-    dense_of.push_back(dn);
-    total_k += qs[j]->k;
-  }
-  const int32_t m = (int32_t)sel.size();
+  Lane &L = ctx->lane0;
+  L.stream = ctx->stream;
+  for (int32_t j = 0; j < nq; ++j) counts[j] = 0;
   ctx->bstats.batches += 1;
   ctx->bstats.overflowed = 0;
-  if (m == 0) return;
-  const size_t bm_bytes = (size_t)total_k * n_words * sizeof(uint32_t);
-  if (ctx->bw.bitmaps_cap < bm_bytes) {
-    clear_graphs(ctx);
-    ensure_buf(ctx, &ctx->bw.bitmaps, &ctx->bw.bitmaps_cap, bm_bytes, false, 0);
-  }
-  batch_workspace(ctx, m, (int64_t)m * n_words);
-  auto &W = ctx->bw;
-  uint32_t *bm = (uint32_t *)W.bitmaps;
-  int32_t kmax = 1;
-  int64_t off = 0;
-  for (int32_t t = 0; t < m; ++t) {
-    const gsm_query *q = qs[sel[t]];
-    const int32_t *dense = dense_of[t].data();
-    fill_filter(ctx, q, dense, W.h_fds[t]);
-    uint64_t est[kMaxK];
-    for (int32_t u = 0; u < q->k; ++u) est[u] = estimate_candidates(ctx, q, u, dense[u]);
-    int32_t order[kMaxK], parent[kMaxK];
-    plan(q->k, q->adj, est, order, parent);
-    uint32_t *base = bm + off;
-    off += (int64_t)q->k * n_words;
-    W.h_bm[t] = base;
-    BatchQuery &bq = W.h_qs[t];
-    std::memset(&bq, 0, sizeof(bq));
-    bq.k = q->k;
-    bq.root_bitmap = base + (size_t)order[0] * n_words;
-    for (int32_t i = 1; i < q->k; ++i) {
-      BatchLevel &L = bq.lv[i];
-      const int32_t u = order[i];
-      for (int32_t j = 0; j < i; ++j) {
-        const int32_t uj = order[j];
-        if (q->adj[u] >> uj & 1u)
-          L.bpos[L.nb++] = j;
-        else if (dense[uj] == dense[u])
-          L.inj[L.ninj++] = j;
-      }
-      L.last = i == q->k - 1;
-      L.bitmap = base + (size_t)u * n_words;
-    }
-    kmax = std::max(kmax, q->k);
-  }
-  CU(cudaMemcpyAsync((void *)W.a.fds, W.h_fds, sizeof(FilterDesc) * m, cudaMemcpyHostToDevice,
-                     ctx->stream));
-  CU(cudaMemcpyAsync((void *)W.a.bm_out, W.h_bm, sizeof(uint32_t *) * m, cudaMemcpyHostToDevice,
-                     ctx->stream));
-  CU(cudaMemcpyAsync((void *)W.a.qs, W.h_qs, sizeof(BatchQuery) * m, cudaMemcpyHostToDevice,
-                     ctx->stream));
-  // launch configuration: tuned for this shape, else the default
-  int32_t mb = 1;
-  while (mb < m) mb <<= 1;
-  const auto bucket = std::make_pair(mb, kmax);
-  int32_t block = 256, grid = ctx->num_sms * 4;
-  ctx->bstats.tuned = 0;
-  auto tn = ctx->tuned.find(bucket);
+  const int32_t kmax = lane_prepare(ctx, L, qs, nq);
+  if (L.m == 0) return;
+  bool tuned = false;
+  auto cfg = batch_config(ctx, L.m, kmax, &tuned);
   bool overflow = false;
   float ms = 0;
-  if (tn != ctx->tuned.end()) {
-    block = tn->second.first;
-    grid = tn->second.second;
-    ctx->bstats.tuned = 1;
-    overflow = batch_launch(ctx, m, kmax, n_words, block, grid, &ms);
-  } else if (flags & GSM_BATCH_AUTOTUNE) {
+  if (!tuned && (flags & GSM_BATCH_AUTOTUNE)) {
     const int32_t cand[][2] = {{128, 8}, {256, 4}, {256, 8}, {512, 2}, {512, 4}, {1024, 2}};
     float best = 1e30f;
     for (const auto &c : cand) {
       float t = 0;
-      overflow = batch_launch(ctx, m, kmax, n_words, c[0], ctx->num_sms * c[1], &t);
-      if (overflow) break;  // same counts for every configuration
+      lane_issue(ctx, L, kmax, c[0], ctx->num_sms * c[1]);
+      overflow = lane_wait(ctx, L, &t);
+      if (overflow) break;  // every configuration gives the same counts
       if (t < best) {
         best = t;
-        block = c[0];
-        grid = ctx->num_sms * c[1];
+        cfg = {c[0], ctx->num_sms * c[1]};
       }
     }
     ms = best;
     if (!overflow) {
-      ctx->tuned[bucket] = {block, grid};
-      ctx->bstats.tuned = 1;
+      int32_t mb = 1;
+      while (mb < L.m) mb <<= 1;
+      ctx->tuned[{mb, kmax}] = cfg;
+      tuned = true;
     }
   } else {
-    overflow = batch_launch(ctx, m, kmax, n_words, block, grid, &ms);
+    lane_issue(ctx, L, kmax, cfg.first, cfg.second);
+    overflow = lane_wait(ctx, L, &ms);
   }
-  ctx->bstats.block_size = block;
-  ctx->bstats.grid = grid;
+  ctx->bstats.tuned = tuned ? 1 : 0;
+  ctx->bstats.block_size = cfg.first;
+  ctx->bstats.grid = cfg.second;
   if (overflow) {
     // the workspace was too small for this batch: run it query by query
     ctx->bstats.overflowed = 1;
     ctx->bstats.fallbacks += 1;
-    for (int32_t t = 0; t < m; ++t) {
+    for (int32_t t = 0; t < L.m; ++t) {
       uint64_t c = 0;
       bool trunc = false;
-      run_query(ctx, qs[sel[t]], false, nullptr, 0, 0, &c, &trunc);
-      counts[sel[t]] = c;
+      run_query(ctx, qs[L.sel[t]], false, nullptr, 0, 0, &c, &trunc);
+      counts[L.sel[t]] = c;
     }
   } else {
-    for (int32_t t = 0; t < m; ++t) counts[sel[t]] = W.h_counts[t];
+    for (int32_t t = 0; t < L.m; ++t) counts[L.sel[t]] = L.h_counts[t];
   }
   ctx->bstats.last_ms =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ served form
+//
+// A request loop on a thread of its own.  Submitted queries wait in a FIFO;
+// whenever a lane (stream + batch workspace) is free, the loop admits waiting
+// queries into a new batch while their estimated peak frontiers fit half the
+// lane's frontier capacity (at least one query per batch), launches it, and
+// goes back to admitting: a request that arrives while batches are running
+// joins the next free lane, so its work overlaps theirs on the device.  A
+// lane's results are collected by polling its completion event.  A batch
+// that overflows its workspace is recounted query by query (a bad estimate
+// costs latency, not correctness).
+
+struct gsm_ctx::Server {
+  struct Req {
+    uint64_t ticket = 0;
+    const gsm_query *q = nullptr;
+    double est_rows = 0;
+    int64_t t_submit = 0, t_admit = 0, t_done = 0;
+    uint64_t count = 0;
+    gsm_status status = GSM_PENDING;
+  };
+  std::thread th;
+  std::mutex mu;
+  std::condition_variable cv;
+  bool stop = false;
+  std::deque<Req> waiting;
+  std::unordered_map<uint64_t, Req> inflight, finished;
+  uint64_t next_ticket = 1;
+  int32_t max_batch = 256;
+  std::vector<std::unique_ptr<Lane>> lanes;
+  gsm_status fatal = GSM_OK;
+};
+
+namespace {
+
+int64_t now_ns() {
+  return std::chrono::duration_cast<std::chrono::nanoseconds>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+// Completes the batch of a lane whose ev_done has fired.
+void server_complete(gsm_ctx *ctx, gsm_ctx::Server &S, Lane &L) {
+  const bool overflow = *L.h_overflow != 0;
+  std::vector<const gsm_query *> qs;
+  {
+    std::lock_guard<std::mutex> lk(S.mu);
+    for (uint64_t t : L.tickets) qs.push_back(S.inflight[t].q);
+  }
+  std::vector<uint64_t> counts(L.tickets.size(), 0);
+  gsm_status st = GSM_OK;
+  if (overflow) {
+    ctx->bstats.fallbacks += 1;
+    st = guarded(ctx, [&] {
+      for (size_t t = 0; t < qs.size(); ++t) {
+        bool trunc = false;
+        run_query(ctx, qs[t], false, nullptr, 0, 0, &counts[t], &trunc);
+      }
+    });
+  } else {
+    for (int32_t t = 0; t < L.m; ++t) counts[L.sel[t]] = L.h_counts[t];
+  }
+  const int64_t t_done = now_ns();
+  std::lock_guard<std::mutex> lk(S.mu);
+  for (size_t t = 0; t < L.tickets.size(); ++t) {
+    auto node = S.inflight.extract(L.tickets[t]);
+    node.mapped().count = counts[t];
+    node.mapped().status = st;
+    node.mapped().t_done = t_done;
+    S.finished.insert(std::move(node));
+  }
+  L.tickets.clear();
+  L.busy = false;
+}
+
+void server_loop(gsm_ctx *ctx) {
+  gsm_ctx::Server &S = *ctx->server;
+  cudaSetDevice(ctx->device);
+  for (;;) {
+    bool progressed = false;
+    // collect finished lanes
+    for (auto &lp : S.lanes) {
+      Lane &L = *lp;
+      if (L.busy && cudaEventQuery(L.ev_done) == cudaSuccess) {
+        server_complete(ctx, S, L);
+        progressed = true;
+      }
+    }
+    // admit waiting requests into free lanes
+    for (auto &lp : S.lanes) {
+      Lane &L = *lp;
+      if (L.busy) continue;
+      std::vector<const gsm_query *> qs;
+      {
+        std::lock_guard<std::mutex> lk(S.mu);
+        if (S.waiting.empty()) break;
+        const double budget = 0.5 * (double)(ctx->batch_caps[0] ? ctx->batch_caps[0]
+                                                                 : kBatchCapRows);
+        double used = 0;
+        const int64_t t_admit = now_ns();
+        while (!S.waiting.empty() && (int32_t)qs.size() < S.max_batch) {
+          gsm_ctx::Server::Req &r = S.waiting.front();
+          if (!qs.empty() && used + r.est_rows > budget) break;
+          used += r.est_rows;
+          r.t_admit = t_admit;
+          qs.push_back(r.q);
+          L.tickets.push_back(r.ticket);
+          S.inflight.emplace(r.ticket, r);
+          S.waiting.pop_front();
+        }
+      }
+      gsm_status st = guarded(ctx, [&] {
+        const int32_t kmax = lane_prepare(ctx, L, qs.data(), (int32_t)qs.size());
+        if (L.m > 0) {
+          bool tuned;
+          auto cfg = batch_config(ctx, L.m, kmax, &tuned);
+          lane_issue(ctx, L, kmax, cfg.first, cfg.second);
+        } else {
+          *L.h_overflow = 0;
+          CU(cudaEventRecord(L.ev_done, L.stream));
+        }
+        ctx->bstats.batches += 1;
+      });
+      if (st != GSM_OK) {
+        std::lock_guard<std::mutex> lk(S.mu);
+        for (uint64_t t : L.tickets) {
+          auto node = S.inflight.extract(t);
+          node.mapped().status = st;
+          node.mapped().t_done = now_ns();
+          S.finished.insert(std::move(node));
+        }
+        L.tickets.clear();
+        continue;
+      }
+      L.busy = true;
+      progressed = true;
+    }
+    std::unique_lock<std::mutex> lk(S.mu);
+    bool any_busy = false;
+    for (auto &lp : S.lanes) any_busy = any_busy || lp->busy;
+    if (S.stop && S.waiting.empty() && !any_busy) break;
+    if (!progressed) {
+      // nothing to do right now: sleep until a submission (or, with work on
+      // the device, briefly, then poll the lanes again)
+      if (any_busy)
+        S.cv.wait_for(lk, std::chrono::microseconds(20));
+      else
+        S.cv.wait(lk, [&] { return S.stop || !S.waiting.empty(); });
+    }
+  }
+}
+
+}  // namespace
+
+namespace {
+
+void clear_all_graphs(gsm_ctx *ctx) {
+  lane_clear_graphs(ctx->lane0);
+  if (ctx->server)
+    for (auto &lp : ctx->server->lanes) lane_clear_graphs(*lp);
 }
 
 }  // namespace
@@ -1225,8 +1462,9 @@ void gsm_destroy(gsm_ctx *ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->server) gsm_server_stop(ctx);
   try {
-    batch_free(ctx);
+    lane_release(ctx, ctx->lane0);
     free_graph(ctx);
     for (auto &b : ctx->blocks) dev_free(ctx, b.ptr, b.cap);
     dev_free(ctx, ctx->scratch, ctx->scratch_cap);
@@ -1468,11 +1706,98 @@ gsm_status gsm_batch_configure(gsm_ctx *ctx, uint64_t cap_rows, uint64_t cap_ele
   return guarded(ctx, [&] {
     CU(cudaSetDevice(ctx->device));
     CU(cudaStreamSynchronize(ctx->stream));
-    batch_free(ctx);
+    if (ctx->server) FAIL(GSM_ERR_INVALID_ARG, "the server is running");
+    lane_release(ctx, ctx->lane0);
     ctx->batch_caps[0] = (int64_t)cap_rows;
     ctx->batch_caps[1] = (int64_t)cap_elems;
     ctx->batch_caps[2] = (int64_t)cap_items;
   });
+}
+
+gsm_status gsm_server_start(gsm_ctx *ctx, int32_t lanes, int32_t max_batch) {
+  if (!ctx || lanes < 1 || lanes > 8 || max_batch < 1 || max_batch > 65535 || ctx->server)
+    return GSM_ERR_INVALID_ARG;
+  if (!ctx->has_graph) return GSM_ERR_NO_GRAPH;
+  auto *S = new gsm_ctx::Server();
+  S->max_batch = max_batch;
+  gsm_status st = guarded(ctx, [&] {
+    CU(cudaSetDevice(ctx->device));
+    for (int32_t j = 0; j < lanes; ++j) {
+      auto L = std::make_unique<Lane>();
+      CU(cudaStreamCreateWithFlags(&L->stream, cudaStreamNonBlocking));
+      L->own_stream = true;
+      S->lanes.push_back(std::move(L));
+    }
+  });
+  if (st != GSM_OK) {
+    for (auto &L : S->lanes)
+      if (L->stream) cudaStreamDestroy(L->stream);
+    delete S;
+    return st;
+  }
+  ctx->server = S;
+  S->th = std::thread(server_loop, ctx);
+  return GSM_OK;
+}
+
+gsm_status gsm_submit(gsm_ctx *ctx, const gsm_query *q, uint64_t *ticket) {
+  if (!ctx || !q || !ticket || !ctx->server) return GSM_ERR_INVALID_ARG;
+  gsm_ctx::Server &S = *ctx->server;
+  gsm_ctx::Server::Req r;
+  r.q = q;
+  r.t_submit = now_ns();
+  int32_t dense[kMaxK], order[kMaxK];
+  r.est_rows = dense_labels(ctx, q, dense) ? plan_estimated(ctx, q, dense, order) : 0.0;
+  {
+    std::lock_guard<std::mutex> lk(S.mu);
+    r.ticket = S.next_ticket++;
+    *ticket = r.ticket;
+    S.waiting.push_back(r);
+  }
+  S.cv.notify_one();
+  return GSM_OK;
+}
+
+gsm_status gsm_poll(gsm_ctx *ctx, uint64_t ticket, gsm_result *out) {
+  if (!ctx || !out || !ctx->server) return GSM_ERR_INVALID_ARG;
+  gsm_ctx::Server &S = *ctx->server;
+  std::lock_guard<std::mutex> lk(S.mu);
+  auto it = S.finished.find(ticket);
+  if (it == S.finished.end()) {
+    if (S.inflight.count(ticket)) return GSM_PENDING;
+    for (const auto &r : S.waiting)
+      if (r.ticket == ticket) return GSM_PENDING;
+    return GSM_ERR_INVALID_ARG;
+  }
+  out->count = it->second.count;
+  out->status = it->second.status;
+  out->t_submit_ns = it->second.t_submit;
+  out->t_admit_ns = it->second.t_admit;
+  out->t_done_ns = it->second.t_done;
+  S.finished.erase(it);
+  return GSM_OK;
+}
+
+gsm_status gsm_server_stop(gsm_ctx *ctx) {
+  if (!ctx || !ctx->server) return GSM_ERR_INVALID_ARG;
+  gsm_ctx::Server *S = ctx->server;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv.notify_all();
+  if (S->th.joinable()) S->th.join();
+  cudaSetDevice(ctx->device);
+  for (auto &L : S->lanes) {
+    try {
+      lane_release(ctx, *L);
+    } catch (...) {
+    }
+    if (L->own_stream && L->stream) cudaStreamDestroy(L->stream);
+  }
+  ctx->server = nullptr;
+  delete S;
+  return GSM_OK;
 }
 
 gsm_status gsm_batch_get_stats(gsm_ctx *ctx, gsm_batch_stats *out) {

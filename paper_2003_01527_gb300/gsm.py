@@ -47,7 +47,7 @@ EXPORTED = [
     "gsm_load_graph", "gsm_query_create", "gsm_query_destroy", "gsm_query_restrict", "gsm_count",
     "gsm_enumerate", "gsm_last_rows", "gsm_candidates", "gsm_plan_order", "gsm_kernel_stats",
     "gsm_last_run_stats", "gsm_candidates_static", "gsm_run_batch", "gsm_batch_get_stats",
-    "gsm_batch_configure",
+    "gsm_batch_configure", "gsm_server_start", "gsm_submit", "gsm_poll", "gsm_server_stop",
 ]
 GSM_BATCH_AUTOTUNE = 1
 GSM_STATIC_SCRATCH_BITMAP_BYTES = 8 << 20
@@ -76,6 +76,12 @@ class gsm_batch_stats(ctypes.Structure):
                 ("batches", ctypes.c_uint64), ("graph_launches", ctypes.c_uint64),
                 ("graphs_built", ctypes.c_uint64), ("fallbacks", ctypes.c_uint64),
                 ("kernels_per_graph", ctypes.c_uint64), ("last_ms", ctypes.c_double)]
+
+
+class gsm_result(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_uint64), ("status", ctypes.c_int32),
+                ("t_submit_ns", ctypes.c_int64), ("t_admit_ns", ctypes.c_int64),
+                ("t_done_ns", ctypes.c_int64)]
 
 
 class gsm_run_stats(ctypes.Structure):
@@ -110,6 +116,10 @@ def _load():
         "gsm_run_batch": (i32, [vp, vp, i32, vp, i32]),
         "gsm_batch_get_stats": (i32, [vp, ctypes.POINTER(gsm_batch_stats)]),
         "gsm_batch_configure": (i32, [vp, u64, u64, u64]),
+        "gsm_server_start": (i32, [vp, i32, i32]),
+        "gsm_submit": (i32, [vp, vp, ctypes.POINTER(u64)]),
+        "gsm_poll": (i32, [vp, u64, ctypes.POINTER(gsm_result)]),
+        "gsm_server_stop": (i32, [vp]),
         "gsm_kernel_stats": (i32, [vp, ctypes.POINTER(gsm_kernel_stat), i32,
                                    ctypes.POINTER(i32), i32]),
         "gsm_last_run_stats": (i32, [vp, ctypes.POINTER(gsm_run_stats)]),
@@ -249,6 +259,31 @@ def gsm_batch_get_stats(ctx: int) -> dict:
 
 def gsm_batch_configure(ctx: int, cap_rows: int = 0, cap_elems: int = 0, cap_items: int = 0):
     _check(ctx, _lib.gsm_batch_configure(ctx, cap_rows, cap_elems, cap_items))
+
+
+def gsm_server_start(ctx: int, lanes: int = 2, max_batch: int = 256) -> None:
+    _check(ctx, _lib.gsm_server_start(ctx, lanes, max_batch))
+
+
+def gsm_submit(ctx: int, q: int) -> int:
+    t = ctypes.c_uint64()
+    _check(ctx, _lib.gsm_submit(ctx, q, ctypes.byref(t)))
+    return t.value
+
+
+def gsm_poll(ctx: int, ticket: int):
+    """None while pending, else a dict with count, status and timestamps (ns)."""
+    r = gsm_result()
+    st = _lib.gsm_poll(ctx, ticket, ctypes.byref(r))
+    if st == GSM_PENDING:
+        return None
+    _check(ctx, st)
+    return {"count": r.count, "status": r.status, "t_submit_ns": r.t_submit_ns,
+            "t_admit_ns": r.t_admit_ns, "t_done_ns": r.t_done_ns}
+
+
+def gsm_server_stop(ctx: int) -> None:
+    _check(ctx, _lib.gsm_server_stop(ctx))
 
 
 def gsm_plan_order(k: int, edges, cand_sizes=None) -> tuple[np.ndarray, np.ndarray]:
