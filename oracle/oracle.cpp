@@ -144,7 +144,8 @@ struct Search {
   bool adj[16][16];
   bool enumerate;
   // search controls (not part of the definition): stop once more than
-  // `limit` embeddings or more than `node_budget` search nodes were seen
+  // `limit` embeddings or more than `node_budget` search steps (nodes entered
+  // plus candidates examined) were taken
   uint64_t limit, node_budget;
   mutable std::atomic<uint64_t> shared_count{0}, shared_nodes{0};
   mutable std::atomic<int> stop{0};  // 1 = limit exceeded, 2 = budget exceeded
@@ -180,6 +181,12 @@ struct Worker {
     int32_t p = f[S.parent[u]];
     for (int64_t e = S.rp[p]; e < S.rp[p + 1]; ++e) {
       int32_t w = S.col[e];
+      // every examined candidate counts towards the search budget, so a
+      // node that scans a hub row is bounded too
+      if (++pend_nodes >= 4096) {
+        flush();
+        if (S.stop.load(std::memory_order_relaxed)) return;
+      }
       if (S.lab[w] != S.qlab[u]) continue;
       bool ok = true;
       for (int32_t j = 0; j < depth && ok; ++j) {
