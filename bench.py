@@ -14,6 +14,12 @@ verification level with its count and write passes, sorting into canonical
 order), enumerating the sorted rows into a device buffer.  The graph is
 resident; L2 is flushed before each timed step (the graph is smaller than L2).
 
+`batched_vs_plain` (same line): the R-MAT scale-18 workload (16 Zipf(1.2)
+labels, 256 random-walk queries of 3-10 vertices with 2-4 non-tree edges, on
+oracle-sized root slices) counted one query per call versus as one batch (one
+CUDA graph), then served under Poisson arrivals at 50-2,000 queries/s with
+p50/p99 latency; every count is checked against the oracle's.
+
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 One JSON line on rank 0.  `--impl reference` times the CPU oracle on a
@@ -37,6 +43,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 GOLDEN = os.path.join(ROOT, "tests", "golden", "rmat16_labelled_slices.json")
+GOLDEN_BATCH = os.path.join(ROOT, "tests", "golden", "rmat18_batched_slices.json")
+SERVE_RATES = (50, 100, 200, 500, 1000, 2000)
 METRIC = "embeddings/sec & queries/sec at 1 GB300 (batched vs plain, bit-exact); p50/p99"
 UNIT = "embeddings/s"
 WORKLOAD = ("R-MAT scale 16 (65,536 vertices, edge factor 16), 8 Zipf(1.0) labels, "
@@ -54,6 +62,119 @@ def load_workload():
     if h.hexdigest() != gold["graph"]["sha256"]:
         raise SystemExit("generated graph differs from the stored workload")
     return g, gold["queries"]
+
+
+def load_batch_workload():
+    from paper_2003_01527_gb300 import inputs as I
+    with open(GOLDEN_BATCH) as f:
+        gold = json.load(f)
+    g, _ = I.rmat_labelled_workload(scale=18, num_labels=16, zipf_s=1.2, num_queries=0, seed=4)
+    h = hashlib.sha256()
+    for a in (g.row_ptr, g.col, g.labels):
+        h.update(np.ascontiguousarray(a, dtype="<i4").tobytes())
+    if h.hexdigest() != gold["graph"]["sha256"]:
+        raise SystemExit("generated batch graph differs from the stored workload")
+    return g, gold["queries"]
+
+
+def pct(xs, p):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, int(round(p / 100 * (len(xs) - 1))))] if xs else None
+
+
+def batched_and_served(gsm, torch, device, serve_seconds):
+    """The batched form (one CUDA graph for all 256 queries) against 256
+    single-query launches, then the served form under Poisson arrivals, on the
+    R-MAT 18 workload; every count checked against the oracle's."""
+    g, queries = load_batch_workload()
+    M = gsm.Matcher(device=device)
+    M.load_graph(g.row_ptr, g.col, g.labels, validate=True)
+    Qs = [M.query(q["k"], q["edges"], q["labels"]).restrict(0, 0, q["root_hi"]) for q in queries]
+    want = [q["count"] for q in queries]
+    emb = sum(want)
+    # plain: one query per call
+    for _ in range(2):
+        got = [M.count(Q) for Q in Qs]
+    if got != want:
+        raise SystemExit("plain counts differ from the oracle's")
+    reps = 3
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        for Q in Qs:
+            M.count(Q)
+    plain_s = (time.perf_counter() - t0) / reps
+    lat = []
+    for Q in Qs:
+        t1 = time.perf_counter()
+        M.count(Q)
+        lat.append((time.perf_counter() - t1) * 1e3)
+    # batched: autotune on the first call, then time
+    got = M.run_batch(Qs, autotune=True)
+    if got != want:
+        raise SystemExit("batched counts differ from the oracle's")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        got = M.run_batch(Qs)
+    batch_s = (time.perf_counter() - t0) / reps
+    if got != want:
+        raise SystemExit("batched counts differ from the oracle's")
+    bst = M.batch_stats()
+    out = {"workload": "R-MAT scale 18 (262,144 vertices, edge factor 16), 16 Zipf(1.2) labels, "
+                       f"{len(Qs)} random-walk queries of 3-10 vertices (tree + 2-4 non-tree "
+                       "edges), each on an oracle-sized root slice",
+           "embeddings_per_pass": emb,
+           "plain": {"queries_per_sec": round(len(Qs) / plain_s, 1),
+                     "embeddings_per_sec": round(emb / plain_s, 1),
+                     "ms_per_pass": round(plain_s * 1e3, 3),
+                     "latency_ms_p50": round(pct(lat, 50), 4),
+                     "latency_ms_p99": round(pct(lat, 99), 4)},
+           "batched": {"queries_per_sec": round(len(Qs) / batch_s, 1),
+                       "embeddings_per_sec": round(emb / batch_s, 1),
+                       "ms_per_pass": round(batch_s * 1e3, 3),
+                       "graph_kernels": bst["kernels_per_graph"],
+                       "block_size": bst["block_size"], "grid": bst["grid"],
+                       "tuned": bst["tuned"]},
+           "bit_exact": True}
+    # served: Poisson arrivals over the same query stream
+    served = []
+    rng = np.random.default_rng(7)
+    for rate in SERVE_RATES:
+        gsm.gsm_server_start(M.ctx, 2, 256)
+        n_req = max(20, int(rate * serve_seconds))
+        gaps = rng.exponential(1.0 / rate, n_req)
+        order = rng.integers(0, len(Qs), n_req)
+        tickets = []
+        t_start = time.perf_counter()
+        next_t = t_start
+        results = {}
+        for j in range(n_req):
+            next_t += gaps[j]
+            while time.perf_counter() < next_t:
+                pass
+            tickets.append((gsm.gsm_submit(M.ctx, Qs[order[j]].handle), int(order[j])))
+        while len(results) < len(tickets):
+            for t, qi in tickets:
+                if t not in results:
+                    r = gsm.gsm_poll(M.ctx, t)
+                    if r is not None:
+                        results[t] = (r, qi)
+            time.sleep(0.0002)
+        wall = time.perf_counter() - t_start
+        gsm.gsm_server_stop(M.ctx)
+        lat = [(r["t_done_ns"] - r["t_submit_ns"]) / 1e6 for r, _ in results.values()]
+        ok = all(r["count"] == want[qi] and r["status"] == 0 for r, qi in results.values())
+        if not ok:
+            raise SystemExit(f"served counts differ from the oracle's at {rate} q/s")
+        served.append({"rate_qps": rate, "requests": n_req,
+                       "throughput_qps": round(n_req / wall, 1),
+                       "embeddings_per_sec": round(sum(want[qi] for _, qi in tickets) / wall, 1),
+                       "latency_ms_p50": round(pct(lat, 50), 3),
+                       "latency_ms_p99": round(pct(lat, 99), 3)})
+    out["served"] = served
+    M.close()
+    return out
 
 
 def peaks():
@@ -238,6 +359,9 @@ def run_gpu(args):
     e2e_value = per_step * world / (statistics.median(e2e_ms) / 1e3)
 
     cpu = cpu_baseline(g, queries) if (rank == 0 and world == 1 and not args.no_cpu) else None
+    batched = None
+    if not args.no_batch and not args.queries:
+        batched = batched_and_served(gsm, torch, local, args.serve_seconds)
 
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
@@ -260,6 +384,7 @@ def run_gpu(args):
         "gpu_launches": launches,
         "clocks": clocks,
         "cpu_baseline": cpu,
+        "batched_vs_plain": batched,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -342,6 +467,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gsm", choices=["gsm", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched and served measurements")
+    ap.add_argument("--serve-seconds", type=float, default=2.0,
+                    help="seconds of Poisson arrivals per served rate")
     ap.add_argument("--queries", default="",
                     help="comma-separated query indices (a smaller case for profiling)")
     args = ap.parse_args()

@@ -102,3 +102,34 @@ def test_batch_unlabelled_shapes(gsm_lib, cuda):
     want = [oracle.count(g, q, root_range=(0, hi)) for q, hi in cases]
     assert m.run_batch(Qs) == want
     m.close()
+
+
+def test_batched_workload_full_size(gsm_lib, cuda):
+    """The R-MAT scale-18 batched workload at full size, as the benchmark runs
+    it: one batch of all 256 query slices against the oracle's stored counts,
+    and the sorted rows of the non-empty slices against its stored digests."""
+    import hashlib
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "rmat18_batched_slices.json")
+    with open(path) as f:
+        gold = json.load(f)
+    g, _ = I.rmat_labelled_workload(scale=18, num_labels=16, zipf_s=1.2, num_queries=0, seed=4)
+    h = hashlib.sha256()
+    for a in (g.row_ptr, g.col, g.labels):
+        h.update(np.ascontiguousarray(a, dtype="<i4").tobytes())
+    assert h.hexdigest() == gold["graph"]["sha256"]
+    m = gsm_lib.Matcher(device=0)
+    m.load_graph(g.row_ptr, g.col, g.labels)
+    Qs = [m.query(q["k"], q["edges"], q["labels"]).restrict(0, 0, q["root_hi"])
+          for q in gold["queries"]]
+    assert m.run_batch(Qs, autotune=True) == [q["count"] for q in gold["queries"]]
+    assert m.batch_stats()["overflowed"] == 0
+    for q, Q in zip(gold["queries"], Qs):
+        if q["count"]:
+            rows, count = m.enumerate(Q)
+            assert count == q["count"]
+            digest = hashlib.sha256(np.ascontiguousarray(rows, dtype="<i4").tobytes()).hexdigest()
+            assert digest == q["rows_sha256"]
+    m.close()
