@@ -126,6 +126,8 @@ struct gsm_ctx {
     unsigned long long *h_counts = nullptr;
     int32_t *h_overflow = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_done = nullptr;
+    uint32_t *zero_bitmap = nullptr;  // root bitmap of padding queries
+    int32_t mb = 0, kb = 0;           // shape of the issued batch (padded)
     std::map<std::tuple<int32_t, int32_t, int32_t, int32_t, int32_t>, cudaGraphExec_t> graphs;
     // a batch in flight (server): which requests, how many queries
     std::vector<uint64_t> tickets;
@@ -937,6 +939,9 @@ void lane_workspace(gsm_ctx *ctx, Lane &L, int32_t nq, int64_t words_total) {
     a.overflow = lane_alloc<int32_t>(ctx, L, 1);
     a.partials = lane_alloc<int64_t>(ctx, L, (int64_t)ctx->num_sms * 32 + 1);
     CU(cudaMallocHost(&L.h_overflow, sizeof(int32_t)));
+    const int32_t nw = (ctx->n + 31) / 32;
+    L.zero_bitmap = lane_alloc<uint32_t>(ctx, L, nw);
+    CU(cudaMemsetAsync(L.zero_bitmap, 0, sizeof(uint32_t) * std::max(nw, 1), L.stream));
     CU(cudaEventCreate(&L.ev0));
     CU(cudaEventCreate(&L.ev1));
     CU(cudaEventCreateWithFlags(&L.ev_done, cudaEventDisableTiming));
@@ -1054,10 +1059,21 @@ cudaGraphExec_t lane_graph(gsm_ctx *ctx, Lane &L, int32_t m, int32_t kmax, int32
   return exec;
 }
 
+// Batch shapes are bucketed so that few graphs serve every batch: the number
+// of queries is rounded up to a power of two (the extra slots hold padding
+// queries that match nothing); the largest query size is kept exact, since
+// every level costs its launches even when it has no rows.
+int32_t bucket_queries(int32_t m) {
+  int32_t b = 1;
+  while (b < m) b <<= 1;
+  return b;
+}
+int32_t bucket_size(int32_t k) { return k; }
+
 // Host part of a batch: labels, filter descriptions, orders, level
-// descriptions, uploaded (asynchronously) to the lane.  L.sel = indices of
-// the queries that can match (a label absent from G means 0).  Returns the
-// largest query size.
+// descriptions, uploaded (asynchronously) to the lane, padded to the bucketed
+// shape (L.mb queries).  L.sel = indices of the queries that can match (a
+// label absent from G means 0).  Returns the bucketed largest query size.
 int32_t lane_prepare(gsm_ctx *ctx, Lane &L, const gsm_query *const *qs, int32_t nq) {
   const int32_t n_words = (ctx->n + 31) / 32;
   L.sel.clear();
@@ -1072,13 +1088,14 @@ int32_t lane_prepare(gsm_ctx *ctx, Lane &L, const gsm_query *const *qs, int32_t 
   }
   L.m = (int32_t)L.sel.size();
   if (L.m == 0) return 0;
+  L.mb = bucket_queries(L.m);
   const size_t bm_bytes = (size_t)total_k * n_words * sizeof(uint32_t);
   if (L.bitmaps_cap < bm_bytes) {
-    lane_clear_graphs(L);
+    // graphs stay valid: bitmap addresses travel in the per-batch descriptors
     CU(cudaStreamSynchronize(L.stream));
     ensure_buf(ctx, &L.bitmaps, &L.bitmaps_cap, bm_bytes, false, 0);
   }
-  lane_workspace(ctx, L, L.m, (int64_t)L.m * n_words);
+  lane_workspace(ctx, L, L.mb, (int64_t)L.mb * n_words);
   uint32_t *bm = (uint32_t *)L.bitmaps;
   int32_t kmax = 1;
   int64_t off = 0;
@@ -1110,20 +1127,28 @@ int32_t lane_prepare(gsm_ctx *ctx, Lane &L, const gsm_query *const *qs, int32_t 
     }
     kmax = std::max(kmax, q->k);
   }
-  CU(cudaMemcpyAsync((void *)L.a.fds, L.h_fds, sizeof(FilterDesc) * L.m, cudaMemcpyHostToDevice,
+  for (int32_t t = L.m; t < L.mb; ++t) {  // padding: no filter work, nothing to count
+    std::memset(&L.h_fds[t], 0, sizeof(FilterDesc));
+    L.h_bm[t] = L.zero_bitmap;
+    std::memset(&L.h_qs[t], 0, sizeof(BatchQuery));
+    L.h_qs[t].k = 1;
+    L.h_qs[t].root_bitmap = L.zero_bitmap;
+  }
+  CU(cudaMemcpyAsync((void *)L.a.fds, L.h_fds, sizeof(FilterDesc) * L.mb, cudaMemcpyHostToDevice,
                      L.stream));
-  CU(cudaMemcpyAsync((void *)L.a.bm_out, L.h_bm, sizeof(uint32_t *) * L.m,
+  CU(cudaMemcpyAsync((void *)L.a.bm_out, L.h_bm, sizeof(uint32_t *) * L.mb,
                      cudaMemcpyHostToDevice, L.stream));
-  CU(cudaMemcpyAsync((void *)L.a.qs, L.h_qs, sizeof(BatchQuery) * L.m, cudaMemcpyHostToDevice,
+  CU(cudaMemcpyAsync((void *)L.a.qs, L.h_qs, sizeof(BatchQuery) * L.mb, cudaMemcpyHostToDevice,
                      L.stream));
-  return kmax;
+  L.kb = bucket_size(kmax);
+  return L.kb;
 }
 
 // Issues the prepared batch: graph launch, then the counts and the overflow
 // flag back to pinned memory, then ev_done (all asynchronous).
 void lane_issue(gsm_ctx *ctx, Lane &L, int32_t kmax, int32_t block, int32_t grid) {
   const int32_t n_words = (ctx->n + 31) / 32;
-  cudaGraphExec_t exec = lane_graph(ctx, L, L.m, kmax, n_words, block, grid);
+  cudaGraphExec_t exec = lane_graph(ctx, L, L.mb, kmax, n_words, block, grid);
   CU(cudaEventRecord(L.ev0, L.stream));
   CU(cudaGraphLaunch(exec, L.stream));
   CU(cudaEventRecord(L.ev1, L.stream));
@@ -1732,6 +1757,37 @@ gsm_status gsm_server_start(gsm_ctx *ctx, int32_t lanes, int32_t max_batch) {
   if (st != GSM_OK) {
     for (auto &L : S->lanes)
       if (L->stream) cudaStreamDestroy(L->stream);
+    delete S;
+    return st;
+  }
+  // Size every lane for the largest batch and capture the graphs of every
+  // shape bucket now, so serving neither allocates nor captures.
+  st = guarded(ctx, [&] {
+    const int32_t n_words = (ctx->n + 31) / 32;
+    const int32_t mb_max = bucket_queries(max_batch);
+    for (auto &Lp : S->lanes) {
+      Lane &L = *Lp;
+      lane_workspace(ctx, L, mb_max, (int64_t)mb_max * n_words);
+      const size_t bm_bytes = std::min<size_t>((size_t)mb_max * kMaxK * n_words * 4,
+                                               size_t(1) << 30);
+      ensure_buf(ctx, &L.bitmaps, &L.bitmaps_cap, bm_bytes, false, 0);
+      for (int32_t mb = 1; mb <= mb_max; mb <<= 1)
+        for (int32_t kb = 1; kb <= kMaxK; ++kb) {
+          bool tuned;
+          auto cfg = batch_config(ctx, mb, kb, &tuned);
+          lane_graph(ctx, L, mb, kb, n_words, cfg.first, cfg.second);
+        }
+      CU(cudaStreamSynchronize(L.stream));
+    }
+  });
+  if (st != GSM_OK) {
+    for (auto &L : S->lanes) {
+      try {
+        lane_release(ctx, *L);
+      } catch (...) {
+      }
+      if (L->stream) cudaStreamDestroy(L->stream);
+    }
     delete S;
     return st;
   }

@@ -158,6 +158,7 @@ __global__ void __launch_bounds__(256) k_b_filter(GraphDev g, const FilterDesc *
   for (int j = threadIdx.x; j < (int)(sizeof(FilterDesc) / 4); j += blockDim.x)
     reinterpret_cast<int32_t *>(&s_d)[j] = reinterpret_cast<const int32_t *>(fds + q)[j];
   __syncthreads();
+  if (s_d.k == 0) return;  // padding slot of a bucketed batch
   filter_warps(g, s_d, bm_out[q], sizes + (int64_t)q * kMaxK,
                ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
                ((int64_t)gridDim.x * blockDim.x) >> 5);

@@ -89,22 +89,24 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
   }
 }
 
-// Column-major -> row-major through a shared-memory tile: 32 rows per block,
-// reads and writes both contiguous.
+// Column-major -> row-major through a shared-memory tile of 256 rows: each
+// column is read with contiguous loads, and the tile's k*256 output ints,
+// which are contiguous in the result, are written with contiguous stores.
 __global__ void __launch_bounds__(256) k_transpose_rows(const int32_t *__restrict__ in,
                                                         int64_t ld, int32_t *__restrict__ out,
                                                         int64_t N, int32_t k) {
-  __shared__ int32_t s_tile[32 * 17];
-  const int64_t r0 = (int64_t)blockIdx.x * 32;
-  for (int t = threadIdx.x; t < 32 * k; t += blockDim.x) {
-    const int j = t / 32, rr = t % 32;
-    if (r0 + rr < N) s_tile[rr * 17 + j] = in[(int64_t)j * ld + r0 + rr];
-  }
+  __shared__ int32_t s_tile[256 * (kMaxK + 1)];
+  const int64_t r0 = (int64_t)blockIdx.x * 256;
+  const int32_t rows = (int32_t)min((int64_t)256, N - r0);
+  const int32_t w = k + 1;  // padded row pitch: conflict-free column writes
+  for (int32_t c = 0; c < k; ++c)
+    if ((int32_t)threadIdx.x < rows)
+      s_tile[threadIdx.x * w + c] = in[(int64_t)c * ld + r0 + threadIdx.x];
   __syncthreads();
-  const int64_t rows = min((int64_t)32, N - r0);
-  for (int t = threadIdx.x; t < rows * k; t += blockDim.x) {
-    const int rr = t / k, j = t % k;
-    out[(r0 + rr) * k + j] = s_tile[rr * 17 + j];
+  int32_t *dst = out + r0 * k;
+  for (int32_t e = threadIdx.x; e < rows * k; e += blockDim.x) {
+    const int32_t rr = e / k, c = e - rr * k;
+    dst[e] = s_tile[rr * w + c];
   }
 }
 
@@ -120,7 +122,7 @@ int launch_sort_rows(int32_t *a, int64_t lda, int32_t *b, int64_t ldb, int64_t N
                      cudaStream_t s, int *launches) {
   if (N <= 0) return 0;
   if (presorted || N == 1) {
-    k_transpose_rows<<<(unsigned)((N + 31) / 32), 256, 0, s>>>(a, lda, b, N, k);
+    k_transpose_rows<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(a, lda, b, N, k);
     if (launches) *launches += 1;
     return 1;
   }
