@@ -67,7 +67,12 @@ def csr_from_pairs(n: int, src: np.ndarray, dst: np.ndarray) -> tuple[np.ndarray
     keep = src != dst
     src, dst = src[keep], dst[keep]
     keys = np.concatenate([(src << 32) | dst, (dst << 32) | src])
-    keys = np.unique(keys)
+    keys.sort()  # sorted distinct keys, as np.unique gives, but far faster here
+    if keys.shape[0]:
+        keep = np.empty(keys.shape[0], dtype=bool)
+        keep[0] = True
+        np.not_equal(keys[1:], keys[:-1], out=keep[1:])
+        keys = keys[keep]
     rows = (keys >> 32).astype(np.int64)
     col = (keys & 0xFFFFFFFF).astype(np.int32)
     counts = np.bincount(rows, minlength=n)
