@@ -57,7 +57,7 @@ def _load():
                                          ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
                                          ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64),
                                          ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32,
-                                         ctypes.c_uint64, ctypes.c_uint64]
+                                         ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p]
             lib.oracle_match.restype = ctypes.c_int
             lib.oracle_max_threads.restype = ctypes.c_int
             _lib = lib
@@ -92,7 +92,7 @@ def max_threads() -> int:
 
 
 def match(g, q, enumerate: bool = True, root_range=None, cap_rows: int | None = None,
-          nthreads: int = 0, limit: int = 0, node_budget: int = 0):
+          nthreads: int = 0, limit: int = 0, node_budget: int = 0, ranges=None):
     """Returns (count, rows, status).
 
     count  -- exact Python int (128-bit on the C side).
@@ -100,18 +100,27 @@ def match(g, q, enumerate: bool = True, root_range=None, cap_rows: int | None = 
               or None.
     root_range -- (lo, hi): only embeddings with f(q_0) in [lo, hi).
     limit / node_budget -- search controls: status LIMIT (more than `limit`
-              embeddings) or BUDGET (more than `node_budget` search nodes)
+              embeddings) or BUDGET (more than `node_budget` search steps)
               means the search gave up and count is meaningless.
+    ranges -- {u: (lo, hi)}: only embeddings with f(u) in [lo, hi) for each
+              listed query vertex u.
     """
     lo, hi = (0, g.n) if root_range is None else root_range
     lib = _load()
     qlab = np.ascontiguousarray(q.labels, dtype=np.int32)
     clo, chi = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    rng_arr = None
+    if ranges:
+        rng_arr = np.zeros(2 * q.k, dtype=np.int64)
+        rng_arr[1::2] = g.n
+        for u, (a, b) in ranges.items():
+            rng_arr[2 * u], rng_arr[2 * u + 1] = a, b
 
     def call(enum, out_ptr, cap):
         return lib.oracle_match(g.n, g.row_ptr, g.col, g.labels, q.k, q.m, _edges(q), qlab,
                                 lo, hi, enum, out_ptr, cap, ctypes.byref(clo), ctypes.byref(chi),
-                                nthreads, limit, node_budget)
+                                nthreads, limit, node_budget,
+                                None if rng_arr is None else rng_arr.ctypes.data)
 
     if not enumerate:
         rc = call(0, None, 0)

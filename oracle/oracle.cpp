@@ -143,6 +143,7 @@ struct Search {
   int32_t parent[16];      // BFS parent (query id) of order[i], -1 for the root
   bool adj[16][16];
   bool enumerate;
+  int64_t rlo[16], rhi[16];  // f(u) must lie in [rlo[u], rhi[u])
   // search controls (not part of the definition): stop once more than
   // `limit` embeddings or more than `node_budget` search steps (nodes entered
   // plus candidates examined) were taken
@@ -188,6 +189,7 @@ struct Worker {
         if (S.stop.load(std::memory_order_relaxed)) return;
       }
       if (S.lab[w] != S.qlab[u]) continue;
+      if (w < S.rlo[u] || w >= S.rhi[u]) continue;
       bool ok = true;
       for (int32_t j = 0; j < depth && ok; ++j) {
         int32_t uj = S.order[j];
@@ -205,20 +207,27 @@ struct Worker {
 // f(q_0) in [root_lo, root_hi).  The count is returned as two 64-bit halves of
 // an unsigned 128-bit integer.  Rows are written sorted, at most cap_rows of
 // them; OR_TRUNCATED if more exist.  nthreads <= 0 uses every core.
+// ranges (may be NULL): int64[2k], f(u) restricted to [ranges[2u], ranges[2u+1])
+// for every query vertex u, i.e. only embeddings inside those ranges count.
 // limit > 0: give up (OR_LIMIT) once more than `limit` embeddings exist;
-// node_budget > 0: give up (OR_BUDGET) after that many search nodes.  Neither
+// node_budget > 0: give up (OR_BUDGET) after that many search steps.  Neither
 // changes what is counted when the call returns OR_OK / OR_TRUNCATED.
 int oracle_match(int32_t n, const int32_t* rp, const int32_t* col, const int32_t* lab,
                  int32_t k, int32_t m, const int32_t* edges, const int32_t* qlab,
                  int64_t root_lo, int64_t root_hi, int32_t enumerate,
                  int32_t* out, uint64_t cap_rows, uint64_t* count_lo, uint64_t* count_hi,
-                 int32_t nthreads, uint64_t limit, uint64_t node_budget) {
+                 int32_t nthreads, uint64_t limit, uint64_t node_budget,
+                 const int64_t* ranges) {
   if (oracle_validate_query(k, m, edges) != OR_OK) return OR_INVALID_QUERY;
   Search S;
   S.rp = rp; S.col = col; S.lab = lab; S.qlab = qlab; S.k = k;
   S.enumerate = enumerate != 0;
   S.limit = limit;
   S.node_budget = node_budget;
+  for (int32_t u = 0; u < 16; ++u) {
+    S.rlo[u] = (ranges && u < k) ? ranges[2 * u] : 0;
+    S.rhi[u] = (ranges && u < k) ? ranges[2 * u + 1] : (int64_t)n;
+  }
   std::memset(S.adj, 0, sizeof(S.adj));
   for (int32_t e = 0; e < m; ++e) {
     S.adj[edges[2 * e]][edges[2 * e + 1]] = true;
@@ -233,8 +242,9 @@ int oracle_match(int32_t n, const int32_t* rp, const int32_t* col, const int32_t
     for (int32_t w = 0; w < k; ++w)
       if (S.adj[u][w] && !seen[w]) { seen[w] = true; S.parent[w] = u; S.order[tail++] = w; }
   }
-  int64_t lo = std::max<int64_t>(0, root_lo), hi = std::min<int64_t>(n, root_hi);
   int32_t root = S.order[0];
+  int64_t lo = std::max<int64_t>(std::max<int64_t>(0, root_lo), S.rlo[root]);
+  int64_t hi = std::min<int64_t>(std::min<int64_t>(n, root_hi), S.rhi[root]);
 #ifdef _OPENMP
   int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
 #else

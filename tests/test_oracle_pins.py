@@ -161,6 +161,23 @@ def test_root_slices_add_up(oracle_lib, small_rmat):
     assert all(((p[:, 0] >= a) & (p[:, 0] < b)).all() for p, a, b in zip(parts, cuts, cuts[1:]))
 
 
+def test_vertex_ranges_filter_brute_force(oracle_lib):
+    """Ranges on any query vertices keep exactly the brute-force embeddings
+    that fall inside them."""
+    rng = np.random.default_rng(77)
+    for g, q in tiny_cases(60, 300):
+        ranges = {}
+        for u in range(q.k):
+            if rng.random() < 0.5:
+                a = int(rng.integers(0, g.n))
+                ranges[u] = (a, int(rng.integers(a, g.n + 1)))
+        want = [f for f in brute.embeddings(g, q)
+                if all(lo <= f[u] < hi for u, (lo, hi) in ranges.items())]
+        count, rows, rc = oracle.match(g, q, ranges=ranges)
+        assert rc == oracle.OK and count == len(want)
+        assert [tuple(r) for r in rows.tolist()] == want
+
+
 def test_generating_walk_is_an_embedding(oracle_lib, small_rmat):
     rng = np.random.default_rng(5)
     for _ in range(10):
