@@ -70,7 +70,7 @@ WINDOW = {u: (0, 1 << 14) for u in range(1, 6)}
 @pytest.mark.parametrize("shape,lo,width,ranges", [("triangle", 0, 4096, None),
                                                    ("triangle", 524_288, 4096, None),
                                                    ("clique4", 1_000_000, 2048, None),
-                                                   ("cycle5", 0, 64, None),
+                                                   ("cycle5", 524_288, 64, None),
                                                    ("path6", 700_000, 64, WINDOW)])
 def test_rmat20_slices_match_oracle(gsm_lib, cuda, rmat20, shape, lo, width, ranges):
     g = rmat20
