@@ -143,8 +143,10 @@ gsm_status gsm_count(gsm_ctx *ctx, const gsm_query *q, uint64_t *count);
  * ascending lexicographic order, column j = f(q_j).  *count receives the total
  * number of embeddings.  If it exceeds cap_rows the first cap_rows rows are
  * written and GSM_ERR_TRUNCATED is returned.  out may be NULL iff cap_rows = 0.
- * Final rows are staged in library-owned device buffers (2 x count x k x 4
- * bytes plus about 1.5 bytes per row of sort histograms, outside the budget).  Errors: as gsm_count, plus GSM_ERR_TRUNCATED. */
+ * Final rows are staged in library-owned device buffers outside the budget:
+ * count x k x 4 bytes of rows plus, unless the matching order is the identity,
+ * two packed sort keys of ceil(k * log2(n) / 64) x 8 bytes per row and about
+ * 1.5 bytes per row of histograms (otherwise a second count x k x 4 buffer).  Errors: as gsm_count, plus GSM_ERR_TRUNCATED. */
 gsm_status gsm_enumerate(gsm_ctx *ctx, const gsm_query *q, int32_t *out, uint64_t cap_rows,
                          uint64_t *count, int32_t flags);
 

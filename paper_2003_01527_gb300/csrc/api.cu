@@ -88,6 +88,8 @@ struct gsm_ctx {
   size_t acc_cap[2] = {0, 0};
   void *sort_tmp = nullptr;  // radix-sort histograms (scale with the result)
   size_t sort_tmp_cap = 0;
+  void *sort_keys = nullptr;  // packed sort keys, two copies
+  size_t sort_keys_cap = 0;
   const int32_t *last_rows = nullptr;  // sorted rows of the last gsm_enumerate
   uint64_t last_count = 0;
   int32_t last_k = 0;
@@ -798,28 +800,46 @@ void run_query(gsm_ctx *ctx, const gsm_query *q, bool enumerate, int32_t *out, u
   if (q->k > 1 && total > 0) {
     bool identity = true;
     for (int32_t j = 0; j < q->k; ++j) identity = identity && R.order[j] == j;
-    const size_t bytes = (size_t)total * q->k * sizeof(int32_t);
-    ensure_buf(ctx, &ctx->acc[1], &ctx->acc_cap[1], bytes, false, 0);
-    const int64_t H = identity ? 0 : sort_hist_elems((int64_t)total);
-    Carve cv;
-    const size_t o_h = cv.add<int32_t>(H), o_ho = cv.add<int64_t>(H + 1),
-                 o_t = cv.add<int64_t>(scan_tmp_elems(H));
-    // outside the budget, like the result buffers it serves
-    ensure_buf(ctx, &ctx->sort_tmp, &ctx->sort_tmp_cap, cv.off, false, 0);
-    char *sc = (char *)ctx->sort_tmp;
     int bits = 1;
     while (bits < 31 && (int64_t(1) << bits) < ctx->n) ++bits;
-    int which = 0;
-    int launches = 0;
-    const double passes = identity ? 0.5 : q->k * ((bits + 7) / 8);
-    timed(ctx, K_SORT, 2.0 * bytes * passes, total, 0, [&] {
-      which = launch_sort_rows((int32_t *)ctx->acc[0], R.acc_ld, (int32_t *)ctx->acc[1],
-                               (int64_t)total, (int64_t)total, q->k, bits, identity,
-                               (int32_t *)(sc + o_h), (int64_t *)(sc + o_ho),
-                               (int64_t *)(sc + o_t), ctx->stream, &launches);
-    });
-    ctx->run.kernel_launches += launches;
-    rows = (int32_t *)ctx->acc[which];
+    const size_t bytes = (size_t)total * q->k * sizeof(int32_t);
+    if (identity) {
+      // already in order: only the layout changes
+      ensure_buf(ctx, &ctx->acc[1], &ctx->acc_cap[1], bytes, false, 0);
+      int launches = 0;
+      timed(ctx, K_SORT, 2.0 * bytes, total, 0, [&] {
+        launch_sort_rows((int32_t *)ctx->acc[0], R.acc_ld, (int32_t *)ctx->acc[1],
+                         (int64_t)total, (int64_t)total, q->k, bits, true, nullptr, nullptr,
+                         nullptr, ctx->stream, &launches);
+      });
+      ctx->run.kernel_launches += launches;
+      rows = (int32_t *)ctx->acc[1];
+    } else {
+      // packed-key radix sort; the sorted rows land row-major in acc[0]
+      const int32_t nw = packed_words(q->k, bits);
+      const size_t key_bytes = (size_t)total * nw * sizeof(uint64_t);
+      ensure_buf(ctx, &ctx->sort_keys, &ctx->sort_keys_cap, 2 * key_bytes, false, 0);
+      const int64_t H = sort_hist_elems((int64_t)total);
+      Carve cv;
+      const size_t o_h = cv.add<int32_t>(H), o_ho = cv.add<int64_t>(H + 1),
+                   o_t = cv.add<int64_t>(scan_tmp_elems(H));
+      // outside the budget, like the result buffers it serves
+      ensure_buf(ctx, &ctx->sort_tmp, &ctx->sort_tmp_cap, cv.off, false, 0);
+      char *sc = (char *)ctx->sort_tmp;
+      uint64_t *ka = (uint64_t *)ctx->sort_keys;
+      uint64_t *kb = ka + (size_t)total * nw;
+      const int digits = (q->k * bits + 7) / 8;
+      int launches = 0;
+      timed(ctx, K_SORT, bytes + 2.0 * key_bytes * digits + bytes, total, 0, [&] {
+        launches = launch_sort_rows_packed((const int32_t *)ctx->acc[0], R.acc_ld,
+                                           (int64_t)total, q->k, bits, ka, kb,
+                                           (int32_t *)ctx->acc[0], (int32_t *)(sc + o_h),
+                                           (int64_t *)(sc + o_ho), (int64_t *)(sc + o_t),
+                                           ctx->stream);
+      });
+      ctx->run.kernel_launches += launches;
+      rows = (int32_t *)ctx->acc[0];
+    }
   }
   ctx->last_rows = rows;
   ctx->last_count = total;
@@ -1497,6 +1517,7 @@ void gsm_destroy(gsm_ctx *ctx) {
     dev_free(ctx, ctx->acc[0], ctx->acc_cap[0]);
     dev_free(ctx, ctx->acc[1], ctx->acc_cap[1]);
     dev_free(ctx, ctx->sort_tmp, ctx->sort_tmp_cap);
+    dev_free(ctx, ctx->sort_keys, ctx->sort_keys_cap);
     dev_free(ctx, ctx->d_small, 256);
   } catch (...) {
   }

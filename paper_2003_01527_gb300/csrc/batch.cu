@@ -310,7 +310,9 @@ __device__ __forceinline__ int32_t b_row(const BTile &b, const int32_t *s_woff,
 
 // Verification pass of one step.  A survivor of a query at its last level
 // is counted into counts[q]; other survivors get their mask bit and count
-// towards their tile.
+// towards their tile.  Thread t of a tile takes the 4 consecutive candidates
+// 4t .. 4t+3 (one row search for all four); the mask bits stay in candidate
+// order (4-bit groups OR-ed across the 8 lanes of a mask word).
 __global__ void __launch_bounds__(1024) k_b_count(
     GraphDev g, const BatchQuery *__restrict__ qs, int32_t i, const BatchStep *state,
     const int32_t *__restrict__ F, const int32_t *__restrict__ rseg,
@@ -318,6 +320,7 @@ __global__ void __launch_bounds__(1024) k_b_count(
     const int64_t *__restrict__ woff, const int32_t *__restrict__ tile_row,
     uint32_t *__restrict__ masks, int32_t *__restrict__ tile_cnt,
     unsigned long long *__restrict__ counts) {
+  static_assert(kItemsPerThread == 4, "one 4-bit group per lane");
   extern __shared__ int32_t s_woff[];
   __shared__ int32_t s_count;
   const int32_t R = (int32_t)state[i].R;
@@ -330,39 +333,62 @@ __global__ void __launch_bounds__(1024) k_b_count(
     if (threadIdx.x == 0) s_count = 0;
     const BTile b = b_stage(woff, tile_row, t, tile_items, s_woff);
     const int32_t x0 = (int32_t)t * tile_items, x1 = min(x0 + tile_items, W);
-    int32_t cnt = 0;
+    const int32_t xb = x0 + warp * 128 + lane * kItemsPerThread;
+    uint32_t bits = 0;
+    int32_t qj[kItemsPerThread] = {-1, -1, -1, -1};  // query of a last-level survivor
+    if (xb < x1) {
+      int32_t rs;
+      int32_t r = b_row(b, s_woff, woff, xb, &rs);
+      int32_t rr = r - b.r0;
+      int32_t re = b.staged ? s_woff[rr + 1] : (int32_t)woff[r + 1];
+      int32_t q = rseg[r], pst = pstart[r], slot = pslot[r];
 #pragma unroll
-    for (int j = 0; j < kItemsPerThread; ++j) {
-      const int32_t x = x0 + j * B + threadIdx.x;
-      bool ok = false;
-      int32_t q = -1, last = 0;
-      if (x < x1) {
-        int32_t rs;
-        const int32_t r = b_row(b, s_woff, woff, x, &rs);
-        q = rseg[r];
+      for (int j = 0; j < kItemsPerThread; ++j) {
+        const int32_t x = xb + j;
+        if (x >= x1) break;
+        while (x >= re) {
+          ++rr;
+          ++r;
+          rs = re;
+          re = b.staged ? s_woff[rr + 1] : (int32_t)woff[r + 1];
+          q = rseg[r];
+          pst = pstart[r];
+          slot = pslot[r];
+        }
         const BatchLevel &L = qs[q].lv[i];
-        last = L.last;
-        const int32_t w = __ldg(g.col + pstart[r] + (x - rs));
-        ok = bm_has(L.bitmap, w);
+        const int32_t w = __ldg(g.col + pst + (x - rs));
+        bool ok = bm_has(L.bitmap, w);
         for (int u = 0; ok && u < L.ninj; ++u) ok = F[L.inj[u] * R + r] != w;
-        const int slot = pslot[r];
         for (int c = 0; ok && c < L.nb; ++c) {
           if (c == slot) continue;
           const int32_t y = F[L.bpos[c] * R + r];
           ok = row_has(g.col, __ldg(g.rp + y), __ldg(g.rp + y + 1), w);
         }
-      }
-      // last-level survivors: one atomic per query per warp
-      const int32_t key = (ok && last) ? q : -1;
-      const uint32_t peers = __match_any_sync(kFull, key);
-      if (key >= 0 && lane == __ffs(peers) - 1)
-        atomicAdd(counts + key, (unsigned long long)__popc(peers));
-      const uint32_t m = __ballot_sync(kFull, ok && !last);
-      if (lane == 0) {
-        masks[(x0 + j * B) / 32 + warp] = m;
-        cnt += __popc(m);
+        if (ok) {
+          if (L.last)
+            qj[j] = q;
+          else
+            bits |= 1u << j;
+        }
       }
     }
+    // last-level survivors: one atomic per query per warp and item slot
+#pragma unroll
+    for (int j = 0; j < kItemsPerThread; ++j) {
+      const uint32_t peers = __match_any_sync(kFull, qj[j]);
+      if (qj[j] >= 0 && lane == __ffs(peers) - 1)
+        atomicAdd(counts + qj[j], (unsigned long long)__popc(peers));
+    }
+    uint32_t word = bits << (4 * (lane & 7));
+    word |= __shfl_xor_sync(kFull, word, 1);
+    word |= __shfl_xor_sync(kFull, word, 2);
+    word |= __shfl_xor_sync(kFull, word, 4);
+    int32_t cnt = 0;
+    if ((lane & 7) == 0) {
+      masks[(x0 + warp * 128) / 32 + (lane >> 3)] = word;
+      cnt = __popc(word);
+    }
+    cnt = __reduce_add_sync(kFull, cnt);
     if (lane == 0 && cnt) atomicAdd(&s_count, cnt);
     __syncthreads();
     if (threadIdx.x == 0) tile_cnt[t] = s_count;

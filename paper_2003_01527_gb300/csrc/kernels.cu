@@ -336,6 +336,12 @@ __device__ __forceinline__ bool check_candidate(const GraphDev &g, const LevelDe
   return true;
 }
 
+// Verification pass.  Thread t of a tile takes the kItemsPerThread consecutive
+// candidates 4t .. 4t+3: one row search serves all of them (rows change inside
+// the group only at a row boundary), and the warp's 128 candidates are
+// consecutive, so its candidate loads cover contiguous bytes.  The survivor
+// bits stay in candidate order: each lane's 4-bit group is shifted into place
+// and OR-ed across the 8 lanes that share a 32-bit mask word.
 template <bool kMasks>
 __global__ void __launch_bounds__(1024) k_extend_count(
     GraphDev g, LevelDesc d, const int32_t *__restrict__ F, int32_t ld,
@@ -343,6 +349,7 @@ __global__ void __launch_bounds__(1024) k_extend_count(
     const int64_t *__restrict__ woff, const int32_t *__restrict__ tile_row, int64_t wa,
     int32_t W, uint32_t *__restrict__ masks, int32_t *__restrict__ tile_cnt,
     unsigned long long *__restrict__ total) {
+  static_assert(kItemsPerThread == 4, "one 4-bit group per lane");
   extern __shared__ int32_t s_woff[];
   __shared__ int32_t s_count;
   const int32_t B = blockDim.x;
@@ -352,23 +359,40 @@ __global__ void __launch_bounds__(1024) k_extend_count(
   if (threadIdx.x == 0) s_count = 0;
   const TileRows t = stage_rows(woff, tile_row, wa, tile_items, s_woff);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int32_t cnt = 0;
+  const int32_t xb = x0 + warp * 128 + lane * kItemsPerThread;
+  uint32_t bits = 0;
+  if (xb < x1) {
+    int32_t rs;
+    int32_t r = item_row(t, s_woff, woff, wa, xb, &rs);
+    int32_t rr = r - t.r0;
+    int32_t re = t.staged ? s_woff[rr + 1] : (int32_t)(woff[r + 1] - wa);
+    int32_t pst = pstart[r], slot = pslot[r];
 #pragma unroll
-  for (int j = 0; j < kItemsPerThread; ++j) {
-    const int32_t x = x0 + j * B + threadIdx.x;
-    bool ok = false;
-    if (x < x1) {
-      int32_t rs;
-      const int32_t r = item_row(t, s_woff, woff, wa, x, &rs);
-      const int32_t w = __ldg(g.col + pstart[r] + (x - rs));
-      ok = check_candidate(g, d, F, ld, r, w, pslot[r]);
-    }
-    const uint32_t m = __ballot_sync(kFull, ok);
-    if (lane == 0) {
-      if (kMasks) masks[(x0 + j * B) / 32 + warp] = m;
-      cnt += __popc(m);
+    for (int j = 0; j < kItemsPerThread; ++j) {
+      const int32_t x = xb + j;
+      if (x >= x1) break;
+      while (x >= re) {  // next row (rows without work are skipped)
+        ++rr;
+        ++r;
+        rs = re;
+        re = t.staged ? s_woff[rr + 1] : (int32_t)(woff[r + 1] - wa);
+        pst = pstart[r];
+        slot = pslot[r];
+      }
+      const int32_t w = __ldg(g.col + pst + (x - rs));
+      if (check_candidate(g, d, F, ld, r, w, slot)) bits |= 1u << j;
     }
   }
+  uint32_t word = bits << (4 * (lane & 7));
+  word |= __shfl_xor_sync(kFull, word, 1);
+  word |= __shfl_xor_sync(kFull, word, 2);
+  word |= __shfl_xor_sync(kFull, word, 4);
+  int32_t cnt = 0;
+  if ((lane & 7) == 0) {
+    if (kMasks) masks[(x0 + warp * 128) / 32 + (lane >> 3)] = word;
+    cnt = __popc(word);
+  }
+  cnt = __reduce_add_sync(kFull, cnt);
   if (lane == 0 && cnt) atomicAdd(&s_count, cnt);
   __syncthreads();
   if (threadIdx.x == 0) {

@@ -125,4 +125,14 @@ int launch_sort_rows(int32_t *a, int64_t lda, int32_t *b, int64_t ldb, int64_t N
                      int32_t bits, bool presorted, int32_t *hist, int64_t *hist_off, int64_t *tmp,
                      cudaStream_t s, int *launches);
 
+// Same result through packed keys: each row becomes a k*bits-bit integer of
+// packed_words(k, bits) 64-bit words (keys_a / keys_b: N words each per word
+// index), sorted by byte digits, and the last pass writes the rows row-major
+// into `out` (N x k, may alias `a` once packing has read it).  Returns the
+// number of kernels launched.
+int32_t packed_words(int32_t k, int32_t bits);
+int launch_sort_rows_packed(const int32_t *a, int64_t lda, int64_t N, int32_t k, int32_t bits,
+                            uint64_t *keys_a, uint64_t *keys_b, int32_t *out, int32_t *hist,
+                            int64_t *hist_off, int64_t *tmp, cudaStream_t s);
+
 }  // namespace gsm
