@@ -60,6 +60,9 @@ def _load():
                                          ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p]
             lib.oracle_match.restype = ctypes.c_int
             lib.oracle_max_threads.restype = ctypes.c_int
+            lib.oracle_refine_round.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.c_int32,
+                                                ctypes.c_int32, i32p, i32p, u8p, u8p]
+            lib.oracle_refine_round.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -85,6 +88,19 @@ def candidates(g, q) -> np.ndarray:
     if rc != OK:
         raise ValueError(f"oracle_candidates failed: {rc}")
     return out
+
+
+def refine(g, q, cand: np.ndarray, rounds: int) -> np.ndarray:
+    """`rounds` rounds of candidate refinement applied to uint8[k, n] sets."""
+    cur = np.ascontiguousarray(cand, dtype=np.uint8)
+    for _ in range(rounds):
+        nxt = np.zeros_like(cur)
+        rc = _load().oracle_refine_round(g.n, g.row_ptr, g.col, q.k, q.m, _edges(q),
+                                         np.ascontiguousarray(q.labels, dtype=np.int32), cur, nxt)
+        if rc != OK:
+            raise ValueError(f"oracle_refine_round failed: {rc}")
+        cur = nxt
+    return cur
 
 
 def max_threads() -> int:

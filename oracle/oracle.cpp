@@ -133,6 +133,46 @@ int oracle_candidates(int32_t n, const int32_t* rp, const int32_t* col, const in
   return OR_OK;
 }
 
+// One round of candidate refinement (the repeated local pruning of Sec. 3.2,
+// "after each iteration of pruning, NE and degree information of the data
+// graph is updated"), in per-label form: v stays a candidate of u iff it was
+// one and, for every label l, v has at least as many neighbours in the union
+// of the candidate sets of u's query neighbours with label l as u has such
+// query neighbours.  cand_in / cand_out: uint8[k * n] (u-major); they may not
+// alias.
+int oracle_refine_round(int32_t n, const int32_t* rp, const int32_t* col, int32_t k, int32_t m,
+                        const int32_t* edges, const int32_t* qlab, const uint8_t* cand_in,
+                        uint8_t* cand_out) {
+  if (oracle_validate_query(k, m, edges) != OR_OK) return OR_INVALID_QUERY;
+  bool adj[16][16] = {};
+  for (int32_t e = 0; e < m; ++e) {
+    adj[edges[2 * e]][edges[2 * e + 1]] = true;
+    adj[edges[2 * e + 1]][edges[2 * e]] = true;
+  }
+  for (int32_t u = 0; u < k; ++u) {
+    // query neighbours of u grouped by label
+    std::map<int32_t, std::vector<int32_t>> groups;
+    for (int32_t w = 0; w < k; ++w)
+      if (adj[u][w]) groups[qlab[w]].push_back(w);
+    for (int32_t v = 0; v < n; ++v) {
+      bool keep = cand_in[(int64_t)u * n + v] != 0;
+      for (auto& gr : groups) {
+        if (!keep) break;
+        int64_t have = 0;
+        for (int64_t e = rp[v]; e < rp[v + 1]; ++e) {
+          const int32_t x = col[e];
+          bool in_union = false;
+          for (int32_t w : gr.second) in_union = in_union || cand_in[(int64_t)w * n + x] != 0;
+          if (in_union) ++have;
+        }
+        if (have < (int64_t)gr.second.size()) keep = false;
+      }
+      cand_out[(int64_t)u * n + v] = keep ? 1 : 0;
+    }
+  }
+  return OR_OK;
+}
+
 struct Search {
   const int32_t* rp;
   const int32_t* col;

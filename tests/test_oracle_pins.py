@@ -252,6 +252,34 @@ def test_candidates_hand_example(oracle_lib):
     assert c2[0].tolist() == [1, 0, 0, 0, 1]
 
 
+@pytest.mark.parametrize("seed", range(2))
+def test_refinement_is_sound_and_monotone(oracle_lib, seed):
+    """Refined candidate sets only shrink, and keep every vertex that some
+    embedding uses (brute force)."""
+    for g, q in tiny_cases(40, 400 + seed):
+        c0 = oracle.candidates(g, q)
+        c1 = oracle.refine(g, q, c0, 1)
+        c3 = oracle.refine(g, q, c0, 3)
+        assert (c1 <= c0).all() and (c3 <= c1).all()
+        for f in brute.embeddings(g, q):
+            for u, v in enumerate(f):
+                assert c3[u, v] == 1
+
+
+def test_refinement_hand_example(oracle_lib):
+    # query: a label-0 vertex joined to a label-1 vertex that has a label-2
+    # neighbour.  Data: v0(0)-v1(1), v1-v2(2), and v3(0)-v4(1) where v4 has
+    # a second neighbour v5 of label 0 but no label-2 neighbour.
+    g = I.graph_from_edges(6, [(0, 1), (1, 2), (3, 4), (4, 5)], [0, 1, 2, 0, 1, 0])
+    q = I.query_from_edges(3, [(0, 1), (1, 2)], [0, 1, 2])
+    c0 = oracle.candidates(g, q)
+    assert c0[1].tolist() == [0, 1, 0, 0, 0, 0]  # v4 lacks a label-2 neighbour
+    assert c0[0].tolist() == [1, 0, 0, 1, 0, 1]  # the first pass keeps v3, v5
+    c1 = oracle.refine(g, q, c0, 1)
+    assert c1[0].tolist() == [1, 0, 0, 0, 0, 0]  # v3, v5 have no candidate neighbour for u1
+    assert c1[1].tolist() == [0, 1, 0, 0, 0, 0]
+
+
 def test_validity_checks(oracle_lib):
     ok = I.graph_from_edges(3, [(0, 1), (1, 2)])
     assert oracle.validate_graph(ok) == oracle.OK
