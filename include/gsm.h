@@ -75,7 +75,12 @@ typedef struct gsm_options {
   void *alloc_ctx;
   int32_t block_size;     /* threads per CTA of the extend kernels; 0 = 256; 128..1024, x32 */
   int64_t chunk_rows;     /* max frontier rows per extend launch; 0 = from the budget */
-  int32_t filter_rounds;  /* extra candidate-refinement rounds (Sec. 3.2); 0 = one pass */
+  /* Candidate-refinement rounds after the first filter pass (Sec. 3.2, 0..64):
+   * a round keeps v in C(u) iff, for every label l, v has at least as many
+   * neighbours in the union of the candidate sets of u's label-l query
+   * neighbours as u has such neighbours.  Results do not depend on it;
+   * gsm_candidates returns the refined sets.  The batched form ignores it. */
+  int32_t filter_rounds;
   int32_t flags;          /* GSM_OPT_* */
 } gsm_options;
 

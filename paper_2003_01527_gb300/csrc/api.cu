@@ -83,6 +83,8 @@ struct gsm_ctx {
   // query-lifetime buffers (outside the budget)
   void *bitmaps = nullptr;
   size_t bitmaps_cap = 0;
+  void *bitmaps2 = nullptr;  // second buffer of the refinement rounds
+  size_t bitmaps2_cap = 0;
   unsigned long long *d_small = nullptr;  // [0..15] sizes, [16] total, [17] err
   void *acc[2] = {nullptr, nullptr};
   size_t acc_cap[2] = {0, 0};
@@ -677,7 +679,9 @@ bool dense_labels(gsm_ctx *ctx, const gsm_query *q, int32_t *dense) {
   return true;
 }
 
-// Filtering step: fills the k candidate bitmaps and returns |C(u)|.
+// Filtering step: fills the k candidate bitmaps and returns |C(u)|; then
+// opt.filter_rounds refinement rounds (double-buffered, so every round reads
+// the previous round's sets only).
 void run_filter(gsm_ctx *ctx, const gsm_query *q, const int32_t *dense, uint64_t *sizes) {
   FilterDesc fd;
   fill_filter(ctx, q, dense, fd);
@@ -688,6 +692,33 @@ void run_filter(gsm_ctx *ctx, const gsm_query *q, const int32_t *dense, uint64_t
   timed(ctx, K_FILTER, 12.0 * ctx->n + bytes, (uint64_t)ctx->n, 1, [&] {
     launch_filter(g, fd, (uint32_t *)ctx->bitmaps, ctx->d_small, ctx->stream);
   });
+  const int32_t rounds = std::max<int32_t>(0, ctx->opt.filter_rounds);
+  if (rounds > 0 && q->k > 1) {
+    RefineDesc rd;
+    std::memset(&rd, 0, sizeof(rd));
+    rd.k = q->k;
+    rd.n_words = fd.n_words;
+    for (int32_t u = 0; u < q->k; ++u) {
+      for (int32_t w = 0; w < q->k; ++w) {
+        if (!(q->adj[u] >> w & 1u)) continue;
+        int32_t gi = 0;
+        while (gi < rd.ngroups[u] && dense[__builtin_ctz(rd.group_mask[u][gi])] != dense[w]) ++gi;
+        if (gi == rd.ngroups[u]) rd.ngroups[u]++;
+        rd.group_mask[u][gi] |= 1u << w;
+        rd.group_need[u][gi]++;
+      }
+    }
+    ensure_buf(ctx, &ctx->bitmaps2, &ctx->bitmaps2_cap, bytes, false, 0);
+    for (int32_t r = 0; r < rounds; ++r) {
+      CU(cudaMemsetAsync(ctx->d_small, 0, sizeof(unsigned long long) * kMaxK, ctx->stream));
+      timed(ctx, K_FILTER, 4.0 * ctx->nnz + 2.0 * bytes, (uint64_t)ctx->n, 1, [&] {
+        launch_refine(g, rd, (const uint32_t *)ctx->bitmaps, (uint32_t *)ctx->bitmaps2,
+                      ctx->d_small, ctx->stream);
+      });
+      std::swap(ctx->bitmaps, ctx->bitmaps2);
+      std::swap(ctx->bitmaps_cap, ctx->bitmaps2_cap);
+    }
+  }
   CU(cudaMemcpyAsync(ctx->h_stage, ctx->d_small, sizeof(uint64_t) * q->k, cudaMemcpyDeviceToHost,
                      ctx->stream));
   CU(cudaStreamSynchronize(ctx->stream));
@@ -1473,7 +1504,8 @@ gsm_status gsm_create(gsm_ctx **out, int32_t device, const gsm_options *opt) {
   if (opt && opt->block_size != 0 &&
       (opt->block_size < 128 || opt->block_size > 1024 || opt->block_size % 32))
     return GSM_ERR_INVALID_ARG;
-  if (opt && opt->chunk_rows < 0) return GSM_ERR_INVALID_ARG;
+  if (opt && (opt->chunk_rows < 0 || opt->filter_rounds < 0 || opt->filter_rounds > 64))
+    return GSM_ERR_INVALID_ARG;
   gsm_ctx *ctx = new gsm_ctx();
   if (opt) ctx->opt = *opt;
   ctx->device = device;
@@ -1514,6 +1546,7 @@ void gsm_destroy(gsm_ctx *ctx) {
     for (auto &b : ctx->blocks) dev_free(ctx, b.ptr, b.cap);
     dev_free(ctx, ctx->scratch, ctx->scratch_cap);
     dev_free(ctx, ctx->bitmaps, ctx->bitmaps_cap);
+    dev_free(ctx, ctx->bitmaps2, ctx->bitmaps2_cap);
     dev_free(ctx, ctx->acc[0], ctx->acc_cap[0]);
     dev_free(ctx, ctx->acc[1], ctx->acc_cap[1]);
     dev_free(ctx, ctx->sort_tmp, ctx->sort_tmp_cap);

@@ -104,6 +104,67 @@ __global__ void __launch_bounds__(256) k_filter(GraphDev g, FilterDesc d,
                ((int64_t)gridDim.x * blockDim.x) >> 5);
 }
 
+// ------------------------------------------------------------ refinement
+
+// One warp per (query vertex u, word of 32 data vertices).  Each candidate v
+// of the word is scanned by the whole warp 256 neighbours at a time; a lane
+// counts, per label group, neighbours in the union of the group's candidate
+// sets, and the scan stops once every group has enough.
+__global__ void __launch_bounds__(256) k_refine(GraphDev g, RefineDesc d,
+                                                const uint32_t *__restrict__ bm_in,
+                                                uint32_t *__restrict__ bm_out,
+                                                unsigned long long *__restrict__ sizes) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp_id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t total = (int64_t)d.k * d.n_words;
+  for (int64_t item = warp_id; item < total; item += n_warps) {
+    const int32_t u = (int32_t)(item / d.n_words);
+    const int64_t grp = item % d.n_words;
+    uint32_t word = bm_in[(int64_t)u * d.n_words + grp];
+    uint32_t out = word;
+    const int ng = d.ngroups[u];
+    if (ng > 0) {
+      uint32_t todo = word;
+      while (todo) {
+        const int bit = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int32_t v = (int32_t)(grp * 32 + bit);
+        const int32_t b = g.rp[v], e = g.rp[v + 1];
+        int32_t cnt[kMaxK];
+#pragma unroll
+        for (int x = 0; x < kMaxK; ++x) cnt[x] = 0;
+        bool pass = false;
+        for (int32_t base = b; base < e && !pass; base += 256) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int32_t idx = base + j * 32 + lane;
+            if (idx < e) {
+              const int32_t w = __ldg(g.col + idx);
+              uint32_t in = 0;  // query vertices whose candidate set holds w
+              for (int uu = 0; uu < d.k; ++uu)
+                in |= ((__ldg(bm_in + (int64_t)uu * d.n_words + (w >> 5)) >> (w & 31)) & 1u) << uu;
+#pragma unroll
+              for (int x = 0; x < kMaxK; ++x)
+                if (x < ng && (in & d.group_mask[u][x])) ++cnt[x];
+            }
+          }
+          bool all = true;
+#pragma unroll
+          for (int x = 0; x < kMaxK; ++x)
+            if (x < ng) all = all && __reduce_add_sync(kFull, cnt[x]) >= d.group_need[u][x];
+          pass = all;  // warp-uniform
+        }
+        if (!pass) out &= ~(1u << bit);
+      }
+    }
+    if (lane == 0) {
+      bm_out[(int64_t)u * d.n_words + grp] = out;
+      if (out) atomicAdd(sizes + u, (unsigned long long)__popc(out));
+    }
+  }
+}
+
 // ------------------------------------------------------------ scans
 
 __device__ __forceinline__ int64_t warp_incl_scan(int64_t x, int lane) {
@@ -519,6 +580,12 @@ void launch_filter(const GraphDev &g, const FilterDesc &d, uint32_t *bitmaps,
   int64_t warps_needed = d.n_words;
   int blocks = grid_for(warps_needed * 32, threads, 152 * 16);
   k_filter<<<blocks, threads, 0, s>>>(g, d, bitmaps, sizes);
+}
+
+void launch_refine(const GraphDev &g, const RefineDesc &d, const uint32_t *bm_in,
+                   uint32_t *bm_out, unsigned long long *sizes, cudaStream_t s) {
+  const int64_t warps = (int64_t)d.k * d.n_words;
+  k_refine<<<grid_for(warps * 32, 256, 152 * 16), 256, 0, s>>>(g, d, bm_in, bm_out, sizes);
 }
 
 int64_t scan_tmp_elems(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }

@@ -61,6 +61,21 @@ void launch_validate_rows(const GraphDev &g, int32_t *err, cudaStream_t s);
 void launch_filter(const GraphDev &g, const FilterDesc &d, uint32_t *bitmaps,
                    unsigned long long *sizes, cudaStream_t s);
 
+// One refinement round (Sec. 3.2 repeated pruning): v stays in C(u) iff it
+// was there and, for every label group of u's query neighbours, v has at least
+// as many neighbours in the union of the group's candidate sets as the group
+// has members.  Reads bm_in, writes bm_out (k bitmaps each), adds the new
+// |C(u)| into sizes[u].
+struct RefineDesc {
+  int32_t k;
+  int32_t n_words;
+  int32_t ngroups[kMaxK];
+  uint32_t group_mask[kMaxK][kMaxK];  // query neighbours of u in group g
+  int32_t group_need[kMaxK][kMaxK];   // their number
+};
+void launch_refine(const GraphDev &g, const RefineDesc &d, const uint32_t *bm_in,
+                   uint32_t *bm_out, unsigned long long *sizes, cudaStream_t s);
+
 // Exclusive scan: out[0..n] with out[n] = total.  tmp needs scan_tmp_elems(n)
 // int64 elements.  The int64 form may run in place (in == out).
 int64_t scan_tmp_elems(int64_t n);

@@ -353,7 +353,7 @@ class Matcher:
 
     def __init__(self, device: int = 0, mem_budget_bytes: int = 0, stream=None,
                  block_size: int = 0, chunk_rows: int = 0, time_kernels: bool = False,
-                 torch_allocator: bool = True):
+                 torch_allocator: bool = True, filter_rounds: int = 0):
         import torch
         self.device = device
         opt = gsm_default_options()
@@ -367,6 +367,7 @@ class Matcher:
                                      else int(stream))
         opt.block_size = block_size
         opt.chunk_rows = chunk_rows
+        opt.filter_rounds = filter_rounds
         opt.flags = GSM_OPT_TIME_KERNELS if time_kernels else 0
         if torch_allocator:
             dev = device

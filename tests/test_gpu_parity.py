@@ -317,3 +317,26 @@ def test_power_law_workload_full_size(M):
         assert digest == item["rows_sha256"]
         nonzero += count > 0
     assert nonzero >= 10
+
+
+def test_refined_candidates_match_oracle_and_results_do_not_change(gsm_lib, rmat12):
+    rng = np.random.default_rng(28)
+    qs = [I.random_walk_query(rmat12, int(rng.integers(3, 9)), rng) for _ in range(8)]
+    sel = selective_walk_queries(rmat12, 4, 4, 7, seed=29)
+    base = {}
+    for rounds in (0, 1, 2):
+        m = gsm_lib.Matcher(device=0, filter_rounds=rounds)
+        load(m, rmat12, validate=False)
+        for j, q in enumerate(qs):
+            bm, sizes = m.candidates(m.query(q.k, q.edges, q.labels))
+            got = gsm_lib.unpack_bitmaps(bm, rmat12.n)
+            want = oracle.refine(rmat12, q, oracle.candidates(rmat12, q), rounds)
+            assert np.array_equal(got, want), (rounds, j)
+            assert sizes.tolist() == want.sum(axis=1).tolist()
+        for j, q in enumerate(sel):
+            rows, count = m.enumerate(m.query(q.k, q.edges, q.labels))
+            if rounds == 0:
+                base[j] = (count, rows)
+            else:
+                assert count == base[j][0] and np.array_equal(rows, base[j][1])
+        m.close()
