@@ -142,6 +142,15 @@ gsm_status gsm_query_restrict(gsm_query *q, int32_t u, int32_t lo, int32_t hi);
  * GSM_ERR_CUDA. */
 gsm_status gsm_count(gsm_ctx *ctx, const gsm_query *q, uint64_t *count);
 
+/* Counts distinct subgraphs: embeddings up to the automorphisms of the
+ * labelled query (the paper's own count |M|/|Q| in Algorithm 1, obtained as
+ * Sec. 3.1 proposes, by node-ID ordering constraints between equivalent query
+ * vertices, so each subgraph is produced once).  *count = gsm_count(q) /
+ * |Aut(Q)|; *automorphisms (may be NULL) receives |Aut(Q)|.  The query must
+ * not be restricted.  Errors: as gsm_count, plus GSM_ERR_INVALID_ARG. */
+gsm_status gsm_count_distinct(gsm_ctx *ctx, const gsm_query *q, uint64_t *count,
+                              uint64_t *automorphisms);
+
 #define GSM_OUT_DEVICE 1 /* `out` is a device pointer */
 
 /* Lists the embeddings of q: out is int32[cap_rows * k], row-major, rows in

@@ -4,6 +4,7 @@
 // frontier chunks so intermediate results stay inside a fixed budget.
 #include <algorithm>
 #include <array>
+#include <functional>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -456,6 +457,92 @@ gsm_status validate_query_edges(int32_t k, int32_t m, const int32_t *edges, uint
   return seen == ((k == 32) ? 0xffffffffu : ((1u << k) - 1u)) ? GSM_OK : GSM_ERR_INVALID_QUERY;
 }
 
+// ------------------------------------------------------------------ symmetry
+
+// Is there an automorphism of the labelled query (a label-preserving
+// permutation that maps edges to edges and non-edges to non-edges) with
+// sigma(x) = x for every x in `fixed` and sigma(a) = b?  Backtracking over
+// query vertices in id order.
+bool aut_exists(int32_t k, const uint32_t *adj, const int32_t *lab, uint32_t fixed, int32_t a,
+                int32_t b) {
+  int32_t sigma[kMaxK];
+  for (int32_t u = 0; u < k; ++u) sigma[u] = -1;
+  for (int32_t u = 0; u < k; ++u)
+    if (fixed >> u & 1u) sigma[u] = u;
+  if (sigma[a] >= 0 && sigma[a] != b) return false;
+  sigma[a] = b;
+  uint32_t used = 0;
+  for (int32_t u = 0; u < k; ++u)
+    if (sigma[u] >= 0) {
+      if (used >> sigma[u] & 1u) return false;
+      used |= 1u << sigma[u];
+    }
+  // consistency of the preassigned part
+  for (int32_t u = 0; u < k; ++u)
+    for (int32_t v = 0; v < k; ++v)
+      if (sigma[u] >= 0 && sigma[v] >= 0 &&
+          ((adj[u] >> v & 1u) != (adj[sigma[u]] >> sigma[v] & 1u)))
+        return false;
+  for (int32_t u = 0; u < k; ++u)
+    if (sigma[u] >= 0 && (lab[u] != lab[sigma[u]] || popc(adj[u]) != popc(adj[sigma[u]])))
+      return false;
+  // extend to the free vertices
+  int32_t freev[kMaxK], nf = 0;
+  for (int32_t u = 0; u < k; ++u)
+    if (sigma[u] < 0) freev[nf++] = u;
+  std::function<bool(int32_t)> go = [&](int32_t t) -> bool {
+    if (t == nf) return true;
+    const int32_t u = freev[t];
+    for (int32_t v = 0; v < k; ++v) {
+      if (used >> v & 1u) continue;
+      if (lab[v] != lab[u] || popc(adj[v]) != popc(adj[u])) continue;
+      bool ok = true;
+      for (int32_t x = 0; x < k && ok; ++x)
+        if (sigma[x] >= 0 && ((adj[u] >> x & 1u) != (adj[v] >> sigma[x] & 1u))) ok = false;
+      if (!ok) continue;
+      sigma[u] = v;
+      used |= 1u << v;
+      if (go(t + 1)) return true;
+      sigma[u] = -1;
+      used &= ~(1u << v);
+    }
+    return false;
+  };
+  return go(0);
+}
+
+// Ordering constraints that keep exactly one embedding per orbit of Aut(Q)
+// (the node-ID ordering of equivalent query vertices the paper proposes,
+// Sec. 3.1, built along a stabilizer chain): repeatedly take the lowest-id
+// vertex u whose orbit under the automorphisms fixing the vertices chosen so
+// far is non-trivial, require f(u) < f(v) for every other v of that orbit,
+// and fix u.  |Aut(Q)| is the product of the orbit sizes.
+uint64_t symmetry_constraints(int32_t k, const uint32_t *adj, const int32_t *lab,
+                              std::vector<std::pair<int32_t, int32_t>> *less) {
+  uint32_t fixed = 0;
+  uint64_t order = 1;
+  for (;;) {
+    int32_t pick = -1;
+    std::vector<int32_t> orbit;
+    for (int32_t u = 0; u < k && pick < 0; ++u) {
+      if (fixed >> u & 1u) continue;
+      std::vector<int32_t> o{u};
+      for (int32_t v = 0; v < k; ++v)
+        if (v != u && !(fixed >> v & 1u) && aut_exists(k, adj, lab, fixed, u, v)) o.push_back(v);
+      if (o.size() > 1) {
+        pick = u;
+        orbit = o;
+      }
+    }
+    if (pick < 0) break;
+    for (int32_t v : orbit)
+      if (v != pick) less->push_back({pick, v});
+    order *= orbit.size();
+    fixed |= 1u << pick;
+  }
+  return order;
+}
+
 // ------------------------------------------------------------------ driver
 
 struct Run {
@@ -727,7 +814,8 @@ void run_filter(gsm_ctx *ctx, const gsm_query *q, const int32_t *dense, uint64_t
 
 // The whole matcher for one query.  out == nullptr and !enumerate: count only.
 void run_query(gsm_ctx *ctx, const gsm_query *q, bool enumerate, int32_t *out, uint64_t cap_rows,
-               int32_t flags, uint64_t *count_out, bool *truncated) {
+               int32_t flags, uint64_t *count_out, bool *truncated,
+               const std::vector<std::pair<int32_t, int32_t>> *less = nullptr) {
   if (!ctx->has_graph) FAIL(GSM_ERR_NO_GRAPH, "no data graph loaded");
   std::memset(&ctx->run, 0, sizeof(ctx->run));
   // nothing is live between calls (an earlier call may have failed mid-way)
@@ -781,6 +869,15 @@ void run_query(gsm_ctx *ctx, const gsm_query *q, bool enumerate, int32_t *out, u
     }
     for (int32_t j = 0; j <= i; ++j) d.out_col[j] = (i == q->k - 1) ? R.order[j] : j;
     d.bitmap = bm + (size_t)u * nw;
+    if (less) {
+      // ordering constraints between pi_i and vertices placed before it
+      for (const auto &c : *less) {
+        for (int32_t j = 0; j < i; ++j) {
+          if (c.first == u && c.second == R.order[j]) d.lt[d.nlt++] = j;   // f(u) < f(pi_j)
+          if (c.second == u && c.first == R.order[j]) d.gt[d.ngt++] = j;   // f(pi_j) < f(u)
+        }
+      }
+    }
   }
 
   CU(cudaMemsetAsync(R.d_total, 0, sizeof(unsigned long long), ctx->stream));
@@ -1760,6 +1857,26 @@ gsm_status gsm_candidates(gsm_ctx *ctx, const gsm_query *q, uint32_t *bitmaps, u
       CU(cudaStreamSynchronize(ctx->stream));
     }
     resolve_timings(ctx);
+  });
+}
+
+gsm_status gsm_count_distinct(gsm_ctx *ctx, const gsm_query *q, uint64_t *count,
+                              uint64_t *automorphisms) {
+  if (!ctx || !q || !count) return GSM_ERR_INVALID_ARG;
+  for (int32_t u = 0; u < q->k; ++u)
+    if (q->lo[u] != 0 || q->hi[u] != 0x7fffffff) {
+      set_err(ctx, "distinct counting needs an unrestricted query");
+      return GSM_ERR_INVALID_ARG;
+    }
+  return guarded(ctx, [&] {
+    CU(cudaSetDevice(ctx->device));
+    std::vector<std::pair<int32_t, int32_t>> less;
+    const uint64_t aut = symmetry_constraints(q->k, q->adj, q->labels, &less);
+    bool trunc = false;
+    run_query(ctx, q, false, nullptr, 0, 0, count, &trunc, &less);
+    if (automorphisms) *automorphisms = aut;
+    resolve_timings(ctx);
+    ctx->run.peak_bytes = ctx->peak_bytes;
   });
 }
 

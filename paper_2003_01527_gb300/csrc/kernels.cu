@@ -389,6 +389,10 @@ __device__ __forceinline__ bool check_candidate(const GraphDev &g, const LevelDe
   if (!bitmap_has(d.bitmap, w)) return false;
   for (int t = 0; t < d.ninj; ++t)
     if (F[d.inj[t] * ld + r] == w) return false;
+  for (int t = 0; t < d.nlt; ++t)
+    if (!(w < F[d.lt[t] * ld + r])) return false;
+  for (int t = 0; t < d.ngt; ++t)
+    if (!(w > F[d.gt[t] * ld + r])) return false;
   for (int b = 0; b < d.nb; ++b) {
     if (b == slot) continue;
     const int32_t x = F[d.bpos[b] * ld + r];

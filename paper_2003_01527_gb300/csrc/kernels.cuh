@@ -39,6 +39,8 @@ struct LevelDesc {
   int32_t inj[kMaxK];
   int32_t out_col[kMaxK + 1]; // output column of position j (0..i); identity except last level
   const uint32_t *bitmap;     // C(pi_i)
+  int32_t nlt, lt[kMaxK];     // symmetry breaking: the new vertex must be < row[lt[t]]
+  int32_t ngt, gt[kMaxK];     //                     and > row[gt[t]]
 };
 
 struct GraphDev {

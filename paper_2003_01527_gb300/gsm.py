@@ -47,7 +47,7 @@ EXPORTED = [
     "gsm_load_graph", "gsm_query_create", "gsm_query_destroy", "gsm_query_restrict", "gsm_count",
     "gsm_enumerate", "gsm_last_rows", "gsm_candidates", "gsm_plan_order", "gsm_kernel_stats",
     "gsm_last_run_stats", "gsm_candidates_static", "gsm_run_batch", "gsm_batch_get_stats",
-    "gsm_batch_configure", "gsm_server_start", "gsm_submit", "gsm_poll", "gsm_server_stop",
+    "gsm_batch_configure", "gsm_count_distinct", "gsm_server_start", "gsm_submit", "gsm_poll", "gsm_server_stop",
 ]
 GSM_BATCH_AUTOTUNE = 1
 GSM_STATIC_SCRATCH_BITMAP_BYTES = 8 << 20
@@ -108,6 +108,7 @@ def _load():
         "gsm_query_destroy": (None, [vp]),
         "gsm_query_restrict": (i32, [vp, i32, i32, i32]),
         "gsm_count": (i32, [vp, vp, ctypes.POINTER(u64)]),
+        "gsm_count_distinct": (i32, [vp, vp, ctypes.POINTER(u64), ctypes.POINTER(u64)]),
         "gsm_enumerate": (i32, [vp, vp, vp, u64, ctypes.POINTER(u64), i32]),
         "gsm_last_rows": (i32, [vp, vp, u64, u64, i32]),
         "gsm_candidates": (i32, [vp, vp, vp, vp]),
@@ -212,6 +213,13 @@ def gsm_count(ctx: int, q: int) -> int:
     c = ctypes.c_uint64()
     _check(ctx, _lib.gsm_count(ctx, q, ctypes.byref(c)))
     return c.value
+
+
+def gsm_count_distinct(ctx: int, q: int) -> tuple[int, int]:
+    """(distinct subgraphs, |Aut(Q)|)."""
+    c, a = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(ctx, _lib.gsm_count_distinct(ctx, q, ctypes.byref(c), ctypes.byref(a)))
+    return c.value, a.value
 
 
 def gsm_enumerate(ctx: int, q: int, out, cap_rows: int, flags: int) -> tuple[int, int]:
@@ -416,6 +424,10 @@ class Matcher:
 
     def count(self, q: Query) -> int:
         return gsm_count(self.ctx, q.handle)
+
+    def count_distinct(self, q: Query) -> tuple[int, int]:
+        """(distinct subgraphs, automorphisms of the query)."""
+        return gsm_count_distinct(self.ctx, q.handle)
 
     def enumerate(self, q: Query, cap_rows: int | None = None, out=None):
         """Returns (rows, count).  With out=None the rows come back as a numpy
