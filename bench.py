@@ -14,6 +14,11 @@ verification level with its count and write passes, sorting into canonical
 order), enumerating the sorted rows into a device buffer.  The graph is
 resident; L2 is flushed before each timed step (the graph is smaller than L2).
 
+`unlabelled_counts` (same line): on unlabelled R-MAT scale 20, the 3-path count
+(checked against sum d(d-1)), the ordered and distinct (symmetry-broken)
+triangle counts (checked: distinct x |Aut| = ordered) and the distinct
+4-clique count.
+
 `batched_vs_plain` (same line): the R-MAT scale-18 workload (16 Zipf(1.2)
 labels, 256 random-walk queries of 3-10 vertices with 2-4 non-tree edges, on
 oracle-sized root slices) counted one query per call versus as one batch (one
@@ -180,6 +185,50 @@ def batched_and_served(gsm, torch, device, serve_seconds):
     return out
 
 
+def unlabelled_counts(gsm, torch, device):
+    """Unlabelled R-MAT scale 20 (1,048,576 vertices, edge factor 16): the
+    ordered 3-path count pinned by sum d(d-1), ordered and distinct
+    (symmetry-broken) triangle counts, and the distinct 4-clique count."""
+    from paper_2003_01527_gb300 import inputs as I
+    g = I.rmat_unlabelled_graph(scale=20, seed=3)
+    d = g.degrees()
+    M = gsm.Matcher(device=device)
+    M.load_graph(g.row_ptr, g.col, g.labels)
+    s = I.unlabelled_shapes()
+    out = {"workload": "R-MAT scale 20 (1,048,576 vertices, edge factor 16), unlabelled",
+           "nnz": g.nnz}
+
+    def timed(fn):
+        fn()  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return r, (time.perf_counter() - t0) * 1e3
+
+    p3 = M.query(3, [(0, 1), (1, 2)])
+    c, ms = timed(lambda: M.count(p3))
+    if c != int((d * (d - 1)).sum()):
+        raise SystemExit("3-path count differs from sum d(d-1)")
+    out["path3"] = {"ordered": c, "ms": round(ms, 3), "embeddings_per_sec": round(c / ms * 1e3, 1)}
+    q = M.query(3, s["triangle"].edges)
+    c, ms = timed(lambda: M.count(q))
+    (dc, aut), dms = timed(lambda: M.count_distinct(q))
+    if dc * aut != c:
+        raise SystemExit("triangle: distinct x |Aut| differs from the ordered count")
+    out["triangle"] = {"ordered": c, "ordered_ms": round(ms, 3),
+                       "ordered_embeddings_per_sec": round(c / ms * 1e3, 1),
+                       "distinct": dc, "automorphisms": aut, "distinct_ms": round(dms, 3)}
+    # the ordered 4-clique count (4.1e11, about a minute) is left to the tests'
+    # scale; the distinct count does 1/24 of the work
+    q = M.query(4, s["clique4"].edges)
+    (dc, aut), dms = timed(lambda: M.count_distinct(q))
+    out["clique4"] = {"distinct": dc, "automorphisms": aut, "distinct_ms": round(dms, 3),
+                      "ordered_implied": dc * aut}
+    M.close()
+    return out
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -332,13 +381,19 @@ def run_gpu(args):
     dom = max(kstats, key=lambda s: s["total_ms"])
     peak, peak_kind = peaks()
     achieved = dom["algo_bytes"] / (dom["total_ms"] / 1e3) / 1e9 if dom["total_ms"] else 0.0
+    # DRAM bytes per launch of the dominant kernel from an ncu capture
+    # (profiles/traffic.json); null when the kernel source changed since
     traffic = None
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof):
         try:
             with open(prof) as f:
-                tr = json.load(f)
-            traffic = tr.get(dom["name"])
+                tr = json.load(f).get(dom["name"])
+            with open(os.path.join(ROOT, "paper_2003_01527_gb300", "csrc", "kernels.cu"),
+                      "rb") as f:
+                src = hashlib.sha256(f.read()).hexdigest()
+            if tr and tr.get("kernels_cu_sha256") == src:
+                traffic = tr["dram_bytes_per_launch"]
         except Exception:
             traffic = None
 
@@ -363,8 +418,10 @@ def run_gpu(args):
 
     cpu = cpu_baseline(g, queries) if (rank == 0 and world == 1 and not args.no_cpu) else None
     batched = None
+    unlabelled = None
     if not args.no_batch and not args.queries:
         batched = batched_and_served(gsm, torch, local, args.serve_seconds)
+        unlabelled = unlabelled_counts(gsm, torch, local)
 
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
@@ -389,6 +446,7 @@ def run_gpu(args):
         "clocks": clocks,
         "cpu_baseline": cpu,
         "batched_vs_plain": batched,
+        "unlabelled_counts": unlabelled,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
