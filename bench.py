@@ -292,6 +292,20 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def combine_ranks(ms_per_step, embeddings_per_step, queries, world, dist=None, device="cpu"):
+    """Whole-job figures of `world` replicas (every rank runs the same
+    workload on its own GPU; no data-path collective): the step time is the
+    maximum over ranks, throughput counts every rank's work."""
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([ms_per_step], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_per_step = float(t.item())
+    value = embeddings_per_step * world / (ms_per_step / 1e3)
+    qps = queries * world / (ms_per_step / 1e3)
+    return ms_per_step, value, qps
+
+
 def rank_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -368,14 +382,9 @@ def run_gpu(args):
     torch.cuda.synchronize()
     kstats = M.kernel_stats(reset=True)
 
-    ms_per_step = ms_total / args.steps
-    if dist:
-        t = torch.tensor([ms_per_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_per_step = float(t.item())
     per_step = embeddings / args.steps
-    value = per_step * world / (ms_per_step / 1e3)
-    qps = len(queries) * world / (ms_per_step / 1e3)
+    ms_per_step, value, qps = combine_ranks(ms_total / args.steps, per_step, len(queries), world,
+                                            dist, device="cuda")
 
     # dominant kernel and its roofline
     dom = max(kstats, key=lambda s: s["total_ms"])
