@@ -79,6 +79,7 @@ struct gsm_ctx {
   int64_t nnz = 0;
   int32_t max_deg = 0;
   int32_t *d_rp = nullptr, *d_col = nullptr, *d_lab = nullptr;
+  int32_t *d_lcol = nullptr, *d_llab = nullptr;  // rows ordered by (label, id)
   std::vector<int32_t> label_values;  // sorted distinct labels; dense id = index
 
   // query-lifetime buffers (outside the budget)
@@ -158,6 +159,12 @@ namespace {
 struct Fail {
   gsm_status code;
 };
+
+GraphDev graph_dev(const gsm_ctx *ctx) {
+  return GraphDev{ctx->n,      ctx->nnz,    ctx->d_rp,
+                  ctx->d_col,  ctx->d_lab,  ctx->d_lcol,
+                  ctx->d_llab, (int32_t)std::max<size_t>(1, ctx->label_values.size())};
+}
 
 void set_err(gsm_ctx *c, const char *fmt, ...) {
   char buf[512];
@@ -775,7 +782,7 @@ void run_filter(gsm_ctx *ctx, const gsm_query *q, const int32_t *dense, uint64_t
   const size_t bytes = (size_t)q->k * fd.n_words * sizeof(uint32_t);
   ensure_buf(ctx, &ctx->bitmaps, &ctx->bitmaps_cap, bytes, false, 0);
   CU(cudaMemsetAsync(ctx->d_small, 0, sizeof(unsigned long long) * kMaxK, ctx->stream));
-  GraphDev g{ctx->n, ctx->nnz, ctx->d_rp, ctx->d_col, ctx->d_lab};
+  GraphDev g = graph_dev(ctx);
   timed(ctx, K_FILTER, 12.0 * ctx->n + bytes, (uint64_t)ctx->n, 1, [&] {
     launch_filter(g, fd, (uint32_t *)ctx->bitmaps, ctx->d_small, ctx->stream);
   });
@@ -831,7 +838,7 @@ void run_query(gsm_ctx *ctx, const gsm_query *q, bool enumerate, int32_t *out, u
   R.q = q;
   R.enumerate = enumerate;
   R.k = q->k;
-  R.g = GraphDev{ctx->n, ctx->nnz, ctx->d_rp, ctx->d_col, ctx->d_lab};
+  R.g = graph_dev(ctx);
   R.block = ctx->opt.block_size > 0 ? ctx->opt.block_size : 256;
   R.chunk_rows = ctx->opt.chunk_rows;
   // masks take W/8 bytes and tile arrays 12 bytes per tile of scratch
@@ -869,6 +876,7 @@ void run_query(gsm_ctx *ctx, const gsm_query *q, bool enumerate, int32_t *out, u
     }
     for (int32_t j = 0; j <= i; ++j) d.out_col[j] = (i == q->k - 1) ? R.order[j] : j;
     d.bitmap = bm + (size_t)u * nw;
+    d.lab = dense[u];
     if (less) {
       // ordering constraints between pi_i and vertices placed before it
       for (const auto &c : *less) {
@@ -1002,7 +1010,10 @@ void free_graph(gsm_ctx *ctx) {
   if (ctx->d_rp) dev_free(ctx, ctx->d_rp, sizeof(int32_t) * (ctx->n + 1));
   if (ctx->d_col) dev_free(ctx, ctx->d_col, sizeof(int32_t) * std::max<int64_t>(ctx->nnz, 1));
   if (ctx->d_lab) dev_free(ctx, ctx->d_lab, sizeof(int32_t) * std::max<int32_t>(ctx->n, 1));
+  if (ctx->d_lcol) dev_free(ctx, ctx->d_lcol, sizeof(int32_t) * std::max<int64_t>(ctx->nnz, 1));
+  if (ctx->d_llab) dev_free(ctx, ctx->d_llab, sizeof(int32_t) * std::max<int64_t>(ctx->nnz, 1));
   ctx->d_rp = ctx->d_col = ctx->d_lab = nullptr;
+  ctx->d_lcol = ctx->d_llab = nullptr;
   ctx->has_graph = false;
   ctx->label_values.clear();
 }
@@ -1185,7 +1196,7 @@ cudaGraphExec_t lane_graph(gsm_ctx *ctx, Lane &L, int32_t m, int32_t kmax, int32
   a.n_words = n_words;
   a.block = block;
   a.grid = grid;
-  GraphDev g{ctx->n, ctx->nnz, ctx->d_rp, ctx->d_col, ctx->d_lab};
+  GraphDev g = graph_dev(ctx);
   cudaGraph_t graph = nullptr;
   CU(cudaStreamBeginCapture(L.stream, cudaStreamCaptureModeThreadLocal));
   const int launches = batch_enqueue(g, a, L.stream);
@@ -1271,6 +1282,7 @@ int32_t lane_prepare(gsm_ctx *ctx, Lane &L, const gsm_query *const *qs, int32_t 
           lv.inj[lv.ninj++] = j;
       }
       lv.last = i == q->k - 1;
+      lv.lab = dense[u];
       lv.bitmap = base + (size_t)u * n_words;
     }
     kmax = std::max(kmax, q->k);
@@ -1728,7 +1740,7 @@ gsm_status gsm_load_graph(gsm_ctx *ctx, int32_t n, int64_t nnz, const int32_t *r
         free_graph(ctx);
         FAIL(GSM_ERR_INVALID_GRAPH, "row_ptr is not a valid CSR offset array");
       }
-      GraphDev g{n, nnz, ctx->d_rp, ctx->d_col, ctx->d_lab};
+      GraphDev g{n, nnz, ctx->d_rp, ctx->d_col, ctx->d_lab, nullptr, nullptr, 1};
       int32_t *err = (int32_t *)(ctx->d_small + kMaxK + 1);
       CU(cudaMemsetAsync(err, 0, sizeof(int32_t), ctx->stream));
       launch_validate(g, err, ctx->stream);
@@ -1747,6 +1759,34 @@ gsm_status gsm_load_graph(gsm_ctx *ctx, int32_t n, int64_t nnz, const int32_t *r
     } else if (!rp_ok) {
       free_graph(ctx);
       FAIL(GSM_ERR_INVALID_GRAPH, "row_ptr is not a valid CSR offset array");
+    }
+    // label-segmented copy of the rows (ordered by (neighbour label, id))
+    ctx->d_lcol = (int32_t *)dev_alloc(ctx, sizeof(int32_t) * std::max<int64_t>(nnz, 1));
+    ctx->d_llab = (int32_t *)dev_alloc(ctx, sizeof(int32_t) * std::max<int64_t>(nnz, 1));
+    if (nnz > 0) {
+      if (ctx->label_values.size() <= 1) {
+        CU(cudaMemcpyAsync(ctx->d_lcol, ctx->d_col, sizeof(int32_t) * nnz,
+                           cudaMemcpyDeviceToDevice, ctx->stream));
+        CU(cudaMemsetAsync(ctx->d_llab, 0, sizeof(int32_t) * nnz, ctx->stream));
+      } else {
+        const int32_t bits = label_segment_bits(n, (int32_t)ctx->label_values.size());
+        const int32_t nw = packed_words(3, bits);
+        const int64_t H = sort_hist_elems(nnz);
+        Carve cv;
+        const size_t o_cols = cv.add<int32_t>(3 * nnz), o_rows = cv.add<int32_t>(3 * nnz),
+                     o_keys = cv.add<uint64_t>(2 * nnz * nw), o_h = cv.add<int32_t>(H),
+                     o_ho = cv.add<int64_t>(H + 1), o_t = cv.add<int64_t>(scan_tmp_elems(H));
+        char *tmpbuf = (char *)dev_alloc(ctx, cv.off);
+        GraphDev g = graph_dev(ctx);
+        launch_label_segments(g, (int32_t)ctx->label_values.size(), (int32_t *)(tmpbuf + o_cols),
+                              (uint64_t *)(tmpbuf + o_keys), (int32_t *)(tmpbuf + o_rows),
+                              (int32_t *)(tmpbuf + o_h), (int64_t *)(tmpbuf + o_ho),
+                              (int64_t *)(tmpbuf + o_t), ctx->d_lcol, ctx->d_llab, ctx->stream);
+        CU(cudaGetLastError());
+        CU(cudaStreamSynchronize(ctx->stream));
+        dev_free(ctx, tmpbuf, cv.off);
+      }
+      CU(cudaStreamSynchronize(ctx->stream));
     }
     ctx->has_graph = true;
   });

@@ -15,6 +15,7 @@
 
 #include "batch.h"
 #include "filter_body.cuh"
+#include "segments.cuh"
 
 namespace gsm {
 namespace {
@@ -25,21 +26,6 @@ constexpr int kPScanTile = 2048;  // 8 elements per thread
 
 __device__ __forceinline__ bool bm_has(const uint32_t *__restrict__ bm, int32_t v) {
   return (__ldg(bm + (v >> 5)) >> (v & 31)) & 1u;
-}
-
-__device__ __forceinline__ bool row_has(const int32_t *__restrict__ col, int32_t beg, int32_t end,
-                                        int32_t key) {
-  int32_t lo = beg, len = end - beg;
-  while (len > 0) {
-    const int32_t half = len >> 1;
-    if (__ldg(col + lo + half) < key) {
-      lo += half + 1;
-      len -= half + 1;
-    } else {
-      len = half;
-    }
-  }
-  return lo < end && __ldg(col + lo) == key;
 }
 
 __device__ __forceinline__ int64_t warp_incl(int64_t x, int lane) {
@@ -228,10 +214,10 @@ __global__ void k_b_pivot(GraphDev g, const BatchQuery *__restrict__ qs, int32_t
     int32_t best = 0x7fffffff, best_start = 0, best_slot = 0;
     for (int b = 0; b < L.nb; ++b) {
       const int32_t x = F[L.bpos[b] * R + r];
-      const int32_t s = __ldg(g.rp + x), e = __ldg(g.rp + x + 1);
-      if (e - s < best) {
-        best = e - s;
-        best_start = s;
+      const int2 seg = label_segment(g, x, L.lab);  // only pi_i's label can match
+      if (seg.y - seg.x < best) {
+        best = seg.y - seg.x;
+        best_start = seg.x;
         best_slot = b;
       }
     }
@@ -356,13 +342,12 @@ __global__ void __launch_bounds__(1024) k_b_count(
           slot = pslot[r];
         }
         const BatchLevel &L = qs[q].lv[i];
-        const int32_t w = __ldg(g.col + pst + (x - rs));
+        const int32_t w = __ldg(g.lcol + pst + (x - rs));
         bool ok = bm_has(L.bitmap, w);
         for (int u = 0; ok && u < L.ninj; ++u) ok = F[L.inj[u] * R + r] != w;
         for (int c = 0; ok && c < L.nb; ++c) {
           if (c == slot) continue;
-          const int32_t y = F[L.bpos[c] * R + r];
-          ok = row_has(g.col, __ldg(g.rp + y), __ldg(g.rp + y + 1), w);
+          ok = row_contains_l(g, F[L.bpos[c] * R + r], L.lab, w);
         }
         if (ok) {
           if (L.last)
@@ -477,7 +462,7 @@ __global__ void __launch_bounds__(1024) k_b_write(
       const int32_t x = x0 + lo * 32 + b_nth_bit(s_mask[lo], q - s_wpre[lo]);
       int32_t rs;
       const int32_t r = b_row(b, s_woff, woff, x, &rs);
-      const int32_t w = __ldg(g.col + pstart[r] + (x - rs));
+      const int32_t w = __ldg(g.lcol + pstart[r] + (x - rs));
       const int64_t pos = base + q;
       for (int c = 0; c < i; ++c) Fn[c * S + pos] = F[c * R + r];
       Fn[i * S + pos] = w;

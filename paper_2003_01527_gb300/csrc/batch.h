@@ -15,6 +15,7 @@ struct BatchLevel {
   int32_t ninj;             // same-label, non-adjacent positions
   int32_t inj[kMaxK];
   int32_t last;             // 1 if pi_i is the query's last vertex
+  int32_t lab;              // dense label of pi_i (the row segment traversed)
   const uint32_t *bitmap;   // C(pi_i)
 };
 

@@ -10,9 +10,11 @@
 //                       non-tree edge of each traversed candidate in one step
 //   k_scan_*            the compaction scan
 //   k_extend_write      Write_to_Partial: survivors to consecutive rows
+#include <algorithm>
 #include <cstdio>
 
 #include "filter_body.cuh"
+#include "segments.cuh"
 #include "kernels.cuh"
 
 namespace gsm {
@@ -301,10 +303,10 @@ __global__ void k_pivot(GraphDev g, LevelDesc d, const int32_t *__restrict__ F, 
     int32_t best = 0x7fffffff, best_start = 0, best_slot = 0;
     for (int b = 0; b < d.nb; ++b) {
       const int32_t x = F[(int64_t)d.bpos[b] * R + r];
-      const int32_t s = __ldg(g.rp + x), e = __ldg(g.rp + x + 1);
-      if (e - s < best) {
-        best = e - s;
-        best_start = s;
+      const int2 seg = label_segment(g, x, d.lab);  // only pi_i's label can match
+      if (seg.y - seg.x < best) {
+        best = seg.y - seg.x;
+        best_start = seg.x;
         best_slot = b;
       }
     }
@@ -396,7 +398,7 @@ __device__ __forceinline__ bool check_candidate(const GraphDev &g, const LevelDe
   for (int b = 0; b < d.nb; ++b) {
     if (b == slot) continue;
     const int32_t x = F[d.bpos[b] * ld + r];
-    if (!row_contains(g.col, __ldg(g.rp + x), __ldg(g.rp + x + 1), w)) return false;
+    if (!row_contains_l(g, x, d.lab, w)) return false;
   }
   return true;
 }
@@ -444,7 +446,7 @@ __global__ void __launch_bounds__(1024) k_extend_count(
         pst = pstart[r];
         slot = pslot[r];
       }
-      const int32_t w = __ldg(g.col + pst + (x - rs));
+      const int32_t w = __ldg(g.lcol + pst + (x - rs));
       if (check_candidate(g, d, F, ld, r, w, slot)) bits |= 1u << j;
     }
   }
@@ -537,7 +539,7 @@ __global__ void __launch_bounds__(1024) k_extend_write(
     const int32_t x = x0 + lo * 32 + nth_set_bit(s_mask[lo], q - s_wpre[lo]);
     int32_t rs;
     const int32_t r = item_row(t, s_woff, woff, wa, x, &rs);
-    const int32_t w = __ldg(g.col + pstart[r] + (x - rs));
+    const int32_t w = __ldg(g.lcol + pstart[r] + (x - rs));
     int32_t *o = out + base + q;
     for (int c = 0; c < i; ++c) o[d.out_col[c] * out_ld] = F[c * ld + r];
     o[d.out_col[i] * out_ld] = w;
@@ -567,7 +569,52 @@ inline int grid_for(int64_t n, int threads, int cap = 152 * 32) {
   return (int)b;
 }
 
+// Edge e of row v becomes the 3-column row (v, label of col[e], col[e]),
+// column-major with leading dimension nnz.
+__global__ void k_edge_rows(GraphDev g, int32_t *__restrict__ cols) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.n; v += stride) {
+    for (int32_t e = g.rp[v]; e < g.rp[v + 1]; ++e) {
+      const int32_t w = g.col[e];
+      cols[e] = (int32_t)v;
+      cols[g.nnz + e] = g.lab[w];
+      cols[2 * g.nnz + e] = w;
+    }
+  }
+}
+
+// Row-major (v, label, id) triples -> the label and id columns.
+__global__ void k_split_segments(const int32_t *__restrict__ rows, int64_t nnz,
+                                 int32_t *__restrict__ out_col, int32_t *__restrict__ out_lab) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride) {
+    out_lab[e] = rows[3 * e + 1];
+    out_col[e] = rows[3 * e + 2];
+  }
+}
+
 }  // namespace
+
+int32_t label_segment_bits(int32_t n, int32_t num_labels) {
+  int32_t bits = 1;
+  const int64_t m = std::max<int64_t>(n, num_labels);
+  while (bits < 31 && (int64_t(1) << bits) < m) ++bits;
+  return bits;
+}
+
+int launch_label_segments(const GraphDev &g, int32_t num_labels, int32_t *edge_cols,
+                          uint64_t *keys, int32_t *rows_out, int32_t *hist, int64_t *hist_off,
+                          int64_t *tmp, int32_t *out_col, int32_t *out_lab, cudaStream_t s) {
+  if (g.nnz == 0) return 0;
+  k_edge_rows<<<grid_for(g.n, 128, 152 * 64), 128, 0, s>>>(g, edge_cols);
+  const int32_t bits = label_segment_bits(g.n, num_labels);
+  const int32_t nw = packed_words(3, bits);
+  int launches = 1 + launch_sort_rows_packed(edge_cols, g.nnz, g.nnz, 3, bits, keys,
+                                             keys + (size_t)g.nnz * nw, rows_out, hist,
+                                             hist_off, tmp, s);
+  k_split_segments<<<grid_for(g.nnz, 256), 256, 0, s>>>(rows_out, g.nnz, out_col, out_lab);
+  return launches + 1;
+}
 
 void launch_validate(const GraphDev &g, int32_t *err, cudaStream_t s) {
   k_validate_rp<<<grid_for((int64_t)g.n + 1, 256), 256, 0, s>>>(g.n, g.nnz, g.rp, err);

@@ -41,14 +41,18 @@ struct LevelDesc {
   const uint32_t *bitmap;     // C(pi_i)
   int32_t nlt, lt[kMaxK];     // symmetry breaking: the new vertex must be < row[lt[t]]
   int32_t ngt, gt[kMaxK];     //                     and > row[gt[t]]
+  int32_t lab;                // dense label of pi_i: only that segment of a row is traversed
 };
 
 struct GraphDev {
   int32_t n;
   int64_t nnz;
   const int32_t *rp;
-  const int32_t *col;
-  const int32_t *lab;  // dense label ids
+  const int32_t *col;   // rows ascending by id
+  const int32_t *lab;   // dense label ids
+  const int32_t *lcol;  // the same rows ordered by (label, id): label segments
+  const int32_t *llab;  // dense label of lcol[e]
+  int32_t num_labels;   // 1: every row is one segment and lcol equals col
 };
 
 // ---- launchers (all asynchronous on `s`) ----
@@ -58,6 +62,15 @@ struct GraphDev {
 void launch_validate(const GraphDev &g, int32_t *err, cudaStream_t s);
 // Row checks; only valid to run once launch_validate reported a sane row_ptr.
 void launch_validate_rows(const GraphDev &g, int32_t *err, cudaStream_t s);
+
+// Label-segmented rows: out_col/out_lab = every row of g ordered by (label
+// of the neighbour, neighbour id).  Uses the packed row sort on the edges as
+// 3-column rows (row, label, id); tmp needs 3*nnz int32 (+ its keys).
+// Returns kernels launched.  keys: 2 * nnz * packed_words(3, bits) uint64.
+int launch_label_segments(const GraphDev &g, int32_t num_labels, int32_t *edge_cols,
+                          uint64_t *keys, int32_t *rows_out, int32_t *hist, int64_t *hist_off,
+                          int64_t *tmp, int32_t *out_col, int32_t *out_lab, cudaStream_t s);
+int32_t label_segment_bits(int32_t n, int32_t num_labels);
 
 // Writes k bitmaps of n_words words and adds |C(u)| into sizes[u].
 void launch_filter(const GraphDev &g, const FilterDesc &d, uint32_t *bitmaps,

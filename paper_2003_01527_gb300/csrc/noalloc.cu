@@ -109,7 +109,7 @@ extern "C" gsm_status gsm_candidates_static(int32_t n, int64_t nnz, const int32_
   // The counters accumulate, and the array keeps the previous call's
   // contents: clear them first.  (The bitmap words are all overwritten.)
   if (cudaMemsetAsync(d_sizes, 0, kCounterBytes, s) != cudaSuccess) return GSM_ERR_CUDA;
-  GraphDev g{n, nnz, row_ptr, col, labels};
+  GraphDev g{n, nnz, row_ptr, col, labels, nullptr, nullptr, 0};  // the filter reads id-sorted rows
   launch_filter(g, fd, d_bitmaps, d_sizes, s);
   if (cudaGetLastError() != cudaSuccess) return GSM_ERR_CUDA;
   const cudaMemcpyKind kind =
