@@ -92,7 +92,7 @@ struct gsm_ctx {
   size_t acc_cap[2] = {0, 0};
   void *sort_tmp = nullptr;  // radix-sort histograms (scale with the result)
   size_t sort_tmp_cap = 0;
-  void *sort_keys = nullptr;  // packed sort keys, two copies
+  void *sort_keys = nullptr;  // the second buffer of the packed-key radix passes
   size_t sort_keys_cap = 0;
   const int32_t *last_rows = nullptr;  // sorted rows of the last gsm_enumerate
   uint64_t last_count = 0;
@@ -563,26 +563,37 @@ struct Run {
   int32_t block;
   int64_t wcap;        // max candidates per extend launch
   int64_t chunk_rows;  // max rows per extend launch (0 = unbounded)
-  uint64_t acc_rows = 0;  // final rows so far (column-major in ctx->acc[0])
-  int64_t acc_ld = 0;     // rows per column of ctx->acc[0]
+  uint64_t acc_rows = 0;  // final rows so far, in ctx->acc[0]
+  int64_t acc_ld = 0;     // rows ctx->acc[0] holds
+  // layout of the final rows in ctx->acc[0]: row-major rows (the result) when
+  // the matching order leaves them in canonical order, else packed sort keys
+  int32_t acc_mode = kSinkRows;
+  int32_t key_bits = 0, key_nw = 0;
+  size_t acc_row_bytes() const {
+    return acc_mode == kSinkKeys ? (size_t)key_nw * sizeof(uint64_t) : (size_t)k * sizeof(int32_t);
+  }
   unsigned __int128 count = 0;
   unsigned long long *d_total;
 };
 
 void recurse(Run &R, int32_t i, const int32_t *F, int64_t rows);
 
-// Grows the column-major final-row accumulator to hold `rows` rows, keeping
-// the R.acc_rows rows already written.
+// Grows the final-row accumulator to hold `rows` rows, keeping the R.acc_rows
+// rows already written (row-major rows, or key words of leading dimension
+// R.acc_ld).
 void ensure_acc(Run &R, uint64_t rows) {
   gsm_ctx *ctx = R.ctx;
   if ((int64_t)rows <= R.acc_ld) return;
   const int64_t ld = std::max<int64_t>((int64_t)rows, R.acc_ld + R.acc_ld / 2);
-  const size_t bytes = (size_t)ld * R.k * sizeof(int32_t);
+  const size_t bytes = (size_t)ld * R.acc_row_bytes();
   void *q = dev_alloc(ctx, bytes);
-  if (R.acc_rows)
-    CU(cudaMemcpy2DAsync(q, ld * sizeof(int32_t), ctx->acc[0], R.acc_ld * sizeof(int32_t),
-                         R.acc_rows * sizeof(int32_t), R.k, cudaMemcpyDeviceToDevice,
+  if (R.acc_rows && R.acc_mode == kSinkKeys)
+    CU(cudaMemcpy2DAsync(q, ld * sizeof(uint64_t), ctx->acc[0], R.acc_ld * sizeof(uint64_t),
+                         R.acc_rows * sizeof(uint64_t), R.key_nw, cudaMemcpyDeviceToDevice,
                          ctx->stream));
+  else if (R.acc_rows)
+    CU(cudaMemcpyAsync(q, ctx->acc[0], R.acc_rows * R.acc_row_bytes(), cudaMemcpyDeviceToDevice,
+                       ctx->stream));
   dev_free(ctx, ctx->acc[0], ctx->acc_cap[0]);
   ctx->acc[0] = q;
   ctx->acc_cap[0] = bytes;
@@ -635,10 +646,11 @@ void process_sub(Run &R, int32_t i, const int32_t *F, int64_t ld, const int32_t 
   const int32_t w_out = i + 1;
   if (last) {
     ensure_acc(R, R.acc_rows + (uint64_t)S);
-    int32_t *out = (int32_t *)ctx->acc[0] + R.acc_rows;
-    timed(ctx, K_WRITE, 4.0 * S * w_out, (uint64_t)S, 1, [&] {
+    const RowSink sink{R.acc_mode, R.k, R.key_bits, R.key_nw, R.acc_ld, (int64_t)R.acc_rows,
+                       ctx->acc[0]};
+    timed(ctx, K_WRITE, (double)S * R.acc_row_bytes(), (uint64_t)S, 1, [&] {
       launch_extend_write(R.g, d, F, ld, pstart, woff, tile_row, wa, wb, R.block, masks,
-                          tile_off, out, R.acc_ld, ctx->stream);
+                          tile_off, sink, ctx->stream);
     });
     R.acc_rows += (uint64_t)S;
     return;
@@ -661,9 +673,10 @@ void process_sub(Run &R, int32_t i, const int32_t *F, int64_t ld, const int32_t 
   }
   const Mark mk = stack_mark(ctx);
   int32_t *Fn = (int32_t *)stack_push(ctx, bytes);
+  const RowSink sink{kSinkColumns, w_out, 0, 0, S, 0, Fn};
   timed(ctx, K_WRITE, 4.0 * S * w_out, (uint64_t)S, 1, [&] {
     launch_extend_write(R.g, d, F, ld, pstart, woff, tile_row, wa, wb, R.block, masks, tile_off,
-                        Fn, S, ctx->stream);
+                        sink, ctx->stream);
   });
   recurse(R, i + 1, Fn, S);
   stack_release(ctx, mk);
@@ -859,6 +872,22 @@ void run_query(gsm_ctx *ctx, const gsm_query *q, bool enumerate, int32_t *out, u
     if (sizes[u] == 0) return;
   plan(q->k, q->adj, sizes, R.order, R.parent);
   for (int32_t i = 0; i < q->k; ++i) ctx->run.order[i] = R.order[i];
+  // The levels emit rows in lexicographic order of the matching order.  If
+  // query vertices sort_cols .. k-1 are placed in increasing id order, rows
+  // that agree on columns 0 .. sort_cols-1 already stand in canonical order,
+  // so only those columns need sorting; sort_cols == 0 (identity order): the
+  // last level writes the result rows directly.
+  int32_t sort_cols = q->k - 1;
+  {
+    int32_t pos[kMaxK];
+    for (int32_t j = 0; j < q->k; ++j) pos[R.order[j]] = j;
+    while (sort_cols > 0 && pos[sort_cols - 1] < pos[sort_cols]) --sort_cols;
+  }
+  int key_bits = 1;
+  while (key_bits < 31 && (int64_t(1) << key_bits) < ctx->n) ++key_bits;
+  R.acc_mode = sort_cols == 0 ? kSinkRows : kSinkKeys;
+  R.key_bits = key_bits;
+  R.key_nw = packed_words(q->k, key_bits);
 
   const int32_t nw = (ctx->n + 31) / 32;
   const uint32_t *bm = (const uint32_t *)ctx->bitmaps;
@@ -903,7 +932,7 @@ void run_query(gsm_ctx *ctx, const gsm_query *q, bool enumerate, int32_t *out, u
     });
   }
   ctx->run.frontier[1] = (uint64_t)R1;
-  R.acc_ld = (int64_t)(ctx->acc_cap[0] / (sizeof(int32_t) * q->k));
+  R.acc_ld = (int64_t)(ctx->acc_cap[0] / R.acc_row_bytes());
   if (q->k == 1) {
     if (enumerate) {
       ensure_acc(R, (uint64_t)R1);
@@ -929,53 +958,35 @@ void run_query(gsm_ctx *ctx, const gsm_query *q, bool enumerate, int32_t *out, u
   *count_out = total;
   if (!enumerate) return;
 
-  // canonical order: rows are already sorted when the matching order is the
-  // identity (levels emit rows in lexicographic order of the matching order);
-  // either way the column-major rows end up row-major in one of the buffers
+  // canonical order: the final rows are already the result (identity-like
+  // order), or their packed keys are sorted on columns 0 .. sort_cols-1 and
+  // unpacked row-major into acc[1]
   int32_t *rows = (int32_t *)ctx->acc[0];
-  if (q->k > 1 && total > 0) {
-    bool identity = true;
-    for (int32_t j = 0; j < q->k; ++j) identity = identity && R.order[j] == j;
-    int bits = 1;
-    while (bits < 31 && (int64_t(1) << bits) < ctx->n) ++bits;
+  if (R.acc_mode == kSinkKeys && total > 0) {
+    const int32_t nw = R.key_nw;
     const size_t bytes = (size_t)total * q->k * sizeof(int32_t);
-    if (identity) {
-      // already in order: only the layout changes
-      ensure_buf(ctx, &ctx->acc[1], &ctx->acc_cap[1], bytes, false, 0);
-      int launches = 0;
-      timed(ctx, K_SORT, 2.0 * bytes, total, 0, [&] {
-        launch_sort_rows((int32_t *)ctx->acc[0], R.acc_ld, (int32_t *)ctx->acc[1],
-                         (int64_t)total, (int64_t)total, q->k, bits, true, nullptr, nullptr,
-                         nullptr, ctx->stream, &launches);
-      });
-      ctx->run.kernel_launches += launches;
-      rows = (int32_t *)ctx->acc[1];
-    } else {
-      // packed-key radix sort; the sorted rows land row-major in acc[0]
-      const int32_t nw = packed_words(q->k, bits);
-      const size_t key_bytes = (size_t)total * nw * sizeof(uint64_t);
-      ensure_buf(ctx, &ctx->sort_keys, &ctx->sort_keys_cap, 2 * key_bytes, false, 0);
-      const int64_t H = sort_hist_elems((int64_t)total);
-      Carve cv;
-      const size_t o_h = cv.add<int32_t>(H), o_ho = cv.add<int64_t>(H + 1),
-                   o_t = cv.add<int64_t>(scan_tmp_elems(H));
-      // outside the budget, like the result buffers it serves
-      ensure_buf(ctx, &ctx->sort_tmp, &ctx->sort_tmp_cap, cv.off, false, 0);
-      char *sc = (char *)ctx->sort_tmp;
-      uint64_t *ka = (uint64_t *)ctx->sort_keys;
-      uint64_t *kb = ka + (size_t)total * nw;
-      const int digits = (q->k * bits + 7) / 8;
-      int launches = 0;
-      timed(ctx, K_SORT, bytes + 2.0 * key_bytes * digits + bytes, total, 0, [&] {
-        launches = launch_sort_rows_packed((const int32_t *)ctx->acc[0], R.acc_ld,
-                                           (int64_t)total, q->k, bits, ka, kb,
-                                           (int32_t *)ctx->acc[0], (int32_t *)(sc + o_h),
-                                           (int64_t *)(sc + o_ho), (int64_t *)(sc + o_t),
-                                           ctx->stream);
-      });
-      ctx->run.kernel_launches += launches;
-      rows = (int32_t *)ctx->acc[0];
-    }
+    const size_t key_bytes = (size_t)R.acc_ld * nw * sizeof(uint64_t);
+    ensure_buf(ctx, &ctx->sort_keys, &ctx->sort_keys_cap, key_bytes, false, 0);
+    ensure_buf(ctx, &ctx->acc[1], &ctx->acc_cap[1], bytes, false, 0);
+    const int64_t H = sort_hist_elems((int64_t)total);
+    Carve cv;
+    const size_t o_h = cv.add<int32_t>(H), o_ho = cv.add<int64_t>(H + 1),
+                 o_t = cv.add<int64_t>(scan_tmp_elems(H));
+    // outside the budget, like the result buffers it serves
+    ensure_buf(ctx, &ctx->sort_tmp, &ctx->sort_tmp_cap, cv.off, false, 0);
+    char *sc = (char *)ctx->sort_tmp;
+    const int digits = (sort_cols * R.key_bits + 7) / 8;
+    const double moved = 2.0 * (double)total * nw * sizeof(uint64_t) * digits;
+    int launches = 0;
+    timed(ctx, K_SORT, moved + (double)bytes, total, 0, [&] {
+      launches = launch_sort_rows_packed(nullptr, 0, (int64_t)total, q->k, R.key_bits, sort_cols,
+                                         (uint64_t *)ctx->acc[0], (uint64_t *)ctx->sort_keys,
+                                         R.acc_ld, (int32_t *)ctx->acc[1], (int32_t *)(sc + o_h),
+                                         (int64_t *)(sc + o_ho), (int64_t *)(sc + o_t),
+                                         ctx->stream);
+    });
+    ctx->run.kernel_launches += launches;
+    rows = (int32_t *)ctx->acc[1];
   }
   ctx->last_rows = rows;
   ctx->last_count = total;

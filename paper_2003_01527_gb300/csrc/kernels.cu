@@ -486,18 +486,19 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, int n) {
   return pos;
 }
 
-// Write pass: survivor q of tile t becomes output row out_base + tile_off[t] +
-// q; thread q of the CTA handles it (survivors are dense over the threads,
-// whatever the survival rate), so each column store of a warp covers 32
-// consecutive rows.  Position c of the input row goes to column out_col[c] of
-// the column-major output (leading dimension out_ld), the new vertex to
-// column out_col[i].
+// Write pass: survivor q of tile t becomes output row sink.row0 + tile_off[t]
+// + q; thread q of the CTA handles it (survivors are dense over the threads,
+// whatever the survival rate), so each store of a warp covers 32 consecutive
+// rows.  Position c of the input row goes to column out_col[c], the new
+// vertex to column out_col[i], of a column-major frontier, a row-major result
+// row, or the row's packed sort key (the last level writes the final layout
+// directly, so no separate transpose or packing pass reads the rows again).
+template <int kMode>
 __global__ void __launch_bounds__(1024) k_extend_write(
     GraphDev g, LevelDesc d, const int32_t *__restrict__ F, int32_t ld,
     const int32_t *__restrict__ pstart, const int64_t *__restrict__ woff,
     const int32_t *__restrict__ tile_row, int64_t wa, int32_t W,
-    const uint32_t *__restrict__ masks, const int64_t *__restrict__ tile_off,
-    int32_t *__restrict__ out, int64_t out_ld) {
+    const uint32_t *__restrict__ masks, const int64_t *__restrict__ tile_off, RowSink sink) {
   extern __shared__ int32_t s_woff[];
   __shared__ uint32_t s_mask[kItemsPerThread * 1024 / 32];
   __shared__ int32_t s_wpre[kItemsPerThread * 1024 / 32];
@@ -540,9 +541,32 @@ __global__ void __launch_bounds__(1024) k_extend_write(
     int32_t rs;
     const int32_t r = item_row(t, s_woff, woff, wa, x, &rs);
     const int32_t w = __ldg(g.lcol + pstart[r] + (x - rs));
-    int32_t *o = out + base + q;
-    for (int c = 0; c < i; ++c) o[d.out_col[c] * out_ld] = F[c * ld + r];
-    o[d.out_col[i] * out_ld] = w;
+    const int64_t row = sink.row0 + base + q;
+    if (kMode == kSinkColumns) {
+      int32_t *o = (int32_t *)sink.out + row;
+      for (int c = 0; c < i; ++c) o[d.out_col[c] * sink.ld] = F[c * ld + r];
+      o[d.out_col[i] * sink.ld] = w;
+    } else if (kMode == kSinkRows) {
+      int32_t *o = (int32_t *)sink.out + row * sink.k;
+      for (int c = 0; c < i; ++c) o[d.out_col[c]] = F[c * ld + r];
+      o[d.out_col[i]] = w;
+    } else {
+      // packed key: column j occupies bits [(k-1-j)*b, (k-j)*b); word t
+      // collects the columns that overlap bits [64t, 64t+64)
+      uint64_t *o = (uint64_t *)sink.out + row;
+      for (int t = 0; t < sink.nw; ++t) {
+        uint64_t kw = 0;
+        for (int c = 0; c <= i; ++c) {
+          const uint64_t v = (uint32_t)(c < i ? F[c * ld + r] : w);
+          const int32_t lo = (sink.k - 1 - d.out_col[c]) * sink.bits - 64 * t;
+          if (lo >= 0 && lo < 64)
+            kw |= v << lo;
+          else if (lo < 0 && lo + sink.bits > 0)
+            kw |= v >> (-lo);
+        }
+        o[t * sink.ld] = kw;
+      }
+    }
   }
 }
 
@@ -609,8 +633,9 @@ int launch_label_segments(const GraphDev &g, int32_t num_labels, int32_t *edge_c
   k_edge_rows<<<grid_for(g.n, 128, 152 * 64), 128, 0, s>>>(g, edge_cols);
   const int32_t bits = label_segment_bits(g.n, num_labels);
   const int32_t nw = packed_words(3, bits);
-  int launches = 1 + launch_sort_rows_packed(edge_cols, g.nnz, g.nnz, 3, bits, keys,
-                                             keys + (size_t)g.nnz * nw, rows_out, hist,
+  // CSR rows are already ordered by (row, id): sorting on (row, label) is enough
+  int launches = 1 + launch_sort_rows_packed(edge_cols, g.nnz, g.nnz, 3, bits, 2, keys,
+                                             keys + (size_t)g.nnz * nw, g.nnz, rows_out, hist,
                                              hist_off, tmp, s);
   k_split_segments<<<grid_for(g.nnz, 256), 256, 0, s>>>(rows_out, g.nnz, out_col, out_lab);
   return launches + 1;
@@ -707,13 +732,20 @@ void launch_extend_count(const GraphDev &g, const LevelDesc &d, const int32_t *F
 void launch_extend_write(const GraphDev &g, const LevelDesc &d, const int32_t *F, int64_t ld,
                          const int32_t *pstart, const int64_t *woff, const int32_t *tile_row,
                          int64_t wa, int64_t wb, int32_t block, const uint32_t *masks,
-                         const int64_t *tile_off, int32_t *out, int64_t out_ld, cudaStream_t s) {
+                         const int64_t *tile_off, const RowSink &sink, cudaStream_t s) {
   const int64_t tiles = extend_tiles(wa, wb, block);
   if (tiles <= 0) return;
   const size_t smem = (size_t)((int64_t)block * kItemsPerThread + 1) * sizeof(int32_t);
-  k_extend_write<<<(unsigned)tiles, block, smem, s>>>(g, d, F, (int32_t)ld, pstart, woff,
-                                                      tile_row, wa, (int32_t)(wb - wa), masks,
-                                                      tile_off, out, out_ld);
+  const int32_t W = (int32_t)(wb - wa);
+  if (sink.mode == kSinkRows)
+    k_extend_write<kSinkRows><<<(unsigned)tiles, block, smem, s>>>(
+        g, d, F, (int32_t)ld, pstart, woff, tile_row, wa, W, masks, tile_off, sink);
+  else if (sink.mode == kSinkKeys)
+    k_extend_write<kSinkKeys><<<(unsigned)tiles, block, smem, s>>>(
+        g, d, F, (int32_t)ld, pstart, woff, tile_row, wa, W, masks, tile_off, sink);
+  else
+    k_extend_write<kSinkColumns><<<(unsigned)tiles, block, smem, s>>>(
+        g, d, F, (int32_t)ld, pstart, woff, tile_row, wa, W, masks, tile_off, sink);
 }
 
 void launch_split_points(const int64_t *woff, int64_t R, int64_t step, int64_t J,

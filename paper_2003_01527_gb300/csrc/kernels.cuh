@@ -129,40 +129,56 @@ void launch_extend_count(const GraphDev &g, const LevelDesc &d, const int32_t *F
                          uint32_t *masks, int32_t *tile_cnt, unsigned long long *total,
                          cudaStream_t s);
 
-// Write pass: survivor q of tile t goes to row tile_off[t] + rank of the
-// column-major output (leading dimension out_ld); input position c goes to
-// column d.out_col[c], the new vertex to column d.out_col[d.i].
+// Where the write pass puts a row.  kSinkColumns: column-major int32 (the
+// frontier layout), column c of row r at out[c*ld + r].  kSinkRows: row-major
+// int32, out[r*k + c] (the result layout).  kSinkKeys: the packed sort key of
+// the row (see launch_sort_rows_packed), word w of row r at out[w*ld + r].
+enum SinkMode : int32_t { kSinkColumns = 0, kSinkRows = 1, kSinkKeys = 2 };
+constexpr int kMaxKeyWords = 8;  // 16 columns x 31 bits < 512
+struct RowSink {
+  int32_t mode;
+  int32_t k;     // row width (kSinkRows, kSinkKeys)
+  int32_t bits;  // key bits per column (kSinkKeys)
+  int32_t nw;    // key words (kSinkKeys)
+  int64_t ld;    // elements per column / per key word
+  int64_t row0;  // row of the first survivor
+  void *out;
+};
+
+// Write pass: survivor q of tile t becomes row sink.row0 + tile_off[t] + rank;
+// input position c goes to column d.out_col[c], the new vertex to column
+// d.out_col[d.i].
 void launch_extend_write(const GraphDev &g, const LevelDesc &d, const int32_t *F, int64_t ld,
                          const int32_t *pstart, const int64_t *woff, const int32_t *tile_row,
                          int64_t wa, int64_t wb, int32_t block, const uint32_t *masks,
-                         const int64_t *tile_off, int32_t *out, int64_t out_ld, cudaStream_t s);
+                         const int64_t *tile_off, const RowSink &sink, cudaStream_t s);
 
 // Row boundaries for work-bounded sub-chunks: bounds[j] = the row r with
 // woff[r] <= j*step < woff[r+1] (clamped to [0, R]); bounds[J] = R.
 void launch_split_points(const int64_t *woff, int64_t R, int64_t step, int64_t J,
                          int64_t *bounds, int64_t *bound_w, cudaStream_t s);
 
-// Lexicographic sort of N rows of k int32 held column-major in `a` (leading
-// dimension lda), by column 0, then 1, ... (LSD radix, 8-bit digits, values
-// < 2^bits).  `b` is column-major scratch (leading dimension ldb >= N).  The
-// sorted rows are written ROW-major into whichever of a / b the last pass does
-// not read; the function returns which (0 = a, 1 = b).  presorted: the rows
-// are already in order and are only transposed into b.  hist needs
-// sort_hist_elems(N) int32, hist_off sort_hist_elems(N)+1 int64, tmp
-// scan_tmp_elems(sort_hist_elems(N)) int64.
+// Histogram elements of the radix passes over N keys.
 int64_t sort_hist_elems(int64_t N);
-int launch_sort_rows(int32_t *a, int64_t lda, int32_t *b, int64_t ldb, int64_t N, int32_t k,
-                     int32_t bits, bool presorted, int32_t *hist, int64_t *hist_off, int64_t *tmp,
-                     cudaStream_t s, int *launches);
 
-// Same result through packed keys: each row becomes a k*bits-bit integer of
-// packed_words(k, bits) 64-bit words (keys_a / keys_b: N words each per word
-// index), sorted by byte digits, and the last pass writes the rows row-major
-// into `out` (N x k, may alias `a` once packing has read it).  Returns the
-// number of kernels launched.
+// Lexicographic sort of N rows of k int32 (values < 2^bits) by column 0,
+// then 1, ...  Each row is a k*bits-bit integer, sum_j c_j << ((k-1-j)*bits),
+// held as packed_words(k, bits) little-endian 64-bit words (word w of row r at
+// keys[w*ld + r], ld >= N).  If `a` is non-null the keys are first packed into
+// keys_a from the column-major rows a (leading dimension lda); otherwise
+// keys_a already holds them.  LSD radix passes over byte digits move the keys
+// between keys_a and keys_b, and the last pass writes the rows row-major into
+// `out` (N x k, must not overlap keys_a / keys_b; it may alias `a`).  Only
+// columns 0 .. sort_cols-1 are sorted on (1 <= sort_cols <= k): the caller
+// guarantees that rows with equal values there already stand in order of
+// the remaining columns, which the stable passes keep.  hist needs
+// sort_hist_elems(N) int32, hist_off sort_hist_elems(N)+1 int64, tmp
+// scan_tmp_elems(sort_hist_elems(N)) int64.  Returns the number of kernels
+// launched.
 int32_t packed_words(int32_t k, int32_t bits);
 int launch_sort_rows_packed(const int32_t *a, int64_t lda, int64_t N, int32_t k, int32_t bits,
-                            uint64_t *keys_a, uint64_t *keys_b, int32_t *out, int32_t *hist,
-                            int64_t *hist_off, int64_t *tmp, cudaStream_t s);
+                            int32_t sort_cols, uint64_t *keys_a, uint64_t *keys_b, int64_t ld,
+                            int32_t *out, int32_t *hist, int64_t *hist_off, int64_t *tmp,
+                            cudaStream_t s);
 
 }  // namespace gsm
