@@ -82,6 +82,10 @@ typedef struct gsm_options {
    * gsm_candidates returns the refined sets.  The batched form ignores it. */
   int32_t filter_rounds;
   int32_t flags;          /* GSM_OPT_* */
+  /* Result staging slots gsm_enumerate_many uses in turn (0 = 8, at most 64):
+   * each holds the staging buffers of one query's rows until they are copied
+   * out, so up to this many queries can be ahead of the copies. */
+  int32_t copy_slots;
 } gsm_options;
 
 /* Fills *opt with the defaults described above. */
@@ -160,9 +164,28 @@ gsm_status gsm_count_distinct(gsm_ctx *ctx, const gsm_query *q, uint64_t *count,
  * Final rows are staged in library-owned device buffers outside the budget:
  * count x k x 4 bytes of rows plus, unless the matching order is the identity,
  * two packed sort keys of ceil(k * log2(n) / 64) x 8 bytes per row and about
- * 1.5 bytes per row of histograms (otherwise a second count x k x 4 buffer).  Errors: as gsm_count, plus GSM_ERR_TRUNCATED. */
+ * 1.5 bytes per row of histograms.  Errors: as gsm_count, plus
+ * GSM_ERR_TRUNCATED. */
 gsm_status gsm_enumerate(gsm_ctx *ctx, const gsm_query *q, int32_t *out, uint64_t cap_rows,
                          uint64_t *count, int32_t flags);
+
+/* gsm_enumerate for nq queries in order: queries[j] lists into outs[j]
+ * (capacity cap_rows[j] rows), counts[j] receives its total.  Same row layout
+ * and order as gsm_enumerate; all outs[] are host pointers, or all device
+ * pointers with GSM_OUT_DEVICE.  The paper has no counterpart: it is the
+ * serving form of the listing.  The copy of query j's rows runs on a second
+ * stream while the next queries compute, so the result staging buffers of
+ * gsm_enumerate exist once per slot (gsm_options.copy_slots; they stay with
+ * the context for later calls).  The call returns after every copy has
+ * finished (also on error); host buffers should be pinned for the copies to
+ * overlap.  gsm_last_rows then refers to the last query; gsm_last_run_stats
+ * describes the last query.  Errors: as gsm_enumerate (GSM_ERR_TRUNCATED if
+ * any query overflowed its capacity: every count is still set, every output
+ * holds its first cap_rows[j] rows); on another error the counts of queries
+ * not yet run are unspecified. */
+gsm_status gsm_enumerate_many(gsm_ctx *ctx, int32_t nq, const gsm_query *const *queries,
+                              int32_t *const *outs, const uint64_t *cap_rows, uint64_t *counts,
+                              int32_t flags);
 
 /* Copies rows [first, first + nrows) of the last gsm_enumerate result on this
  * context (kept in library buffers until the next gsm_count / gsm_enumerate /

@@ -90,6 +90,25 @@ struct gsm_ctx {
   unsigned long long *d_small = nullptr;  // [0..15] sizes, [16] total, [17] err
   void *acc[2] = {nullptr, nullptr};
   size_t acc_cap[2] = {0, 0};
+  // gsm_enumerate_many: the result buffers (acc, sort_keys) come in several
+  // slots used in turn; while the rows of one query are copied out on
+  // copy_stream, the next queries compute into the other slots.  A slot's
+  // `copied` event marks the end of its last copy out; the compute stream
+  // waits for it before reusing the slot.  The active slot's buffers are
+  // acc / sort_keys above, the others are parked.
+  struct ResultSlot {
+    void *acc[2] = {nullptr, nullptr};
+    size_t acc_cap[2] = {0, 0};
+    void *sort_keys = nullptr;
+    size_t sort_keys_cap = 0;
+    cudaEvent_t copied = nullptr;
+    bool pending = false;
+  };
+  std::deque<ResultSlot> parked;
+  cudaEvent_t active_copied = nullptr;
+  bool active_pending = false;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t rows_ready = nullptr;
   void *sort_tmp = nullptr;  // radix-sort histograms (scale with the result)
   size_t sort_tmp_cap = 0;
   void *sort_keys = nullptr;  // the second buffer of the packed-key radix passes
@@ -108,7 +127,10 @@ struct gsm_ctx {
   void *scratch = nullptr;
   size_t scratch_cap = 0;
 
-  int64_t *h_stage = nullptr;  // pinned staging for small device->host reads
+  // small device->host reads: a kernel writes them into mapped pinned memory
+  // (the copy engines stay free for result copies in flight)
+  int64_t *h_stage = nullptr;
+  void *d_stage = nullptr;  // device view of h_stage
   int32_t num_sms = 0;
 
   // batched form: per-label sorted degrees (order estimates without the
@@ -337,10 +359,18 @@ struct Carve {
   }
 };
 
-int64_t read_i64(gsm_ctx *ctx, const int64_t *dptr) {
-  CU(cudaMemcpyAsync(ctx->h_stage, dptr, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+// Copies `bytes` (a multiple of 4, at most 4096) from device memory into
+// ctx->h_stage once the stream's earlier work is done.
+void fetch(gsm_ctx *ctx, const void *dptr, size_t bytes) {
+  launch_fetch(dptr, ctx->d_stage, bytes, ctx->stream);
+  ctx->run.kernel_launches += 1;
+  CU(cudaGetLastError());
   CU(cudaStreamSynchronize(ctx->stream));
-  return ctx->h_stage[0];
+}
+
+int64_t read_i64(gsm_ctx *ctx, const int64_t *dptr) {
+  fetch(ctx, dptr, sizeof(int64_t));
+  return ((volatile int64_t *)ctx->h_stage)[0];
 }
 
 // ---- kernel timing ----
@@ -826,16 +856,15 @@ void run_filter(gsm_ctx *ctx, const gsm_query *q, const int32_t *dense, uint64_t
       std::swap(ctx->bitmaps_cap, ctx->bitmaps2_cap);
     }
   }
-  CU(cudaMemcpyAsync(ctx->h_stage, ctx->d_small, sizeof(uint64_t) * q->k, cudaMemcpyDeviceToHost,
-                     ctx->stream));
-  CU(cudaStreamSynchronize(ctx->stream));
+  fetch(ctx, ctx->d_small, sizeof(uint64_t) * q->k);
   std::memcpy(sizes, ctx->h_stage, sizeof(uint64_t) * q->k);
 }
 
 // The whole matcher for one query.  out == nullptr and !enumerate: count only.
 void run_query(gsm_ctx *ctx, const gsm_query *q, bool enumerate, int32_t *out, uint64_t cap_rows,
                int32_t flags, uint64_t *count_out, bool *truncated,
-               const std::vector<std::pair<int32_t, int32_t>> *less = nullptr) {
+               const std::vector<std::pair<int32_t, int32_t>> *less = nullptr,
+               bool copy_async = false) {
   if (!ctx->has_graph) FAIL(GSM_ERR_NO_GRAPH, "no data graph loaded");
   std::memset(&ctx->run, 0, sizeof(ctx->run));
   // nothing is live between calls (an earlier call may have failed mid-way)
@@ -949,9 +978,7 @@ void run_query(gsm_ctx *ctx, const gsm_query *q, bool enumerate, int32_t *out, u
   if (enumerate || q->k == 1) {
     total = R.acc_rows;
   } else {
-    CU(cudaMemcpyAsync(ctx->h_stage, R.d_total, sizeof(uint64_t), cudaMemcpyDeviceToHost,
-                       ctx->stream));
-    CU(cudaStreamSynchronize(ctx->stream));
+    fetch(ctx, R.d_total, sizeof(uint64_t));
     total = (uint64_t)ctx->h_stage[0];
   }
   ctx->run.frontier[q->k] = total;
@@ -991,13 +1018,24 @@ void run_query(gsm_ctx *ctx, const gsm_query *q, bool enumerate, int32_t *out, u
   ctx->last_rows = rows;
   ctx->last_count = total;
   const uint64_t ncopy = std::min<uint64_t>(total, cap_rows);
-  if (ncopy) {
-    CU(cudaMemcpyAsync(out, rows, (size_t)ncopy * q->k * sizeof(int32_t),
-                       (flags & GSM_OUT_DEVICE) ? cudaMemcpyDeviceToDevice
-                                                : cudaMemcpyDeviceToHost,
-                       ctx->stream));
+  const cudaMemcpyKind kind =
+      (flags & GSM_OUT_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (copy_async) {
+    // copy out on the copy stream once the rows are complete; the compute
+    // stream goes on with the next query in the other result slot
+    if (ncopy) {
+      CU(cudaEventRecord(ctx->rows_ready, ctx->stream));
+      CU(cudaStreamWaitEvent(ctx->copy_stream, ctx->rows_ready, 0));
+      CU(cudaMemcpyAsync(out, rows, (size_t)ncopy * q->k * sizeof(int32_t), kind,
+                         ctx->copy_stream));
+      CU(cudaEventRecord(ctx->active_copied, ctx->copy_stream));
+      ctx->active_pending = true;
+    }
+  } else {
+    if (ncopy)
+      CU(cudaMemcpyAsync(out, rows, (size_t)ncopy * q->k * sizeof(int32_t), kind, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
   }
-  CU(cudaStreamSynchronize(ctx->stream));
   *truncated = total > cap_rows;
 }
 
@@ -1624,7 +1662,8 @@ gsm_status gsm_create(gsm_ctx **out, int32_t device, const gsm_options *opt) {
   if (opt && opt->block_size != 0 &&
       (opt->block_size < 128 || opt->block_size > 1024 || opt->block_size % 32))
     return GSM_ERR_INVALID_ARG;
-  if (opt && (opt->chunk_rows < 0 || opt->filter_rounds < 0 || opt->filter_rounds > 64))
+  if (opt && (opt->chunk_rows < 0 || opt->filter_rounds < 0 || opt->filter_rounds > 64 ||
+              opt->copy_slots < 0 || opt->copy_slots > 64))
     return GSM_ERR_INVALID_ARG;
   gsm_ctx *ctx = new gsm_ctx();
   if (opt) ctx->opt = *opt;
@@ -1643,7 +1682,8 @@ gsm_status gsm_create(gsm_ctx **out, int32_t device, const gsm_options *opt) {
     ctx->budget = ctx->opt.mem_budget_bytes ? ctx->opt.mem_budget_bytes : free_b / 10 * 9;
     ctx->scratch_limit = ctx->budget / 4;
     ctx->stack_limit = ctx->budget - ctx->scratch_limit;
-    CU(cudaMallocHost(&ctx->h_stage, 4096));
+    CU(cudaHostAlloc(&ctx->h_stage, 4096, cudaHostAllocMapped));
+    CU(cudaHostGetDevicePointer(&ctx->d_stage, ctx->h_stage, 0));
     CU(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device));
     ctx->d_small = (unsigned long long *)dev_alloc(ctx, 256);
   });
@@ -1671,6 +1711,11 @@ void gsm_destroy(gsm_ctx *ctx) {
     dev_free(ctx, ctx->acc[1], ctx->acc_cap[1]);
     dev_free(ctx, ctx->sort_tmp, ctx->sort_tmp_cap);
     dev_free(ctx, ctx->sort_keys, ctx->sort_keys_cap);
+    for (auto &p : ctx->parked) {
+      dev_free(ctx, p.acc[0], p.acc_cap[0]);
+      dev_free(ctx, p.acc[1], p.acc_cap[1]);
+      dev_free(ctx, p.sort_keys, p.sort_keys_cap);
+    }
     dev_free(ctx, ctx->d_small, 256);
   } catch (...) {
   }
@@ -1680,6 +1725,11 @@ void gsm_destroy(gsm_ctx *ctx) {
     cudaEventDestroy(p.b);
   }
   if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+  if (ctx->rows_ready) cudaEventDestroy(ctx->rows_ready);
+  if (ctx->active_copied) cudaEventDestroy(ctx->active_copied);
+  for (auto &p : ctx->parked)
+    if (p.copied) cudaEventDestroy(p.copied);
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
@@ -1722,14 +1772,34 @@ gsm_status gsm_load_graph(gsm_ctx *ctx, int32_t n, int64_t nnz, const int32_t *r
                        ctx->stream));
     if (nnz)
       CU(cudaMemcpyAsync(ctx->d_col, col, sizeof(int32_t) * nnz, kind, ctx->stream));
-    // dense label ids: index into the sorted distinct label values
-    std::vector<int32_t> vals(h_lab);
-    std::sort(vals.begin(), vals.end());
-    vals.erase(std::unique(vals.begin(), vals.end()), vals.end());
-    if (vals.empty()) vals.push_back(0);
-    std::vector<int32_t> dense(n);
-    for (int32_t v = 0; v < n; ++v)
-      dense[v] = (int32_t)(std::lower_bound(vals.begin(), vals.end(), h_lab[v]) - vals.begin());
+    // dense label ids: index into the sorted distinct label values (a table
+    // over the value range when it is small, else a sort)
+    std::vector<int32_t> vals, dense(n);
+    {
+      int64_t lo = 0, hi = -1;
+      if (n) {
+        const auto mm = std::minmax_element(h_lab.begin(), h_lab.end());
+        lo = *mm.first;
+        hi = *mm.second;
+      }
+      if (n && hi - lo < 4 * (int64_t)n + 4096) {
+        std::vector<int32_t> id((size_t)(hi - lo + 1), -1);
+        for (int32_t v = 0; v < n; ++v) id[(size_t)(h_lab[v] - lo)] = 0;
+        for (size_t x = 0; x < id.size(); ++x)
+          if (id[x] == 0) {
+            id[x] = (int32_t)vals.size();
+            vals.push_back((int32_t)(lo + (int64_t)x));
+          }
+        for (int32_t v = 0; v < n; ++v) dense[v] = id[(size_t)(h_lab[v] - lo)];
+      } else {
+        vals = h_lab;
+        std::sort(vals.begin(), vals.end());
+        vals.erase(std::unique(vals.begin(), vals.end()), vals.end());
+        for (int32_t v = 0; v < n; ++v)
+          dense[v] = (int32_t)(std::lower_bound(vals.begin(), vals.end(), h_lab[v]) - vals.begin());
+      }
+      if (vals.empty()) vals.push_back(0);
+    }
     ctx->label_values = vals;
     if (n)
       CU(cudaMemcpyAsync(ctx->d_lab, dense.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice,
@@ -1742,9 +1812,19 @@ gsm_status gsm_load_graph(gsm_ctx *ctx, int32_t n, int64_t nnz, const int32_t *r
       md = std::max(md, dv);
     }
     ctx->max_deg = md;
+    // degrees of every label in ascending order: a counting sort by degree,
+    // then a stable split by label
     ctx->deg_by_label.assign(vals.size(), {});
-    for (int32_t v = 0; v < n; ++v) ctx->deg_by_label[dense[v]].push_back(h_rp[v + 1] - h_rp[v]);
-    for (auto &d : ctx->deg_by_label) std::sort(d.begin(), d.end());
+    if (n && rp_ok) {
+      std::vector<int32_t> start((size_t)md + 2, 0), by_deg(n);
+      for (int32_t v = 0; v < n; ++v) start[(size_t)(h_rp[v + 1] - h_rp[v]) + 1]++;
+      for (size_t d = 1; d < start.size(); ++d) start[d] += start[d - 1];
+      for (int32_t v = 0; v < n; ++v) by_deg[start[(size_t)(h_rp[v + 1] - h_rp[v])]++] = v;
+      std::vector<int32_t> per_label(vals.size(), 0);
+      for (int32_t v = 0; v < n; ++v) per_label[dense[v]]++;
+      for (size_t l = 0; l < vals.size(); ++l) ctx->deg_by_label[l].reserve(per_label[l]);
+      for (int32_t v : by_deg) ctx->deg_by_label[dense[v]].push_back(h_rp[v + 1] - h_rp[v]);
+    }
     CU(cudaStreamSynchronize(ctx->stream));
     if (flags & GSM_VALIDATE) {
       if (!rp_ok) {
@@ -1758,8 +1838,7 @@ gsm_status gsm_load_graph(gsm_ctx *ctx, int32_t n, int64_t nnz, const int32_t *r
       launch_validate_rows(g, err, ctx->stream);
       CU(cudaGetLastError());
       int32_t h_err = 0;
-      CU(cudaMemcpyAsync(ctx->h_stage, err, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
-      CU(cudaStreamSynchronize(ctx->stream));
+      fetch(ctx, err, sizeof(int32_t));
       std::memcpy(&h_err, ctx->h_stage, sizeof(int32_t));
       if (h_err) {
         free_graph(ctx);
@@ -1845,6 +1924,80 @@ gsm_status gsm_count(gsm_ctx *ctx, const gsm_query *q, uint64_t *count) {
     resolve_timings(ctx);
     ctx->run.peak_bytes = ctx->peak_bytes;
   });
+  return st;
+}
+
+namespace {
+// Parks the active result buffers and takes the oldest parked slot (creating
+// slots until there are `slots` of them); what the compute stream does next
+// waits until that slot's last copy out has finished.
+void next_result_slot(gsm_ctx *ctx, int32_t slots) {
+  gsm_ctx::ResultSlot cur;
+  for (int j = 0; j < 2; ++j) {
+    cur.acc[j] = ctx->acc[j];
+    cur.acc_cap[j] = ctx->acc_cap[j];
+  }
+  cur.sort_keys = ctx->sort_keys;
+  cur.sort_keys_cap = ctx->sort_keys_cap;
+  cur.copied = ctx->active_copied;
+  cur.pending = ctx->active_pending;
+  ctx->parked.push_back(cur);
+  while ((int32_t)ctx->parked.size() < slots) ctx->parked.emplace_front();
+  gsm_ctx::ResultSlot nxt = ctx->parked.front();
+  ctx->parked.pop_front();
+  for (int j = 0; j < 2; ++j) {
+    ctx->acc[j] = nxt.acc[j];
+    ctx->acc_cap[j] = nxt.acc_cap[j];
+  }
+  ctx->sort_keys = nxt.sort_keys;
+  ctx->sort_keys_cap = nxt.sort_keys_cap;
+  ctx->active_copied = nxt.copied;
+  ctx->active_pending = nxt.pending;
+  if (!ctx->active_copied)
+    CU(cudaEventCreateWithFlags(&ctx->active_copied, cudaEventDisableTiming));
+  if (ctx->active_pending) {
+    CU(cudaStreamWaitEvent(ctx->stream, ctx->active_copied, 0));
+    ctx->active_pending = false;
+  }
+}
+}  // namespace
+
+gsm_status gsm_enumerate_many(gsm_ctx *ctx, int32_t nq, const gsm_query *const *queries,
+                              int32_t *const *outs, const uint64_t *cap_rows, uint64_t *counts,
+                              int32_t flags) {
+  if (!ctx || nq < 0 || (flags & ~GSM_OUT_DEVICE)) return GSM_ERR_INVALID_ARG;
+  if (nq > 0 && (!queries || !outs || !cap_rows || !counts)) return GSM_ERR_INVALID_ARG;
+  for (int32_t j = 0; j < nq; ++j)
+    if (!queries[j] || (cap_rows[j] > 0 && !outs[j])) return GSM_ERR_INVALID_ARG;
+  int32_t first_trunc = -1;
+  gsm_status st = guarded(ctx, [&] {
+    CU(cudaSetDevice(ctx->device));
+    if (!ctx->copy_stream) {
+      CU(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+      CU(cudaEventCreateWithFlags(&ctx->rows_ready, cudaEventDisableTiming));
+    }
+    const int32_t slots = ctx->opt.copy_slots > 0 ? ctx->opt.copy_slots : 8;
+    for (int32_t j = 0; j < nq; ++j) {
+      next_result_slot(ctx, slots);
+      bool trunc = false;
+      run_query(ctx, queries[j], true, outs[j], cap_rows[j], flags, &counts[j], &trunc, nullptr,
+                true);
+      if (trunc && first_trunc < 0) first_trunc = j;
+    }
+    CU(cudaStreamSynchronize(ctx->copy_stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    resolve_timings(ctx);
+    ctx->run.peak_bytes = ctx->peak_bytes;
+  });
+  // no copy into the caller's buffers outlives the call, whatever happened
+  if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
+  ctx->active_pending = false;
+  for (auto &p : ctx->parked) p.pending = false;
+  if (st == GSM_OK && first_trunc >= 0) {
+    set_err(ctx, "query %d: %llu embeddings, capacity %llu rows", first_trunc,
+            (unsigned long long)counts[first_trunc], (unsigned long long)cap_rows[first_trunc]);
+    return GSM_ERR_TRUNCATED;
+  }
   return st;
 }
 

@@ -76,22 +76,21 @@ __global__ void k_validate_rp(int32_t n, int64_t nnz, const int32_t *__restrict_
   }
 }
 
+// One warp per vertex; lanes stride over the row.
 __global__ void k_validate_rows(int32_t n, const int32_t *__restrict__ rp,
                                 const int32_t *__restrict__ col, int32_t *err) {
-  int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
-    int32_t b = rp[v], e = rp[v + 1];
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+    const int32_t b = rp[v], e = rp[v + 1];
     int32_t flags = 0;
-    for (int32_t idx = b; idx < e; ++idx) {
-      int32_t w = col[idx];
+    for (int32_t idx = b + lane; idx < e; idx += 32) {
+      const int32_t w = col[idx];
       if (w < 0 || w >= n || w == (int32_t)v || (idx > b && col[idx - 1] >= w)) {
         flags |= 1;
-        break;
+        continue;
       }
-      if (!row_contains(col, rp[w], rp[w + 1], (int32_t)v)) {
-        flags |= 2;
-        break;
-      }
+      if (!row_contains(col, rp[w], rp[w + 1], (int32_t)v)) flags |= 2;
     }
     if (flags) atomicOr(err, flags);
   }
@@ -586,6 +585,10 @@ __global__ void k_split_points(const int64_t *__restrict__ woff, int64_t R, int6
   bound_w[j] = woff[r];
 }
 
+__global__ void k_fetch(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst, int32_t n) {
+  for (int32_t i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
 inline int grid_for(int64_t n, int threads, int cap = 152 * 32) {
   int64_t b = (n + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -595,10 +598,13 @@ inline int grid_for(int64_t n, int threads, int cap = 152 * 32) {
 
 // Edge e of row v becomes the 3-column row (v, label of col[e], col[e]),
 // column-major with leading dimension nnz.
+// One warp per vertex (rows of power-law graphs are very uneven).
 __global__ void k_edge_rows(GraphDev g, int32_t *__restrict__ cols) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.n; v += stride) {
-    for (int32_t e = g.rp[v]; e < g.rp[v + 1]; ++e) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < g.n; v += warps) {
+    const int32_t e1 = g.rp[v + 1];
+    for (int32_t e = g.rp[v] + lane; e < e1; e += 32) {
       const int32_t w = g.col[e];
       cols[e] = (int32_t)v;
       cols[g.nnz + e] = g.lab[w];
@@ -630,7 +636,7 @@ int launch_label_segments(const GraphDev &g, int32_t num_labels, int32_t *edge_c
                           uint64_t *keys, int32_t *rows_out, int32_t *hist, int64_t *hist_off,
                           int64_t *tmp, int32_t *out_col, int32_t *out_lab, cudaStream_t s) {
   if (g.nnz == 0) return 0;
-  k_edge_rows<<<grid_for(g.n, 128, 152 * 64), 128, 0, s>>>(g, edge_cols);
+  k_edge_rows<<<grid_for((int64_t)g.n * 32, 256, 152 * 8), 256, 0, s>>>(g, edge_cols);
   const int32_t bits = label_segment_bits(g.n, num_labels);
   const int32_t nw = packed_words(3, bits);
   // CSR rows are already ordered by (row, id): sorting on (row, label) is enough
@@ -641,13 +647,18 @@ int launch_label_segments(const GraphDev &g, int32_t num_labels, int32_t *edge_c
   return launches + 1;
 }
 
+void launch_fetch(const void *src, void *dst, size_t bytes, cudaStream_t s) {
+  const int32_t n = (int32_t)(std::min<size_t>(bytes, 4096) / 4);
+  if (n > 0) k_fetch<<<1, 128, 0, s>>>((const uint32_t *)src, (uint32_t *)dst, n);
+}
+
 void launch_validate(const GraphDev &g, int32_t *err, cudaStream_t s) {
   k_validate_rp<<<grid_for((int64_t)g.n + 1, 256), 256, 0, s>>>(g.n, g.nnz, g.rp, err);
   // rows are only read if row_ptr is sane; the host checks err in between
 }
 
 void launch_validate_rows(const GraphDev &g, int32_t *err, cudaStream_t s) {
-  k_validate_rows<<<grid_for(g.n, 128), 128, 0, s>>>(g.n, g.rp, g.col, err);
+  k_validate_rows<<<grid_for((int64_t)g.n * 32, 256, 152 * 8), 256, 0, s>>>(g.n, g.rp, g.col, err);
 }
 
 void launch_filter(const GraphDev &g, const FilterDesc &d, uint32_t *bitmaps,

@@ -158,6 +158,11 @@ void launch_extend_write(const GraphDev &g, const LevelDesc &d, const int32_t *F
 void launch_split_points(const int64_t *woff, int64_t R, int64_t step, int64_t J,
                          int64_t *bounds, int64_t *bound_w, cudaStream_t s);
 
+// Copies `bytes` (a multiple of 4, at most 4096) from src to dst with one
+// small kernel; dst is typically the device view of mapped pinned host memory,
+// so small reads back to the host do not queue behind copy-engine transfers.
+void launch_fetch(const void *src, void *dst, size_t bytes, cudaStream_t s);
+
 // Histogram elements of the radix passes over N keys.
 int64_t sort_hist_elems(int64_t N);
 

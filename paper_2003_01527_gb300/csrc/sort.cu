@@ -30,22 +30,19 @@ __global__ void __launch_bounds__(256) k_pack_keys(const int32_t *__restrict__ i
                                                    uint64_t *__restrict__ keys, int64_t kld) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= N) return;
-  uint64_t w[kMaxWords];
-#pragma unroll
-  for (int i = 0; i < kMaxWords; ++i) w[i] = 0;
-  for (int32_t j = 0; j < k; ++j) {
-    const uint64_t v = (uint32_t)in[(int64_t)j * ld + r];
-    const int32_t pos = (k - 1 - j) * b;  // bit offset of column j
-    const int32_t wi = pos >> 6, sh = pos & 63;
-#pragma unroll
-    for (int i = 0; i < kMaxWords; ++i) {
-      if (i == wi) w[i] |= v << sh;
-      if (i == wi + 1 && sh + b > 64) w[i] |= v >> (64 - sh);
+  // word t collects the columns that overlap bits [64t, 64t+64)
+  for (int32_t t = 0; t < nw; ++t) {
+    uint64_t w = 0;
+    for (int32_t j = 0; j < k; ++j) {
+      const uint64_t v = (uint32_t)in[(int64_t)j * ld + r];
+      const int32_t lo = (k - 1 - j) * b - 64 * t;
+      if (lo >= 0 && lo < 64)
+        w |= v << lo;
+      else if (lo < 0 && lo + b > 0)
+        w |= v >> (-lo);
     }
+    keys[(int64_t)t * kld + r] = w;
   }
-#pragma unroll
-  for (int i = 0; i < kMaxWords; ++i)
-    if (i < nw) keys[(int64_t)i * kld + r] = w[i];
 }
 
 // Byte digit of the packed key at bit position p (a digit may straddle two
@@ -131,6 +128,96 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter_keys(
   }
 }
 
+// The same pass for keys of NW <= 2 words, a tile at a time: every thread
+// first loads all its keys (item c*256 + t of the tile for chunk c), so the
+// loads of a tile are in flight together; each warp then counts its digits
+// per chunk with match_any into s_cnt[(chunk, warp)][digit], one exclusive
+// scan per digit over the 64 (chunk, warp) entries turns the counts into tile
+// offsets, and every key goes straight to hist_off + offset + rank.
+template <int NW>
+__device__ __forceinline__ uint32_t tile_digit(const uint64_t (&kk)[NW], int32_t wi, int32_t sh) {
+  uint64_t lo = kk[0], hi = 0;
+  if (NW > 1) {
+    if (wi == 0) {
+      hi = kk[NW - 1];
+    } else {
+      lo = kk[NW - 1];
+    }
+  }
+  uint64_t v = lo >> sh;
+  if (sh > 56) v |= hi << (64 - sh);
+  return (uint32_t)(v & 0xffu);
+}
+
+template <int NW, bool kUnpack>
+__global__ void __launch_bounds__(kSortThreads) k_scatter_tile(
+    const uint64_t *__restrict__ in, uint64_t *__restrict__ out_keys,
+    int32_t *__restrict__ out_rows, int64_t ld, int64_t N, int32_t k, int32_t b, int32_t p,
+    const int64_t *__restrict__ hist_off, int64_t nblocks) {
+  constexpr int kWarps = kSortThreads / 32;
+  constexpr int kSlots = kSortChunks * kWarps;
+  __shared__ __align__(16) uint16_t s_cnt[kSlots][kBins];
+  __shared__ int64_t s_base[kBins];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  uint64_t key[kSortChunks][NW];
+#pragma unroll
+  for (int c = 0; c < kSortChunks; ++c) {
+    const int64_t idx = base + c * kSortThreads + threadIdx.x;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) key[c][w] = idx < N ? in[(int64_t)w * ld + idx] : 0;
+  }
+  s_base[threadIdx.x] = hist_off[(int64_t)threadIdx.x * nblocks + blockIdx.x];
+  {
+    uint4 *z = reinterpret_cast<uint4 *>(&s_cnt[0][0]);
+    constexpr int kVec = kSlots * kBins * 2 / 16;
+    for (int e = threadIdx.x; e < kVec; e += kSortThreads) z[e] = make_uint4(0, 0, 0, 0);
+  }
+  __syncthreads();
+  const int32_t wi = p >> 6, sh = p & 63;
+  const uint32_t lt = (1u << lane) - 1u;
+  uint32_t dg[kSortChunks];
+  int32_t rk[kSortChunks];
+#pragma unroll
+  for (int c = 0; c < kSortChunks; ++c) {
+    const bool valid = base + c * kSortThreads + threadIdx.x < N;
+    dg[c] = valid ? tile_digit<NW>(key[c], wi, sh) : kBins;
+    const uint32_t peers = __match_any_sync(kFull, dg[c]);
+    rk[c] = __popc(peers & lt);
+    if (valid && rk[c] == 0) s_cnt[c * kWarps + warp][dg[c]] = (uint16_t)__popc(peers);
+  }
+  __syncthreads();
+  {
+    int32_t run = 0;
+    for (int e = 0; e < kSlots; ++e) {
+      const int32_t v = s_cnt[e][threadIdx.x];
+      s_cnt[e][threadIdx.x] = (uint16_t)run;
+      run += v;
+    }
+  }
+  __syncthreads();
+  const uint64_t mask_b = (1ull << b) - 1ull;
+#pragma unroll
+  for (int c = 0; c < kSortChunks; ++c) {
+    if (dg[c] == kBins) continue;
+    const int64_t pos = s_base[dg[c]] + s_cnt[c * kWarps + warp][dg[c]] + rk[c];
+    if (kUnpack) {
+      int32_t *dst = out_rows + pos * k;
+      for (int32_t j = 0; j < k; ++j) {
+        const int32_t bp = (k - 1 - j) * b;
+        const int32_t bw = bp >> 6, bs = bp & 63;
+        uint64_t v = (NW > 1 && bw == 1) ? key[c][NW - 1] : key[c][0];
+        v >>= bs;
+        if (NW > 1 && bw == 0 && bs + b > 64) v |= key[c][NW - 1] << (64 - bs);
+        dst[j] = (int32_t)(v & mask_b);
+      }
+    } else {
+#pragma unroll
+      for (int w = 0; w < NW; ++w) out_keys[(int64_t)w * ld + pos] = key[c][w];
+    }
+  }
+}
+
 }  // namespace
 
 int64_t sort_hist_elems(int64_t N) {
@@ -166,7 +253,20 @@ int launch_sort_rows_packed(const int32_t *a, int64_t lda, int64_t N, int32_t k,
     const int32_t p = lo_bit + 8 * dg;
     k_hist_keys<<<(unsigned)nb, kSortThreads, 0, s>>>(src, ld, N, nw, p, hist, nb);
     launch_scan_i32(hist, hist_off, nb * kBins, tmp, s);
-    if (dg == digits - 1)
+    const bool last = dg == digits - 1;
+    if (nw == 1 && last)
+      k_scatter_tile<1, true><<<(unsigned)nb, kSortThreads, 0, s>>>(src, dst, out, ld, N, k,
+                                                                    bits, p, hist_off, nb);
+    else if (nw == 1)
+      k_scatter_tile<1, false><<<(unsigned)nb, kSortThreads, 0, s>>>(src, dst, out, ld, N, k,
+                                                                     bits, p, hist_off, nb);
+    else if (nw == 2 && last)
+      k_scatter_tile<2, true><<<(unsigned)nb, kSortThreads, 0, s>>>(src, dst, out, ld, N, k,
+                                                                    bits, p, hist_off, nb);
+    else if (nw == 2)
+      k_scatter_tile<2, false><<<(unsigned)nb, kSortThreads, 0, s>>>(src, dst, out, ld, N, k,
+                                                                     bits, p, hist_off, nb);
+    else if (last)
       k_scatter_keys<true><<<(unsigned)nb, kSortThreads, 0, s>>>(src, dst, out, ld, N, nw, k,
                                                                  bits, p, hist_off, nb);
     else

@@ -45,7 +45,7 @@ MAX_K = 16
 EXPORTED = [
     "gsm_default_options", "gsm_create", "gsm_destroy", "gsm_last_error", "gsm_status_string",
     "gsm_load_graph", "gsm_query_create", "gsm_query_destroy", "gsm_query_restrict", "gsm_count",
-    "gsm_enumerate", "gsm_last_rows", "gsm_candidates", "gsm_plan_order", "gsm_kernel_stats",
+    "gsm_enumerate", "gsm_enumerate_many", "gsm_last_rows", "gsm_candidates", "gsm_plan_order", "gsm_kernel_stats",
     "gsm_last_run_stats", "gsm_candidates_static", "gsm_run_batch", "gsm_batch_get_stats",
     "gsm_batch_configure", "gsm_count_distinct", "gsm_server_start", "gsm_submit", "gsm_poll", "gsm_server_stop",
 ]
@@ -61,7 +61,8 @@ class gsm_options(ctypes.Structure):
     _fields_ = [("mem_budget_bytes", ctypes.c_size_t), ("stream", ctypes.c_void_p),
                 ("alloc", _alloc_fn), ("free", _free_fn), ("alloc_ctx", ctypes.c_void_p),
                 ("block_size", ctypes.c_int32), ("chunk_rows", ctypes.c_int64),
-                ("filter_rounds", ctypes.c_int32), ("flags", ctypes.c_int32)]
+                ("filter_rounds", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("copy_slots", ctypes.c_int32)]
 
 
 class gsm_kernel_stat(ctypes.Structure):
@@ -110,6 +111,7 @@ def _load():
         "gsm_count": (i32, [vp, vp, ctypes.POINTER(u64)]),
         "gsm_count_distinct": (i32, [vp, vp, ctypes.POINTER(u64), ctypes.POINTER(u64)]),
         "gsm_enumerate": (i32, [vp, vp, vp, u64, ctypes.POINTER(u64), i32]),
+        "gsm_enumerate_many": (i32, [vp, i32, vp, vp, vp, vp, i32]),
         "gsm_last_rows": (i32, [vp, vp, u64, u64, i32]),
         "gsm_candidates": (i32, [vp, vp, vp, vp]),
         "gsm_plan_order": (i32, [i32, i32, vp, vp, vp, vp]),
@@ -228,6 +230,20 @@ def gsm_enumerate(ctx: int, q: int, out, cap_rows: int, flags: int) -> tuple[int
     st = _lib.gsm_enumerate(ctx, q, _ptr(out), cap_rows, ctypes.byref(c), flags)
     _check(ctx, st, (GSM_OK, GSM_ERR_TRUNCATED))
     return c.value, st
+
+
+def gsm_enumerate_many(ctx: int, queries, outs, cap_rows, flags: int) -> tuple[np.ndarray, int]:
+    """queries: gsm_query handles; outs: buffers (host, or device with
+    GSM_OUT_DEVICE); cap_rows: capacities in rows.  Returns (uint64 counts,
+    status); status is GSM_OK or GSM_ERR_TRUNCATED."""
+    nq = len(queries)
+    qa = (ctypes.c_void_p * max(nq, 1))(*queries)
+    oa = (ctypes.c_void_p * max(nq, 1))(*[_ptr(o) for o in outs])
+    caps = np.ascontiguousarray(np.asarray(cap_rows, dtype=np.uint64).reshape(nq))
+    counts = np.zeros(max(nq, 1), dtype=np.uint64)
+    st = _lib.gsm_enumerate_many(ctx, nq, qa, oa, _ptr(caps), _ptr(counts), flags)
+    _check(ctx, st, (GSM_OK, GSM_ERR_TRUNCATED))
+    return counts[:nq], st
 
 
 def gsm_last_rows(ctx: int, out, first: int, nrows: int, flags: int) -> None:
@@ -361,7 +377,7 @@ class Matcher:
 
     def __init__(self, device: int = 0, mem_budget_bytes: int = 0, stream=None,
                  block_size: int = 0, chunk_rows: int = 0, time_kernels: bool = False,
-                 torch_allocator: bool = True, filter_rounds: int = 0):
+                 torch_allocator: bool = True, filter_rounds: int = 0, copy_slots: int = 0):
         import torch
         self.device = device
         opt = gsm_default_options()
@@ -376,6 +392,7 @@ class Matcher:
         opt.block_size = block_size
         opt.chunk_rows = chunk_rows
         opt.filter_rounds = filter_rounds
+        opt.copy_slots = copy_slots
         opt.flags = GSM_OPT_TIME_KERNELS if time_kernels else 0
         if torch_allocator:
             dev = device
@@ -446,6 +463,17 @@ class Matcher:
         buf = np.empty((max(cap_rows, 1), q.k), dtype=np.int32)
         count, _ = gsm_enumerate(self.ctx, q.handle, buf if cap_rows else None, cap_rows, 0)
         return buf[:min(count, cap_rows)], count
+
+    def enumerate_many(self, queries, outs) -> list[int]:
+        """Lists every Query of `queries` into the matching buffer of `outs`
+        (int32 numpy arrays or tensors of cap_rows*k elements, all on the host
+        or all CUDA); copies overlap the next query's compute.  Returns the
+        counts."""
+        flags = GSM_OUT_DEVICE if outs and _is_cuda(outs[0]) else 0
+        caps = [int(o.numel() if hasattr(o, "numel") else o.size) // q.k
+                for q, o in zip(queries, outs)]
+        counts, _ = gsm_enumerate_many(self.ctx, [q.handle for q in queries], outs, caps, flags)
+        return [int(c) for c in counts]
 
     def candidates(self, q: Query):
         nw = (self.n + 31) // 32
