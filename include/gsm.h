@@ -179,7 +179,8 @@ gsm_status gsm_enumerate(gsm_ctx *ctx, const gsm_query *q, int32_t *out, uint64_
  * the context for later calls).  The call returns after every copy has
  * finished (also on error); host buffers should be pinned for the copies to
  * overlap.  gsm_last_rows then refers to the last query; gsm_last_run_stats
- * describes the last query.  Errors: as gsm_enumerate (GSM_ERR_TRUNCATED if
+ * counts the kernel launches of the whole call and the peak budgeted bytes
+ * over its queries, and its other fields describe the last query.  Errors: as gsm_enumerate (GSM_ERR_TRUNCATED if
  * any query overflowed its capacity: every count is still set, every output
  * holds its first cap_rows[j] rows); on another error the counts of queries
  * not yet run are unspecified. */

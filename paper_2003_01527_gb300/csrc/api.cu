@@ -1977,17 +1977,21 @@ gsm_status gsm_enumerate_many(gsm_ctx *ctx, int32_t nq, const gsm_query *const *
       CU(cudaEventCreateWithFlags(&ctx->rows_ready, cudaEventDisableTiming));
     }
     const int32_t slots = ctx->opt.copy_slots > 0 ? ctx->opt.copy_slots : 8;
+    uint64_t launches = 0, peak = 0;
     for (int32_t j = 0; j < nq; ++j) {
       next_result_slot(ctx, slots);
       bool trunc = false;
       run_query(ctx, queries[j], true, outs[j], cap_rows[j], flags, &counts[j], &trunc, nullptr,
                 true);
+      launches += ctx->run.kernel_launches;
+      peak = std::max<uint64_t>(peak, ctx->peak_bytes);
       if (trunc && first_trunc < 0) first_trunc = j;
     }
     CU(cudaStreamSynchronize(ctx->copy_stream));
     CU(cudaStreamSynchronize(ctx->stream));
     resolve_timings(ctx);
-    ctx->run.peak_bytes = ctx->peak_bytes;
+    ctx->run.kernel_launches = launches;
+    ctx->run.peak_bytes = peak;
   });
   // no copy into the caller's buffers outlives the call, whatever happened
   if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);

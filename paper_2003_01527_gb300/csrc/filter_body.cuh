@@ -6,12 +6,37 @@
 
 namespace gsm {
 
+// Requirement test of query vertex set `vneed` against per-slot neighbour
+// counts cnt[] (slot s counts neighbours labelled d.slot_label[s]).
+template <typename Desc>
+__device__ __forceinline__ uint32_t nlc_pass(const Desc &d, uint32_t vneed,
+                                             const int32_t (&cnt)[kMaxK]) {
+  uint32_t pass = 0;
+  for (int u = 0; u < d.k; ++u) {
+    if (!((vneed >> u) & 1u)) continue;
+    bool ok = true;
+    for (int r = 0; r < d.nreq[u]; ++r) {
+      const int slot = d.req_slot[u][r];
+      int32_t c = 0;
+#pragma unroll
+      for (int s = 0; s < kMaxK; ++s) c = (s == slot) ? cnt[s] : c;
+      ok = ok && c >= d.req_cnt[u][r];
+    }
+    if (ok) pass |= 1u << u;
+  }
+  return pass;
+}
+
 // One warp handles 32 consecutive data vertices per iteration (warps
 // warp_id, warp_id + n_warps, ...).  Each lane first applies the label /
-// degree / range test for its own vertex; vertices that also need per-label
-// neighbour counts are then scanned one at a time by the whole warp (coalesced
-// reads of the CSR row, labels gathered through L2), and the k bitmap words
-// of the group are formed by ballots.  Lane u adds |C(u)| into sizes[u].
+// degree / range test for its own vertex.  A vertex that also needs per-label
+// neighbour counts is first counted by its own lane over its first
+// kLaneScan neighbours (most rows of a power-law graph end there); only a
+// vertex whose requirements are still unmet and whose row goes on is then
+// scanned by the whole warp (coalesced reads of the CSR row, labels gathered
+// through L2).  The k bitmap words of the group are formed by ballots.  Lane u
+// adds |C(u)| into sizes[u].
+constexpr int kLaneScan = 32;
 template <typename Desc>
 __device__ __forceinline__ void filter_warps(const GraphDev &g, const Desc &d,
                                              uint32_t *__restrict__ bitmaps,
@@ -39,7 +64,26 @@ __device__ __forceinline__ void filter_warps(const GraphDev &g, const Desc &d,
       }
     }
     uint32_t result = pre & ~need;
-    uint32_t todo = __ballot_sync(kFull, need != 0);
+    bool rest = false;
+    if (need) {
+      const int32_t b = g.rp[v], e = g.rp[v + 1];
+      const int32_t e1 = min(e, b + kLaneScan);
+      int32_t cnt[kMaxK];
+#pragma unroll
+      for (int s = 0; s < kMaxK; ++s) cnt[s] = 0;
+#pragma unroll 4
+      for (int32_t idx = b; idx < e1; ++idx) {
+        const int32_t lw = __ldg(g.lab + __ldg(g.col + idx));
+#pragma unroll
+        for (int s = 0; s < kMaxK; ++s)
+          if (s < d.nslots && lw == d.slot_label[s]) ++cnt[s];
+      }
+      const uint32_t pass = nlc_pass(d, need, cnt);
+      result |= pass;
+      rest = pass != need && e > e1;
+      need = rest ? need : 0;
+    }
+    uint32_t todo = __ballot_sync(kFull, rest);
     while (todo) {
       const int src = __ffs(todo) - 1;
       todo &= todo - 1;
@@ -66,19 +110,7 @@ __device__ __forceinline__ void filter_warps(const GraphDev &g, const Desc &d,
 #pragma unroll
         for (int s = 0; s < kMaxK; ++s)
           if (s < d.nslots) tot[s] = __reduce_add_sync(kFull, cnt[s]);
-        pass = 0;
-        for (int u = 0; u < d.k; ++u) {
-          if (!((vneed >> u) & 1u)) continue;
-          bool ok = true;
-          for (int r = 0; r < d.nreq[u]; ++r) {
-            const int slot = d.req_slot[u][r];
-            int32_t c = 0;
-#pragma unroll
-            for (int s = 0; s < kMaxK; ++s) c = (s == slot) ? tot[s] : c;
-            ok = ok && c >= d.req_cnt[u][r];
-          }
-          if (ok) pass |= 1u << u;
-        }
+        pass = nlc_pass(d, vneed, tot);
         if (pass == vneed) break;  // warp-uniform: tot is the same in every lane
       }
       if (lane == src) result |= pass;

@@ -264,6 +264,48 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const T *in, int64_t
   if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = partial[nb];
 }
 
+// Whole scan in one CTA for short inputs (one launch instead of three): tiles
+// of kOneThreads x kScanIpt elements in order, with a running carry.
+// In-place safe for the same reason as k_scan_down.
+constexpr int kOneThreads = 512;
+constexpr int64_t kOneCtaMax = 4 * kOneThreads * kScanIpt;  // longest input taken
+template <typename T>
+__global__ void __launch_bounds__(kOneThreads) k_scan_one_cta(const T *in, int64_t n,
+                                                              int64_t *out) {
+  constexpr int kTile = kOneThreads * kScanIpt;
+  __shared__ int64_t s_val[kTile];
+  __shared__ int64_t s_warp[33];
+  int64_t carry = 0;
+  for (int64_t base = 0; base < n; base += kTile) {
+#pragma unroll
+    for (int j = 0; j < kScanIpt; ++j) {
+      const int64_t idx = base + j * kOneThreads + threadIdx.x;
+      s_val[j * kOneThreads + threadIdx.x] = idx < n ? (int64_t)in[idx] : 0;
+    }
+    __syncthreads();
+    int64_t loc[kScanIpt];
+    int64_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < kScanIpt; ++j) {
+      loc[j] = sum;
+      sum += s_val[threadIdx.x * kScanIpt + j];
+    }
+    int64_t total;
+    const int64_t off = carry + block_excl_scan(sum, s_warp, &total);
+#pragma unroll
+    for (int j = 0; j < kScanIpt; ++j) s_val[threadIdx.x * kScanIpt + j] = off + loc[j];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kScanIpt; ++j) {
+      const int64_t idx = base + j * kOneThreads + threadIdx.x;
+      if (idx < n) out[idx] = s_val[j * kOneThreads + threadIdx.x];
+    }
+    carry += total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[n] = carry;
+}
+
 // ------------------------------------------------------------ bitmap -> list
 
 __global__ void k_bitmap_popc(const uint32_t *__restrict__ bm, int32_t n_words,
@@ -682,6 +724,10 @@ void scan_impl(const T *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t 
   const int64_t nb = (n + kScanTile - 1) / kScanTile;
   if (nb == 0) {
     cudaMemsetAsync(out, 0, sizeof(int64_t), s);
+    return;
+  }
+  if (n <= kOneCtaMax) {
+    k_scan_one_cta<T><<<1, kOneThreads, 0, s>>>(in, n, out);
     return;
   }
   k_scan_reduce<T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, tmp);
