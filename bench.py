@@ -391,18 +391,21 @@ def run_gpu(args):
     peak, peak_kind = peaks()
     achieved = dom["algo_bytes"] / (dom["total_ms"] / 1e3) / 1e9 if dom["total_ms"] else 0.0
     # DRAM bytes per launch of the dominant kernel from an ncu capture
-    # (profiles/traffic.json); null when the kernel source changed since
+    # (profiles/traffic.json); null when the kernel's source file changed since
     traffic = None
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof):
         try:
             with open(prof) as f:
                 tr = json.load(f).get(dom["name"])
-            with open(os.path.join(ROOT, "paper_2003_01527_gb300", "csrc", "kernels.cu"),
-                      "rb") as f:
-                src = hashlib.sha256(f.read()).hexdigest()
-            if tr and tr.get("kernels_cu_sha256") == src:
-                traffic = tr["dram_bytes_per_launch"]
+            if tr:
+                h = hashlib.sha256()
+                for name in tr["sources"]:
+                    with open(os.path.join(ROOT, "paper_2003_01527_gb300", "csrc", name),
+                              "rb") as f:
+                        h.update(f.read())
+                if tr.get("sources_sha256") == h.hexdigest():
+                    traffic = tr["dram_bytes_per_launch"]
         except Exception:
             traffic = None
 
