@@ -61,6 +61,11 @@ typedef void *(*gsm_alloc_fn)(void *alloc_ctx, size_t bytes, void *stream);
 typedef void (*gsm_free_fn)(void *alloc_ctx, void *ptr, size_t bytes, void *stream);
 
 #define GSM_OPT_TIME_KERNELS 1 /* record per-kernel CUDA-event times (gsm_kernel_stats) */
+/* Verify and write every level in two passes (count with survivor masks, then
+ * write).  Without it a level takes one pass (decoupled look-back over its
+ * tiles) whenever its output has room for one row per candidate, and two
+ * passes otherwise; results are identical either way. */
+#define GSM_OPT_TWO_PASS 2
 
 typedef struct gsm_options {
   /* Cap on device memory for intermediate frontiers and scratch, in bytes.

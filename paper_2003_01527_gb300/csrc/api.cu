@@ -39,9 +39,9 @@ struct KStat {
   uint64_t items = 0;
 };
 
-enum KernelId { K_FILTER, K_LIST, K_PIVOT, K_COUNT, K_WRITE, K_SORT, K_NUM };
+enum KernelId { K_FILTER, K_LIST, K_PIVOT, K_COUNT, K_WRITE, K_SORT, K_FUSED, K_NUM };
 const char *kKernelNames[K_NUM] = {"filter", "bitmap_to_list", "pivot_scan",
-                                   "extend_count", "extend_write", "sort_rows"};
+                                   "extend_count", "extend_write", "sort_rows", "extend_fused"};
 
 struct Pending {
   int kid;
@@ -606,7 +606,14 @@ struct Run {
   unsigned long long *d_total;
 };
 
-void recurse(Run &R, int32_t i, const int32_t *F, int64_t rows);
+void recurse(Run &R, int32_t i, const int32_t *F, int64_t ld, int64_t rows);
+void process_fused(Run &R, int32_t i, const int32_t *F, int64_t ld, const int32_t *pstart,
+                   const uint8_t *pslot, const int64_t *woff, int64_t ra, int64_t rb, int64_t wa,
+                   int64_t wb);
+
+// Largest result staging (bytes) the single-pass last level may reserve for
+// its upper bound of one row per candidate.
+constexpr double kFusedResultBytes = 4.0 * (1ull << 30);
 
 // Grows the final-row accumulator to hold `rows` rows, keeping the R.acc_rows
 // rows already written (row-major rows, or key words of leading dimension
@@ -643,6 +650,25 @@ void process_sub(Run &R, int32_t i, const int32_t *F, int64_t ld, const int32_t 
   const double read_bytes = (double)nrows * (4.0 * i + 13.0) + 4.0 * (double)W;
   ctx->run.chunks += 1;
   const bool count_only = last && !R.enumerate;
+  const int32_t w_out = i + 1;
+  if (!count_only && !(ctx->opt.flags & GSM_OPT_TWO_PASS)) {
+    // single pass (count and write together) when the output has room for
+    // every candidate surviving: W rows of the next frontier (plus its
+    // per-row arrays) on the stack, or W result rows
+    bool fits;
+    if (last) {
+      fits = (double)W * (double)R.acc_row_bytes() <= kFusedResultBytes;
+    } else {
+      const size_t need = align_up((size_t)W * w_out * sizeof(int32_t)) +
+                          align_up(4 * (size_t)W) + align_up((size_t)W) +
+                          align_up(8 * ((size_t)W + 1));
+      fits = (int64_t)W * w_out < (int64_t(1) << 31) - 1 && stack_fits(ctx, need);
+    }
+    if (fits) {
+      process_fused(R, i, F, ld, pstart, pslot, woff, ra, rb, wa, wb);
+      return;
+    }
+  }
   Carve cv;
   const size_t o_row = cv.add<int32_t>(tiles + 1);
   const size_t o_mask = count_only ? 0 : cv.add<uint32_t>(tiles * (tile_items / 32));
@@ -652,7 +678,7 @@ void process_sub(Run &R, int32_t i, const int32_t *F, int64_t ld, const int32_t 
   char *sc = (char *)scratch_get(ctx, cv.off);
   int32_t *tile_row = (int32_t *)(sc + o_row);
   timed(ctx, K_PIVOT, 8.0 * (nrows + tiles), (uint64_t)tiles, 1, [&] {
-    launch_tile_rows(woff, ra, rb, wa, wb, R.block, tile_row, ctx->stream);
+    launch_tile_rows(woff, ra, rb, wa, wb, R.block, tile_row, nullptr, ctx->stream);
   });
   if (count_only) {
     timed(ctx, K_COUNT, read_bytes, (uint64_t)W, 1, [&] {
@@ -673,7 +699,6 @@ void process_sub(Run &R, int32_t i, const int32_t *F, int64_t ld, const int32_t 
         [&] { launch_scan_i32(tile_cnt, tile_off, tiles, tmp, ctx->stream); });
   const int64_t S = read_i64(ctx, tile_off + tiles);
   if (S == 0) return;
-  const int32_t w_out = i + 1;
   if (last) {
     ensure_acc(R, R.acc_rows + (uint64_t)S);
     const RowSink sink{R.acc_mode, R.k, R.key_bits, R.key_nw, R.acc_ld, (int64_t)R.acc_rows,
@@ -708,12 +733,63 @@ void process_sub(Run &R, int32_t i, const int32_t *F, int64_t ld, const int32_t 
     launch_extend_write(R.g, d, F, ld, pstart, woff, tile_row, wa, wb, R.block, masks, tile_off,
                         sink, ctx->stream);
   });
-  recurse(R, i + 1, Fn, S);
+  recurse(R, i + 1, Fn, S, S);
   stack_release(ctx, mk);
 }
 
-// Extends rows of width i (F, `rows` of them) through the remaining levels.
-void recurse(Run &R, int32_t i, const int32_t *F, int64_t rows) {
+// The single-pass form of process_sub's count and write passes
+// (k_extend_fused); the caller checked that the output has room for W rows.
+void process_fused(Run &R, int32_t i, const int32_t *F, int64_t ld, const int32_t *pstart,
+                   const uint8_t *pslot, const int64_t *woff, int64_t ra, int64_t rb, int64_t wa,
+                   int64_t wb) {
+  gsm_ctx *ctx = R.ctx;
+  const LevelDesc &d = R.lv[i];
+  const bool last = i == R.k - 1;
+  const int64_t W = wb - wa, nrows = rb - ra;
+  const int64_t tiles = extend_tiles(wa, wb, R.block);
+  const int32_t w_out = i + 1;
+  Carve cv;
+  const size_t o_row = cv.add<int32_t>(tiles + 1);
+  const size_t o_lb = cv.add<unsigned long long>(tiles + kLbExtra);
+  char *sc = (char *)scratch_get(ctx, cv.off);
+  int32_t *tile_row = (int32_t *)(sc + o_row);
+  unsigned long long *lb = (unsigned long long *)(sc + o_lb);
+  timed(ctx, K_PIVOT, 8.0 * (nrows + tiles) + 8.0 * tiles, (uint64_t)tiles, 1, [&] {
+    launch_tile_rows(woff, ra, rb, wa, wb, R.block, tile_row, lb, ctx->stream);
+  });
+  const double read_bytes = (double)nrows * (4.0 * i + 13.0) + 4.0 * (double)W;
+  const Mark mk = stack_mark(ctx);
+  RowSink sink;
+  int32_t *Fn = nullptr;
+  if (last) {
+    ensure_acc(R, R.acc_rows + (uint64_t)W);
+    sink = RowSink{R.acc_mode, R.k, R.key_bits, R.key_nw, R.acc_ld, (int64_t)R.acc_rows,
+                   ctx->acc[0]};
+  } else {
+    Fn = (int32_t *)stack_push(ctx, (size_t)W * w_out * sizeof(int32_t));
+    sink = RowSink{kSinkColumns, w_out, 0, 0, W, 0, Fn};
+  }
+  timed(ctx, K_FUSED, read_bytes, (uint64_t)W, 1, [&] {
+    launch_extend_fused(R.g, d, F, ld, pstart, pslot, woff, tile_row, wa, wb, R.block, lb, sink,
+                        ctx->stream);
+  });
+  fetch(ctx, lb + tiles + 1, 2 * sizeof(unsigned long long));
+  const int64_t S = ((volatile int64_t *)ctx->h_stage)[0];
+  const int64_t gave_up = ((volatile int64_t *)ctx->h_stage)[1];
+  if (gave_up) FAIL(GSM_ERR_TIMEOUT, "a verification tile waited too long for its predecessors");
+  ctx->kstats[K_FUSED].algo_bytes +=
+      (double)S * (last ? (double)R.acc_row_bytes() : 4.0 * w_out);
+  if (last) {
+    R.acc_rows += (uint64_t)S;
+    return;
+  }
+  if (S > 0) recurse(R, i + 1, Fn, W, S);
+  stack_release(ctx, mk);
+}
+
+// Extends rows of width i (F, `rows` of them, leading dimension ld) through
+// the remaining levels.
+void recurse(Run &R, int32_t i, const int32_t *F, int64_t ld, int64_t rows) {
   gsm_ctx *ctx = R.ctx;
   if (rows <= 0) return;
   const LevelDesc &d = R.lv[i];
@@ -723,7 +799,7 @@ void recurse(Run &R, int32_t i, const int32_t *F, int64_t rows) {
   int64_t *woff = (int64_t *)stack_push(ctx, sizeof(int64_t) * (rows + 1));
   int64_t *tmp = (int64_t *)scratch_get(ctx, sizeof(int64_t) * scan_tmp_elems(rows));
   timed(ctx, K_PIVOT, (double)rows * (4.0 * d.nb + 8.0 * d.nb + 13.0 + 16.0), (uint64_t)rows, 4, [&] {
-    launch_pivot(R.g, d, F, rows, pstart, pslot, woff, ctx->stream);
+    launch_pivot(R.g, d, F, ld, rows, pstart, pslot, woff, ctx->stream);
     launch_scan_i64(woff, woff, rows, tmp, ctx->stream);
   });
   const int64_t W = read_i64(ctx, woff + rows);
@@ -732,7 +808,7 @@ void recurse(Run &R, int32_t i, const int32_t *F, int64_t rows) {
   const bool split_w = W > R.wcap;
   const bool split_r = R.chunk_rows > 0 && rows > R.chunk_rows;
   if (!split_w && !split_r) {
-    process_sub(R, i, F, rows, pstart, pslot, woff, 0, rows, 0, W);
+    process_sub(R, i, F, ld, pstart, pslot, woff, 0, rows, 0, W);
   } else {
     // row boundaries: work targets (each piece <= wcap) merged with multiples of chunk_rows
     std::vector<int64_t> bnd, bw;
@@ -768,7 +844,7 @@ void recurse(Run &R, int32_t i, const int32_t *F, int64_t rows) {
     }
     CU(cudaStreamSynchronize(ctx->stream));
     for (size_t j = 0; j + 1 < bnd.size(); ++j)
-      process_sub(R, i, F, rows, pstart, pslot, woff, bnd[j], bnd[j + 1], bw[j], bw[j + 1]);
+      process_sub(R, i, F, ld, pstart, pslot, woff, bnd[j], bnd[j + 1], bw[j], bw[j + 1]);
   }
   stack_release(ctx, mk);
 }
@@ -970,7 +1046,7 @@ void run_query(gsm_ctx *ctx, const gsm_query *q, bool enumerate, int32_t *out, u
     }
     R.acc_rows = (uint64_t)R1;
   } else {
-    recurse(R, 1, F1, R1);
+    recurse(R, 1, F1, R1, R1);
   }
   stack_release(ctx, mk);
 

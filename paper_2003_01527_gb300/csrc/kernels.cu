@@ -336,14 +336,14 @@ __global__ void k_bitmap_emit(const uint32_t *__restrict__ bm, int32_t n_words,
 // consecutive rows, or writing one position of 32 consecutive survivors,
 // touches 128 contiguous bytes.
 
-__global__ void k_pivot(GraphDev g, LevelDesc d, const int32_t *__restrict__ F, int64_t R,
-                        int32_t *__restrict__ pstart, uint8_t *__restrict__ pslot,
+__global__ void k_pivot(GraphDev g, LevelDesc d, const int32_t *__restrict__ F, int64_t ld,
+                        int64_t R, int32_t *__restrict__ pstart, uint8_t *__restrict__ pslot,
                         int64_t *__restrict__ work) {
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R; r += stride) {
     int32_t best = 0x7fffffff, best_start = 0, best_slot = 0;
     for (int b = 0; b < d.nb; ++b) {
-      const int32_t x = F[(int64_t)d.bpos[b] * R + r];
+      const int32_t x = F[(int64_t)d.bpos[b] * ld + r];
       const int2 seg = label_segment(g, x, d.lab);  // only pi_i's label can match
       if (seg.y - seg.x < best) {
         best = seg.y - seg.x;
@@ -361,8 +361,13 @@ __global__ void k_pivot(GraphDev g, LevelDesc d, const int32_t *__restrict__ F, 
 // (rows partition the items, so exactly one row writes each entry);
 // tile_row[tiles] = rb - 1.  Rows < 2^31.
 __global__ void k_tile_rows(const int64_t *__restrict__ woff, int64_t ra, int64_t rb, int64_t wa,
-                            int64_t tile_items, int64_t tiles, int32_t *__restrict__ tile_row) {
+                            int64_t tile_items, int64_t tiles, int32_t *__restrict__ tile_row,
+                            unsigned long long *__restrict__ lookback) {
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  if (lookback)
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tiles + kLbExtra;
+         t += stride)
+      lookback[t] = 0;
   for (int64_t r = ra + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rb; r += stride) {
     const int64_t s = woff[r] - wa, e = woff[r + 1] - wa;
     if (e <= s) continue;
@@ -389,10 +394,11 @@ struct TileRows {
 
 __device__ __forceinline__ TileRows stage_rows(const int64_t *__restrict__ woff,
                                                const int32_t *__restrict__ tile_row, int64_t wa,
-                                               int32_t tile_items, int32_t *s_woff) {
+                                               int32_t tile_items, int32_t *s_woff,
+                                               int32_t tile) {
   TileRows t;
-  t.r0 = tile_row[blockIdx.x];
-  t.span = tile_row[blockIdx.x + 1] + 1 - t.r0;
+  t.r0 = tile_row[tile];
+  t.span = tile_row[tile + 1] + 1 - t.r0;
   t.staged = t.span <= tile_items;
   if (t.staged)
     for (int32_t j = threadIdx.x; j <= t.span; j += blockDim.x)
@@ -465,7 +471,7 @@ __global__ void __launch_bounds__(1024) k_extend_count(
   const int32_t x0 = blockIdx.x * tile_items;
   const int32_t x1 = min(x0 + tile_items, W);
   if (threadIdx.x == 0) s_count = 0;
-  const TileRows t = stage_rows(woff, tile_row, wa, tile_items, s_woff);
+  const TileRows t = stage_rows(woff, tile_row, wa, tile_items, s_woff, blockIdx.x);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int32_t xb = x0 + warp * 128 + lane * kItemsPerThread;
   uint32_t bits = 0;
@@ -506,6 +512,40 @@ __global__ void __launch_bounds__(1024) k_extend_count(
   if (threadIdx.x == 0) {
     if (tile_cnt) tile_cnt[blockIdx.x] = s_count;
     if (total && s_count) atomicAdd(total, (unsigned long long)s_count);
+  }
+}
+
+// Writes row r of F extended by w as output row `row` of the sink (see
+// RowSink): position c goes to column d.out_col[c], w to d.out_col[d.i].
+template <int kMode>
+__device__ __forceinline__ void put_row(const RowSink &sink, const LevelDesc &d,
+                                        const int32_t *__restrict__ F, int32_t ld, int32_t r,
+                                        int32_t w, int64_t row) {
+  const int32_t i = d.i;
+  if (kMode == kSinkColumns) {
+    int32_t *o = (int32_t *)sink.out + row;
+    for (int c = 0; c < i; ++c) o[d.out_col[c] * sink.ld] = F[c * ld + r];
+    o[d.out_col[i] * sink.ld] = w;
+  } else if (kMode == kSinkRows) {
+    int32_t *o = (int32_t *)sink.out + row * sink.k;
+    for (int c = 0; c < i; ++c) o[d.out_col[c]] = F[c * ld + r];
+    o[d.out_col[i]] = w;
+  } else {
+    // packed key: column j occupies bits [(k-1-j)*b, (k-j)*b); word t
+    // collects the columns that overlap bits [64t, 64t+64)
+    uint64_t *o = (uint64_t *)sink.out + row;
+    for (int t = 0; t < sink.nw; ++t) {
+      uint64_t kw = 0;
+      for (int c = 0; c <= i; ++c) {
+        const uint64_t v = (uint32_t)(c < i ? F[c * ld + r] : w);
+        const int32_t lo = (sink.k - 1 - d.out_col[c]) * sink.bits - 64 * t;
+        if (lo >= 0 && lo < 64)
+          kw |= v << lo;
+        else if (lo < 0 && lo + sink.bits > 0)
+          kw |= v >> (-lo);
+      }
+      o[t * sink.ld] = kw;
+    }
   }
 }
 
@@ -552,7 +592,7 @@ __global__ void __launch_bounds__(1024) k_extend_write(
   const int32_t x0 = blockIdx.x * tile_items;
   for (int32_t w = threadIdx.x; w < tile_words; w += B)
     s_mask[w] = masks[blockIdx.x * tile_words + w];
-  const TileRows t = stage_rows(woff, tile_row, wa, tile_items, s_woff);
+  const TileRows t = stage_rows(woff, tile_row, wa, tile_items, s_woff, blockIdx.x);
   const int lane = threadIdx.x & 31;
   if (threadIdx.x < 32) {
     int32_t carry = 0;
@@ -570,7 +610,6 @@ __global__ void __launch_bounds__(1024) k_extend_write(
     }
   }
   __syncthreads();
-  const int32_t i = d.i;
   for (int32_t q = threadIdx.x; q < cnt; q += B) {
     // word holding survivor q: the last word whose prefix count is <= q
     int32_t lo = 0, hi = tile_words;
@@ -582,33 +621,170 @@ __global__ void __launch_bounds__(1024) k_extend_write(
     int32_t rs;
     const int32_t r = item_row(t, s_woff, woff, wa, x, &rs);
     const int32_t w = __ldg(g.lcol + pstart[r] + (x - rs));
-    const int64_t row = sink.row0 + base + q;
-    if (kMode == kSinkColumns) {
-      int32_t *o = (int32_t *)sink.out + row;
-      for (int c = 0; c < i; ++c) o[d.out_col[c] * sink.ld] = F[c * ld + r];
-      o[d.out_col[i] * sink.ld] = w;
-    } else if (kMode == kSinkRows) {
-      int32_t *o = (int32_t *)sink.out + row * sink.k;
-      for (int c = 0; c < i; ++c) o[d.out_col[c]] = F[c * ld + r];
-      o[d.out_col[i]] = w;
-    } else {
-      // packed key: column j occupies bits [(k-1-j)*b, (k-j)*b); word t
-      // collects the columns that overlap bits [64t, 64t+64)
-      uint64_t *o = (uint64_t *)sink.out + row;
-      for (int t = 0; t < sink.nw; ++t) {
-        uint64_t kw = 0;
-        for (int c = 0; c <= i; ++c) {
-          const uint64_t v = (uint32_t)(c < i ? F[c * ld + r] : w);
-          const int32_t lo = (sink.k - 1 - d.out_col[c]) * sink.bits - 64 * t;
-          if (lo >= 0 && lo < 64)
-            kw |= v << lo;
-          else if (lo < 0 && lo + sink.bits > 0)
-            kw |= v >> (-lo);
-        }
-        o[t * sink.ld] = kw;
+    put_row<kMode>(sink, d, F, ld, r, w, sink.row0 + base + q);
+  }
+}
+
+__device__ __forceinline__ unsigned long long load_relaxed(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Count and write in one pass (single-pass compaction): a tile takes its
+// index from a ticket counter, so every tile it may wait for has started;
+// it verifies its candidates as k_extend_count does, ranks its survivors
+// with a block scan, publishes its survivor count, and finds the number of
+// survivors of all earlier tiles by looking back over their published words
+// (decoupled look-back: a word holds either a tile's own count or its
+// inclusive prefix).  Survivors are then written directly at their final
+// rows, in candidate order, as the two-pass form would write them.
+// lookback: tiles words, then the ticket, the survivor total and an error
+// word, all zero at launch.  A wait that exceeds kLbSpinLimit polls sets the
+// error word and goes on with the prefix found so far (rows stay in bounds;
+// the host reports the error).
+template <int kMode>
+__global__ void __launch_bounds__(1024) k_extend_fused(
+    GraphDev g, LevelDesc d, const int32_t *__restrict__ F, int32_t ld,
+    const int32_t *__restrict__ pstart, const uint8_t *__restrict__ pslot,
+    const int64_t *__restrict__ woff, const int32_t *__restrict__ tile_row, int64_t wa,
+    int32_t W, int32_t tiles, unsigned long long *__restrict__ lookback, RowSink sink) {
+  static_assert(kItemsPerThread == 4, "four candidates per thread");
+  extern __shared__ int32_t s_woff[];
+  __shared__ int32_t s_tile;
+  __shared__ int32_t s_warp[33];
+  __shared__ long long s_prefix;
+  if (threadIdx.x == 0) s_tile = (int32_t)atomicAdd(lookback + tiles, 1ull);
+  __syncthreads();
+  const int32_t tile = s_tile;
+  const int32_t B = blockDim.x;
+  const int32_t tile_items = B * kItemsPerThread;
+  const int32_t x0 = tile * tile_items;
+  const int32_t x1 = min(x0 + tile_items, W);
+  const TileRows t = stage_rows(woff, tile_row, wa, tile_items, s_woff, tile);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int32_t xb = x0 + warp * 128 + lane * kItemsPerThread;
+  uint32_t bits = 0;
+  int32_t rj[kItemsPerThread], wj[kItemsPerThread];
+  if (xb < x1) {
+    int32_t rs;
+    int32_t r = item_row(t, s_woff, woff, wa, xb, &rs);
+    int32_t rr = r - t.r0;
+    int32_t re = t.staged ? s_woff[rr + 1] : (int32_t)(woff[r + 1] - wa);
+    int32_t pst = pstart[r], slot = pslot[r];
+#pragma unroll
+    for (int j = 0; j < kItemsPerThread; ++j) {
+      rj[j] = r;
+      wj[j] = 0;
+      const int32_t x = xb + j;
+      if (x >= x1) continue;
+      while (x >= re) {  // next row (rows without work are skipped)
+        ++rr;
+        ++r;
+        rs = re;
+        re = t.staged ? s_woff[rr + 1] : (int32_t)(woff[r + 1] - wa);
+        pst = pstart[r];
+        slot = pslot[r];
       }
+      const int32_t w = __ldg(g.lcol + pst + (x - rs));
+      rj[j] = r;
+      wj[j] = w;
+      if (check_candidate(g, d, F, ld, r, w, slot)) bits |= 1u << j;
     }
   }
+  // block exclusive scan of the per-thread survivor counts (thread order is
+  // candidate order)
+  const int32_t c = __popc(bits);
+  int32_t incl = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const int nwarps = B >> 5;
+    const int32_t v = lane < nwarps ? s_warp[lane] : 0;
+    int32_t wi = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(kFull, wi, o);
+      if (lane >= o) wi += y;
+    }
+    if (lane < nwarps) s_warp[lane] = wi - v;
+    if (lane == 31) s_warp[32] = wi;
+  }
+  __syncthreads();
+  // every thread is past the verification: the staged work offsets are no
+  // longer needed, and the survivors (row, vertex) go there in rank order
+  {
+    int32_t *s_pair = s_woff;
+    int32_t q = (incl - c) + s_warp[warp];
+#pragma unroll
+    for (int j = 0; j < kItemsPerThread; ++j)
+      if ((bits >> j) & 1u) {
+        s_pair[2 * q] = rj[j];
+        s_pair[2 * q + 1] = wj[j];
+        ++q;
+      }
+  }
+  if (warp == 0) {
+    // warp-wide look-back: lane l examines tile window_end - l; the window
+    // moves back by 32 tiles while it holds only tile counts
+    const unsigned long long T = (unsigned long long)s_warp[32];
+    unsigned long long prefix = 0;
+    if (tile == 0) {
+      if (lane == 0) atomicExch(lookback, kLbInclusive | T);
+    } else {
+      if (lane == 0) atomicExch(lookback + tile, kLbAggregate | T);
+      int32_t window_end = tile - 1;
+      int32_t polls = 0;
+      bool gave_up = false;
+      while (true) {
+        const int32_t j = window_end - lane;
+        unsigned long long st = j >= 0 ? load_relaxed(lookback + j) : kLbInclusive;
+        unsigned long long flag = st & ~kLbValue;
+        // wait until every tile of the window has published
+        while (__any_sync(kFull, flag == 0)) {
+          if (++polls > kLbSpinLimit) {
+            gave_up = true;
+            break;
+          }
+          __nanosleep(32);
+          if (flag == 0) {
+            st = load_relaxed(lookback + j);
+            flag = st & ~kLbValue;
+          }
+        }
+        if (gave_up) break;
+        const uint32_t has_prefix = __ballot_sync(kFull, flag == kLbInclusive);
+        // tiles up to the nearest inclusive prefix (the lowest such lane)
+        const int32_t stop = has_prefix ? __ffs(has_prefix) - 1 : 31;
+        unsigned long long v = lane <= stop ? (st & kLbValue) : 0;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+        prefix += v;
+        if (has_prefix) break;
+        window_end -= 32;
+      }
+      if (lane == 0) {
+        if (gave_up) atomicExch(lookback + tiles + 2, 1ull);
+        atomicExch(lookback + tile, kLbInclusive | (prefix + T));
+      }
+    }
+    if (lane == 0) {
+      if (T) atomicAdd(lookback + tiles + 1, T);
+      s_prefix = (long long)prefix;
+    }
+  }
+  __syncthreads();
+  // survivor q of the tile is written by thread q (q, q + B, ...): each store
+  // of a warp covers 32 consecutive output rows
+  const int32_t T = s_warp[32];
+  const int64_t base = sink.row0 + s_prefix;
+  for (int32_t q = threadIdx.x; q < T; q += B)
+    put_row<kMode>(sink, d, F, ld, s_woff[2 * q], s_woff[2 * q + 1], base + q);
 }
 
 __global__ void k_split_points(const int64_t *__restrict__ woff, int64_t R, int64_t step,
@@ -750,9 +926,9 @@ void launch_bitmap_to_list(const uint32_t *bitmap, int32_t n_words, int32_t *cnt
   k_bitmap_emit<<<grid_for(n_words, 256), 256, 0, s>>>(bitmap, n_words, off, out);
 }
 
-void launch_pivot(const GraphDev &g, const LevelDesc &d, const int32_t *F, int64_t R,
+void launch_pivot(const GraphDev &g, const LevelDesc &d, const int32_t *F, int64_t ld, int64_t R,
                   int32_t *pstart, uint8_t *pslot, int64_t *work, cudaStream_t s) {
-  k_pivot<<<grid_for(R, 256, 152 * 64), 256, 0, s>>>(g, d, F, R, pstart, pslot, work);
+  k_pivot<<<grid_for(R, 256, 152 * 64), 256, 0, s>>>(g, d, F, ld, R, pstart, pslot, work);
 }
 
 int64_t extend_tiles(int64_t wa, int64_t wb, int32_t block) {
@@ -761,11 +937,13 @@ int64_t extend_tiles(int64_t wa, int64_t wb, int32_t block) {
 }
 
 void launch_tile_rows(const int64_t *woff, int64_t ra, int64_t rb, int64_t wa, int64_t wb,
-                      int32_t block, int32_t *tile_row, cudaStream_t s) {
+                      int32_t block, int32_t *tile_row, unsigned long long *lookback,
+                      cudaStream_t s) {
   const int64_t tiles = extend_tiles(wa, wb, block);
   if (tiles <= 0) return;
-  k_tile_rows<<<grid_for(rb - ra, 256, 152 * 64), 256, 0, s>>>(
-      woff, ra, rb, wa, (int64_t)block * kItemsPerThread, tiles, tile_row);
+  const int64_t n = std::max<int64_t>(rb - ra, lookback ? tiles + kLbExtra : 0);
+  k_tile_rows<<<grid_for(n, 256, 152 * 64), 256, 0, s>>>(
+      woff, ra, rb, wa, (int64_t)block * kItemsPerThread, tiles, tile_row, lookback);
 }
 
 void launch_extend_count(const GraphDev &g, const LevelDesc &d, const int32_t *F, int64_t ld,
@@ -803,6 +981,27 @@ void launch_extend_write(const GraphDev &g, const LevelDesc &d, const int32_t *F
   else
     k_extend_write<kSinkColumns><<<(unsigned)tiles, block, smem, s>>>(
         g, d, F, (int32_t)ld, pstart, woff, tile_row, wa, W, masks, tile_off, sink);
+}
+
+void launch_extend_fused(const GraphDev &g, const LevelDesc &d, const int32_t *F, int64_t ld,
+                         const int32_t *pstart, const uint8_t *pslot, const int64_t *woff,
+                         const int32_t *tile_row, int64_t wa, int64_t wb, int32_t block,
+                         unsigned long long *lookback, const RowSink &sink, cudaStream_t s) {
+  const int64_t tiles = extend_tiles(wa, wb, block);
+  if (tiles <= 0) return;
+  const int32_t W = (int32_t)(wb - wa), T = (int32_t)tiles;
+  // the staged work offsets (tile items + 1 ints), later the survivor pairs
+  // (2 ints per item): at most 32 KB for 1,024 threads
+  const size_t smem = (size_t)((int64_t)block * kItemsPerThread * 2 + 1) * sizeof(int32_t);
+  if (sink.mode == kSinkRows)
+    k_extend_fused<kSinkRows><<<(unsigned)tiles, block, smem, s>>>(
+        g, d, F, (int32_t)ld, pstart, pslot, woff, tile_row, wa, W, T, lookback, sink);
+  else if (sink.mode == kSinkKeys)
+    k_extend_fused<kSinkKeys><<<(unsigned)tiles, block, smem, s>>>(
+        g, d, F, (int32_t)ld, pstart, pslot, woff, tile_row, wa, W, T, lookback, sink);
+  else
+    k_extend_fused<kSinkColumns><<<(unsigned)tiles, block, smem, s>>>(
+        g, d, F, (int32_t)ld, pstart, pslot, woff, tile_row, wa, W, T, lookback, sink);
 }
 
 void launch_split_points(const int64_t *woff, int64_t R, int64_t step, int64_t J,

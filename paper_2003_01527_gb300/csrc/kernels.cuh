@@ -107,8 +107,8 @@ void launch_bitmap_to_list(const uint32_t *bitmap, int32_t n_words, int32_t *cnt
 // Per row: pick the mapped neighbour of pi_i with the fewest neighbours (the
 // pivot) and record its CSR start, its slot in bpos, and its degree as work
 // (int64, so the work array can be scanned in place into offsets).  F has
-// leading dimension R.
-void launch_pivot(const GraphDev &g, const LevelDesc &d, const int32_t *F, int64_t R,
+// leading dimension ld >= R.
+void launch_pivot(const GraphDev &g, const LevelDesc &d, const int32_t *F, int64_t ld, int64_t R,
                   int32_t *pstart, uint8_t *pslot, int64_t *work, cudaStream_t s);
 
 // Number of extend tiles for candidates [wa, wb).
@@ -117,8 +117,10 @@ int64_t extend_tiles(int64_t wa, int64_t wb, int32_t block);
 // tile_row[0..tiles]: first row of every tile of candidates [wa, wb) of rows
 // [ra, rb) (woff = exclusive work offsets of the level).
 // Limits of one extend launch: wb - wa < 2^30, rows < 2^31, ld * (i+1) < 2^31.
+// Also zeroes lookback[0 .. tiles + kLbExtra) when lookback is non-null.
 void launch_tile_rows(const int64_t *woff, int64_t ra, int64_t rb, int64_t wa, int64_t wb,
-                      int32_t block, int32_t *tile_row, cudaStream_t s);
+                      int32_t block, int32_t *tile_row, unsigned long long *lookback,
+                      cudaStream_t s);
 
 // Verification pass over candidates [wa, wb): writes one survivor bit per
 // candidate into masks (if non-null), one survivor count per tile into
@@ -152,6 +154,22 @@ void launch_extend_write(const GraphDev &g, const LevelDesc &d, const int32_t *F
                          const int32_t *pstart, const int64_t *woff, const int32_t *tile_row,
                          int64_t wa, int64_t wb, int32_t block, const uint32_t *masks,
                          const int64_t *tile_off, const RowSink &sink, cudaStream_t s);
+
+// Single-pass form of the count and write passes (not for the count-only
+// last level): survivors of candidates [wa, wb) go to rows sink.row0 + 0, 1,
+// ... in candidate order, exactly where the two passes put them.  lookback
+// needs extend_tiles(wa, wb, block) + kLbExtra words, zeroed (launch_tile_rows
+// does it); afterwards word tiles + 1 holds the survivor count and word
+// tiles + 2 is non-zero if a tile gave up waiting for its predecessors.  The
+// sink needs room for wb - wa rows.
+constexpr int kLbExtra = 3;
+constexpr unsigned long long kLbAggregate = 1ull << 62, kLbInclusive = 2ull << 62;
+constexpr unsigned long long kLbValue = (1ull << 62) - 1;
+constexpr int32_t kLbSpinLimit = 1 << 20;
+void launch_extend_fused(const GraphDev &g, const LevelDesc &d, const int32_t *F, int64_t ld,
+                         const int32_t *pstart, const uint8_t *pslot, const int64_t *woff,
+                         const int32_t *tile_row, int64_t wa, int64_t wb, int32_t block,
+                         unsigned long long *lookback, const RowSink &sink, cudaStream_t s);
 
 // Row boundaries for work-bounded sub-chunks: bounds[j] = the row r with
 // woff[r] <= j*step < woff[r+1] (clamped to [0, R]); bounds[J] = R.

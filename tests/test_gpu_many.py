@@ -28,7 +28,7 @@ def workload(g, num, seed):
     return out
 
 
-@pytest.mark.parametrize("opts", [{}, {"copy_slots": 1},
+@pytest.mark.parametrize("opts", [{}, {"copy_slots": 1}, {"two_pass": True},
                                   {"copy_slots": 2, "mem_budget_bytes": 1 << 21, "chunk_rows": 300}])
 def test_many_host_and_device_match_oracle(gsm_lib, cuda, rmat12, opts):
     g = rmat12
@@ -36,7 +36,7 @@ def test_many_host_and_device_match_oracle(gsm_lib, cuda, rmat12, opts):
     # a query whose label is absent from the graph: no embedding
     items.insert(0, (I.query_from_edges(3, [(0, 1), (1, 2)], [0, 99, 0]), 0,
                      np.zeros((0, 3), np.int32)))
-    m = gsm_lib.Matcher(device=0, **opts)
+    m = gsm_lib.Matcher(device=0, time_kernels=True, **opts)
     m.load_graph(g.row_ptr, g.col, g.labels, validate=True)
     Qs = [m.query(q.k, q.edges, q.labels) for q, _, _ in items]
     host = [torch.zeros(max(c, 1) * q.k, dtype=torch.int32).pin_memory() for q, c, _ in items]
@@ -47,6 +47,12 @@ def test_many_host_and_device_match_oracle(gsm_lib, cuda, rmat12, opts):
         for (q, c, rows), o in zip(items, outs):
             got = o.cpu().numpy()[:c * q.k].reshape(c, q.k)
             assert np.array_equal(got, rows)
+    # which form of the verification levels ran
+    launches = {st["name"]: st["launches"] for st in m.kernel_stats()}
+    if opts.get("two_pass"):
+        assert launches["extend_fused"] == 0 and launches["extend_write"] > 0
+    else:
+        assert launches["extend_fused"] > 0
     # the last query's rows stay readable through gsm_last_rows
     q, c, rows = items[-1]
     buf = np.zeros((max(c, 1), q.k), np.int32)

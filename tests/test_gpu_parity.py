@@ -155,7 +155,8 @@ def test_results_do_not_depend_on_chunking_or_block_size(gsm_lib, rmat12):
     ref = None
     for opts in ({}, {"chunk_rows": 1}, {"chunk_rows": 7}, {"block_size": 128},
                  {"block_size": 1024}, {"block_size": 512, "chunk_rows": 33},
-                 {"mem_budget_bytes": 1 << 21}):
+                 {"mem_budget_bytes": 1 << 21}, {"two_pass": True},
+                 {"two_pass": True, "block_size": 1024, "chunk_rows": 33}):
         m = gsm_lib.Matcher(device=0, **opts)
         load(m, rmat12, validate=False)
         out = [m.enumerate(m.query(q.k, q.edges, q.labels)) for q in qs]
