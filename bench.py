@@ -334,7 +334,8 @@ def run_gpu(args):
     if args.queries:
         keep = [int(x) for x in args.queries.split(",")]
         queries = [queries[i] for i in keep]
-    M = gsm.Matcher(device=local, time_kernels=True, filter_rounds=args.filter_rounds)
+    M = gsm.Matcher(device=local, time_kernels=True, filter_rounds=args.filter_rounds,
+                    block_size=args.block_size)
     M.load_graph(g.row_ptr, g.col, g.labels, validate=True)
     Qs = [M.query(q["k"], q["edges"], q["labels"]).restrict(0, 0, q["root_hi"]) for q in queries]
     outs = [torch.empty(max(q["count"], 1) * q["k"], dtype=torch.int32, device="cuda")
@@ -448,6 +449,7 @@ def run_gpu(args):
                    "embeddings_per_step": per_step, "mode": "enumerate, sorted rows on device",
                    "l2": "flushed (512 MB write) before every timed step",
                    "filter_rounds": args.filter_rounds,
+                   "block_size": args.block_size or 256,
                    "parallelism": f"replicas x{world}"},
         "queries_per_sec": round(qps, 2),
         "roofline": {"bound": "hbm", "kernel": dom["name"], "achieved": round(achieved, 1),
@@ -551,6 +553,8 @@ def main():
                     help="seconds of Poisson arrivals per served rate")
     ap.add_argument("--filter-rounds", type=int, default=0,
                     help="candidate refinement rounds after the first filter pass")
+    ap.add_argument("--block-size", type=int, default=0,
+                    help="threads per CTA of the verification kernels (0 = the library's)")
     ap.add_argument("--queries", default="",
                     help="comma-separated query indices (a smaller case for profiling)")
     args = ap.parse_args()

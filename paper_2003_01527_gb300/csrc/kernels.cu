@@ -648,7 +648,8 @@ __global__ void __launch_bounds__(1024) k_extend_fused(
     GraphDev g, LevelDesc d, const int32_t *__restrict__ F, int32_t ld,
     const int32_t *__restrict__ pstart, const uint8_t *__restrict__ pslot,
     const int64_t *__restrict__ woff, const int32_t *__restrict__ tile_row, int64_t wa,
-    int32_t W, int32_t tiles, unsigned long long *__restrict__ lookback, RowSink sink) {
+    int32_t W, int32_t tiles, unsigned long long *__restrict__ lookback, RowSink sink,
+    bool stage_out) {
   static_assert(kItemsPerThread == 4, "four candidates per thread");
   extern __shared__ int32_t s_woff[];
   __shared__ int32_t s_tile;
@@ -779,10 +780,25 @@ __global__ void __launch_bounds__(1024) k_extend_fused(
     }
   }
   __syncthreads();
-  // survivor q of the tile is written by thread q (q, q + B, ...): each store
-  // of a warp covers 32 consecutive output rows
   const int32_t T = s_warp[32];
   const int64_t base = sink.row0 + s_prefix;
+  if (kMode == kSinkRows && stage_out) {
+    // the tile's result rows are one contiguous block of T*k ints: assemble
+    // them in shared memory, then store the block with contiguous stores
+    const int32_t k = sink.k;
+    int32_t *s_out = s_woff + 2 * tile_items;
+    for (int32_t q = threadIdx.x; q < T; q += B) {
+      const int32_t r = s_woff[2 * q];
+      for (int cc = 0; cc < d.i; ++cc) s_out[q * k + d.out_col[cc]] = F[cc * ld + r];
+      s_out[q * k + d.out_col[d.i]] = s_woff[2 * q + 1];
+    }
+    __syncthreads();
+    int32_t *dst = (int32_t *)sink.out + base * k;
+    for (int32_t e = threadIdx.x; e < T * k; e += B) dst[e] = s_out[e];
+    return;
+  }
+  // survivor q of the tile is written by thread q (q, q + B, ...): each store
+  // of a warp covers 32 consecutive output rows
   for (int32_t q = threadIdx.x; q < T; q += B)
     put_row<kMode>(sink, d, F, ld, s_woff[2 * q], s_woff[2 * q + 1], base + q);
 }
@@ -991,17 +1007,22 @@ void launch_extend_fused(const GraphDev &g, const LevelDesc &d, const int32_t *F
   if (tiles <= 0) return;
   const int32_t W = (int32_t)(wb - wa), T = (int32_t)tiles;
   // the staged work offsets (tile items + 1 ints), later the survivor pairs
-  // (2 ints per item): at most 32 KB for 1,024 threads
-  const size_t smem = (size_t)((int64_t)block * kItemsPerThread * 2 + 1) * sizeof(int32_t);
+  // (2 ints per item): at most 32 KB for 1,024 threads; result rows are
+  // assembled after them when k ints per item also fit in 48 KB
+  const int64_t items = (int64_t)block * kItemsPerThread;
+  size_t smem = (size_t)(items * 2 + 1) * sizeof(int32_t);
+  const size_t smem_rows = (size_t)(items * (2 + sink.k) + 1) * sizeof(int32_t);
+  const bool stage = sink.mode == kSinkRows && smem_rows <= 48 * 1024;
+  if (stage) smem = smem_rows;
   if (sink.mode == kSinkRows)
     k_extend_fused<kSinkRows><<<(unsigned)tiles, block, smem, s>>>(
-        g, d, F, (int32_t)ld, pstart, pslot, woff, tile_row, wa, W, T, lookback, sink);
+        g, d, F, (int32_t)ld, pstart, pslot, woff, tile_row, wa, W, T, lookback, sink, stage);
   else if (sink.mode == kSinkKeys)
     k_extend_fused<kSinkKeys><<<(unsigned)tiles, block, smem, s>>>(
-        g, d, F, (int32_t)ld, pstart, pslot, woff, tile_row, wa, W, T, lookback, sink);
+        g, d, F, (int32_t)ld, pstart, pslot, woff, tile_row, wa, W, T, lookback, sink, false);
   else
     k_extend_fused<kSinkColumns><<<(unsigned)tiles, block, smem, s>>>(
-        g, d, F, (int32_t)ld, pstart, pslot, woff, tile_row, wa, W, T, lookback, sink);
+        g, d, F, (int32_t)ld, pstart, pslot, woff, tile_row, wa, W, T, lookback, sink, false);
 }
 
 void launch_split_points(const int64_t *woff, int64_t R, int64_t step, int64_t J,
