@@ -16,6 +16,7 @@
 #include "filter_body.cuh"
 #include "segments.cuh"
 #include "kernels.cuh"
+#include "verify.cuh"
 
 namespace gsm {
 namespace {
@@ -24,10 +25,6 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kScanThreads = 256;
 constexpr int kScanIpt = 8;
 constexpr int kScanTile = kScanThreads * kScanIpt;
-
-__device__ __forceinline__ bool bitmap_has(const uint32_t *__restrict__ bm, int32_t v) {
-  return (__ldg(bm + (v >> 5)) >> (v & 31)) & 1u;
-}
 
 // Binary search of key in the ascending slice col[beg, end).
 __device__ __forceinline__ bool row_contains(const int32_t *__restrict__ col, int32_t beg,
@@ -377,79 +374,6 @@ __global__ void k_tile_rows(const int64_t *__restrict__ woff, int64_t ra, int64_
   if (blockIdx.x == 0 && threadIdx.x == 0) tile_row[tiles] = (int32_t)(rb - 1);
 }
 
-// Inside one launch every index is 32-bit: candidates are numbered locally
-// from wa (a launch covers fewer than 2^30), rows and frontier elements stay
-// below 2^31 (the driver chunks frontiers to that), only output addresses of
-// the final rows are 64-bit.
-//
-// A tile's rows [r0, r0+span): their work offsets, relative to wa, are staged
-// in shared memory when they fit (span <= tile items: always, unless rows
-// without work pile up); items then find their row by binary search there,
-// otherwise in the global offsets.
-struct TileRows {
-  int32_t r0;
-  int32_t span;
-  bool staged;
-};
-
-__device__ __forceinline__ TileRows stage_rows(const int64_t *__restrict__ woff,
-                                               const int32_t *__restrict__ tile_row, int64_t wa,
-                                               int32_t tile_items, int32_t *s_woff,
-                                               int32_t tile) {
-  TileRows t;
-  t.r0 = tile_row[tile];
-  t.span = tile_row[tile + 1] + 1 - t.r0;
-  t.staged = t.span <= tile_items;
-  if (t.staged)
-    for (int32_t j = threadIdx.x; j <= t.span; j += blockDim.x)
-      s_woff[j] = (int32_t)(woff[t.r0 + j] - wa);
-  __syncthreads();
-  return t;
-}
-
-// Row of local item x and the local offset where that row's candidates start.
-__device__ __forceinline__ int32_t item_row(const TileRows &t, const int32_t *s_woff,
-                                            const int64_t *__restrict__ woff, int64_t wa,
-                                            int32_t x, int32_t *row_start) {
-  int32_t lo = 0, hi = t.span;  // largest j in [0, span) with offset(r0+j) <= x
-  if (t.staged) {
-    while (hi - lo > 1) {
-      const int32_t mid = (lo + hi) >> 1;
-      if (s_woff[mid] <= x) lo = mid; else hi = mid;
-    }
-    *row_start = s_woff[lo];
-  } else {
-    while (hi - lo > 1) {
-      const int32_t mid = (lo + hi) >> 1;
-      if (woff[t.r0 + mid] - wa <= x) lo = mid; else hi = mid;
-    }
-    *row_start = (int32_t)(woff[t.r0 + lo] - wa);
-  }
-  return t.r0 + lo;
-}
-
-// The one-step check of Sec. 3.2 verification for candidate w of row r:
-// label + signature (bitmap of C(pi_i)), injectivity against same-label,
-// non-adjacent positions, and presence of every query edge to a mapped
-// neighbour other than the pivot (binary search in that neighbour's row).
-__device__ __forceinline__ bool check_candidate(const GraphDev &g, const LevelDesc &d,
-                                                const int32_t *__restrict__ F, int32_t ld,
-                                                int32_t r, int32_t w, int slot) {
-  if (!bitmap_has(d.bitmap, w)) return false;
-  for (int t = 0; t < d.ninj; ++t)
-    if (F[d.inj[t] * ld + r] == w) return false;
-  for (int t = 0; t < d.nlt; ++t)
-    if (!(w < F[d.lt[t] * ld + r])) return false;
-  for (int t = 0; t < d.ngt; ++t)
-    if (!(w > F[d.gt[t] * ld + r])) return false;
-  for (int b = 0; b < d.nb; ++b) {
-    if (b == slot) continue;
-    const int32_t x = F[d.bpos[b] * ld + r];
-    if (!row_contains_l(g, x, d.lab, w)) return false;
-  }
-  return true;
-}
-
 // Verification pass.  Thread t of a tile takes the kItemsPerThread consecutive
 // candidates 4t .. 4t+3: one row search serves all of them (rows change inside
 // the group only at a row boundary), and the warp's 128 candidates are
@@ -494,7 +418,7 @@ __global__ void __launch_bounds__(1024) k_extend_count(
         slot = pslot[r];
       }
       const int32_t w = __ldg(g.lcol + pst + (x - rs));
-      if (check_candidate(g, d, F, ld, r, w, slot)) bits |= 1u << j;
+      if (check_candidate(g, d, ColumnRow{F, ld, r}, w, slot)) bits |= 1u << j;
     }
   }
   uint32_t word = bits << (4 * (lane & 7));
@@ -512,40 +436,6 @@ __global__ void __launch_bounds__(1024) k_extend_count(
   if (threadIdx.x == 0) {
     if (tile_cnt) tile_cnt[blockIdx.x] = s_count;
     if (total && s_count) atomicAdd(total, (unsigned long long)s_count);
-  }
-}
-
-// Writes row r of F extended by w as output row `row` of the sink (see
-// RowSink): position c goes to column d.out_col[c], w to d.out_col[d.i].
-template <int kMode>
-__device__ __forceinline__ void put_row(const RowSink &sink, const LevelDesc &d,
-                                        const int32_t *__restrict__ F, int32_t ld, int32_t r,
-                                        int32_t w, int64_t row) {
-  const int32_t i = d.i;
-  if (kMode == kSinkColumns) {
-    int32_t *o = (int32_t *)sink.out + row;
-    for (int c = 0; c < i; ++c) o[d.out_col[c] * sink.ld] = F[c * ld + r];
-    o[d.out_col[i] * sink.ld] = w;
-  } else if (kMode == kSinkRows) {
-    int32_t *o = (int32_t *)sink.out + row * sink.k;
-    for (int c = 0; c < i; ++c) o[d.out_col[c]] = F[c * ld + r];
-    o[d.out_col[i]] = w;
-  } else {
-    // packed key: column j occupies bits [(k-1-j)*b, (k-j)*b); word t
-    // collects the columns that overlap bits [64t, 64t+64)
-    uint64_t *o = (uint64_t *)sink.out + row;
-    for (int t = 0; t < sink.nw; ++t) {
-      uint64_t kw = 0;
-      for (int c = 0; c <= i; ++c) {
-        const uint64_t v = (uint32_t)(c < i ? F[c * ld + r] : w);
-        const int32_t lo = (sink.k - 1 - d.out_col[c]) * sink.bits - 64 * t;
-        if (lo >= 0 && lo < 64)
-          kw |= v << lo;
-        else if (lo < 0 && lo + sink.bits > 0)
-          kw |= v >> (-lo);
-      }
-      o[t * sink.ld] = kw;
-    }
   }
 }
 
@@ -621,14 +511,8 @@ __global__ void __launch_bounds__(1024) k_extend_write(
     int32_t rs;
     const int32_t r = item_row(t, s_woff, woff, wa, x, &rs);
     const int32_t w = __ldg(g.lcol + pstart[r] + (x - rs));
-    put_row<kMode>(sink, d, F, ld, r, w, sink.row0 + base + q);
+    put_row<kMode>(sink, d, ColumnRow{F, ld, r}, w, sink.row0 + base + q);
   }
-}
-
-__device__ __forceinline__ unsigned long long load_relaxed(const unsigned long long *p) {
-  unsigned long long v;
-  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
 }
 
 // Count and write in one pass (single-pass compaction): a tile takes its
@@ -690,7 +574,7 @@ __global__ void __launch_bounds__(1024) k_extend_fused(
       const int32_t w = __ldg(g.lcol + pst + (x - rs));
       rj[j] = r;
       wj[j] = w;
-      if (check_candidate(g, d, F, ld, r, w, slot)) bits |= 1u << j;
+      if (check_candidate(g, d, ColumnRow{F, ld, r}, w, slot)) bits |= 1u << j;
     }
   }
   // block exclusive scan of the per-thread survivor counts (thread order is
@@ -800,7 +684,7 @@ __global__ void __launch_bounds__(1024) k_extend_fused(
   // survivor q of the tile is written by thread q (q, q + B, ...): each store
   // of a warp covers 32 consecutive output rows
   for (int32_t q = threadIdx.x; q < T; q += B)
-    put_row<kMode>(sink, d, F, ld, s_woff[2 * q], s_woff[2 * q + 1], base + q);
+    put_row<kMode>(sink, d, ColumnRow{F, ld, s_woff[2 * q]}, s_woff[2 * q + 1], base + q);
 }
 
 __global__ void k_split_points(const int64_t *__restrict__ woff, int64_t R, int64_t step,

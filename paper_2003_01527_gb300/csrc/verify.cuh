@@ -1,0 +1,135 @@
+// Device helpers of the verification kernels (extend count, write, single
+// pass): tile row staging, the candidate check and the row writer.
+#pragma once
+
+#include "kernels.cuh"
+#include "segments.cuh"
+
+namespace gsm {
+
+__device__ __forceinline__ bool bitmap_has(const uint32_t *__restrict__ bm, int32_t v) {
+  return (__ldg(bm + (v >> 5)) >> (v & 31)) & 1u;
+}
+
+// Inside one launch every index is 32-bit: candidates are numbered locally
+// from wa (a launch covers fewer than 2^30), rows and frontier elements stay
+// below 2^31 (the driver chunks frontiers to that), only output addresses of
+// the final rows are 64-bit.
+//
+// A tile's rows [r0, r0+span): their work offsets, relative to wa, are staged
+// in shared memory when they fit (span <= tile items: always, unless rows
+// without work pile up); items then find their row by binary search there,
+// otherwise in the global offsets.
+struct TileRows {
+  int32_t r0;
+  int32_t span;
+  bool staged;
+};
+
+__device__ __forceinline__ TileRows stage_rows(const int64_t *__restrict__ woff,
+                                               const int32_t *__restrict__ tile_row, int64_t wa,
+                                               int32_t tile_items, int32_t *s_woff,
+                                               int32_t tile) {
+  TileRows t;
+  t.r0 = tile_row[tile];
+  t.span = tile_row[tile + 1] + 1 - t.r0;
+  t.staged = t.span <= tile_items;
+  if (t.staged)
+    for (int32_t j = threadIdx.x; j <= t.span; j += blockDim.x)
+      s_woff[j] = (int32_t)(woff[t.r0 + j] - wa);
+  __syncthreads();
+  return t;
+}
+
+// Row of local item x and the local offset where that row's candidates start.
+__device__ __forceinline__ int32_t item_row(const TileRows &t, const int32_t *s_woff,
+                                            const int64_t *__restrict__ woff, int64_t wa,
+                                            int32_t x, int32_t *row_start) {
+  int32_t lo = 0, hi = t.span;  // largest j in [0, span) with offset(r0+j) <= x
+  if (t.staged) {
+    while (hi - lo > 1) {
+      const int32_t mid = (lo + hi) >> 1;
+      if (s_woff[mid] <= x) lo = mid; else hi = mid;
+    }
+    *row_start = s_woff[lo];
+  } else {
+    while (hi - lo > 1) {
+      const int32_t mid = (lo + hi) >> 1;
+      if (woff[t.r0 + mid] - wa <= x) lo = mid; else hi = mid;
+    }
+    *row_start = (int32_t)(woff[t.r0 + lo] - wa);
+  }
+  return t.r0 + lo;
+}
+
+// Position c of row r of a column-major frontier (leading dimension ld).
+struct ColumnRow {
+  const int32_t *__restrict__ F;
+  int32_t ld, r;
+  __device__ __forceinline__ int32_t operator()(int c) const { return F[c * ld + r]; }
+};
+
+// The one-step check of Sec. 3.2 verification for candidate w of a partial
+// embedding (row(c) = the image of pi_c): label + signature (bitmap of
+// C(pi_i)), injectivity against same-label, non-adjacent positions, the
+// ordering constraints, and presence of every query edge to a mapped
+// neighbour other than the pivot (binary search in that neighbour's label
+// segment).
+template <typename Row>
+__device__ __forceinline__ bool check_candidate(const GraphDev &g, const LevelDesc &d,
+                                                const Row &row, int32_t w, int slot) {
+  if (!bitmap_has(d.bitmap, w)) return false;
+  for (int t = 0; t < d.ninj; ++t)
+    if (row(d.inj[t]) == w) return false;
+  for (int t = 0; t < d.nlt; ++t)
+    if (!(w < row(d.lt[t]))) return false;
+  for (int t = 0; t < d.ngt; ++t)
+    if (!(w > row(d.gt[t]))) return false;
+  for (int b = 0; b < d.nb; ++b) {
+    if (b == slot) continue;
+    if (!row_contains_l(g, row(d.bpos[b]), d.lab, w)) return false;
+  }
+  return true;
+}
+
+// Writes the partial embedding `src` (src(c) = image of pi_c, c < d.i)
+// extended by w as output row `row` of the sink (see RowSink): position c goes
+// to column d.out_col[c], w to d.out_col[d.i].
+template <int kMode, typename Row>
+__device__ __forceinline__ void put_row(const RowSink &sink, const LevelDesc &d, const Row &src,
+                                        int32_t w, int64_t row) {
+  const int32_t i = d.i;
+  if (kMode == kSinkColumns) {
+    int32_t *o = (int32_t *)sink.out + row;
+    for (int c = 0; c < i; ++c) o[d.out_col[c] * sink.ld] = src(c);
+    o[d.out_col[i] * sink.ld] = w;
+  } else if (kMode == kSinkRows) {
+    int32_t *o = (int32_t *)sink.out + row * sink.k;
+    for (int c = 0; c < i; ++c) o[d.out_col[c]] = src(c);
+    o[d.out_col[i]] = w;
+  } else {
+    // packed key: column j occupies bits [(k-1-j)*b, (k-j)*b); word t
+    // collects the columns that overlap bits [64t, 64t+64)
+    uint64_t *o = (uint64_t *)sink.out + row;
+    for (int t = 0; t < sink.nw; ++t) {
+      uint64_t kw = 0;
+      for (int c = 0; c <= i; ++c) {
+        const uint64_t v = (uint32_t)(c < i ? src(c) : w);
+        const int32_t lo = (sink.k - 1 - d.out_col[c]) * sink.bits - 64 * t;
+        if (lo >= 0 && lo < 64)
+          kw |= v << lo;
+        else if (lo < 0 && lo + sink.bits > 0)
+          kw |= v >> (-lo);
+      }
+      o[t * sink.ld] = kw;
+    }
+  }
+}
+
+__device__ __forceinline__ unsigned long long load_relaxed(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+}  // namespace gsm
