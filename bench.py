@@ -16,6 +16,10 @@ is resident; L2 is flushed before each timed step (the graph is smaller than
 L2).  The end-to-end figure (`e2e`) uploads the graph from pinned host memory
 and lists every slice into pinned host buffers through the same call.
 
+`compressed_frontiers` (same line): the same slices with frontier rows kept
+as (parent row, new vertex) instead of full tuples, against the default
+layout: time per step and peak budgeted frontier memory, rows checked.
+
 `unlabelled_counts` (same line): on unlabelled R-MAT scale 20, the 3-path count
 (checked against sum d(d-1)), the ordered and distinct (symmetry-broken)
 triangle counts (checked: distinct x |Aut| = ordered) and the distinct
@@ -184,6 +188,42 @@ def batched_and_served(gsm, torch, device, serve_seconds):
     gsm.gsm_server_stop(M.ctx)
     out["served"] = served
     M.close()
+    return out
+
+
+def compressed_frontiers(gsm, torch, device, g, queries, steps):
+    """The same query slices with compressed partial results (frontier rows
+    as (parent row, new vertex)): time per step, peak budgeted frontier memory
+    against the uncompressed path, rows checked against the oracle digests."""
+    out = {}
+    for name, compressed in (("columns", False), ("compressed", True)):
+        M = gsm.Matcher(device=device, compressed=compressed)
+        M.load_graph(g.row_ptr, g.col, g.labels)
+        Qs = [M.query(q["k"], q["edges"], q["labels"]).restrict(0, 0, q["root_hi"])
+              for q in queries]
+        outs = [torch.empty(max(q["count"], 1) * q["k"], dtype=torch.int32, device="cuda")
+                for q in queries]
+        peak = 0
+        for Q, o in zip(Qs, outs):  # one query per call: the peak of each
+            M.enumerate(Q, out=o)
+            peak = max(peak, M.last_run_stats()["peak_bytes"])
+        for q, o in zip(queries, outs):
+            rows = o[:q["count"] * q["k"]].cpu().numpy().astype("<i4")
+            if hashlib.sha256(rows.tobytes()).hexdigest() != q["rows_sha256"]:
+                raise SystemExit(f"{name} frontiers: result mismatch on a query slice")
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(M.stream)
+        for _ in range(steps):
+            counts = M.enumerate_many(Qs, outs)
+        ev1.record(M.stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / steps
+        out[name] = {"ms_per_step": round(ms, 3),
+                     "embeddings_per_sec": round(sum(counts) / (ms / 1e3), 1),
+                     "peak_budgeted_bytes": int(peak)}
+        M.close()
+    out["bit_exact"] = True
     return out
 
 
@@ -436,6 +476,9 @@ def run_gpu(args):
     cpu = cpu_baseline(g, queries) if (rank == 0 and world == 1 and not args.no_cpu) else None
     batched = None
     unlabelled = None
+    compressed = None
+    if not args.queries:
+        compressed = compressed_frontiers(gsm, torch, local, g, queries, 5)
     if not args.no_batch and not args.queries:
         batched = batched_and_served(gsm, torch, local, args.serve_seconds)
         unlabelled = unlabelled_counts(gsm, torch, local)
@@ -465,6 +508,7 @@ def run_gpu(args):
         "cpu_baseline": cpu,
         "batched_vs_plain": batched,
         "unlabelled_counts": unlabelled,
+        "compressed_frontiers": compressed,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

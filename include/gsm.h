@@ -66,6 +66,14 @@ typedef void (*gsm_free_fn)(void *alloc_ctx, void *ptr, size_t bytes, void *stre
  * tiles) whenever its output has room for one row per candidate, and two
  * passes otherwise; results are identical either way. */
 #define GSM_OPT_TWO_PASS 2
+/* Compressed partial results (the lossless form of Sec. 3.2's hashed partial
+ * results): a frontier row of width i is stored as (parent row, new vertex),
+ * 8 bytes whatever i, instead of i vertex ids, and decoded through the parent
+ * rows of the earlier levels (kept alive by the depth-first chunking).  Less
+ * memory and write traffic per level for deep queries, i-1 dependent loads
+ * per row read; results are identical.  Levels always take the single pass
+ * (rows are split until one row per candidate fits). */
+#define GSM_OPT_COMPRESSED_FRONTIERS 4
 
 typedef struct gsm_options {
   /* Cap on device memory for intermediate frontiers and scratch, in bytes.

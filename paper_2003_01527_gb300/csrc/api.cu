@@ -23,6 +23,7 @@
 
 #include "batch.h"
 #include "gsm.h"
+#include "compressed.cuh"
 #include "kernels.cuh"
 #include "query_access.h"
 
@@ -787,6 +788,53 @@ void process_fused(Run &R, int32_t i, const int32_t *F, int64_t ld, const int32_
   stack_release(ctx, mk);
 }
 
+// Row boundaries of the launches over rows [0, rows) of a level whose work
+// offsets are woff (W candidates in all): pieces of at most R.wcap
+// candidates, merged with multiples of chunk_rows; bw receives the work
+// offset at every boundary.
+void level_chunks(Run &R, const int64_t *woff, int64_t rows, int64_t W,
+                  std::vector<int64_t> &bnd, std::vector<int64_t> &bw) {
+  gsm_ctx *ctx = R.ctx;
+  const bool split_w = W > R.wcap;
+  const bool split_r = R.chunk_rows > 0 && rows > R.chunk_rows;
+  if (!split_w && !split_r) {
+    bnd = {0, rows};
+    bw = {0, W};
+    return;
+  }
+  if (split_w) {
+    const int64_t step = std::max<int64_t>(1, R.wcap - ctx->max_deg);
+    const int64_t J = (W + step - 1) / step;
+    Carve cv;
+    const size_t o_b = cv.add<int64_t>(J + 1), o_w = cv.add<int64_t>(J + 1);
+    char *sc = (char *)scratch_get(ctx, cv.off);
+    launch_split_points(woff, rows, step, J, (int64_t *)(sc + o_b), (int64_t *)(sc + o_w),
+                        ctx->stream);
+    CU(cudaGetLastError());
+    bnd.resize(J + 1);
+    CU(cudaMemcpyAsync(bnd.data(), sc + o_b, sizeof(int64_t) * (J + 1), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    bnd[0] = 0;
+  } else {
+    bnd = {0, rows};
+  }
+  if (split_r) {
+    std::vector<int64_t> extra;
+    for (int64_t r = R.chunk_rows; r < rows; r += R.chunk_rows) extra.push_back(r);
+    bnd.insert(bnd.end(), extra.begin(), extra.end());
+  }
+  std::sort(bnd.begin(), bnd.end());
+  bnd.erase(std::unique(bnd.begin(), bnd.end()), bnd.end());
+  // work offset at every boundary
+  bw.resize(bnd.size());
+  for (size_t j = 0; j < bnd.size(); ++j) {
+    CU(cudaMemcpyAsync(&bw[j], woff + bnd[j], sizeof(int64_t), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+  }
+  CU(cudaStreamSynchronize(ctx->stream));
+}
+
 // Extends rows of width i (F, `rows` of them, leading dimension ld) through
 // the remaining levels.
 void recurse(Run &R, int32_t i, const int32_t *F, int64_t ld, int64_t rows) {
@@ -805,47 +853,123 @@ void recurse(Run &R, int32_t i, const int32_t *F, int64_t ld, int64_t rows) {
   const int64_t W = read_i64(ctx, woff + rows);
   ctx->run.frontier[i] += (uint64_t)rows;
   ctx->run.candidates[i] += (uint64_t)W;
-  const bool split_w = W > R.wcap;
-  const bool split_r = R.chunk_rows > 0 && rows > R.chunk_rows;
-  if (!split_w && !split_r) {
-    process_sub(R, i, F, ld, pstart, pslot, woff, 0, rows, 0, W);
-  } else {
-    // row boundaries: work targets (each piece <= wcap) merged with multiples of chunk_rows
-    std::vector<int64_t> bnd, bw;
-    if (split_w) {
-      const int64_t step = std::max<int64_t>(1, R.wcap - ctx->max_deg);
-      const int64_t J = (W + step - 1) / step;
-      Carve cv;
-      const size_t o_b = cv.add<int64_t>(J + 1), o_w = cv.add<int64_t>(J + 1);
-      char *sc = (char *)scratch_get(ctx, cv.off);
-      launch_split_points(woff, rows, step, J, (int64_t *)(sc + o_b), (int64_t *)(sc + o_w),
-                          ctx->stream);
-      CU(cudaGetLastError());
-      bnd.resize(J + 1);
-      CU(cudaMemcpyAsync(bnd.data(), sc + o_b, sizeof(int64_t) * (J + 1), cudaMemcpyDeviceToHost,
-                         ctx->stream));
-      CU(cudaStreamSynchronize(ctx->stream));
-      bnd[0] = 0;
+  std::vector<int64_t> bnd, bw;
+  level_chunks(R, woff, rows, W, bnd, bw);
+  for (size_t j = 0; j + 1 < bnd.size(); ++j)
+    process_sub(R, i, F, ld, pstart, pslot, woff, bnd[j], bnd[j + 1], bw[j], bw[j + 1]);
+  stack_release(ctx, mk);
+}
+
+// ---- compressed frontiers (GSM_OPT_COMPRESSED_FRONTIERS): a row of width i
+// is (parent row of width i-1, new vertex); levels otherwise as above, always
+// in the single pass
+
+void recurse_c(Run &R, int32_t i, const CFrontier &f, int64_t rows);
+
+void process_c(Run &R, int32_t i, const CFrontier &f, const int32_t *pstart, const uint8_t *pslot,
+               const int64_t *woff, int64_t ra, int64_t rb, int64_t wa, int64_t wb) {
+  gsm_ctx *ctx = R.ctx;
+  const LevelDesc &d = R.lv[i];
+  const bool last = i == R.k - 1;
+  const int64_t W = wb - wa, nrows = rb - ra;
+  if (W <= 0) return;
+  const bool count_only = last && !R.enumerate;
+  if (!count_only) {
+    // room for one output row per candidate, else split the rows
+    bool fits;
+    if (last) {
+      fits = (double)W * (double)R.acc_row_bytes() <= kFusedResultBytes;
     } else {
-      bnd = {0, rows};
+      const size_t need = 2 * align_up(4 * (size_t)W) + align_up(4 * (size_t)W) +
+                          align_up((size_t)W) + align_up(8 * ((size_t)W + 1));
+      fits = stack_fits(ctx, need);
     }
-    if (split_r) {
-      std::vector<int64_t> extra;
-      for (int64_t r = R.chunk_rows; r < rows; r += R.chunk_rows) extra.push_back(r);
-      bnd.insert(bnd.end(), extra.begin(), extra.end());
+    if (!fits) {
+      if (nrows <= 1)
+        FAIL(GSM_ERR_BUDGET, "the %lld candidates of one row need more than the budget",
+             (long long)W);
+      const int64_t mid = ra + nrows / 2;
+      const int64_t wmid = read_i64(ctx, woff + mid);
+      process_c(R, i, f, pstart, pslot, woff, ra, mid, wa, wmid);
+      process_c(R, i, f, pstart, pslot, woff, mid, rb, wmid, wb);
+      return;
     }
-    std::sort(bnd.begin(), bnd.end());
-    bnd.erase(std::unique(bnd.begin(), bnd.end()), bnd.end());
-    // work offset at every boundary
-    bw.resize(bnd.size());
-    for (size_t j = 0; j < bnd.size(); ++j) {
-      CU(cudaMemcpyAsync(&bw[j], woff + bnd[j], sizeof(int64_t), cudaMemcpyDeviceToHost,
-                         ctx->stream));
-    }
-    CU(cudaStreamSynchronize(ctx->stream));
-    for (size_t j = 0; j + 1 < bnd.size(); ++j)
-      process_sub(R, i, F, ld, pstart, pslot, woff, bnd[j], bnd[j + 1], bw[j], bw[j + 1]);
   }
+  ctx->run.chunks += 1;
+  const int64_t tiles = extend_tiles(wa, wb, R.block);
+  Carve cv;
+  const size_t o_row = cv.add<int32_t>(tiles + 1);
+  const size_t o_lb = cv.add<unsigned long long>(tiles + kLbExtra);
+  char *sc = (char *)scratch_get(ctx, cv.off);
+  int32_t *tile_row = (int32_t *)(sc + o_row);
+  unsigned long long *lb = (unsigned long long *)(sc + o_lb);
+  timed(ctx, K_PIVOT, 8.0 * (nrows + tiles) + 8.0 * tiles, (uint64_t)tiles, 1, [&] {
+    launch_tile_rows(woff, ra, rb, wa, wb, R.block, tile_row, lb, ctx->stream);
+  });
+  // candidate reads: the pivot start and the row (decoded through i-1
+  // parent indices, 8 bytes each) per row, 4 bytes per candidate
+  const double read_bytes = (double)nrows * (8.0 * i + 5.0) + 4.0 * (double)W;
+  const Mark mk = stack_mark(ctx);
+  CSink sink{};
+  int32_t *Pn = nullptr, *Vn = nullptr;
+  if (count_only) {
+    sink.mode = kCSinkCount;
+    sink.total = R.d_total;
+  } else if (last) {
+    ensure_acc(R, R.acc_rows + (uint64_t)W);
+    sink.mode = R.acc_mode == kSinkKeys ? kCSinkKeys : kCSinkRows;
+    sink.rows = RowSink{R.acc_mode, R.k, R.key_bits, R.key_nw, R.acc_ld, (int64_t)R.acc_rows,
+                        ctx->acc[0]};
+  } else {
+    Pn = (int32_t *)stack_push(ctx, 4 * (size_t)W);
+    Vn = (int32_t *)stack_push(ctx, 4 * (size_t)W);
+    sink.mode = kCSinkPairs;
+    sink.pn = Pn;
+    sink.vn = Vn;
+  }
+  timed(ctx, K_FUSED, read_bytes, (uint64_t)W, 1, [&] {
+    launch_cextend(R.g, d, f, i, pstart, pslot, woff, tile_row, wa, wb, R.block, lb, sink,
+                   ctx->stream);
+  });
+  if (count_only) return;
+  fetch(ctx, lb + tiles + 1, 2 * sizeof(unsigned long long));
+  const int64_t S = ((volatile int64_t *)ctx->h_stage)[0];
+  if (((volatile int64_t *)ctx->h_stage)[1])
+    FAIL(GSM_ERR_TIMEOUT, "a verification tile waited too long for its predecessors");
+  ctx->kstats[K_FUSED].algo_bytes += (double)S * (last ? (double)R.acc_row_bytes() : 8.0);
+  if (last) {
+    R.acc_rows += (uint64_t)S;
+    return;
+  }
+  if (S > 0) {
+    CFrontier next = f;
+    next.V[i + 1] = Vn;
+    next.P[i + 1] = Pn;
+    recurse_c(R, i + 1, next, S);
+  }
+  stack_release(ctx, mk);
+}
+
+void recurse_c(Run &R, int32_t i, const CFrontier &f, int64_t rows) {
+  gsm_ctx *ctx = R.ctx;
+  if (rows <= 0) return;
+  const LevelDesc &d = R.lv[i];
+  const Mark mk = stack_mark(ctx);
+  int32_t *pstart = (int32_t *)stack_push(ctx, sizeof(int32_t) * rows);
+  uint8_t *pslot = (uint8_t *)stack_push(ctx, rows);
+  int64_t *woff = (int64_t *)stack_push(ctx, sizeof(int64_t) * (rows + 1));
+  int64_t *tmp = (int64_t *)scratch_get(ctx, sizeof(int64_t) * scan_tmp_elems(rows));
+  timed(ctx, K_PIVOT, (double)rows * (8.0 * i + 8.0 * d.nb + 13.0 + 16.0), (uint64_t)rows, 4, [&] {
+    launch_cpivot(R.g, d, f, i, rows, pstart, pslot, woff, ctx->stream);
+    launch_scan_i64(woff, woff, rows, tmp, ctx->stream);
+  });
+  const int64_t W = read_i64(ctx, woff + rows);
+  ctx->run.frontier[i] += (uint64_t)rows;
+  ctx->run.candidates[i] += (uint64_t)W;
+  std::vector<int64_t> bnd, bw;
+  level_chunks(R, woff, rows, W, bnd, bw);
+  for (size_t j = 0; j + 1 < bnd.size(); ++j)
+    process_c(R, i, f, pstart, pslot, woff, bnd[j], bnd[j + 1], bw[j], bw[j + 1]);
   stack_release(ctx, mk);
 }
 
@@ -1045,6 +1169,10 @@ void run_query(gsm_ctx *ctx, const gsm_query *q, bool enumerate, int32_t *out, u
                          ctx->stream));
     }
     R.acc_rows = (uint64_t)R1;
+  } else if (ctx->opt.flags & GSM_OPT_COMPRESSED_FRONTIERS) {
+    CFrontier f{};
+    f.V[1] = F1;
+    recurse_c(R, 1, f, R1);
   } else {
     recurse(R, 1, F1, R1, R1);
   }

@@ -577,35 +577,16 @@ __global__ void __launch_bounds__(1024) k_extend_fused(
       if (check_candidate(g, d, ColumnRow{F, ld, r}, w, slot)) bits |= 1u << j;
     }
   }
-  // block exclusive scan of the per-thread survivor counts (thread order is
-  // candidate order)
+  // rank of this thread's survivors in the tile (thread order is candidate
+  // order)
   const int32_t c = __popc(bits);
-  int32_t incl = c;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int32_t y = __shfl_up_sync(kFull, incl, o);
-    if (lane >= o) incl += y;
-  }
-  if (lane == 31) s_warp[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    const int nwarps = B >> 5;
-    const int32_t v = lane < nwarps ? s_warp[lane] : 0;
-    int32_t wi = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int32_t y = __shfl_up_sync(kFull, wi, o);
-      if (lane >= o) wi += y;
-    }
-    if (lane < nwarps) s_warp[lane] = wi - v;
-    if (lane == 31) s_warp[32] = wi;
-  }
-  __syncthreads();
+  int32_t T;
+  const int32_t rank = block_rank(c, s_warp, &T);
   // every thread is past the verification: the staged work offsets are no
   // longer needed, and the survivors (row, vertex) go there in rank order
   {
     int32_t *s_pair = s_woff;
-    int32_t q = (incl - c) + s_warp[warp];
+    int32_t q = rank;
 #pragma unroll
     for (int j = 0; j < kItemsPerThread; ++j)
       if ((bits >> j) & 1u) {
@@ -615,56 +596,10 @@ __global__ void __launch_bounds__(1024) k_extend_fused(
       }
   }
   if (warp == 0) {
-    // warp-wide look-back: lane l examines tile window_end - l; the window
-    // moves back by 32 tiles while it holds only tile counts
-    const unsigned long long T = (unsigned long long)s_warp[32];
-    unsigned long long prefix = 0;
-    if (tile == 0) {
-      if (lane == 0) atomicExch(lookback, kLbInclusive | T);
-    } else {
-      if (lane == 0) atomicExch(lookback + tile, kLbAggregate | T);
-      int32_t window_end = tile - 1;
-      int32_t polls = 0;
-      bool gave_up = false;
-      while (true) {
-        const int32_t j = window_end - lane;
-        unsigned long long st = j >= 0 ? load_relaxed(lookback + j) : kLbInclusive;
-        unsigned long long flag = st & ~kLbValue;
-        // wait until every tile of the window has published
-        while (__any_sync(kFull, flag == 0)) {
-          if (++polls > kLbSpinLimit) {
-            gave_up = true;
-            break;
-          }
-          __nanosleep(32);
-          if (flag == 0) {
-            st = load_relaxed(lookback + j);
-            flag = st & ~kLbValue;
-          }
-        }
-        if (gave_up) break;
-        const uint32_t has_prefix = __ballot_sync(kFull, flag == kLbInclusive);
-        // tiles up to the nearest inclusive prefix (the lowest such lane)
-        const int32_t stop = has_prefix ? __ffs(has_prefix) - 1 : 31;
-        unsigned long long v = lane <= stop ? (st & kLbValue) : 0;
-#pragma unroll
-        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-        prefix += v;
-        if (has_prefix) break;
-        window_end -= 32;
-      }
-      if (lane == 0) {
-        if (gave_up) atomicExch(lookback + tiles + 2, 1ull);
-        atomicExch(lookback + tile, kLbInclusive | (prefix + T));
-      }
-    }
-    if (lane == 0) {
-      if (T) atomicAdd(lookback + tiles + 1, T);
-      s_prefix = (long long)prefix;
-    }
+    const unsigned long long prefix = lookback_prefix(lookback, tile, tiles, T, lane);
+    if (lane == 0) s_prefix = (long long)prefix;
   }
   __syncthreads();
-  const int32_t T = s_warp[32];
   const int64_t base = sink.row0 + s_prefix;
   if (kMode == kSinkRows && stage_out) {
     // the tile's result rows are one contiguous block of T*k ints: assemble

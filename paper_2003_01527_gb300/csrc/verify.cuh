@@ -132,4 +132,91 @@ __device__ __forceinline__ unsigned long long load_relaxed(const unsigned long l
   return v;
 }
 
+
+// Exclusive rank of this thread's c items among the block's (threads in
+// order) and the block total; s_warp holds 33 ints; contains two barriers.
+__device__ __forceinline__ int32_t block_rank(int32_t c, int32_t *s_warp, int32_t *total) {
+  constexpr unsigned kAll = 0xffffffffu;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t incl = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t y = __shfl_up_sync(kAll, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const int nwarps = blockDim.x >> 5;
+    const int32_t v = lane < nwarps ? s_warp[lane] : 0;
+    int32_t wi = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(kAll, wi, o);
+      if (lane >= o) wi += y;
+    }
+    if (lane < nwarps) s_warp[lane] = wi - v;
+    if (lane == 31) s_warp[32] = wi;
+  }
+  __syncthreads();
+  *total = s_warp[32];
+  return incl - c + s_warp[warp];
+}
+
+// Decoupled look-back for tile `tile` of a level with T survivors, run by
+// one whole warp: publishes the tile's count, reads the published words of
+// the 32 preceding tiles at a time (lane l: tile window_end - l) until one
+// holds an inclusive prefix, publishes the tile's own inclusive prefix and
+// adds T to the level total (word tiles + 1).  Returns the number of
+// survivors of all earlier tiles in every lane.  A wait longer than
+// kLbSpinLimit polls sets word tiles + 2 and returns the (smaller) sum found
+// so far.
+__device__ __forceinline__ unsigned long long lookback_prefix(unsigned long long *lookback,
+                                                              int32_t tile, int32_t tiles,
+                                                              unsigned long long T, int lane) {
+  constexpr unsigned kAll = 0xffffffffu;
+  unsigned long long prefix = 0;
+  if (tile == 0) {
+    if (lane == 0) atomicExch(lookback, kLbInclusive | T);
+  } else {
+    if (lane == 0) atomicExch(lookback + tile, kLbAggregate | T);
+    int32_t window_end = tile - 1;
+    int32_t polls = 0;
+    bool gave_up = false;
+    while (true) {
+      const int32_t j = window_end - lane;
+      unsigned long long st = j >= 0 ? load_relaxed(lookback + j) : kLbInclusive;
+      unsigned long long flag = st & ~kLbValue;
+      // wait until every tile of the window has published
+      while (__any_sync(kAll, flag == 0)) {
+        if (++polls > kLbSpinLimit) {
+          gave_up = true;
+          break;
+        }
+        __nanosleep(32);
+        if (flag == 0) {
+          st = load_relaxed(lookback + j);
+          flag = st & ~kLbValue;
+        }
+      }
+      if (gave_up) break;
+      const uint32_t has_prefix = __ballot_sync(kAll, flag == kLbInclusive);
+      // tiles up to the nearest inclusive prefix (the lowest such lane)
+      const int32_t stop = has_prefix ? __ffs(has_prefix) - 1 : 31;
+      unsigned long long v = lane <= stop ? (st & kLbValue) : 0;
+#pragma unroll
+      for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kAll, v, o);
+      prefix += v;
+      if (has_prefix) break;
+      window_end -= 32;
+    }
+    if (lane == 0) {
+      if (gave_up) atomicExch(lookback + tiles + 2, 1ull);
+      atomicExch(lookback + tile, kLbInclusive | (prefix + T));
+    }
+  }
+  if (lane == 0 && T) atomicAdd(lookback + tiles + 1, T);
+  return prefix;
+}
+
 }  // namespace gsm

@@ -38,6 +38,7 @@ GSM_VALIDATE = 2
 GSM_OUT_DEVICE = 1
 GSM_OPT_TIME_KERNELS = 1
 GSM_OPT_TWO_PASS = 2
+GSM_OPT_COMPRESSED_FRONTIERS = 4
 
 MAX_K = 16
 
@@ -379,7 +380,7 @@ class Matcher:
     def __init__(self, device: int = 0, mem_budget_bytes: int = 0, stream=None,
                  block_size: int = 0, chunk_rows: int = 0, time_kernels: bool = False,
                  torch_allocator: bool = True, filter_rounds: int = 0, copy_slots: int = 0,
-                 two_pass: bool = False):
+                 two_pass: bool = False, compressed: bool = False):
         import torch
         self.device = device
         opt = gsm_default_options()
@@ -396,7 +397,8 @@ class Matcher:
         opt.filter_rounds = filter_rounds
         opt.copy_slots = copy_slots
         opt.flags = (GSM_OPT_TIME_KERNELS if time_kernels else 0) | \
-            (GSM_OPT_TWO_PASS if two_pass else 0)
+            (GSM_OPT_TWO_PASS if two_pass else 0) | \
+            (GSM_OPT_COMPRESSED_FRONTIERS if compressed else 0)
         if torch_allocator:
             dev = device
 
