@@ -13,7 +13,7 @@ __device__ __forceinline__ bool bitmap_has(const uint32_t *__restrict__ bm, int3
 
 // Inside one launch every index is 32-bit: candidates are numbered locally
 // from wa (a launch covers fewer than 2^30), rows and frontier elements stay
-// below 2^31 (the driver chunks frontiers to that), only output addresses of
+// below 2^31 (the host code chunks frontiers to that), only output addresses of
 // the final rows are 64-bit.
 //
 // A tile's rows [r0, r0+span): their work offsets, relative to wa, are staged
