@@ -608,6 +608,8 @@ struct Run {
 };
 
 void recurse(Run &R, int32_t i, const int32_t *F, int64_t ld, int64_t rows);
+void recurse_rest(Run &R, int32_t i, const int32_t *F, int64_t ld, int64_t rows,
+                  const int32_t *pstart, const uint8_t *pslot, const int64_t *woff, int64_t W);
 void process_fused(Run &R, int32_t i, const int32_t *F, int64_t ld, const int32_t *pstart,
                    const uint8_t *pslot, const int64_t *woff, int64_t ra, int64_t rb, int64_t wa,
                    int64_t wb);
@@ -696,7 +698,7 @@ void process_sub(Run &R, int32_t i, const int32_t *F, int64_t ld, const int32_t 
     launch_extend_count(R.g, d, F, ld, pstart, pslot, woff, tile_row, wa, wb, R.block, masks,
                         tile_cnt, nullptr, ctx->stream);
   });
-  timed(ctx, K_PIVOT, 12.0 * tiles, (uint64_t)tiles, 3,
+  timed(ctx, K_PIVOT, 12.0 * tiles, (uint64_t)tiles, scan_kernels(tiles),
         [&] { launch_scan_i32(tile_cnt, tile_off, tiles, tmp, ctx->stream); });
   const int64_t S = read_i64(ctx, tile_off + tiles);
   if (S == 0) return;
@@ -752,6 +754,8 @@ void process_fused(Run &R, int32_t i, const int32_t *F, int64_t ld, const int32_
   Carve cv;
   const size_t o_row = cv.add<int32_t>(tiles + 1);
   const size_t o_lb = cv.add<unsigned long long>(tiles + kLbExtra);
+  // the work scan of the next level (sized for up to W rows)
+  const size_t o_tmp = last ? 0 : cv.add<int64_t>(scan_tmp_elems(W));
   char *sc = (char *)scratch_get(ctx, cv.off);
   int32_t *tile_row = (int32_t *)(sc + o_row);
   unsigned long long *lb = (unsigned long long *)(sc + o_lb);
@@ -774,17 +778,39 @@ void process_fused(Run &R, int32_t i, const int32_t *F, int64_t ld, const int32_
     launch_extend_fused(R.g, d, F, ld, pstart, pslot, woff, tile_row, wa, wb, R.block, lb, sink,
                         ctx->stream);
   });
-  fetch(ctx, lb + tiles + 1, 2 * sizeof(unsigned long long));
-  const int64_t S = ((volatile int64_t *)ctx->h_stage)[0];
-  const int64_t gave_up = ((volatile int64_t *)ctx->h_stage)[1];
-  if (gave_up) FAIL(GSM_ERR_TIMEOUT, "a verification tile waited too long for its predecessors");
-  ctx->kstats[K_FUSED].algo_bytes +=
-      (double)S * (last ? (double)R.acc_row_bytes() : 4.0 * w_out);
+  const int64_t *S_dev = (const int64_t *)(lb + tiles + 1);
   if (last) {
+    fetch(ctx, S_dev, 2 * sizeof(unsigned long long));
+    const int64_t S = ((volatile int64_t *)ctx->h_stage)[0];
+    if (((volatile int64_t *)ctx->h_stage)[1])
+      FAIL(GSM_ERR_TIMEOUT, "a verification tile waited too long for its predecessors");
+    ctx->kstats[K_FUSED].algo_bytes += (double)S * (double)R.acc_row_bytes();
     R.acc_rows += (uint64_t)S;
     return;
   }
-  if (S > 0) recurse(R, i + 1, Fn, W, S);
+  // the next level's pivot choice and work scan run before the host learns
+  // S (they read it on the device; their arrays were reserved for W rows),
+  // so one read-back serves both levels
+  const LevelDesc &dn = R.lv[i + 1];
+  int32_t *pstart2 = (int32_t *)stack_push(ctx, sizeof(int32_t) * W);
+  uint8_t *pslot2 = (uint8_t *)stack_push(ctx, W);
+  int64_t *woff2 = (int64_t *)stack_push(ctx, sizeof(int64_t) * (W + 1));
+  timed(ctx, K_PIVOT, 0.0, 0, 1 + scan_kernels(W), [&] {
+    launch_pivot(R.g, dn, Fn, W, W, pstart2, pslot2, woff2, ctx->stream, S_dev);
+    launch_scan_i64_dev(woff2, woff2, W, S_dev, (int64_t *)(sc + o_tmp), ctx->stream);
+  });
+  launch_fetch_level(lb + tiles + 1, woff2, ctx->d_stage, ctx->stream);
+  ctx->run.kernel_launches += 1;
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(ctx->stream));
+  const int64_t S = ((volatile int64_t *)ctx->h_stage)[0];
+  if (((volatile int64_t *)ctx->h_stage)[1])
+    FAIL(GSM_ERR_TIMEOUT, "a verification tile waited too long for its predecessors");
+  const int64_t W2 = ((volatile int64_t *)ctx->h_stage)[2];
+  ctx->kstats[K_FUSED].algo_bytes += (double)S * 4.0 * w_out;
+  ctx->kstats[K_PIVOT].algo_bytes += (double)S * (4.0 * dn.nb + 8.0 * dn.nb + 13.0 + 16.0);
+  ctx->kstats[K_PIVOT].items += (uint64_t)S;
+  if (S > 0) recurse_rest(R, i + 1, Fn, W, S, pstart2, pslot2, woff2, W2);
   stack_release(ctx, mk);
 }
 
@@ -846,18 +872,25 @@ void recurse(Run &R, int32_t i, const int32_t *F, int64_t ld, int64_t rows) {
   uint8_t *pslot = (uint8_t *)stack_push(ctx, rows);
   int64_t *woff = (int64_t *)stack_push(ctx, sizeof(int64_t) * (rows + 1));
   int64_t *tmp = (int64_t *)scratch_get(ctx, sizeof(int64_t) * scan_tmp_elems(rows));
-  timed(ctx, K_PIVOT, (double)rows * (4.0 * d.nb + 8.0 * d.nb + 13.0 + 16.0), (uint64_t)rows, 4, [&] {
+  timed(ctx, K_PIVOT, (double)rows * (4.0 * d.nb + 8.0 * d.nb + 13.0 + 16.0), (uint64_t)rows,
+        1 + scan_kernels(rows), [&] {
     launch_pivot(R.g, d, F, ld, rows, pstart, pslot, woff, ctx->stream);
     launch_scan_i64(woff, woff, rows, tmp, ctx->stream);
   });
   const int64_t W = read_i64(ctx, woff + rows);
-  ctx->run.frontier[i] += (uint64_t)rows;
-  ctx->run.candidates[i] += (uint64_t)W;
+  recurse_rest(R, i, F, ld, rows, pstart, pslot, woff, W);
+  stack_release(ctx, mk);
+}
+
+// The part of recurse after the pivot and work scan (W = total candidates).
+void recurse_rest(Run &R, int32_t i, const int32_t *F, int64_t ld, int64_t rows,
+                  const int32_t *pstart, const uint8_t *pslot, const int64_t *woff, int64_t W) {
+  R.ctx->run.frontier[i] += (uint64_t)rows;
+  R.ctx->run.candidates[i] += (uint64_t)W;
   std::vector<int64_t> bnd, bw;
   level_chunks(R, woff, rows, W, bnd, bw);
   for (size_t j = 0; j + 1 < bnd.size(); ++j)
     process_sub(R, i, F, ld, pstart, pslot, woff, bnd[j], bnd[j + 1], bw[j], bw[j + 1]);
-  stack_release(ctx, mk);
 }
 
 // ---- compressed frontiers (GSM_OPT_COMPRESSED_FRONTIERS): a row of width i
@@ -959,7 +992,8 @@ void recurse_c(Run &R, int32_t i, const CFrontier &f, int64_t rows) {
   uint8_t *pslot = (uint8_t *)stack_push(ctx, rows);
   int64_t *woff = (int64_t *)stack_push(ctx, sizeof(int64_t) * (rows + 1));
   int64_t *tmp = (int64_t *)scratch_get(ctx, sizeof(int64_t) * scan_tmp_elems(rows));
-  timed(ctx, K_PIVOT, (double)rows * (8.0 * i + 8.0 * d.nb + 13.0 + 16.0), (uint64_t)rows, 4, [&] {
+  timed(ctx, K_PIVOT, (double)rows * (8.0 * i + 8.0 * d.nb + 13.0 + 16.0), (uint64_t)rows,
+        1 + scan_kernels(rows), [&] {
     launch_cpivot(R.g, d, f, i, rows, pstart, pslot, woff, ctx->stream);
     launch_scan_i64(woff, woff, rows, tmp, ctx->stream);
   });
@@ -1155,7 +1189,7 @@ void run_query(gsm_ctx *ctx, const gsm_query *q, bool enumerate, int32_t *out, u
     const size_t o_cnt = cv.add<int32_t>(nw), o_off = cv.add<int64_t>(nw + 1),
                  o_tmp = cv.add<int64_t>(scan_tmp_elems(nw));
     char *sc = (char *)scratch_get(ctx, cv.off);
-    timed(ctx, K_LIST, nw * 4.0 + 4.0 * R1, (uint64_t)R1, 5, [&] {
+    timed(ctx, K_LIST, nw * 4.0 + 4.0 * R1, (uint64_t)R1, 2 + scan_kernels(nw), [&] {
       launch_bitmap_to_list(bm + (size_t)R.order[0] * nw, nw, (int32_t *)(sc + o_cnt),
                             (int64_t *)(sc + o_off), (int64_t *)(sc + o_tmp), F1, ctx->stream);
     });

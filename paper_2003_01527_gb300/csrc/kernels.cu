@@ -197,7 +197,9 @@ __device__ int64_t block_excl_scan(int64_t x, int64_t *s_warp, int64_t *total) {
 
 template <typename T>
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const T *in, int64_t n,
-                                                              int64_t *partial) {
+                                                              int64_t *partial,
+                                                              const int64_t *n_dev) {
+  if (n_dev) n = *n_dev;  // the actual length (n is then the launch's bound)
   __shared__ int64_t s_warp[33];
   const int64_t base = (int64_t)blockIdx.x * kScanTile;
   int64_t sum = 0;
@@ -230,7 +232,9 @@ __global__ void __launch_bounds__(1024) k_scan_partials(int64_t *partial, int64_
 template <typename T>
 __global__ void __launch_bounds__(kScanThreads) k_scan_down(const T *in, int64_t n,
                                                             const int64_t *__restrict__ partial,
-                                                            int64_t nb, int64_t *out) {
+                                                            int64_t nb, int64_t *out,
+                                                            const int64_t *n_dev) {
+  if (n_dev) n = *n_dev;
   __shared__ int64_t s_val[kScanTile];
   __shared__ int64_t s_warp[33];
   const int64_t base = (int64_t)blockIdx.x * kScanTile;
@@ -268,7 +272,9 @@ constexpr int kOneThreads = 512;
 constexpr int64_t kOneCtaMax = 4 * kOneThreads * kScanIpt;  // longest input taken
 template <typename T>
 __global__ void __launch_bounds__(kOneThreads) k_scan_one_cta(const T *in, int64_t n,
-                                                              int64_t *out) {
+                                                              int64_t *out,
+                                                              const int64_t *n_dev) {
+  if (n_dev) n = *n_dev;
   constexpr int kTile = kOneThreads * kScanIpt;
   __shared__ int64_t s_val[kTile];
   __shared__ int64_t s_warp[33];
@@ -335,7 +341,8 @@ __global__ void k_bitmap_emit(const uint32_t *__restrict__ bm, int32_t n_words,
 
 __global__ void k_pivot(GraphDev g, LevelDesc d, const int32_t *__restrict__ F, int64_t ld,
                         int64_t R, int32_t *__restrict__ pstart, uint8_t *__restrict__ pslot,
-                        int64_t *__restrict__ work) {
+                        int64_t *__restrict__ work, const int64_t *R_dev) {
+  if (R_dev) R = *R_dev;  // the actual row count (R is then the launch's bound)
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R; r += stride) {
     int32_t best = 0x7fffffff, best_start = 0, best_slot = 0;
@@ -642,6 +649,17 @@ __global__ void k_fetch(const uint32_t *__restrict__ src, uint32_t *__restrict__
   for (int32_t i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
 }
 
+// dst[0] = S (survivor count), dst[1] = the error word, dst[2] = woff[S].
+__global__ void k_fetch_level(const unsigned long long *__restrict__ words,
+                              const int64_t *__restrict__ woff, long long *__restrict__ dst) {
+  if (threadIdx.x == 0) {
+    const long long S = (long long)words[0];
+    dst[0] = S;
+    dst[1] = (long long)words[1];
+    dst[2] = (long long)woff[S];
+  }
+}
+
 inline int grid_for(int64_t n, int threads, int cap = 152 * 32) {
   int64_t b = (n + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -700,6 +718,11 @@ int launch_label_segments(const GraphDev &g, int32_t num_labels, int32_t *edge_c
   return launches + 1;
 }
 
+void launch_fetch_level(const unsigned long long *words, const int64_t *woff, void *dst,
+                        cudaStream_t s) {
+  k_fetch_level<<<1, 32, 0, s>>>(words, woff, (long long *)dst);
+}
+
 void launch_fetch(const void *src, void *dst, size_t bytes, cudaStream_t s) {
   const int32_t n = (int32_t)(std::min<size_t>(bytes, 4096) / 4);
   if (n > 0) k_fetch<<<1, 128, 0, s>>>((const uint32_t *)src, (uint32_t *)dst, n);
@@ -731,19 +754,27 @@ void launch_refine(const GraphDev &g, const RefineDesc &d, const uint32_t *bm_in
 int64_t scan_tmp_elems(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
 
 template <typename T>
-void scan_impl(const T *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t s) {
+// n_dev (optional): the length is read on the device, n is its upper bound
+// (the grids are sized by n; tiles past the length contribute zero).
+void scan_impl(const T *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t s,
+               const int64_t *n_dev = nullptr) {
   const int64_t nb = (n + kScanTile - 1) / kScanTile;
   if (nb == 0) {
     cudaMemsetAsync(out, 0, sizeof(int64_t), s);
     return;
   }
   if (n <= kOneCtaMax) {
-    k_scan_one_cta<T><<<1, kOneThreads, 0, s>>>(in, n, out);
+    k_scan_one_cta<T><<<1, kOneThreads, 0, s>>>(in, n, out, n_dev);
     return;
   }
-  k_scan_reduce<T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, tmp);
+  k_scan_reduce<T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, tmp, n_dev);
   k_scan_partials<<<1, 1024, 0, s>>>(tmp, nb);
-  k_scan_down<T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, tmp, nb, out);
+  k_scan_down<T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, tmp, nb, out, n_dev);
+}
+
+int scan_kernels(int64_t n) {
+  if (n <= 0) return 0;
+  return n <= kOneCtaMax ? 1 : 3;
 }
 
 void launch_scan_i32(const int32_t *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t s) {
@@ -754,6 +785,11 @@ void launch_scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *tmp, c
   scan_impl<int64_t>(in, out, n, tmp, s);
 }
 
+void launch_scan_i64_dev(const int64_t *in, int64_t *out, int64_t n_max, const int64_t *n_dev,
+                         int64_t *tmp, cudaStream_t s) {
+  scan_impl<int64_t>(in, out, n_max, tmp, s, n_dev);
+}
+
 void launch_bitmap_to_list(const uint32_t *bitmap, int32_t n_words, int32_t *cnt, int64_t *off,
                            int64_t *tmp, int32_t *out, cudaStream_t s) {
   k_bitmap_popc<<<grid_for(n_words, 256), 256, 0, s>>>(bitmap, n_words, cnt);
@@ -762,8 +798,9 @@ void launch_bitmap_to_list(const uint32_t *bitmap, int32_t n_words, int32_t *cnt
 }
 
 void launch_pivot(const GraphDev &g, const LevelDesc &d, const int32_t *F, int64_t ld, int64_t R,
-                  int32_t *pstart, uint8_t *pslot, int64_t *work, cudaStream_t s) {
-  k_pivot<<<grid_for(R, 256, 152 * 64), 256, 0, s>>>(g, d, F, ld, R, pstart, pslot, work);
+                  int32_t *pstart, uint8_t *pslot, int64_t *work, cudaStream_t s,
+                  const int64_t *R_dev) {
+  k_pivot<<<grid_for(R, 256, 152 * 64), 256, 0, s>>>(g, d, F, ld, R, pstart, pslot, work, R_dev);
 }
 
 int64_t extend_tiles(int64_t wa, int64_t wb, int32_t block) {

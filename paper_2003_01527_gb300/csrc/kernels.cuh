@@ -94,8 +94,14 @@ void launch_refine(const GraphDev &g, const RefineDesc &d, const uint32_t *bm_in
 // Exclusive scan: out[0..n] with out[n] = total.  tmp needs scan_tmp_elems(n)
 // int64 elements.  The int64 form may run in place (in == out).
 int64_t scan_tmp_elems(int64_t n);
+// Kernels one scan of n elements launches (n <= 0: a memset, no kernel).
+int scan_kernels(int64_t n);
 void launch_scan_i32(const int32_t *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t s);
 void launch_scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t s);
+// The same with the length read on the device (*n_dev <= n_max; tmp sized
+// for n_max; out needs n_max + 1 elements).
+void launch_scan_i64_dev(const int64_t *in, int64_t *out, int64_t n_max, const int64_t *n_dev,
+                         int64_t *tmp, cudaStream_t s);
 
 // Bitmap -> ascending vertex list.  cnt: int32[n_words], off: int64[n_words+1]
 // (scratch), tmp: scan_tmp_elems(n_words).
@@ -108,8 +114,10 @@ void launch_bitmap_to_list(const uint32_t *bitmap, int32_t n_words, int32_t *cnt
 // pivot) and record its CSR start, its slot in bpos, and its degree as work
 // (int64, so the work array can be scanned in place into offsets).  F has
 // leading dimension ld >= R.
+// With R_dev the row count is read on the device and R is its upper bound.
 void launch_pivot(const GraphDev &g, const LevelDesc &d, const int32_t *F, int64_t ld, int64_t R,
-                  int32_t *pstart, uint8_t *pslot, int64_t *work, cudaStream_t s);
+                  int32_t *pstart, uint8_t *pslot, int64_t *work, cudaStream_t s,
+                  const int64_t *R_dev = nullptr);
 
 // Number of extend tiles for candidates [wa, wb).
 int64_t extend_tiles(int64_t wa, int64_t wb, int32_t block);
@@ -180,6 +188,11 @@ void launch_split_points(const int64_t *woff, int64_t R, int64_t step, int64_t J
 // small kernel; dst is typically the device view of mapped pinned host memory,
 // so small reads back to the host do not queue behind copy-engine transfers.
 void launch_fetch(const void *src, void *dst, size_t bytes, cudaStream_t s);
+// After a single-pass level and the next level's pivot and work scan: dst
+// (3 x int64) = the survivor count S (words[0]), the error word (words[1]) and
+// woff[S], the next level's candidate total.
+void launch_fetch_level(const unsigned long long *words, const int64_t *woff, void *dst,
+                        cudaStream_t s);
 
 // Histogram elements of the radix passes over N keys.
 int64_t sort_hist_elems(int64_t N);
