@@ -78,7 +78,9 @@ typedef void (*gsm_free_fn)(void *alloc_ctx, void *ptr, size_t bytes, void *stre
 typedef struct gsm_options {
   /* Cap on device memory for intermediate frontiers and scratch, in bytes.
    * 0 = 90% of the device memory free at gsm_create.  The graph, candidate
-   * bitmaps and final result buffers are not counted. */
+   * bitmaps and final result buffers are not counted.  A single-pass level
+   * reserves its output for one row per candidate when that fits the cap;
+   * otherwise it sizes the output exactly (two passes) or splits its rows. */
   size_t mem_budget_bytes;
   /* cudaStream_t every kernel and copy is issued on; NULL = a stream the
    * library creates and owns. */
@@ -175,10 +177,12 @@ gsm_status gsm_count_distinct(gsm_ctx *ctx, const gsm_query *q, uint64_t *count,
  * number of embeddings.  If it exceeds cap_rows the first cap_rows rows are
  * written and GSM_ERR_TRUNCATED is returned.  out may be NULL iff cap_rows = 0.
  * Final rows are staged in library-owned device buffers outside the budget:
- * count x k x 4 bytes of rows plus, unless the matching order is the identity,
- * two packed sort keys of ceil(k * log2(n) / 64) x 8 bytes per row and about
- * 1.5 bytes per row of histograms.  Errors: as gsm_count, plus
- * GSM_ERR_TRUNCATED. */
+ * count x k x 4 bytes of rows plus, unless the matching order already gives
+ * canonical order, two packed sort keys of ceil(k * log2(n) / 64) x 8 bytes
+ * per row and about 1.5 bytes per row of histograms.  A single-pass last
+ * level reserves room for one row per candidate it checks (at most 4 GiB;
+ * beyond that it takes two passes), so the staging can exceed the count.
+ * Errors: as gsm_count, plus GSM_ERR_TRUNCATED. */
 gsm_status gsm_enumerate(gsm_ctx *ctx, const gsm_query *q, int32_t *out, uint64_t cap_rows,
                          uint64_t *count, int32_t flags);
 
