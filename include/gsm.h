@@ -348,6 +348,20 @@ gsm_status gsm_candidates_static(int32_t n, int64_t nnz, const int32_t *row_ptr,
                                  const int32_t *col, const int32_t *labels, const gsm_query *q,
                                  uint32_t *bitmaps, uint64_t *sizes, int32_t flags, void *stream);
 
+/* The symmetry breaking behind gsm_count_distinct (host only, no device
+ * work): Sec. 3.1's node-ID ordering constraints between equivalent query
+ * vertices, built along a stabilizer chain of Aut(Q) (the automorphisms of
+ * the query that keep labels and edges).  *automorphisms = |Aut(Q)|;
+ * constraint t is f(pairs[2t]) < f(pairs[2t+1]) for an embedding f, and of
+ * the |Aut(Q)| embeddings f o sigma (sigma in Aut(Q)) exactly one meets every
+ * constraint.  labels may be NULL (all 0).  cap = room in pairs (in pairs of
+ * int32); *npairs = the number of constraints (at most k(k-1)/2), also when
+ * cap is too small.  Errors: GSM_ERR_INVALID_QUERY, GSM_ERR_INVALID_ARG (null
+ * outputs, or cap < *npairs). */
+gsm_status gsm_query_symmetry(int32_t k, int32_t m, const int32_t *edges, const int32_t *labels,
+                              uint64_t *automorphisms, int32_t *pairs, int32_t cap,
+                              int32_t *npairs);
+
 /* The matching order of Sec. 3.2 (host only, no device work): order[i] is the
  * i-th query vertex placed, parent[i] the position (< i) of its spanning-tree
  * parent (-1 for i = 0).  The first vertex minimises the candidate count

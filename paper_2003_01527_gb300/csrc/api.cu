@@ -2489,6 +2489,27 @@ gsm_status gsm_plan_order(int32_t k, int32_t m, const int32_t *edges, const uint
   return GSM_OK;
 }
 
+gsm_status gsm_query_symmetry(int32_t k, int32_t m, const int32_t *edges, const int32_t *labels,
+                              uint64_t *automorphisms, int32_t *pairs, int32_t cap,
+                              int32_t *npairs) {
+  if (!automorphisms || !npairs || cap < 0 || (cap > 0 && !pairs)) return GSM_ERR_INVALID_ARG;
+  uint32_t adj[kMaxK];
+  gsm_status st = validate_query_edges(k, m, edges, adj);
+  if (st != GSM_OK) return st;
+  int32_t lab[kMaxK] = {};
+  if (labels)
+    for (int32_t u = 0; u < k; ++u) lab[u] = labels[u];
+  std::vector<std::pair<int32_t, int32_t>> less;
+  *automorphisms = symmetry_constraints(k, adj, lab, &less);
+  *npairs = (int32_t)less.size();
+  if ((int32_t)less.size() > cap) return GSM_ERR_INVALID_ARG;
+  for (size_t t = 0; t < less.size(); ++t) {
+    pairs[2 * t] = less[t].first;
+    pairs[2 * t + 1] = less[t].second;
+  }
+  return GSM_OK;
+}
+
 gsm_status gsm_kernel_stats(gsm_ctx *ctx, gsm_kernel_stat *out, int32_t max, int32_t *n,
                             int32_t reset) {
   if (!ctx || (max > 0 && !out)) return GSM_ERR_INVALID_ARG;

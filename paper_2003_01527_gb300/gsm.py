@@ -46,10 +46,11 @@ MAX_K = 16
 # exports each of them.
 EXPORTED = [
     "gsm_default_options", "gsm_create", "gsm_destroy", "gsm_last_error", "gsm_status_string",
-    "gsm_load_graph", "gsm_query_create", "gsm_query_destroy", "gsm_query_restrict", "gsm_count",
-    "gsm_enumerate", "gsm_enumerate_many", "gsm_last_rows", "gsm_candidates", "gsm_plan_order", "gsm_kernel_stats",
-    "gsm_last_run_stats", "gsm_candidates_static", "gsm_run_batch", "gsm_batch_get_stats",
-    "gsm_batch_configure", "gsm_count_distinct", "gsm_server_start", "gsm_submit", "gsm_poll", "gsm_server_stop",
+    "gsm_load_graph", "gsm_query_create", "gsm_query_destroy", "gsm_query_restrict",
+    "gsm_count", "gsm_enumerate", "gsm_enumerate_many", "gsm_last_rows", "gsm_candidates",
+    "gsm_plan_order", "gsm_query_symmetry", "gsm_kernel_stats", "gsm_last_run_stats",
+    "gsm_candidates_static", "gsm_run_batch", "gsm_batch_get_stats", "gsm_batch_configure",
+    "gsm_count_distinct", "gsm_server_start", "gsm_submit", "gsm_poll", "gsm_server_stop",
 ]
 GSM_BATCH_AUTOTUNE = 1
 GSM_STATIC_SCRATCH_BITMAP_BYTES = 8 << 20
@@ -117,6 +118,7 @@ def _load():
         "gsm_last_rows": (i32, [vp, vp, u64, u64, i32]),
         "gsm_candidates": (i32, [vp, vp, vp, vp]),
         "gsm_plan_order": (i32, [i32, i32, vp, vp, vp, vp]),
+        "gsm_query_symmetry": (i32, [i32, i32, vp, vp, vp, vp, i32, vp]),
         "gsm_candidates_static": (i32, [i32, i64, vp, vp, vp, vp, vp, vp, i32, vp]),
         "gsm_run_batch": (i32, [vp, vp, i32, vp, i32]),
         "gsm_batch_get_stats": (i32, [vp, ctypes.POINTER(gsm_batch_stats)]),
@@ -310,6 +312,22 @@ def gsm_poll(ctx: int, ticket: int):
 
 def gsm_server_stop(ctx: int) -> None:
     _check(ctx, _lib.gsm_server_stop(ctx))
+
+
+def gsm_query_symmetry(k: int, edges, labels=None) -> tuple[int, list[tuple[int, int]]]:
+    """(|Aut(Q)|, ordering constraints [(u, v): f(u) < f(v)]) of a query."""
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1))
+    lab = None if labels is None else np.ascontiguousarray(np.asarray(labels, dtype=np.int32))
+    cap = k * (k - 1) // 2
+    pairs = np.zeros(max(2 * cap, 2), dtype=np.int32)
+    aut = ctypes.c_uint64()
+    n = ctypes.c_int32()
+    st = _lib.gsm_query_symmetry(k, e.size // 2, _ptr(e) if e.size else None,
+                                 _ptr(lab) if lab is not None else None, ctypes.byref(aut),
+                                 _ptr(pairs), cap, ctypes.byref(n))
+    if st != GSM_OK:
+        raise GsmError(st, "gsm_query_symmetry")
+    return aut.value, [(int(pairs[2 * t]), int(pairs[2 * t + 1])) for t in range(n.value)]
 
 
 def gsm_plan_order(k: int, edges, cand_sizes=None) -> tuple[np.ndarray, np.ndarray]:
