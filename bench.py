@@ -564,7 +564,7 @@ def run_reference(args):
     emb, secs = 0, 0.0
     samples = []
     for _ in range(args.steps):
-        e, s, used = oracle_sample(g, queries, budget_s=10.0)
+        e, s, used = oracle_sample(g, queries, budget_s=5.0)
         emb += e
         secs += s
         samples = used
