@@ -89,3 +89,20 @@ def test_one_embedding_per_orbit(gsm_lib, oracle_lib):
             images = {tuple(r[p[u]] for u in range(k)) for p in perms}
             assert sum(satisfies(x, pairs) for x in images) == 1
         checked += 1
+
+
+def test_invalid_queries_are_rejected(gsm_lib):
+    import ctypes
+    with np.testing.assert_raises(gsm_lib.GsmError):
+        gsm_lib.gsm_query_symmetry(3, [(0, 1)])            # disconnected
+    with np.testing.assert_raises(gsm_lib.GsmError):
+        gsm_lib.gsm_query_symmetry(0, [])                  # k outside 1..16
+    with np.testing.assert_raises(gsm_lib.GsmError):
+        gsm_lib.gsm_query_symmetry(3, [(0, 1), (1, 1)])    # self-loop
+    # too little room for the constraints: the count is still reported
+    e = np.array([0, 1, 1, 2, 2, 0], dtype=np.int32)       # triangle: 3 constraints
+    aut, n = ctypes.c_uint64(), ctypes.c_int32()
+    pairs = np.zeros(2, dtype=np.int32)
+    st = gsm_lib._lib.gsm_query_symmetry(3, 3, e.ctypes.data, None, ctypes.byref(aut),
+                                         pairs.ctypes.data, 1, ctypes.byref(n))
+    assert st == gsm_lib.GSM_ERR_INVALID_ARG and n.value == 3 and aut.value == 6
