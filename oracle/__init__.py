@@ -63,6 +63,10 @@ def _load():
             lib.oracle_refine_round.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.c_int32,
                                                 ctypes.c_int32, i32p, i32p, u8p, u8p]
             lib.oracle_refine_round.restype = ctypes.c_int
+            lib.oracle_cliques.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.c_int32,
+                                           ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64),
+                                           ctypes.POINTER(ctypes.c_uint64)]
+            lib.oracle_cliques.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -101,6 +105,18 @@ def refine(g, q, cand: np.ndarray, rounds: int) -> np.ndarray:
             raise ValueError(f"oracle_refine_round failed: {rc}")
         cur = nxt
     return cur
+
+
+def cliques(g, k: int, nthreads: int = 0) -> int:
+    """Number of k-cliques of g (each once), by degree-ordered listing: an
+    algorithm independent of ``match``; K_k has k! ordered embeddings per
+    clique."""
+    lo, hi = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    rc = _load().oracle_cliques(g.n, g.row_ptr, g.col, k, nthreads, ctypes.byref(lo),
+                                ctypes.byref(hi))
+    if rc != OK:
+        raise ValueError(f"oracle_cliques failed: {rc}")
+    return lo.value + (hi.value << 64)
 
 
 def max_threads() -> int:

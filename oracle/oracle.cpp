@@ -28,11 +28,14 @@
 //
 // Also here: the definition of the candidate filter of Sec. 3.2 (label, degree
 // and neighbourhood test) written out per (query vertex, data vertex) pair,
-// and the graph/query validity checks of the library's contract.
+// the graph/query validity checks of the library's contract, and an
+// independent k-clique counter (degree-ordered listing) that pins the
+// matcher's clique counts on graphs too large for the backtracking.
 #include <algorithm>
 #include <atomic>
 #include <cstdint>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <vector>
 
@@ -330,6 +333,91 @@ int oracle_match(int32_t n, const int32_t* rp, const int32_t* col, const int32_t
   for (uint64_t i = 0; i < ncopy; ++i)
     std::memcpy(out + i * k, all.data() + idx[i] * k, sizeof(int32_t) * k);
   return nrows > cap_rows ? OR_TRUNCATED : OR_OK;
+}
+
+// Number of k-cliques of an undirected graph (3 <= k <= 8), each clique
+// counted once, by the textbook degree-ordered listing (Chiba and Nishizeki's
+// arboricity method): rank the vertices by (degree, id), keep every edge
+// only from its lower- to its higher-ranked end (N+(v)), and grow cliques
+// along increasing rank, each step keeping the common out-neighbours of the
+// vertices chosen so far.  It shares nothing with the backtracking matcher
+// above (different order, no query, no injectivity test), so it pins the
+// matcher's count of the k-clique query at sizes the matcher cannot reach:
+// ordered embeddings of K_k = k! x this count.  The count is returned as two
+// 64-bit halves of an unsigned 128-bit integer.
+int oracle_cliques(int32_t n, const int32_t* rp, const int32_t* col, int32_t k,
+                   int32_t nthreads, uint64_t* count_lo, uint64_t* count_hi) {
+  if (n < 0 || k < 3 || k > 8) return OR_INVALID_ARG;
+  auto higher = [&](int32_t a, int32_t b) {  // rank(b) > rank(a)
+    const int32_t da = rp[a + 1] - rp[a], db = rp[b + 1] - rp[b];
+    return db > da || (db == da && b > a);
+  };
+  std::vector<int64_t> op(n + 1, 0);
+  for (int32_t v = 0; v < n; ++v) {
+    int64_t c = 0;
+    for (int64_t e = rp[v]; e < rp[v + 1]; ++e) c += higher(v, col[e]) ? 1 : 0;
+    op[v + 1] = op[v] + c;
+  }
+  std::vector<int32_t> out(op[n] > 0 ? op[n] : 1);
+  for (int32_t v = 0; v < n; ++v) {
+    int64_t p = op[v];
+    for (int64_t e = rp[v]; e < rp[v + 1]; ++e)
+      if (higher(v, col[e])) out[p++] = col[e];
+  }
+#ifdef _OPENMP
+  int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#else
+  int nt = 1;
+#endif
+  std::vector<unsigned __int128> part(nt, 0);
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nt)
+#endif
+  {
+#ifdef _OPENMP
+    const int tid = omp_get_thread_num();
+#else
+    const int tid = 0;
+#endif
+    // mark[x] == stamp[d] iff x is in the candidate list of depth d
+    std::vector<uint64_t> mark(n > 0 ? n : 1, 0);
+    uint64_t next_stamp = 0;
+    std::vector<std::vector<int32_t>> lists(k);
+    unsigned __int128 local = 0;
+    // depth d holds the common out-neighbours of the d chosen vertices
+    std::function<void(int32_t)> grow = [&](int32_t d) {
+      const std::vector<int32_t>& cur = lists[d];
+      if (d == k - 1) {
+        local += cur.size();
+        return;
+      }
+      const uint64_t stamp = ++next_stamp;
+      for (int32_t x : cur) mark[x] = stamp;
+      for (int32_t u : cur) {
+        std::vector<int32_t>& nxt = lists[d + 1];
+        nxt.clear();
+        for (int64_t e = op[u]; e < op[u + 1]; ++e)
+          if (mark[out[e]] == stamp) nxt.push_back(out[e]);
+        if ((int32_t)nxt.size() >= k - 1 - d) {
+          grow(d + 1);
+          for (int32_t x : nxt) mark[x] = stamp;  // deeper levels re-marked them
+        }
+      }
+    };
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 64)
+#endif
+    for (int32_t v = 0; v < n; ++v) {
+      lists[1].assign(out.begin() + op[v], out.begin() + op[v + 1]);
+      if ((int32_t)lists[1].size() >= k - 1) grow(1);
+    }
+    part[tid] = local;
+  }
+  unsigned __int128 total = 0;
+  for (auto p : part) total += p;
+  *count_lo = (uint64_t)total;
+  *count_hi = (uint64_t)(total >> 64);
+  return OR_OK;
 }
 
 int oracle_max_threads(void) {

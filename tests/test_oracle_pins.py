@@ -12,7 +12,10 @@
 * invariants: slices of f(q_0) add up, the generating walk of a random-walk
   query is one of its embeddings, removing a query edge gives a superset;
 * the candidate filter of Sec. 3.2: soundness against brute force and a
-  hand-worked example.
+  hand-worked example;
+* the independent k-clique counter (degree-ordered listing) that pins the
+  full-size R-MAT 20 clique counts: C(n, k) in K_n, tr(A^3)/6, k! x cliques =
+  the matcher's count of K_k (which brute force pins in turn).
 """
 import math
 
@@ -123,6 +126,40 @@ def test_unlabelled_closed_forms(oracle_lib, small_rmat):
     a3d = A3.diagonal().astype(object)
     assert oracle.count(g, s["cycle5"]) == \
         tr5 - 5 * tr3 - 5 * int(sum((d[i] - 2) * a3d[i] for i in range(g.n)))
+
+
+def test_clique_counter_closed_forms(oracle_lib):
+    for n in (3, 4, 6, 9, 12):
+        g = I.graph_from_edges(n, [(i, j) for i in range(n) for j in range(i + 1, n)])
+        for k in range(3, min(n, 8) + 1):
+            assert oracle.cliques(g, k) == math.comb(n, k)
+    # K_{3,3} and a 6-cycle have no triangle; two disjoint K4 have 8 triangles, 2 K4
+    k33 = I.graph_from_edges(6, [(i, j) for i in range(3) for j in range(3, 6)])
+    c6 = I.graph_from_edges(6, [(i, (i + 1) % 6) for i in range(6)])
+    two_k4 = I.graph_from_edges(8, [(a + i, a + j) for a in (0, 4) for i in range(4)
+                                    for j in range(i + 1, 4)])
+    assert oracle.cliques(k33, 3) == 0 and oracle.cliques(c6, 3) == 0
+    assert oracle.cliques(two_k4, 3) == 8 and oracle.cliques(two_k4, 4) == 2
+    assert oracle.cliques(two_k4, 5) == 0
+
+
+def test_clique_counter_against_trace_and_matcher(oracle_lib, small_rmat):
+    g = I.make_graph(small_rmat.n, small_rmat.row_ptr, small_rmat.col,
+                     np.zeros(small_rmat.n, dtype=np.int32))
+    A = adj(g)
+    assert 6 * oracle.cliques(g, 3) == int((A @ A @ A).diagonal().sum())
+    rng = np.random.default_rng(21)
+    for t in range(12):
+        n = int(rng.integers(6, 40))
+        m = int(rng.integers(n, n * (n - 1) // 2 + 1))
+        _, rp, col = I.erdos_renyi(n, m, seed=100 + t)
+        h = I.make_graph(n, rp, col, np.zeros(n, dtype=np.int32))
+        for k in (3, 4, 5):
+            kk = I.query_from_edges(k, [(i, j) for i in range(k) for j in range(i + 1, k)])
+            assert oracle.count(h, kk) == math.factorial(k) * oracle.cliques(h, k)
+    for k in (3, 4):
+        kk = I.query_from_edges(k, [(i, j) for i in range(k) for j in range(i + 1, k)])
+        assert oracle.count(g, kk) == math.factorial(k) * oracle.cliques(g, k)
 
 
 def test_labelled_triangle_closed_form(oracle_lib, small_rmat):
