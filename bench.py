@@ -22,8 +22,9 @@ layout: time per step and peak budgeted frontier memory, rows checked.
 
 `unlabelled_counts` (same line): on unlabelled R-MAT scale 20, the 3-path count
 (checked against sum d(d-1)), the ordered and distinct (symmetry-broken)
-triangle counts (checked: distinct x |Aut| = ordered) and the distinct
-4-clique count.
+triangle and 4-clique counts (checked against k! x the oracle's clique count,
+tests/golden/rmat20_unlabelled.json), and the 5-cycle and 6-path on the
+stored root slices (checked against the oracle's counts).
 
 `batched_vs_plain` (same line): the R-MAT scale-18 workload (16 Zipf(1.2)
 labels, 256 random-walk queries of 3-10 vertices with 2-4 non-tree edges, on
@@ -57,6 +58,9 @@ sys.path.insert(0, ROOT)
 
 GOLDEN = os.path.join(ROOT, "tests", "golden", "rmat16_labelled_slices.json")
 GOLDEN_BATCH = os.path.join(ROOT, "tests", "golden", "rmat18_batched_slices.json")
+GOLDEN_RMAT20 = os.path.join(ROOT, "tests", "golden", "rmat20_unlabelled.json")
+GOLDEN_SERVED = os.path.join(ROOT, "tests", "golden", "rmat22_served_slices.json")
+SERVED22_RATES = (50, 100, 200, 500, 1000, 2000)
 SERVE_RATES = (50, 100, 200, 500, 1000, 2000, 5000, 10000)
 METRIC = "embeddings/sec & queries/sec at 1 GB300 (batched vs plain, bit-exact); p50/p99"
 UNIT = "embeddings/s"
@@ -150,6 +154,50 @@ def batched_and_served(gsm, torch, device, serve_seconds):
                        "block_size": bst["block_size"], "grid": bst["grid"],
                        "tuned": bst["tuned"]},
            "bit_exact": True}
+    # enumerate mode: every query's sorted rows in device memory, the batch
+    # (one graph, rows canonicalised per query) against one gsm_enumerate per
+    # query; rows checked against the oracle's digests
+    outs = [torch.empty(max(c, 1) * q["k"], dtype=torch.int32, device="cuda")
+            for c, q in zip(want, queries)]
+
+    def digests_ok(rows_list):
+        for q, r in zip(queries, rows_list):
+            a = np.ascontiguousarray(r, dtype="<i4").reshape(-1)
+            if hashlib.sha256(a.tobytes()).hexdigest() != q["rows_sha256"]:
+                return False
+        return True
+
+    for Q, o in zip(Qs, outs):
+        M.enumerate(Q, out=o)
+    if not digests_ok([o[:c * q["k"]].cpu().numpy() for o, c, q in zip(outs, want, queries)]):
+        raise SystemExit("plain enumerate rows differ from the oracle's")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        for Q, o in zip(Qs, outs):
+            M.enumerate(Q, out=o)
+    torch.cuda.synchronize()
+    plain_e = (time.perf_counter() - t0) / reps
+    got, rows = M.run_batch(Qs, enumerate=True, device=True)
+    if got != want or not digests_ok([r.cpu().numpy() for r in rows]):
+        raise SystemExit("batched enumerate rows differ from the oracle's")
+    del rows
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        got, rows = M.run_batch(Qs, enumerate=True, device=True)
+        del rows
+    torch.cuda.synchronize()
+    batch_e = (time.perf_counter() - t0) / reps
+    out["enumerate"] = {
+        "mode": "sorted rows in device memory",
+        "plain": {"queries_per_sec": round(len(Qs) / plain_e, 1),
+                  "embeddings_per_sec": round(emb / plain_e, 1),
+                  "ms_per_pass": round(plain_e * 1e3, 3)},
+        "batched": {"queries_per_sec": round(len(Qs) / batch_e, 1),
+                    "embeddings_per_sec": round(emb / batch_e, 1),
+                    "ms_per_pass": round(batch_e * 1e3, 3)},
+        "bit_exact": True}
     # served: Poisson arrivals over the same query stream
     served = []
     rng = np.random.default_rng(7)
@@ -191,6 +239,112 @@ def batched_and_served(gsm, torch, device, serve_seconds):
     return out
 
 
+def load_served_workload():
+    from paper_2003_01527_gb300 import inputs as I
+    with open(GOLDEN_SERVED) as f:
+        gold = json.load(f)
+    n, rp, col = I.rmat(22, 16, *I.RMAT_ABC, seed=5)
+    g = I.make_graph(n, rp, col, I.zipf_labels(n, 32, 1.0, seed=105))
+    h = hashlib.sha256()
+    for a in (g.row_ptr, g.col, g.labels):
+        h.update(np.ascontiguousarray(a, dtype="<i4").tobytes())
+    if h.hexdigest() != gold["graph"]["sha256"]:
+        raise SystemExit("generated R-MAT 22 graph differs from the stored workload")
+    return g, gold["queries"]
+
+
+def served_rmat22(gsm, torch, device, requests_per_rate, rates=SERVED22_RATES):
+    """The served form on the resident R-MAT scale-22 graph (4,194,304
+    vertices, 32 Zipf(1.0) labels): Poisson arrivals at each rate of the
+    configured range, requests drawn from a pool of random-walk queries of
+    3-12 vertices on oracle-sized root slices, against the plain form (one
+    gsm_count per request, run serially on a second context) fed the same
+    arrival stream.  Every count is checked against the oracle's."""
+    g, queries = load_served_workload()
+    S = gsm.Matcher(device=device)  # serves
+    P = gsm.Matcher(device=device)  # plain, serial
+    S.load_graph(g.row_ptr, g.col, g.labels, validate=True)
+    P.load_graph(g.row_ptr, g.col, g.labels)
+    def make_q(m, q):
+        Q = m.query(q["k"], q["edges"], q["labels"]).restrict(0, 0, q["root_hi"])
+        for u in range(1, q["k"]):
+            Q.restrict(u, 0, q["window"])
+        return Q
+
+    SQ = [make_q(S, q) for q in queries]
+    PQ = [make_q(P, q) for q in queries]
+    want = [q["count"] for q in queries]
+    if [P.count(Q) for Q in PQ] != want:
+        raise SystemExit("R-MAT 22 plain counts differ from the oracle's")
+    del g
+    rng = np.random.default_rng(9)
+    gsm.gsm_server_start(S.ctx, 2, 256)
+    rows = []
+    for rate in rates:
+        n_req = requests_per_rate
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+        pick = rng.integers(0, len(queries), n_req)
+        emb = int(sum(want[j] for j in pick))
+        # served: submit at the arrival times, results polled afterwards
+        # (latency = the library's submit -> done timestamps)
+        tickets = []
+        t0 = time.perf_counter()
+        for a, j in zip(arrivals, pick):
+            wait = t0 + a - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+            tickets.append((gsm.gsm_submit(S.ctx, SQ[j].handle), int(j)))
+        results = {}
+        while len(results) < len(tickets):
+            for t, j in tickets:
+                if t not in results:
+                    r = gsm.gsm_poll(S.ctx, t)
+                    if r is not None:
+                        results[t] = (r, j)
+            time.sleep(0.0002)
+        last_done = max(r["t_done_ns"] for r, _ in results.values())
+        first_sub = min(r["t_submit_ns"] for r, _ in results.values())
+        wall_s = (last_done - first_sub) / 1e9
+        if not all(r["status"] == 0 and r["count"] == want[j] for r, j in results.values()):
+            raise SystemExit(f"served R-MAT 22 counts differ from the oracle's at {rate} q/s")
+        lat = [(r["t_done_ns"] - r["t_submit_ns"]) / 1e6 for r, _ in results.values()]
+        # plain, serially, on the same arrival stream
+        plat = []
+        t0 = time.perf_counter()
+        done = t0
+        for a, j in zip(arrivals, pick):
+            arr = t0 + a
+            wait = arr - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+            if P.count(PQ[j]) != want[j]:
+                raise SystemExit(f"plain R-MAT 22 count differs at {rate} q/s")
+            done = time.perf_counter()
+            plat.append((done - arr) * 1e3)
+        pwall = done - (t0 + arrivals[0])
+        rows.append({"rate_qps": rate, "requests": n_req, "embeddings": emb,
+                     "served": {"throughput_qps": round(n_req / wall_s, 1),
+                                "embeddings_per_sec": round(emb / wall_s, 1),
+                                "latency_ms_p50": round(pct(lat, 50), 3),
+                                "latency_ms_p99": round(pct(lat, 99), 3)},
+                     "plain_serial": {"throughput_qps": round(n_req / pwall, 1),
+                                      "embeddings_per_sec": round(emb / pwall, 1),
+                                      "latency_ms_p50": round(pct(plat, 50), 3),
+                                      "latency_ms_p99": round(pct(plat, 99), 3)}})
+    gsm.gsm_server_stop(S.ctx)
+    st = S.batch_stats()
+    S.close()
+    P.close()
+    ks = sorted({q["k"] for q in queries})
+    return {"workload": "R-MAT scale 22 (4,194,304 vertices, edge factor 16), 32 Zipf(1.0) "
+                        f"labels, resident; a pool of {len(queries)} random-walk queries of "
+                        f"{ks[0]}-{ks[-1]} vertices (induced edges), every query vertex "
+                        f"restricted to ids below {queries[0]['window']} and the root to an "
+                        "oracle-sized prefix",
+            "lanes": 2, "max_batch": 256, "batches": st["batches"],
+            "bit_exact": True, "rates": rows}
+
+
 def compressed_frontiers(gsm, torch, device, g, queries, steps):
     """The same query slices with compressed partial results (frontier rows
     as (parent row, new vertex)): time per step, peak budgeted frontier memory
@@ -227,18 +381,69 @@ def compressed_frontiers(gsm, torch, device, g, queries, steps):
     return out
 
 
-def unlabelled_counts(gsm, torch, device):
+def lookahead_leg(gsm, torch, device, g, queries, steps):
+    """The same query slices with the k-look-ahead of Sec. 3.2 off, at 1 and
+    at 2: candidates checked and partial embeddings kept over all levels,
+    and time per step; rows checked against the oracle digests."""
+    out = {}
+    for la in (0, 1, 2):
+        M = gsm.Matcher(device=device, lookahead=la)
+        M.load_graph(g.row_ptr, g.col, g.labels)
+        Qs = [M.query(q["k"], q["edges"], q["labels"]).restrict(0, 0, q["root_hi"])
+              for q in queries]
+        outs = [torch.empty(max(q["count"], 1) * q["k"], dtype=torch.int32, device="cuda")
+                for q in queries]
+        cand, kept = 0, 0
+        for Q, o, q in zip(Qs, outs, queries):
+            M.enumerate(Q, out=o)
+            st = M.last_run_stats()
+            cand += sum(st["candidates"])
+            kept += sum(st["frontier"][1:q["k"]])
+            rows = o[:q["count"] * q["k"]].cpu().numpy().astype("<i4")
+            if hashlib.sha256(rows.tobytes()).hexdigest() != q["rows_sha256"]:
+                raise SystemExit(f"look-ahead {la}: result mismatch on a query slice")
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(M.stream)
+        for _ in range(steps):
+            counts = M.enumerate_many(Qs, outs)
+        ev1.record(M.stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / steps
+        out[f"lookahead_{la}"] = {"ms_per_step": round(ms, 3),
+                                  "embeddings_per_sec": round(sum(counts) / (ms / 1e3), 1),
+                                  "candidates_checked": int(cand),
+                                  "partial_embeddings_kept": int(kept)}
+        M.close()
+    out["bit_exact"] = True
+    return out
+
+
+def unlabelled_counts(gsm, torch, device, ordered_k4=True):
     """Unlabelled R-MAT scale 20 (1,048,576 vertices, edge factor 16): the
-    ordered 3-path count pinned by sum d(d-1), ordered and distinct
-    (symmetry-broken) triangle counts, and the distinct 4-clique count."""
+    ordered 3-path count pinned by sum d(d-1); ordered and distinct
+    (symmetry-broken) triangle counts and distinct and ordered 4-clique
+    counts, pinned by the oracle's clique listing stored in
+    tests/golden/rmat20_unlabelled.json (ordered = k! x cliques); and the
+    5-cycle and 6-path on the stored root slices, each count equal to the
+    oracle's."""
     from paper_2003_01527_gb300 import inputs as I
     g = I.rmat_unlabelled_graph(scale=20, seed=3)
+    with open(GOLDEN_RMAT20) as f:
+        gold = json.load(f)
+    h = hashlib.sha256()
+    for a in (g.row_ptr, g.col, g.labels):
+        h.update(np.ascontiguousarray(a, dtype="<i4").tobytes())
+    if h.hexdigest() != gold["graph"]["sha256"]:
+        raise SystemExit("generated R-MAT 20 graph differs from the stored workload")
+    tri_n, k4_n = gold["cliques"]["3"], gold["cliques"]["4"]
     d = g.degrees()
     M = gsm.Matcher(device=device)
     M.load_graph(g.row_ptr, g.col, g.labels)
     s = I.unlabelled_shapes()
     out = {"workload": "R-MAT scale 20 (1,048,576 vertices, edge factor 16), unlabelled",
-           "nnz": g.nnz}
+           "nnz": g.nnz, "pins": "3-path: sum d(d-1); triangle, 4-clique: k! x the oracle's "
+                                 "clique count; 5-cycle, 6-path slices: the oracle's counts"}
 
     def timed(fn):
         fn()  # warm-up
@@ -256,17 +461,39 @@ def unlabelled_counts(gsm, torch, device):
     q = M.query(3, s["triangle"].edges)
     c, ms = timed(lambda: M.count(q))
     (dc, aut), dms = timed(lambda: M.count_distinct(q))
-    if dc * aut != c:
-        raise SystemExit("triangle: distinct x |Aut| differs from the ordered count")
+    if c != 6 * tri_n or dc != tri_n or aut != 6:
+        raise SystemExit("triangle counts differ from the oracle's clique count")
     out["triangle"] = {"ordered": c, "ordered_ms": round(ms, 3),
                        "ordered_embeddings_per_sec": round(c / ms * 1e3, 1),
                        "distinct": dc, "automorphisms": aut, "distinct_ms": round(dms, 3)}
-    # the ordered 4-clique count (4.1e11, about a minute) is left to the tests'
-    # scale; the distinct count does 1/24 of the work
     q = M.query(4, s["clique4"].edges)
     (dc, aut), dms = timed(lambda: M.count_distinct(q))
-    out["clique4"] = {"distinct": dc, "automorphisms": aut, "distinct_ms": round(dms, 3),
-                      "ordered_implied": dc * aut}
+    if dc != k4_n or aut != 24:
+        raise SystemExit("distinct 4-clique count differs from the oracle's clique count")
+    out["clique4"] = {"distinct": dc, "automorphisms": aut, "distinct_ms": round(dms, 3)}
+    if ordered_k4:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c = M.count(q)
+        ms = (time.perf_counter() - t0) * 1e3
+        if c != 24 * k4_n:
+            raise SystemExit("ordered 4-clique count differs from 4! x the oracle's")
+        out["clique4"].update({"ordered": c, "ordered_ms": round(ms, 1),
+                               "ordered_embeddings_per_sec": round(c / ms * 1e3, 1)})
+    slices = []
+    for sl in gold["slices"]:
+        qs = s[sl["shape"]]
+        Q = M.query(qs.k, qs.edges).restrict(0, sl["root_lo"], sl["root_hi"])
+        if sl["window"]:
+            for u in range(1, qs.k):
+                Q.restrict(u, 0, sl["window"])
+        c, ms = timed(lambda: M.count(Q))
+        if c != sl["count"]:
+            raise SystemExit(f"{sl['shape']} slice count differs from the oracle's")
+        slices.append({"shape": sl["shape"], "roots": [sl["root_lo"], sl["root_hi"]],
+                       "other_vertices_below": sl["window"], "ordered": c,
+                       "ms": round(ms, 3), "embeddings_per_sec": round(c / ms * 1e3, 1)})
+    out["slices"] = slices
     M.close()
     return out
 
@@ -374,54 +601,71 @@ def run_gpu(args):
     if args.queries:
         keep = [int(x) for x in args.queries.split(",")]
         queries = [queries[i] for i in keep]
-    M = gsm.Matcher(device=local, time_kernels=True, filter_rounds=args.filter_rounds,
+    # two contexts on the same graph: M (no per-kernel events) is timed for
+    # the headline; MK records CUDA events around every kernel and is timed
+    # in a second pass for the per-kernel split and the roofline
+    M = gsm.Matcher(device=local, time_kernels=False, filter_rounds=args.filter_rounds,
                     block_size=args.block_size)
+    MK = gsm.Matcher(device=local, time_kernels=True, filter_rounds=args.filter_rounds,
+                     block_size=args.block_size)
     M.load_graph(g.row_ptr, g.col, g.labels, validate=True)
+    MK.load_graph(g.row_ptr, g.col, g.labels)
     Qs = [M.query(q["k"], q["edges"], q["labels"]).restrict(0, 0, q["root_hi"]) for q in queries]
+    QKs = [MK.query(q["k"], q["edges"], q["labels"]).restrict(0, 0, q["root_hi"])
+           for q in queries]
     outs = [torch.empty(max(q["count"], 1) * q["k"], dtype=torch.int32, device="cuda")
             for q in queries]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
-    stream = M.stream  # the library issues every kernel on this stream
 
-    def step():
+    def step(m, qs):
         # one gsm_enumerate_many call: every query slice listed into its
         # device buffer, each copy overlapping the following queries
-        counts = M.enumerate_many(Qs, outs)
-        return sum(counts), M.last_run_stats()["kernel_launches"]
+        counts = m.enumerate_many(qs, outs)
+        return sum(counts), m.last_run_stats()["kernel_launches"]
 
     # warm-up, and bit-exact check against the stored oracle digests
     for _ in range(max(args.warmup, 3)):
-        step()
-    for q, Q, out in zip(queries, Qs, outs):
-        _, c = M.enumerate(Q, out=out)
-        rows = out[:c * q["k"]].cpu().numpy().astype("<i4")
-        if c != q["count"] or hashlib.sha256(rows.tobytes()).hexdigest() != q["rows_sha256"]:
-            raise SystemExit(f"result mismatch on a query slice (count {c} vs {q['count']})")
-    M.kernel_stats(reset=True)
+        step(M, Qs)
+        step(MK, QKs)
+    for m, qs in ((M, Qs), (MK, QKs)):
+        for q, Q, out in zip(queries, qs, outs):
+            _, c = m.enumerate(Q, out=out)
+            rows = out[:c * q["k"]].cpu().numpy().astype("<i4")
+            if c != q["count"] or hashlib.sha256(rows.tobytes()).hexdigest() != q["rows_sha256"]:
+                raise SystemExit(f"result mismatch on a query slice (count {c} vs {q['count']})")
 
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    sampler = ClockSampler(local)
-    sampler.start()
-    ms_total, embeddings, launches = 0.0, 0, 0
-    for _ in range(args.steps):
-        flush.fill_(1)
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
+    def timed_steps(m, qs, clocks=False):
+        """K steps, L2 flushed before each, CUDA events on the library's stream."""
+        if dist:
+            dist.barrier()
         torch.cuda.synchronize()
-        ev0.record(stream)
-        e, l = step()
-        ev1.record(stream)
+        sampler = ClockSampler(local) if clocks else None
+        if sampler:
+            sampler.start()
+        ms, emb, nl = 0.0, 0, 0
+        for _ in range(args.steps):
+            flush.fill_(1)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record(m.stream)
+            e, l = step(m, qs)
+            ev1.record(m.stream)
+            torch.cuda.synchronize()
+            ms += ev0.elapsed_time(ev1)
+            emb += e
+            nl += l
+        ck = sampler.stop() if sampler else None
+        if dist:
+            dist.barrier()
         torch.cuda.synchronize()
-        ms_total += ev0.elapsed_time(ev1)
-        embeddings += e
-        launches += l
-    clocks = sampler.stop()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    kstats = M.kernel_stats(reset=True)
+        return ms, emb, nl, ck
+
+    ms_total, embeddings, launches, clocks = timed_steps(M, Qs, clocks=True)
+    MK.kernel_stats(reset=True)
+    ms_k, _, _, _ = timed_steps(MK, QKs)
+    kstats = MK.kernel_stats(reset=True)
+    MK.close()
 
     per_step = embeddings / args.steps
     ms_per_step, value, qps = combine_ranks(ms_total / args.steps, per_step, len(queries), world,
@@ -477,11 +721,16 @@ def run_gpu(args):
     batched = None
     unlabelled = None
     compressed = None
+    lookahead = None
     if not args.queries:
         compressed = compressed_frontiers(gsm, torch, local, g, queries, 5)
+        lookahead = lookahead_leg(gsm, torch, local, g, queries, 5)
+    served22 = None
     if not args.no_batch and not args.queries:
         batched = batched_and_served(gsm, torch, local, args.serve_seconds)
-        unlabelled = unlabelled_counts(gsm, torch, local)
+        unlabelled = unlabelled_counts(gsm, torch, local, ordered_k4=not args.no_ordered_k4)
+    if not args.no_serve22 and not args.queries:
+        served22 = served_rmat22(gsm, torch, local, args.serve22_requests)
 
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
@@ -501,6 +750,10 @@ def run_gpu(args):
         "kernels": {s["name"]: {"launches": s["launches"], "ms": round(s["total_ms"], 3),
                                 "algo_GB": round(s["algo_bytes"] / 1e9, 4)}
                     for s in kstats if s["launches"]},
+        "kernel_split": {"note": "per-kernel CUDA events on every launch, from a second "
+                                 "timed pass of the same steps (the headline pass records "
+                                 "no per-kernel events)",
+                         "ms_per_step_with_events": round(ms_k / args.steps, 4)},
         "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": round(statistics.median(e2e_ms), 3)},
         "gpu_launches": launches,
@@ -509,6 +762,8 @@ def run_gpu(args):
         "batched_vs_plain": batched,
         "unlabelled_counts": unlabelled,
         "compressed_frontiers": compressed,
+        "lookahead": lookahead,
+        "served_rmat22": served22,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -520,36 +775,59 @@ def run_gpu(args):
 # --------------------------------------------------------------- CPU oracle
 
 
-def oracle_sample(g, queries, budget_s=20.0):
-    """The oracle on a bounded sample: the non-empty query slices in order,
-    each over a sub-range of its roots, until about budget_s seconds of work."""
+# The oracle's sample of the plain workload: the first 1/16 of the root range
+# of every non-empty query slice (a fixed list, the same for every step and
+# for both CPU legs), and, for the single-core figure, the first five of
+# those sub-slices.
+ORACLE_SAMPLE_DIV = 16
+ORACLE_ONE_CORE_SLICES = 5
+
+
+def oracle_slices(queries, one_core=False):
+    out = [(i, max(1, q["root_hi"] // ORACLE_SAMPLE_DIV)) for i, q in enumerate(queries)
+           if q["count"] > 0]
+    return out[:ORACLE_ONE_CORE_SLICES] if one_core else out
+
+
+def oracle_sample(g, queries, one_core=False):
+    """The oracle on its fixed sample (oracle_slices): (embeddings listed and
+    sorted, seconds, slice names, threads used)."""
     import oracle
     from paper_2003_01527_gb300 import inputs as I
+    nthreads = 1 if one_core else 0
     t_total, emb, used = 0.0, 0, []
-    for i, q in enumerate(queries):
-        if q["count"] == 0:
-            continue
+    for i, hi in oracle_slices(queries, one_core):
+        q = queries[i]
         qq = I.query_from_edges(q["k"], q["edges"], q["labels"])
-        hi = max(1, q["root_hi"] // 4)
         t0 = time.perf_counter()
-        c, _, rc = oracle.match(g, qq, enumerate=True, root_range=(0, hi))
-        dt = time.perf_counter() - t0
-        t_total += dt
+        c, _, rc = oracle.match(g, qq, enumerate=True, root_range=(0, hi), nthreads=nthreads)
+        t_total += time.perf_counter() - t0
         emb += c
         used.append(f"q{i}[0,{hi})")
-        if t_total > budget_s:
-            break
-    return emb, t_total, used
+    return emb, t_total, used, (1 if one_core else oracle.max_threads())
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def cpu_baseline(g, queries):
-    import oracle
-    emb, secs, used = oracle_sample(g, queries)
-    return {"value": round(emb / secs, 1), "unit": UNIT, "cores": oracle.max_threads(),
-            "kind": "oracle",
-            "sample": f"{len(used)} query slices, first quarter of each root range "
-                      f"({', '.join(used)}): {emb} embeddings enumerated and sorted in "
-                      f"{secs:.1f} s"}
+    emb, secs, used, cores = oracle_sample(g, queries)
+    emb1, secs1, used1, _ = oracle_sample(g, queries, one_core=True)
+    return {"value": round(emb / secs, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{len(used)} query slices, first 1/{ORACLE_SAMPLE_DIV} of each root range "
+                      f"({', '.join(used)}): {emb} embeddings listed and sorted in {secs:.2f} s",
+            "one_core": {"value": round(emb1 / secs1, 1), "cores": 1,
+                         "sample": f"{', '.join(used1)}: {emb1} embeddings in {secs1:.2f} s"},
+            "cpu_model": cpu_model(), "nproc": os.cpu_count()}
 
 
 def run_reference(args):
@@ -560,24 +838,27 @@ def run_reference(args):
     oracle.build()
     g, queries = load_workload()
     for _ in range(args.warmup):
-        oracle_sample(g, queries, budget_s=2.0)
+        oracle_sample(g, queries)
     emb, secs = 0, 0.0
-    samples = []
+    samples, cores = [], 0
     for _ in range(args.steps):
-        e, s, used = oracle_sample(g, queries, budget_s=5.0)
+        e, t, used, cores = oracle_sample(g, queries)
         emb += e
-        secs += s
+        secs += t
         samples = used
     value = emb / secs
+    sample = (f"{len(samples)} query slices, first 1/{ORACLE_SAMPLE_DIV} of each root range "
+              f"({', '.join(samples)}), the same every step")
     line = {
         "impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(secs / args.steps * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic (seeded R-MAT + random-walk queries)",
-        "config": {"workload": WORKLOAD, "sample": ", ".join(samples)},
-        "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": oracle.max_threads(),
-                         "kind": "oracle", "sample": ", ".join(samples)},
+        "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": cores,
+                         "kind": "oracle", "sample": sample, "cpu_model": cpu_model(),
+                         "nproc": os.cpu_count()},
         "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -594,7 +875,13 @@ def main():
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched and served measurements")
     ap.add_argument("--serve-seconds", type=float, default=2.0,
-                    help="seconds of Poisson arrivals per served rate")
+                    help="seconds of Poisson arrivals per served rate (R-MAT 18 leg)")
+    ap.add_argument("--no-serve22", action="store_true",
+                    help="skip the served R-MAT 22 leg")
+    ap.add_argument("--serve22-requests", type=int, default=2000,
+                    help="requests per arrival rate of the served R-MAT 22 leg")
+    ap.add_argument("--no-ordered-k4", action="store_true",
+                    help="skip the ordered 4-clique count of the R-MAT 20 leg")
     ap.add_argument("--filter-rounds", type=int, default=0,
                     help="candidate refinement rounds after the first filter pass")
     ap.add_argument("--block-size", type=int, default=0,

@@ -74,6 +74,12 @@ typedef void (*gsm_free_fn)(void *alloc_ctx, void *ptr, size_t bytes, void *stre
  * per row read; results are identical.  Levels always take the single pass
  * (rows are split until one row per candidate fits). */
 #define GSM_OPT_COMPRESSED_FRONTIERS 4
+/* Fault injection for tests of the bounded waits: in every single-pass level
+ * of the default frontier layout, the second tile never publishes its
+ * survivor count, so the waits of the tiles after it run out
+ * (lookback_spin_limit) and the call returns GSM_ERR_TIMEOUT.  Nothing hangs
+ * and every row stays inside its buffer; the context stays usable. */
+#define GSM_OPT_INJECT_LOOKBACK_STALL 8
 
 typedef struct gsm_options {
   /* Cap on device memory for intermediate frontiers and scratch, in bytes.
@@ -101,6 +107,25 @@ typedef struct gsm_options {
    * each holds the staging buffers of one query's rows until they are copied
    * out, so up to this many queries can be ahead of the copies. */
   int32_t copy_slots;
+  /* Bound of every wait of a single-pass level on the counts of earlier
+   * tiles (polls of about 32 ns; 0 = 2^20).  A wait that runs out ends the
+   * call with GSM_ERR_TIMEOUT; the rows written stay inside the buffers. */
+  int32_t lookback_spin_limit;
+  /* k-look-ahead of the verification levels (Sec. 3.2, "1- and 2-look-ahead";
+   * 0 = off, 1, 2): a candidate w for pi_i is dropped when the query
+   * neighbours of pi_i placed later cannot all be mapped to distinct
+   * neighbours of w outside the partial embedding (1: by label counts; 2:
+   * also by their candidate sets, over the first 64 same-label neighbours).
+   * Both tests are necessary conditions, so results do not depend on it; it
+   * trades extra work per surviving candidate for smaller frontiers.  The
+   * batched form ignores it. */
+  int32_t lookahead;
+  /* Device memory for adjacency bitmaps of the data graph's hubs (vertices of
+   * degree >= 32, highest degree first, ceil(n/32) x 4 bytes each), used to
+   * check non-tree edges against a hub with one bit probe instead of a binary
+   * search of its row.  0 = 512 MiB; negative = no bitmaps.  Built by
+   * gsm_load_graph, outside the memory budget; results do not depend on it. */
+  int64_t hub_bitmap_bytes;
 } gsm_options;
 
 /* Fills *opt with the defaults described above. */
@@ -207,7 +232,8 @@ gsm_status gsm_enumerate_many(gsm_ctx *ctx, int32_t nq, const gsm_query *const *
 
 /* Copies rows [first, first + nrows) of the last gsm_enumerate result on this
  * context (kept in library buffers until the next gsm_count / gsm_enumerate /
- * gsm_candidates call) into out (host, or device with GSM_OUT_DEVICE).
+ * gsm_candidates / gsm_run_batch call) into out (host, or device with
+ * GSM_OUT_DEVICE).
  * Errors: GSM_ERR_INVALID_ARG (range outside the last result), GSM_ERR_CUDA. */
 gsm_status gsm_last_rows(gsm_ctx *ctx, int32_t *out, uint64_t first, uint64_t nrows,
                          int32_t flags);
@@ -231,10 +257,12 @@ gsm_status gsm_candidates(gsm_ctx *ctx, const gsm_query *q, uint32_t *bitmaps, u
  * order of each query uses label/degree histograms of G as its P_f estimate
  * (the VF3 estimate the paper cites in Sec. 3.2) instead of the candidate
  * counts, so the order is known before the filter runs.  Results equal
- * gsm_count's for every query.  The batch works in a fixed-capacity
- * workspace (about 1.4 GB, allocated on first use, outside the memory budget:
- * 2^24 frontier rows, 2^27 frontier elements, 2^28 candidates per level); a
- * batch that would exceed it is rerun query by query on the gsm_count path.
+ * gsm_count's (and gsm_enumerate's rows) for every query.  The batch works in
+ * a fixed-capacity workspace (about 1.4 GB, allocated on first use, outside
+ * the memory budget: 2^24 frontier rows, 2^27 frontier elements, 2^28
+ * candidates per level, and for listing batches a result arena of 2^28 ints);
+ * a batch that would exceed it is rerun query by query on the single-query
+ * path.
  */
 typedef struct gsm_batch_stats {
   int32_t block_size;        /* threads per CTA used by the last batch */
@@ -251,62 +279,92 @@ typedef struct gsm_batch_stats {
 
 #define GSM_BATCH_AUTOTUNE 1 /* time candidate (block size, grid) pairs for new batch shapes */
 
-/* Counts the embeddings of qs[0..nq) (counts[j] as gsm_count would return
- * for qs[j]).  Shapes (number of queries, largest query) seen before reuse
- * their captured graph.  With GSM_BATCH_AUTOTUNE, the first batch of a shape
- * is run once per candidate configuration (every run gives the same counts)
- * and the fastest is kept for that shape.  nq <= 65535.
+/* The result of one query of the batched or served form.  In count mode
+ * rows is NULL.  In enumerate mode rows holds the count x k result rows
+ * (row-major int32, query-id column order, sorted lexicographically, as
+ * gsm_enumerate returns them), NULL when count is 0; the buffer belongs to
+ * the library until gsm_result_free.  on_device = 1: rows is device memory
+ * of the context's device (from the context's allocator), else host memory. */
+typedef struct gsm_result {
+  uint64_t count;
+  gsm_status status;     /* GSM_OK or the error that ended the query */
+  int64_t t_submit_ns;   /* served form: steady-clock timestamps (same clock for all) */
+  int64_t t_admit_ns;
+  int64_t t_done_ns;
+  int32_t k;             /* row width (enumerate mode) */
+  int32_t on_device;
+  int32_t *rows;
+} gsm_result;
+
+/* Releases r->rows (through the context's allocator when on_device) and sets
+ * it to NULL; ctx is the context that produced the result.  NULL rows are
+ * fine. */
+void gsm_result_free(gsm_ctx *ctx, gsm_result *r);
+
+/* Runs qs[0..nq) as one batch.  counts[j] receives what gsm_count would
+ * return for qs[j].  results = NULL: count only.  Otherwise every query also
+ * lists its rows: results[j] receives the count and the sorted rows of qs[j]
+ * (host memory, or device memory with GSM_OUT_DEVICE), which the caller
+ * releases with gsm_result_free.  Shapes (number of queries, largest query,
+ * count or list) seen before reuse their captured graph.  With
+ * GSM_BATCH_AUTOTUNE, the first batch of a shape is run once per candidate
+ * configuration (every run gives the same results) and the fastest is kept
+ * for that shape.  nq <= 65535.
  * Errors: GSM_ERR_INVALID_ARG, GSM_ERR_NO_GRAPH, GSM_ERR_OOM, GSM_ERR_CUDA, and
- * the errors of gsm_count on the fallback path. */
+ * the errors of gsm_count / gsm_enumerate on the fallback path (on an error
+ * no rows are left allocated). */
 gsm_status gsm_run_batch(gsm_ctx *ctx, const gsm_query *const *qs, int32_t nq, uint64_t *counts,
-                         int32_t flags);
+                         gsm_result *results, int32_t flags);
 
 gsm_status gsm_batch_get_stats(gsm_ctx *ctx, gsm_batch_stats *out);
 
 /* Sets the batch workspace capacities (0 keeps the default): frontier rows
- * (< 2^31), frontier elements (rows x width, < 2^31) and candidates per level
- * (< 2^30).  Frees the current workspace; the next batch allocates the new one.
+ * (< 2^31), frontier elements (rows x width, < 2^31), candidates per level
+ * (< 2^30) and result-arena ints of listing batches (< 2^40).  Frees the
+ * current workspace; the next batch allocates the new one.
  * Errors: GSM_ERR_INVALID_ARG. */
 gsm_status gsm_batch_configure(gsm_ctx *ctx, uint64_t cap_rows, uint64_t cap_elems,
-                               uint64_t cap_items);
+                               uint64_t cap_items, uint64_t cap_result_elems);
 
 /* ---- Served form: a request loop with continuous batching ----
  *
  * gsm_server_start starts a thread that owns the context until
- * gsm_server_stop: meanwhile only gsm_submit, gsm_poll and gsm_server_stop may
- * be called on the context (from any threads).  Submitted queries wait in
- * arrival order; whenever one of `lanes` batch lanes (a stream with its own
- * batch workspace) is free, the waiting queries are admitted into a new batch
- * while the sum of their estimated peak frontier sizes (from label/degree
- * histograms, Sec. 3.2's P_f) stays within half a lane's frontier capacity --
- * at least one query per batch, at most max_batch.  Queries that arrive while
- * batches run are admitted as soon as a lane frees, so their work overlaps the
- * running batches on the device.  A batch that overflows its workspace is
- * recounted query by query.  Every result equals gsm_count's for that query.
+ * gsm_server_stop: meanwhile only gsm_submit, gsm_poll, gsm_result_free and
+ * gsm_server_stop may be called on the context (from any threads).  Submitted
+ * queries wait in arrival order; whenever one of `lanes` batch lanes (a stream
+ * with its own batch workspace) is free, the waiting queries are admitted
+ * into a new batch while the sum of their estimated peak frontier sizes (from
+ * label/degree histograms, Sec. 3.2's P_f) stays within half a lane's
+ * frontier capacity -- at least one query per batch, at most max_batch.
+ * Queries that arrive while batches run are admitted as soon as a lane frees,
+ * so their work overlaps the running batches on the device.  A batch that
+ * overflows its workspace is rerun query by query.  Every result equals
+ * gsm_count's (gsm_enumerate's rows) for that query.
  */
-typedef struct gsm_result {
-  uint64_t count;
-  gsm_status status;     /* GSM_OK or the error that ended the query */
-  int64_t t_submit_ns;   /* steady-clock timestamps (same clock for all) */
-  int64_t t_admit_ns;
-  int64_t t_done_ns;
-} gsm_result;
 
-/* lanes 1..8, max_batch 1..65535.  Errors: GSM_ERR_INVALID_ARG (also if a
- * server already runs), GSM_ERR_NO_GRAPH, GSM_ERR_CUDA. */
+/* lanes 1..8, max_batch 1..65535.  Captures the batch graphs of every shape
+ * (count and enumerate mode) before it returns, so serving does not capture.
+ * Errors: GSM_ERR_INVALID_ARG (also if a server already runs),
+ * GSM_ERR_NO_GRAPH, GSM_ERR_CUDA. */
 gsm_status gsm_server_start(gsm_ctx *ctx, int32_t lanes, int32_t max_batch);
 
-/* Queues q; *ticket identifies it.  q must stay alive until its result has
- * been polled.  Thread-safe.  Errors: GSM_ERR_INVALID_ARG (no server). */
-gsm_status gsm_submit(gsm_ctx *ctx, const gsm_query *q, uint64_t *ticket);
+#define GSM_MODE_COUNT 0      /* the result carries the count only */
+#define GSM_MODE_ENUMERATE 1  /* ... and the sorted rows, in host memory */
+
+/* Queues q in `mode`; *ticket identifies it.  q must stay alive until its
+ * result has been polled.  Thread-safe.  Errors: GSM_ERR_INVALID_ARG (no
+ * server, bad mode). */
+gsm_status gsm_submit(gsm_ctx *ctx, const gsm_query *q, int32_t mode, uint64_t *ticket);
 
 /* GSM_PENDING while the query waits or runs; once done, fills *out, forgets
- * the ticket and returns GSM_OK (out->status holds the query's own status).
- * Thread-safe.  Errors: GSM_ERR_INVALID_ARG (unknown ticket, no server). */
+ * the ticket and returns GSM_OK (out->status holds the query's own status;
+ * in enumerate mode out->rows passes to the caller, who releases it with
+ * gsm_result_free).  Thread-safe.  Errors: GSM_ERR_INVALID_ARG (unknown
+ * ticket, no server). */
 gsm_status gsm_poll(gsm_ctx *ctx, uint64_t ticket, gsm_result *out);
 
 /* Finishes every submitted query, stops the thread and frees the lanes
- * (results not yet polled are dropped). */
+ * (results not yet polled are dropped, their rows released). */
 gsm_status gsm_server_stop(gsm_ctx *ctx);
 
 /* Size of the fixed device array behind gsm_candidates_static: bitmap words of

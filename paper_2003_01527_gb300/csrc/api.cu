@@ -7,6 +7,7 @@
 #include <functional>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -81,6 +82,10 @@ struct gsm_ctx {
   int32_t max_deg = 0;
   int32_t *d_rp = nullptr, *d_col = nullptr, *d_lab = nullptr;
   int32_t *d_lcol = nullptr, *d_llab = nullptr;  // rows ordered by (label, id)
+  int32_t *d_hub = nullptr;        // hub index of every vertex, -1 = none
+  uint32_t *d_hub_bits = nullptr;  // adjacency bitmaps of the hubs
+  int32_t hub_count = 0, hub_min_deg = 0;
+  size_t hub_bits_bytes = 0;
   std::vector<int32_t> label_values;  // sorted distinct labels; dense id = index
 
   // query-lifetime buffers (outside the budget)
@@ -137,7 +142,7 @@ struct gsm_ctx {
   // batched form: per-label sorted degrees (order estimates without the
   // filter's results); lanes = stream + fixed-capacity workspace + graphs
   std::vector<std::vector<int32_t>> deg_by_label;
-  int64_t batch_caps[3] = {0, 0, 0};  // rows, elements, candidates (0 = default)
+  int64_t batch_caps[4] = {0, 0, 0, 0};  // rows, elements, candidates, result elements (0 = default)
   struct BatchLane {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -157,7 +162,18 @@ struct gsm_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_done = nullptr;
     uint32_t *zero_bitmap = nullptr;  // root bitmap of padding queries
     int32_t mb = 0, kb = 0;           // shape of the issued batch (padded)
-    std::map<std::tuple<int32_t, int32_t, int32_t, int32_t, int32_t>, cudaGraphExec_t> graphs;
+    // enumerate batches: the result arena (allocated on first use), the step
+    // sizes read back after a batch, each selected query's matching order and
+    // whether it lists rows, and the buffers of the canonical sort
+    int32_t enumerate = 0;
+    int64_t cap_final = 0;
+    BatchStep *h_state = nullptr;
+    std::vector<std::array<int32_t, kMaxK>> orders;
+    std::vector<int32_t> lists;
+    void *srt[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    size_t srt_cap[5] = {0, 0, 0, 0, 0};
+    std::map<std::tuple<int32_t, int32_t, int32_t, int32_t, int32_t, int32_t>, cudaGraphExec_t>
+        graphs;
     // a batch in flight (server): which requests, how many queries
     std::vector<uint64_t> tickets;
     std::vector<int32_t> sel;
@@ -184,9 +200,17 @@ struct Fail {
 };
 
 GraphDev graph_dev(const gsm_ctx *ctx) {
-  return GraphDev{ctx->n,      ctx->nnz,    ctx->d_rp,
-                  ctx->d_col,  ctx->d_lab,  ctx->d_lcol,
-                  ctx->d_llab, (int32_t)std::max<size_t>(1, ctx->label_values.size())};
+  return GraphDev{ctx->n,
+                  ctx->nnz,
+                  ctx->d_rp,
+                  ctx->d_col,
+                  ctx->d_lab,
+                  ctx->d_lcol,
+                  ctx->d_llab,
+                  (int32_t)std::max<size_t>(1, ctx->label_values.size()),
+                  ctx->hub_count ? ctx->d_hub : nullptr,
+                  ctx->hub_count ? ctx->d_hub_bits : nullptr,
+                  (ctx->n + 31) / 32};
 }
 
 void set_err(gsm_ctx *c, const char *fmt, ...) {
@@ -592,6 +616,8 @@ struct Run {
   LevelDesc lv[kMaxK];
   GraphDev g;
   int32_t block;
+  int32_t spin_limit;  // polls a look-back wait may take
+  int32_t stall_tile;  // GSM_OPT_INJECT_LOOKBACK_STALL: the tile that withholds its count
   int64_t wcap;        // max candidates per extend launch
   int64_t chunk_rows;  // max rows per extend launch (0 = unbounded)
   uint64_t acc_rows = 0;  // final rows so far, in ctx->acc[0]
@@ -776,7 +802,7 @@ void process_fused(Run &R, int32_t i, const int32_t *F, int64_t ld, const int32_
   }
   timed(ctx, K_FUSED, read_bytes, (uint64_t)W, 1, [&] {
     launch_extend_fused(R.g, d, F, ld, pstart, pslot, woff, tile_row, wa, wb, R.block, lb, sink,
-                        ctx->stream);
+                        R.spin_limit, R.stall_tile, ctx->stream);
   });
   const int64_t *S_dev = (const int64_t *)(lb + tiles + 1);
   if (last) {
@@ -962,7 +988,7 @@ void process_c(Run &R, int32_t i, const CFrontier &f, const int32_t *pstart, con
   }
   timed(ctx, K_FUSED, read_bytes, (uint64_t)W, 1, [&] {
     launch_cextend(R.g, d, f, i, pstart, pslot, woff, tile_row, wa, wb, R.block, lb, sink,
-                   ctx->stream);
+                   R.spin_limit, ctx->stream);
   });
   if (count_only) return;
   fetch(ctx, lb + tiles + 1, 2 * sizeof(unsigned long long));
@@ -1116,6 +1142,8 @@ void run_query(gsm_ctx *ctx, const gsm_query *q, bool enumerate, int32_t *out, u
   R.k = q->k;
   R.g = graph_dev(ctx);
   R.block = ctx->opt.block_size > 0 ? ctx->opt.block_size : 256;
+  R.spin_limit = ctx->opt.lookback_spin_limit > 0 ? ctx->opt.lookback_spin_limit : kLbSpinLimit;
+  R.stall_tile = (ctx->opt.flags & GSM_OPT_INJECT_LOOKBACK_STALL) ? 1 : -1;
   R.chunk_rows = ctx->opt.chunk_rows;
   // masks take W/8 bytes and tile arrays 12 bytes per tile of scratch
   R.wcap = std::max<int64_t>((int64_t)ctx->max_deg + 1,
@@ -1169,6 +1197,34 @@ void run_query(gsm_ctx *ctx, const gsm_query *q, bool enumerate, int32_t *out, u
     for (int32_t j = 0; j <= i; ++j) d.out_col[j] = (i == q->k - 1) ? R.order[j] : j;
     d.bitmap = bm + (size_t)u * nw;
     d.lab = dense[u];
+    d.la = std::max<int32_t>(0, ctx->opt.lookahead);
+    d.cand = bm;
+    d.n_words = nw;
+    if (d.la) {
+      // query neighbours of pi_i placed after it, grouped by label
+      uint32_t placed = 0;
+      for (int32_t j = 0; j <= i; ++j) placed |= 1u << R.order[j];
+      for (int32_t w = 0; w < q->k; ++w) {
+        if (!(q->adj[u] >> w & 1u) || (placed >> w & 1u)) continue;
+        int32_t t = 0;
+        while (t < d.nla && d.la_lab[t] != dense[w]) ++t;
+        if (t == d.nla) {
+          d.la_lab[t] = dense[w];
+          d.nla++;
+        }
+        d.la_need[t]++;
+        d.la_uq[t] |= 1u << w;
+      }
+      for (int32_t t = 0; t < d.nla; ++t)
+        for (int32_t j = 0; j < i; ++j) {
+          const int32_t uj = R.order[j];
+          if (dense[uj] != d.la_lab[t]) continue;
+          if (q->adj[u] >> uj & 1u)
+            d.la_known[t]++;
+          else
+            d.la_pos[t] |= 1u << j;
+        }
+    }
     if (less) {
       // ordering constraints between pi_i and vertices placed before it
       for (const auto &c : *less) {
@@ -1290,6 +1346,49 @@ gsm_status guarded(gsm_ctx *ctx, F &&f) {
   }
 }
 
+// Adjacency bitmaps of the hubs: vertices of degree >= kHubMinDegree, the
+// highest degrees first, as many as fit opt.hub_bitmap_bytes (ceil(n/32)
+// words each).  A non-tree edge check against a hub is then one bit probe
+// instead of a binary search of its long row.
+constexpr int32_t kHubMinDegree = 32;
+constexpr int64_t kHubBytesDefault = int64_t(512) << 20;
+
+void build_hubs(gsm_ctx *ctx, const std::vector<int32_t> &h_rp) {
+  const int32_t n = ctx->n;
+  const int64_t budget =
+      ctx->opt.hub_bitmap_bytes == 0 ? kHubBytesDefault : ctx->opt.hub_bitmap_bytes;
+  const int32_t words = (n + 31) / 32;
+  if (budget <= 0 || n == 0) return;
+  const int64_t cap = budget / ((int64_t)words * 4);
+  std::vector<int32_t> hubs;
+  for (int32_t v = 0; v < n; ++v)
+    if (h_rp[v + 1] - h_rp[v] >= kHubMinDegree) hubs.push_back(v);
+  std::sort(hubs.begin(), hubs.end(), [&](int32_t a, int32_t b) {
+    const int32_t da = h_rp[a + 1] - h_rp[a], db = h_rp[b + 1] - h_rp[b];
+    return da != db ? da > db : a < b;
+  });
+  if ((int64_t)hubs.size() > cap) hubs.resize((size_t)cap);
+  if (hubs.empty()) return;
+  const int32_t H = (int32_t)hubs.size();
+  std::vector<int32_t> idx(n, -1);
+  for (int32_t h = 0; h < H; ++h) idx[hubs[h]] = h;
+  ctx->d_hub = (int32_t *)dev_alloc(ctx, sizeof(int32_t) * n);
+  ctx->hub_bits_bytes = (size_t)H * words * sizeof(uint32_t);
+  ctx->d_hub_bits = (uint32_t *)dev_alloc(ctx, ctx->hub_bits_bytes);
+  int32_t *d_list = (int32_t *)dev_alloc(ctx, sizeof(int32_t) * H);
+  CU(cudaMemcpyAsync(ctx->d_hub, idx.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CU(cudaMemcpyAsync(d_list, hubs.data(), sizeof(int32_t) * H, cudaMemcpyHostToDevice,
+                     ctx->stream));
+  GraphDev g = graph_dev(ctx);
+  launch_hub_bitmaps(g, d_list, H, words, ctx->d_hub_bits, ctx->stream);
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(ctx->stream));
+  dev_free(ctx, d_list, sizeof(int32_t) * H);
+  ctx->hub_count = H;
+  ctx->hub_min_deg = h_rp[hubs.back() + 1] - h_rp[hubs.back()];
+}
+
 void clear_all_graphs(gsm_ctx *ctx);
 
 void free_graph(gsm_ctx *ctx) {
@@ -1299,6 +1398,12 @@ void free_graph(gsm_ctx *ctx) {
   if (ctx->d_lab) dev_free(ctx, ctx->d_lab, sizeof(int32_t) * std::max<int32_t>(ctx->n, 1));
   if (ctx->d_lcol) dev_free(ctx, ctx->d_lcol, sizeof(int32_t) * std::max<int64_t>(ctx->nnz, 1));
   if (ctx->d_llab) dev_free(ctx, ctx->d_llab, sizeof(int32_t) * std::max<int64_t>(ctx->nnz, 1));
+  if (ctx->d_hub) dev_free(ctx, ctx->d_hub, sizeof(int32_t) * std::max<int32_t>(ctx->n, 1));
+  if (ctx->d_hub_bits) dev_free(ctx, ctx->d_hub_bits, ctx->hub_bits_bytes);
+  ctx->d_hub = nullptr;
+  ctx->d_hub_bits = nullptr;
+  ctx->hub_count = 0;
+  ctx->hub_bits_bytes = 0;
   ctx->d_rp = ctx->d_col = ctx->d_lab = nullptr;
   ctx->d_lcol = ctx->d_llab = nullptr;
   ctx->has_graph = false;
@@ -1316,6 +1421,7 @@ using Lane = gsm_ctx::BatchLane;
 constexpr int64_t kBatchCapRows = int64_t(1) << 24;
 constexpr int64_t kBatchCapElems = int64_t(1) << 27;
 constexpr int64_t kBatchCapItems = int64_t(1) << 28;
+constexpr int64_t kBatchCapFinal = int64_t(1) << 28;  // result arena elements (1 GiB)
 
 template <typename T>
 T *lane_alloc(gsm_ctx *ctx, Lane &L, int64_t elems) {
@@ -1349,6 +1455,9 @@ void lane_release(gsm_ctx *ctx, Lane &L) {
   if (L.h_bm) cudaFreeHost(L.h_bm);
   if (L.h_counts) cudaFreeHost(L.h_counts);
   if (L.h_overflow) cudaFreeHost(L.h_overflow);
+  if (L.h_state) cudaFreeHost(L.h_state);
+  for (int j = 0; j < 5; ++j)
+    if (L.srt[j]) dev_free(ctx, L.srt[j], L.srt_cap[j]);
   if (L.bitmaps) dev_free(ctx, L.bitmaps, L.bitmaps_cap);
   for (cudaEvent_t e : {L.ev0, L.ev1, L.ev_done})
     if (e) cudaEventDestroy(e);
@@ -1381,7 +1490,11 @@ void lane_workspace(gsm_ctx *ctx, Lane &L, int32_t nq, int64_t words_total) {
     a.tile_cnt = lane_alloc<int32_t>(ctx, L, tiles);
     a.tile_off = lane_alloc<int64_t>(ctx, L, tiles);
     a.masks = lane_alloc<uint32_t>(ctx, L, L.cap_items / 32 + 256);  // + a tile of the largest block
+    a.fmasks = lane_alloc<uint32_t>(ctx, L, L.cap_items / 32 + 256);
+    a.ftile_cnt = lane_alloc<int32_t>(ctx, L, tiles);
+    a.ftile_off = lane_alloc<int64_t>(ctx, L, tiles);
     a.state = lane_alloc<BatchStep>(ctx, L, kMaxK + 1);
+    CU(cudaMallocHost(&L.h_state, sizeof(BatchStep) * (kMaxK + 1)));
     a.overflow = lane_alloc<int32_t>(ctx, L, 1);
     a.partials = lane_alloc<int64_t>(ctx, L, (int64_t)ctx->num_sms * 32 + 1);
     CU(cudaMallocHost(&L.h_overflow, sizeof(int32_t)));
@@ -1433,6 +1546,76 @@ void lane_workspace(gsm_ctx *ctx, Lane &L, int32_t nq, int64_t words_total) {
   if (moved) lane_clear_graphs(L);  // captured graphs hold the old pointers
 }
 
+// The result arena of enumerate batches, allocated on first use (captured
+// graphs of enumerate batches hold its address, so it never moves).
+void lane_final(gsm_ctx *ctx, Lane &L) {
+  if (L.a.final_rows) return;
+  L.cap_final = ctx->batch_caps[3] ? ctx->batch_caps[3] : kBatchCapFinal;
+  L.a.cap_final = L.cap_final;
+  L.a.final_rows = lane_alloc<int32_t>(ctx, L, L.cap_final);
+}
+
+// Grows lane sort buffer j to `bytes` (contents not kept).
+void *lane_srt(gsm_ctx *ctx, Lane &L, int j, size_t bytes) {
+  if (L.srt_cap[j] < bytes) CU(cudaStreamSynchronize(L.stream));  // the old buffer may be in use
+  ensure_buf(ctx, &L.srt[j], &L.srt_cap[j], bytes, false, 0);
+  return L.srt[j];
+}
+
+// Columns 0 .. sort_cols-1 of rows that the levels emitted in lexicographic
+// order of the matching order still need sorting (see run_query); 0: none.
+int32_t unsorted_columns(int32_t k, const int32_t *order) {
+  int32_t pos[kMaxK];
+  for (int32_t j = 0; j < k; ++j) pos[order[j]] = j;
+  int32_t sort_cols = k - 1;
+  while (sort_cols > 0 && pos[sort_cols - 1] < pos[sort_cols]) --sort_cols;
+  return sort_cols;
+}
+
+// N row-major result rows of k int32 in query-id column order, emitted in
+// lexicographic order of the matching order `order`, written into dst (device)
+// in canonical (lexicographic) order: a copy when the order already is
+// canonical, else a packed-key radix sort of the unsorted leading columns.
+void canonical_rows(gsm_ctx *ctx, Lane &L, const int32_t *src, int64_t N, int32_t k,
+                    const int32_t *order, int32_t *dst) {
+  if (N <= 0) return;
+  const int32_t sort_cols = unsorted_columns(k, order);
+  if (sort_cols == 0) {
+    CU(cudaMemcpyAsync(dst, src, (size_t)N * k * sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                       L.stream));
+    return;
+  }
+  int32_t bits = 1;
+  while (bits < 31 && (int64_t(1) << bits) < ctx->n) ++bits;
+  const int32_t nw = packed_words(k, bits);
+  const int64_t H = sort_hist_elems(N);
+  uint64_t *ka = (uint64_t *)lane_srt(ctx, L, 0, (size_t)N * nw * sizeof(uint64_t));
+  uint64_t *kb = (uint64_t *)lane_srt(ctx, L, 1, (size_t)N * nw * sizeof(uint64_t));
+  int32_t *hist = (int32_t *)lane_srt(ctx, L, 2, (size_t)H * sizeof(int32_t));
+  int64_t *hoff = (int64_t *)lane_srt(
+      ctx, L, 3, (size_t)(H + 1 + scan_tmp_elems(H) + 1) * sizeof(int64_t));
+  launch_pack_rows(src, N, k, bits, ka, N, L.stream);
+  launch_sort_rows_packed(nullptr, 0, N, k, bits, sort_cols, ka, kb, N, dst, hist, hoff,
+                          hoff + H + 1, L.stream);
+  CU(cudaGetLastError());
+}
+
+// Element offset in the result arena of every selected query that listed
+// rows (-1 for the others), from the step sizes read back after the batch:
+// step k-1 holds the queries of k vertices, in batch order.
+std::vector<int64_t> lane_row_offsets(const Lane &L, const unsigned long long *counts) {
+  std::vector<int64_t> off(L.m, -1);
+  int64_t next[kMaxK + 1];
+  for (int32_t i = 0; i <= kMaxK; ++i) next[i] = L.h_state[i].FB;
+  for (int32_t t = 0; t < L.m; ++t) {
+    const int32_t k = L.h_qs[t].k;
+    if (!L.lists[t] || k < 2) continue;
+    off[t] = next[k - 1];
+    next[k - 1] += (int64_t)counts[t] * k;
+  }
+  return off;
+}
+
 // Estimated |C(u)|: vertices with u's label and at least u's degree (the
 // label / degree probability the paper borrows from VF3), scaled by u's
 // restriction range.
@@ -1474,10 +1657,12 @@ double plan_estimated(gsm_ctx *ctx, const gsm_query *q, const int32_t *dense, in
 
 cudaGraphExec_t lane_graph(gsm_ctx *ctx, Lane &L, int32_t m, int32_t kmax, int32_t n_words,
                            int32_t block, int32_t grid) {
-  const auto key = std::make_tuple(m, kmax, n_words, block, grid);
+  const auto key = std::make_tuple(m, kmax, n_words, block, grid, L.enumerate);
   auto it = L.graphs.find(key);
   if (it != L.graphs.end()) return it->second;
+  if (L.enumerate) lane_final(ctx, L);
   BatchArgs a = L.a;
+  a.enumerate = L.enumerate;
   a.nq = m;
   a.kmax = kmax;
   a.n_words = n_words;
@@ -1519,10 +1704,16 @@ int32_t bucket_size(int32_t k) { return k; }
 // Host part of a batch: labels, filter descriptions, orders, level
 // descriptions, uploaded (asynchronously) to the lane, padded to the bucketed
 // shape (L.mb queries).  L.sel = indices of the queries that can match (a
-// label absent from G means 0).  Returns the bucketed largest query size.
-int32_t lane_prepare(gsm_ctx *ctx, Lane &L, const gsm_query *const *qs, int32_t nq) {
+// label absent from G means 0).  lists (may be null): lists[j] != 0 if query
+// j lists its rows (queries of two or more vertices write them into the
+// result arena).  Returns the bucketed largest query size.
+int32_t lane_prepare(gsm_ctx *ctx, Lane &L, const gsm_query *const *qs, int32_t nq,
+                     const int32_t *lists = nullptr) {
   const int32_t n_words = (ctx->n + 31) / 32;
   L.sel.clear();
+  L.orders.clear();
+  L.lists.clear();
+  L.enumerate = 0;
   std::vector<std::array<int32_t, kMaxK>> dense_of;
   int64_t total_k = 0;
   for (int32_t j = 0; j < nq; ++j) {
@@ -1558,6 +1749,13 @@ int32_t lane_prepare(gsm_ctx *ctx, Lane &L, const gsm_query *const *qs, int32_t 
     std::memset(&bq, 0, sizeof(bq));
     bq.k = q->k;
     bq.root_bitmap = base + (size_t)order[0] * n_words;
+    bq.enumerate = (lists && lists[L.sel[t]] && q->k >= 2) ? 1 : 0;
+    L.enumerate |= bq.enumerate;
+    for (int32_t j = 0; j < q->k; ++j) bq.out_col[j] = order[j];
+    std::array<int32_t, kMaxK> ord{};
+    for (int32_t j = 0; j < q->k; ++j) ord[j] = order[j];
+    L.orders.push_back(ord);
+    L.lists.push_back(lists && lists[L.sel[t]] ? 1 : 0);
     for (int32_t i = 1; i < q->k; ++i) {
       BatchLevel &lv = bq.lv[i];
       const int32_t u = order[i];
@@ -1603,6 +1801,8 @@ void lane_issue(gsm_ctx *ctx, Lane &L, int32_t kmax, int32_t block, int32_t grid
                      cudaMemcpyDeviceToHost, L.stream));
   CU(cudaMemcpyAsync(L.h_overflow, L.a.overflow, sizeof(int32_t), cudaMemcpyDeviceToHost,
                      L.stream));
+  CU(cudaMemcpyAsync(L.h_state, L.a.state, sizeof(BatchStep) * (kMaxK + 1),
+                     cudaMemcpyDeviceToHost, L.stream));
   CU(cudaEventRecord(L.ev_done, L.stream));
   ctx->bstats.graph_launches += 1;
   ctx->bstats.block_size = block;
@@ -1625,16 +1825,80 @@ std::pair<int32_t, int32_t> batch_config(gsm_ctx *ctx, int32_t m, int32_t kmax, 
   return {256, ctx->num_sms * 4};
 }
 
+// Result rows of one query through the single-query path (count rows into a
+// new buffer: host memory, or device memory from the context's allocator).
+void single_query_rows(gsm_ctx *ctx, const gsm_query *q, bool on_device, gsm_result *r) {
+  uint64_t c = 0;
+  bool trunc = false;
+  run_query(ctx, q, true, nullptr, 0, 0, &c, &trunc);
+  r->count = c;
+  r->k = q->k;
+  r->on_device = on_device ? 1 : 0;
+  r->rows = nullptr;
+  if (c == 0) return;
+  const size_t bytes = (size_t)c * q->k * sizeof(int32_t);
+  if (on_device) {
+    r->rows = (int32_t *)dev_alloc(ctx, bytes);
+    CU(cudaMemcpyAsync(r->rows, ctx->last_rows, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  } else {
+    r->rows = (int32_t *)std::malloc(bytes);
+    if (!r->rows) FAIL(GSM_ERR_OOM, "host allocation of %zu bytes failed", bytes);
+    CU(cudaMemcpyAsync(r->rows, ctx->last_rows, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  CU(cudaStreamSynchronize(ctx->stream));
+}
+
+void release_rows(gsm_ctx *ctx, gsm_result *r) {
+  if (!r->rows) return;
+  if (r->on_device)
+    dev_free(ctx, r->rows, (size_t)r->count * r->k * sizeof(int32_t));
+  else
+    std::free(r->rows);
+  r->rows = nullptr;
+}
+
+// Rows of selected query t of a finished listing batch on lane L (its
+// arena rows canonicalised) into r: host memory, or device memory.
+void lane_query_rows(gsm_ctx *ctx, Lane &L, int32_t t, int64_t arena_off, uint64_t count,
+                     int32_t k, bool on_device, gsm_result *r) {
+  r->count = count;
+  r->k = k;
+  r->on_device = on_device ? 1 : 0;
+  r->rows = nullptr;
+  if (count == 0) return;
+  const size_t bytes = (size_t)count * k * sizeof(int32_t);
+  const int32_t *src = L.a.final_rows + arena_off;
+  if (on_device) {
+    r->rows = (int32_t *)dev_alloc(ctx, bytes);
+    canonical_rows(ctx, L, src, (int64_t)count, k, L.orders[t].data(), r->rows);
+  } else {
+    int32_t *stage = (int32_t *)lane_srt(ctx, L, 4, bytes);
+    canonical_rows(ctx, L, src, (int64_t)count, k, L.orders[t].data(), stage);
+    r->rows = (int32_t *)std::malloc(bytes);
+    if (!r->rows) FAIL(GSM_ERR_OOM, "host allocation of %zu bytes failed", bytes);
+    CU(cudaMemcpyAsync(r->rows, stage, bytes, cudaMemcpyDeviceToHost, L.stream));
+  }
+}
+
 void run_batch(gsm_ctx *ctx, const gsm_query *const *qs, int32_t nq, uint64_t *counts,
-               int32_t flags) {
+               gsm_result *results, int32_t flags) {
   if (!ctx->has_graph) FAIL(GSM_ERR_NO_GRAPH, "no data graph loaded");
   const auto t0 = std::chrono::steady_clock::now();
   Lane &L = ctx->lane0;
   L.stream = ctx->stream;
-  for (int32_t j = 0; j < nq; ++j) counts[j] = 0;
+  const bool on_device = flags & GSM_OUT_DEVICE;
+  for (int32_t j = 0; j < nq; ++j) {
+    counts[j] = 0;
+    if (results) {
+      std::memset(&results[j], 0, sizeof(gsm_result));
+      results[j].k = qs[j]->k;
+      results[j].on_device = on_device ? 1 : 0;
+    }
+  }
   ctx->bstats.batches += 1;
   ctx->bstats.overflowed = 0;
-  const int32_t kmax = lane_prepare(ctx, L, qs, nq);
+  std::vector<int32_t> lists(nq, results ? 1 : 0);
+  const int32_t kmax = lane_prepare(ctx, L, qs, nq, lists.data());
   if (L.m == 0) return;
   bool tuned = false;
   auto cfg = batch_config(ctx, L.m, kmax, &tuned);
@@ -1647,7 +1911,7 @@ void run_batch(gsm_ctx *ctx, const gsm_query *const *qs, int32_t nq, uint64_t *c
       float t = 0;
       lane_issue(ctx, L, kmax, c[0], ctx->num_sms * c[1]);
       overflow = lane_wait(ctx, L, &t);
-      if (overflow) break;  // every configuration gives the same counts
+      if (overflow) break;  // every configuration gives the same results
       if (t < best) {
         best = t;
         cfg = {c[0], ctx->num_sms * c[1]};
@@ -1667,19 +1931,44 @@ void run_batch(gsm_ctx *ctx, const gsm_query *const *qs, int32_t nq, uint64_t *c
   ctx->bstats.tuned = tuned ? 1 : 0;
   ctx->bstats.block_size = cfg.first;
   ctx->bstats.grid = cfg.second;
-  if (overflow) {
-    // the workspace was too small for this batch: run it query by query
-    ctx->bstats.overflowed = 1;
-    ctx->bstats.fallbacks += 1;
-    for (int32_t t = 0; t < L.m; ++t) {
-      uint64_t c = 0;
-      bool trunc = false;
-      run_query(ctx, qs[L.sel[t]], false, nullptr, 0, 0, &c, &trunc);
-      counts[L.sel[t]] = c;
+  try {
+    if (overflow) {
+      // the workspace was too small for this batch: run it query by query
+      ctx->bstats.overflowed = 1;
+      ctx->bstats.fallbacks += 1;
+      for (int32_t t = 0; t < L.m; ++t) {
+        const int32_t j = L.sel[t];
+        if (results) {
+          single_query_rows(ctx, qs[j], on_device, &results[j]);
+          counts[j] = results[j].count;
+        } else {
+          uint64_t c = 0;
+          bool trunc = false;
+          run_query(ctx, qs[j], false, nullptr, 0, 0, &c, &trunc);
+          counts[j] = c;
+        }
+      }
+    } else {
+      for (int32_t t = 0; t < L.m; ++t) counts[L.sel[t]] = L.h_counts[t];
+      if (results) {
+        const std::vector<int64_t> off = lane_row_offsets(L, L.h_counts);
+        for (int32_t t = 0; t < L.m; ++t) {
+          const int32_t j = L.sel[t];
+          if (qs[j]->k == 1)  // one-vertex queries: their candidate list
+            single_query_rows(ctx, qs[j], on_device, &results[j]);
+          else
+            lane_query_rows(ctx, L, t, off[t], L.h_counts[t], qs[j]->k, on_device, &results[j]);
+        }
+        CU(cudaStreamSynchronize(L.stream));
+      }
     }
-  } else {
-    for (int32_t t = 0; t < L.m; ++t) counts[L.sel[t]] = L.h_counts[t];
+  } catch (...) {
+    if (results)
+      for (int32_t j = 0; j < nq; ++j) release_rows(ctx, &results[j]);
+    throw;
   }
+  if (results)
+    for (int32_t j = 0; j < nq; ++j) results[j].count = counts[j];
   ctx->bstats.last_ms =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
@@ -1702,9 +1991,11 @@ struct gsm_ctx::Server {
   struct Req {
     uint64_t ticket = 0;
     const gsm_query *q = nullptr;
+    int32_t mode = GSM_MODE_COUNT;
     double est_rows = 0;
     int64_t t_submit = 0, t_admit = 0, t_done = 0;
     uint64_t count = 0;
+    int32_t *rows = nullptr;  // enumerate mode: host rows, handed over by gsm_poll
     gsm_status status = GSM_PENDING;
   };
   std::thread th;
@@ -1727,32 +2018,64 @@ int64_t now_ns() {
       .count();
 }
 
-// Completes the batch of a lane whose ev_done has fired.
+// Completes the batch of a lane whose ev_done has fired: counts, and the
+// sorted rows of the requests in enumerate mode.
 void server_complete(gsm_ctx *ctx, gsm_ctx::Server &S, Lane &L) {
   const bool overflow = *L.h_overflow != 0;
   std::vector<const gsm_query *> qs;
+  std::vector<int32_t> modes;
   {
     std::lock_guard<std::mutex> lk(S.mu);
-    for (uint64_t t : L.tickets) qs.push_back(S.inflight[t].q);
+    for (uint64_t t : L.tickets) {
+      qs.push_back(S.inflight[t].q);
+      modes.push_back(S.inflight[t].mode);
+    }
   }
-  std::vector<uint64_t> counts(L.tickets.size(), 0);
-  gsm_status st = GSM_OK;
-  if (overflow) {
-    ctx->bstats.fallbacks += 1;
-    st = guarded(ctx, [&] {
-      for (size_t t = 0; t < qs.size(); ++t) {
-        bool trunc = false;
-        run_query(ctx, qs[t], false, nullptr, 0, 0, &counts[t], &trunc);
+  const size_t nr = L.tickets.size();
+  std::vector<uint64_t> counts(nr, 0);
+  std::vector<gsm_result> res(nr);
+  for (auto &r : res) std::memset(&r, 0, sizeof(r));
+  gsm_status st = guarded(ctx, [&] {
+    try {
+      if (overflow) {
+        ctx->bstats.fallbacks += 1;
+        for (size_t t = 0; t < nr; ++t) {
+          if (modes[t] == GSM_MODE_ENUMERATE) {
+            single_query_rows(ctx, qs[t], false, &res[t]);
+            counts[t] = res[t].count;
+          } else {
+            bool trunc = false;
+            run_query(ctx, qs[t], false, nullptr, 0, 0, &counts[t], &trunc);
+          }
+        }
+      } else {
+        for (int32_t t = 0; t < L.m; ++t) counts[L.sel[t]] = L.h_counts[t];
+        if (L.enumerate || std::count(modes.begin(), modes.end(), GSM_MODE_ENUMERATE)) {
+          const std::vector<int64_t> off = lane_row_offsets(L, L.h_counts);
+          for (int32_t t = 0; t < L.m; ++t) {
+            const int32_t j = L.sel[t];
+            if (modes[j] != GSM_MODE_ENUMERATE) continue;
+            if (qs[j]->k == 1)
+              single_query_rows(ctx, qs[j], false, &res[j]);
+            else
+              lane_query_rows(ctx, L, t, off[t], L.h_counts[t], qs[j]->k, false, &res[j]);
+          }
+          CU(cudaStreamSynchronize(L.stream));
+        }
       }
-    });
-  } else {
-    for (int32_t t = 0; t < L.m; ++t) counts[L.sel[t]] = L.h_counts[t];
-  }
+    } catch (...) {
+      for (auto &r : res) release_rows(ctx, &r);
+      throw;
+    }
+  });
+  if (st != GSM_OK)
+    for (auto &r : res) release_rows(ctx, &r);
   const int64_t t_done = now_ns();
   std::lock_guard<std::mutex> lk(S.mu);
-  for (size_t t = 0; t < L.tickets.size(); ++t) {
+  for (size_t t = 0; t < nr; ++t) {
     auto node = S.inflight.extract(L.tickets[t]);
     node.mapped().count = counts[t];
+    node.mapped().rows = res[t].rows;
     node.mapped().status = st;
     node.mapped().t_done = t_done;
     S.finished.insert(std::move(node));
@@ -1779,6 +2102,7 @@ void server_loop(gsm_ctx *ctx) {
       Lane &L = *lp;
       if (L.busy) continue;
       std::vector<const gsm_query *> qs;
+      std::vector<int32_t> lists;
       {
         std::lock_guard<std::mutex> lk(S.mu);
         if (S.waiting.empty()) break;
@@ -1792,13 +2116,14 @@ void server_loop(gsm_ctx *ctx) {
           used += r.est_rows;
           r.t_admit = t_admit;
           qs.push_back(r.q);
+          lists.push_back(r.mode == GSM_MODE_ENUMERATE ? 1 : 0);
           L.tickets.push_back(r.ticket);
           S.inflight.emplace(r.ticket, r);
           S.waiting.pop_front();
         }
       }
       gsm_status st = guarded(ctx, [&] {
-        const int32_t kmax = lane_prepare(ctx, L, qs.data(), (int32_t)qs.size());
+        const int32_t kmax = lane_prepare(ctx, L, qs.data(), (int32_t)qs.size(), lists.data());
         if (L.m > 0) {
           bool tuned;
           auto cfg = batch_config(ctx, L.m, kmax, &tuned);
@@ -1901,7 +2226,8 @@ gsm_status gsm_create(gsm_ctx **out, int32_t device, const gsm_options *opt) {
       (opt->block_size < 128 || opt->block_size > 1024 || opt->block_size % 32))
     return GSM_ERR_INVALID_ARG;
   if (opt && (opt->chunk_rows < 0 || opt->filter_rounds < 0 || opt->filter_rounds > 64 ||
-              opt->copy_slots < 0 || opt->copy_slots > 64))
+              opt->copy_slots < 0 || opt->copy_slots > 64 || opt->lookback_spin_limit < 0 ||
+              opt->lookahead < 0 || opt->lookahead > 2))
     return GSM_ERR_INVALID_ARG;
   gsm_ctx *ctx = new gsm_ctx();
   if (opt) ctx->opt = *opt;
@@ -2116,6 +2442,7 @@ gsm_status gsm_load_graph(gsm_ctx *ctx, int32_t n, int64_t nnz, const int32_t *r
       }
       CU(cudaStreamSynchronize(ctx->stream));
     }
+    build_hubs(ctx, h_rp);
     ctx->has_graph = true;
   });
 }
@@ -2327,23 +2654,39 @@ gsm_status gsm_count_distinct(gsm_ctx *ctx, const gsm_query *q, uint64_t *count,
 }
 
 gsm_status gsm_run_batch(gsm_ctx *ctx, const gsm_query *const *qs, int32_t nq, uint64_t *counts,
-                         int32_t flags) {
+                         gsm_result *results, int32_t flags) {
   if (!ctx || nq < 0 || nq > 65535 || (nq > 0 && (!qs || !counts)) ||
-      (flags & ~GSM_BATCH_AUTOTUNE))
+      (flags & ~(GSM_BATCH_AUTOTUNE | GSM_OUT_DEVICE)))
     return GSM_ERR_INVALID_ARG;
   for (int32_t j = 0; j < nq; ++j)
     if (!qs[j]) return GSM_ERR_INVALID_ARG;
+  if (ctx->server) {
+    set_err(ctx, "the server is running");
+    return GSM_ERR_INVALID_ARG;
+  }
   return guarded(ctx, [&] {
     CU(cudaSetDevice(ctx->device));
-    run_batch(ctx, qs, nq, counts, flags);
+    run_batch(ctx, qs, nq, counts, results, flags);
     resolve_timings(ctx);
   });
 }
 
+void gsm_result_free(gsm_ctx *ctx, gsm_result *r) {
+  if (!r || !r->rows) return;
+  if (r->on_device) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+  }
+  try {
+    release_rows(ctx, r);
+  } catch (...) {
+  }
+}
+
 gsm_status gsm_batch_configure(gsm_ctx *ctx, uint64_t cap_rows, uint64_t cap_elems,
-                               uint64_t cap_items) {
+                               uint64_t cap_items, uint64_t cap_result_elems) {
   if (!ctx || cap_rows >= (uint64_t(1) << 31) || cap_elems >= (uint64_t(1) << 31) ||
-      cap_items >= (uint64_t(1) << 30))
+      cap_items >= (uint64_t(1) << 30) || cap_result_elems >= (uint64_t(1) << 40))
     return GSM_ERR_INVALID_ARG;
   return guarded(ctx, [&] {
     CU(cudaSetDevice(ctx->device));
@@ -2353,6 +2696,7 @@ gsm_status gsm_batch_configure(gsm_ctx *ctx, uint64_t cap_rows, uint64_t cap_ele
     ctx->batch_caps[0] = (int64_t)cap_rows;
     ctx->batch_caps[1] = (int64_t)cap_elems;
     ctx->batch_caps[2] = (int64_t)cap_items;
+    ctx->batch_caps[3] = (int64_t)cap_result_elems;
   });
 }
 
@@ -2388,12 +2732,16 @@ gsm_status gsm_server_start(gsm_ctx *ctx, int32_t lanes, int32_t max_batch) {
       const size_t bm_bytes = std::min<size_t>((size_t)mb_max * kMaxK * n_words * 4,
                                                size_t(1) << 30);
       ensure_buf(ctx, &L.bitmaps, &L.bitmaps_cap, bm_bytes, false, 0);
-      for (int32_t mb = 1; mb <= mb_max; mb <<= 1)
-        for (int32_t kb = 1; kb <= kMaxK; ++kb) {
-          bool tuned;
-          auto cfg = batch_config(ctx, mb, kb, &tuned);
-          lane_graph(ctx, L, mb, kb, n_words, cfg.first, cfg.second);
-        }
+      for (int32_t e = 0; e <= 1; ++e) {  // count and enumerate batches
+        L.enumerate = e;
+        for (int32_t mb = 1; mb <= mb_max; mb <<= 1)
+          for (int32_t kb = 1; kb <= kMaxK; ++kb) {
+            bool tuned;
+            auto cfg = batch_config(ctx, mb, kb, &tuned);
+            lane_graph(ctx, L, mb, kb, n_words, cfg.first, cfg.second);
+          }
+      }
+      L.enumerate = 0;
       CU(cudaStreamSynchronize(L.stream));
     }
   });
@@ -2413,11 +2761,14 @@ gsm_status gsm_server_start(gsm_ctx *ctx, int32_t lanes, int32_t max_batch) {
   return GSM_OK;
 }
 
-gsm_status gsm_submit(gsm_ctx *ctx, const gsm_query *q, uint64_t *ticket) {
-  if (!ctx || !q || !ticket || !ctx->server) return GSM_ERR_INVALID_ARG;
+gsm_status gsm_submit(gsm_ctx *ctx, const gsm_query *q, int32_t mode, uint64_t *ticket) {
+  if (!ctx || !q || !ticket || !ctx->server ||
+      (mode != GSM_MODE_COUNT && mode != GSM_MODE_ENUMERATE))
+    return GSM_ERR_INVALID_ARG;
   gsm_ctx::Server &S = *ctx->server;
   gsm_ctx::Server::Req r;
   r.q = q;
+  r.mode = mode;
   r.t_submit = now_ns();
   int32_t dense[kMaxK], order[kMaxK];
   r.est_rows = dense_labels(ctx, q, dense) ? plan_estimated(ctx, q, dense, order) : 0.0;
@@ -2447,6 +2798,9 @@ gsm_status gsm_poll(gsm_ctx *ctx, uint64_t ticket, gsm_result *out) {
   out->t_submit_ns = it->second.t_submit;
   out->t_admit_ns = it->second.t_admit;
   out->t_done_ns = it->second.t_done;
+  out->k = it->second.q->k;
+  out->on_device = 0;
+  out->rows = it->second.rows;  // the caller owns them now
   S.finished.erase(it);
   return GSM_OK;
 }
@@ -2468,6 +2822,7 @@ gsm_status gsm_server_stop(gsm_ctx *ctx) {
     }
     if (L->own_stream && L->stream) cudaStreamDestroy(L->stream);
   }
+  for (auto &kv : S->finished) std::free(kv.second.rows);  // never polled
   ctx->server = nullptr;
   delete S;
   return GSM_OK;

@@ -16,6 +16,7 @@
 #include "batch.h"
 #include "filter_body.cuh"
 #include "segments.cuh"
+#include "verify.cuh"
 
 namespace gsm {
 namespace {
@@ -131,7 +132,7 @@ __global__ void __launch_bounds__(kPScanThreads) k_pscan_down(const T *in, const
 // Zeroes the step sizes and stores the number of root-bitmap words (the
 // length of the level-1 scan) where the scan can read it.
 __global__ void k_b_init(BatchStep *state, int64_t words) {
-  for (int j = threadIdx.x; j <= kMaxK; j += blockDim.x) state[j] = BatchStep{0, 0, 0, 0};
+  for (int j = threadIdx.x; j <= kMaxK; j += blockDim.x) state[j] = BatchStep{0, 0, 0, 0, 0, 0};
   __syncthreads();
   if (threadIdx.x == 0) state[0].W = words;
 }
@@ -295,20 +296,24 @@ __device__ __forceinline__ int32_t b_row(const BTile &b, const int32_t *s_woff,
 }
 
 // Verification pass of one step.  A survivor of a query at its last level
-// is counted into counts[q]; other survivors get their mask bit and count
-// towards their tile.  Thread t of a tile takes the 4 consecutive candidates
-// 4t .. 4t+3 (one row search for all four); the mask bits stay in candidate
-// order (4-bit groups OR-ed across the 8 lanes of a mask word).
+// is counted into counts[q] (and, for a query that lists its rows, marked in
+// fmasks and counted towards its tile in ftile_cnt); other survivors get
+// their mask bit and count towards their tile.  The check is the
+// single-query path's (check_candidate).  Thread t of a tile takes the 4
+// consecutive candidates 4t .. 4t+3 (one row search for all four); the mask
+// bits stay in candidate order (4-bit groups OR-ed across the 8 lanes of a
+// mask word).
 __global__ void __launch_bounds__(1024) k_b_count(
     GraphDev g, const BatchQuery *__restrict__ qs, int32_t i, const BatchStep *state,
     const int32_t *__restrict__ F, const int32_t *__restrict__ rseg,
     const int32_t *__restrict__ pstart, const uint8_t *__restrict__ pslot,
     const int64_t *__restrict__ woff, const int32_t *__restrict__ tile_row,
     uint32_t *__restrict__ masks, int32_t *__restrict__ tile_cnt,
-    unsigned long long *__restrict__ counts) {
+    unsigned long long *__restrict__ counts, uint32_t *__restrict__ fmasks,
+    int32_t *__restrict__ ftile_cnt) {
   static_assert(kItemsPerThread == 4, "one 4-bit group per lane");
   extern __shared__ int32_t s_woff[];
-  __shared__ int32_t s_count;
+  __shared__ int32_t s_count, s_fcount;
   const int32_t R = (int32_t)state[i].R;
   const int32_t W = (int32_t)state[i].W;
   const int64_t tiles = state[i].tiles;
@@ -316,11 +321,11 @@ __global__ void __launch_bounds__(1024) k_b_count(
   const int32_t tile_items = B * kItemsPerThread;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-    if (threadIdx.x == 0) s_count = 0;
+    if (threadIdx.x == 0) s_count = s_fcount = 0;
     const BTile b = b_stage(woff, tile_row, t, tile_items, s_woff);
     const int32_t x0 = (int32_t)t * tile_items, x1 = min(x0 + tile_items, W);
     const int32_t xb = x0 + warp * 128 + lane * kItemsPerThread;
-    uint32_t bits = 0;
+    uint32_t bits = 0, fbits = 0;
     int32_t qj[kItemsPerThread] = {-1, -1, -1, -1};  // query of a last-level survivor
     if (xb < x1) {
       int32_t rs;
@@ -343,17 +348,13 @@ __global__ void __launch_bounds__(1024) k_b_count(
         }
         const BatchLevel &L = qs[q].lv[i];
         const int32_t w = __ldg(g.lcol + pst + (x - rs));
-        bool ok = bm_has(L.bitmap, w);
-        for (int u = 0; ok && u < L.ninj; ++u) ok = F[L.inj[u] * R + r] != w;
-        for (int c = 0; ok && c < L.nb; ++c) {
-          if (c == slot) continue;
-          ok = row_contains_l(g, F[L.bpos[c] * R + r], L.lab, w);
-        }
-        if (ok) {
-          if (L.last)
+        if (check_candidate(g, L, ColumnRow{F, R, r}, w, slot)) {
+          if (L.last) {
             qj[j] = q;
-          else
+            if (fmasks && qs[q].enumerate) fbits |= 1u << j;
+          } else {
             bits |= 1u << j;
+          }
         }
       }
     }
@@ -375,8 +376,24 @@ __global__ void __launch_bounds__(1024) k_b_count(
     }
     cnt = __reduce_add_sync(kFull, cnt);
     if (lane == 0 && cnt) atomicAdd(&s_count, cnt);
+    if (fmasks) {
+      uint32_t fw = fbits << (4 * (lane & 7));
+      fw |= __shfl_xor_sync(kFull, fw, 1);
+      fw |= __shfl_xor_sync(kFull, fw, 2);
+      fw |= __shfl_xor_sync(kFull, fw, 4);
+      int32_t fc = 0;
+      if ((lane & 7) == 0) {
+        fmasks[(x0 + warp * 128) / 32 + (lane >> 3)] = fw;
+        fc = __popc(fw);
+      }
+      fc = __reduce_add_sync(kFull, fc);
+      if (lane == 0 && fc) atomicAdd(&s_fcount, fc);
+    }
     __syncthreads();
-    if (threadIdx.x == 0) tile_cnt[t] = s_count;
+    if (threadIdx.x == 0) {
+      tile_cnt[t] = s_count;
+      if (ftile_cnt) ftile_cnt[t] = s_fcount;
+    }
     __syncthreads();
   }
 }
@@ -472,6 +489,88 @@ __global__ void __launch_bounds__(1024) k_b_write(
   }
 }
 
+// Result rows of step i: FS = ftile_off[tiles]; they take arena elements
+// [FB, FB + FS*(i+1)) and the next step's rows start after them.  Over the
+// arena's capacity: overflow, and no row is written.
+__global__ void k_b_fadvance(int32_t i, BatchStep *state, const int64_t *__restrict__ ftile_off,
+                             int64_t cap_final, int32_t *overflow) {
+  const int64_t tiles = state[i].tiles;
+  const int64_t FS = tiles > 0 ? ftile_off[tiles] : 0;
+  const int64_t FB = state[i].FB;
+  if (FB + FS * (i + 1) > cap_final) {
+    *overflow = 1;
+    state[i].FS = 0;
+    state[i + 1].FB = FB;
+  } else {
+    state[i].FS = FS;
+    state[i + 1].FB = FB + FS * (i + 1);
+  }
+}
+
+// Writes the result rows of step i: result survivor q of tile t becomes row
+// ftile_off[t] + q of the step, row-major from arena element FB, position c
+// of the frontier row going to column out_col[c] of its query (the new
+// vertex to column out_col[i]).
+__global__ void __launch_bounds__(1024) k_b_fwrite(
+    GraphDev g, const BatchQuery *__restrict__ qs, int32_t i, const BatchStep *state,
+    const int32_t *__restrict__ F, const int32_t *__restrict__ rseg,
+    const int32_t *__restrict__ pstart, const int64_t *__restrict__ woff,
+    const int32_t *__restrict__ tile_row, const uint32_t *__restrict__ fmasks,
+    const int64_t *__restrict__ ftile_off, int32_t *__restrict__ final_rows) {
+  extern __shared__ int32_t s_woff[];
+  __shared__ uint32_t s_mask[kItemsPerThread * 1024 / 32];
+  __shared__ int32_t s_wpre[kItemsPerThread * 1024 / 32];
+  const int32_t R = (int32_t)state[i].R;
+  const int64_t tiles = state[i].tiles;
+  const int64_t FS = state[i].FS, FB = state[i].FB;
+  if (FS == 0) return;  // nothing to write, or over capacity
+  const int32_t B = blockDim.x;
+  const int32_t tile_items = B * kItemsPerThread;
+  const int32_t tile_words = tile_items / 32;
+  const int lane = threadIdx.x & 31;
+  const int32_t width = i + 1;
+  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int64_t base = ftile_off[t];
+    const int32_t cnt = (int32_t)(ftile_off[t + 1] - base);
+    if (cnt == 0) continue;  // uniform across the block
+    for (int32_t w = threadIdx.x; w < tile_words; w += B) s_mask[w] = fmasks[t * tile_words + w];
+    const BTile b = b_stage(woff, tile_row, t, tile_items, s_woff);
+    if (threadIdx.x < 32) {
+      int32_t carry = 0;
+      for (int32_t c = 0; c < tile_words; c += 32) {
+        const int32_t idx = c + lane;
+        const int32_t v = idx < tile_words ? __popc(s_mask[idx]) : 0;
+        int32_t incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int32_t y = __shfl_up_sync(kFull, incl, o);
+          if (lane >= o) incl += y;
+        }
+        if (idx < tile_words) s_wpre[idx] = carry + incl - v;
+        carry += __shfl_sync(kFull, incl, 31);
+      }
+    }
+    __syncthreads();
+    const int32_t x0 = (int32_t)t * tile_items;
+    for (int32_t q = threadIdx.x; q < cnt; q += B) {
+      int32_t lo = 0, hi = tile_words;
+      while (hi - lo > 1) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (s_wpre[mid] <= q) lo = mid; else hi = mid;
+      }
+      const int32_t x = x0 + lo * 32 + b_nth_bit(s_mask[lo], q - s_wpre[lo]);
+      int32_t rs;
+      const int32_t r = b_row(b, s_woff, woff, x, &rs);
+      const int32_t w = __ldg(g.lcol + pstart[r] + (x - rs));
+      const int32_t *oc = qs[rseg[r]].out_col;
+      int32_t *dst = final_rows + FB + (base + q) * width;
+      for (int c = 0; c < i; ++c) dst[oc[c]] = F[c * R + r];
+      dst[oc[i]] = w;
+    }
+    __syncthreads();
+  }
+}
+
 // Address of a field of state[i] (device memory; no host access).
 const int64_t *step_field(const BatchStep *state, int32_t i, size_t off) {
   return reinterpret_cast<const int64_t *>(reinterpret_cast<const char *>(state) +
@@ -518,13 +617,23 @@ int batch_enqueue(const GraphDev &g, const BatchArgs &a, cudaStream_t s) {
     k_b_check_work<<<1, 1, 0, s>>>(i, a.state, a.woff, a.cap_items, tile_items, a.overflow);
     k_b_tile_rows<<<G, 256, 0, s>>>(i, a.state, a.woff, tile_items, a.tile_row);
     k_b_count<<<G, B, smem, s>>>(g, a.qs, i, a.state, a.F[cur], a.rseg[cur], a.pstart, a.pslot,
-                                 a.woff, a.tile_row, a.masks, a.tile_cnt, a.counts);
+                                 a.woff, a.tile_row, a.masks, a.tile_cnt, a.counts,
+                                 a.enumerate ? a.fmasks : nullptr,
+                                 a.enumerate ? a.ftile_cnt : nullptr);
     pscan<int32_t>(a.tile_cnt, step_field(a.state, i, offsetof(BatchStep, tiles)), a.tile_off,
                    a.partials, G, s);
     k_b_advance<<<1, 1, 0, s>>>(i, a.state, a.tile_off, a.cap_rows, a.cap_elems, a.overflow);
     k_b_write<<<G, B, smem, s>>>(g, i, a.state, a.F[cur], a.rseg[cur], a.pstart, a.woff,
                                  a.tile_row, a.masks, a.tile_off, a.F[nxt], a.rseg[nxt]);
     launches += 12;
+    if (a.enumerate) {
+      pscan<int32_t>(a.ftile_cnt, step_field(a.state, i, offsetof(BatchStep, tiles)),
+                     a.ftile_off, a.partials, G, s);
+      k_b_fadvance<<<1, 1, 0, s>>>(i, a.state, a.ftile_off, a.cap_final, a.overflow);
+      k_b_fwrite<<<G, B, smem, s>>>(g, a.qs, i, a.state, a.F[cur], a.rseg[cur], a.pstart, a.woff,
+                                    a.tile_row, a.fmasks, a.ftile_off, a.final_rows);
+      launches += 5;
+    }
   }
   return launches;
 }

@@ -17,18 +17,23 @@ struct BatchLevel {
   int32_t last;             // 1 if pi_i is the query's last vertex
   int32_t lab;              // dense label of pi_i (the row segment traversed)
   const uint32_t *bitmap;   // C(pi_i)
+  int32_t nlt, lt[kMaxK];   // ordering constraints (none in the batched form)
+  int32_t ngt, gt[kMaxK];
 };
 
 struct BatchQuery {
   int32_t k;
+  int32_t enumerate;            // 1: the last level writes result rows
+  int32_t out_col[kMaxK];       // result column of row position j (= pi_j)
   const uint32_t *root_bitmap;  // C(pi_0)
   BatchLevel lv[kMaxK];         // lv[1 .. k-1]
 };
 
 // Device-side sizes of one level (rows at level i, candidates checked while
-// extending it, tiles, survivors that continue).
+// extending it, tiles, survivors that continue; FB = first element of the
+// step's result rows in the result arena, FS = result rows the step writes).
 struct BatchStep {
-  int64_t R, W, tiles, S;
+  int64_t R, W, tiles, S, FB, FS;
 };
 
 struct BatchArgs {
@@ -53,6 +58,17 @@ struct BatchArgs {
   uint32_t *masks;                // [cap_items / 32 + 32]
   int32_t *tile_cnt;              // [cap_items / 128 + 2]
   int64_t *tile_off;              // [cap_items / 128 + 3]
+  // enumerate batches (enumerate = 1): result rows of the queries that list
+  // them.  The rows of step i (queries with k = i + 1) are row-major, k ints
+  // each, in query-id column order, from element state[i].FB on; within a
+  // step the queries follow batch order, each query's rows in lexicographic
+  // order of its matching order.
+  int32_t enumerate;
+  int64_t cap_final;              // arena elements
+  int32_t *final_rows;            // [cap_final]
+  uint32_t *fmasks;               // [cap_items / 32 + 256]
+  int32_t *ftile_cnt;             // [cap_items / 128 + 2]
+  int64_t *ftile_off;             // [cap_items / 128 + 3]
 };
 
 // Issues the whole batch on stream s (no host synchronisation, fixed launch

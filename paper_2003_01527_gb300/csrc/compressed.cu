@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(1024) k_cextend(
     GraphDev g, LevelDesc d, CFrontier f, int32_t i, const int32_t *__restrict__ pstart,
     const uint8_t *__restrict__ pslot, const int64_t *__restrict__ woff,
     const int32_t *__restrict__ tile_row, int64_t wa, int32_t W, int32_t tiles,
-    unsigned long long *__restrict__ lookback, CSink sink) {
+    unsigned long long *__restrict__ lookback, CSink sink, int32_t spin_limit) {
   static_assert(kItemsPerThread == 4, "four candidates per thread");
   extern __shared__ int32_t s_woff[];
   __shared__ int32_t s_tile;
@@ -101,7 +101,9 @@ __global__ void __launch_bounds__(1024) k_cextend(
       const int32_t w = __ldg(g.lcol + pst + (x - rs));
       rj[j] = r;
       wj[j] = w;
-      if (check_candidate(g, d, ArrayRow{vals}, w, slot)) bits |= 1u << j;
+      if (check_candidate(g, d, ArrayRow{vals}, w, slot) &&
+          (!d.la || lookahead_ok(g, d, ArrayRow{vals}, w)))
+        bits |= 1u << j;
     }
   }
   const int32_t c = __popc(bits);
@@ -123,7 +125,7 @@ __global__ void __launch_bounds__(1024) k_cextend(
       }
   }
   if (warp == 0) {
-    const unsigned long long prefix = lookback_prefix(lookback, tile, tiles, T, lane);
+    const unsigned long long prefix = lookback_prefix(lookback, tile, tiles, T, lane, spin_limit);
     if (lane == 0) s_prefix = (long long)prefix;
   }
   __syncthreads();
@@ -159,7 +161,8 @@ void launch_cpivot(const GraphDev &g, const LevelDesc &d, const CFrontier &f, in
 void launch_cextend(const GraphDev &g, const LevelDesc &d, const CFrontier &f, int32_t i,
                     const int32_t *pstart, const uint8_t *pslot, const int64_t *woff,
                     const int32_t *tile_row, int64_t wa, int64_t wb, int32_t block,
-                    unsigned long long *lookback, const CSink &sink, cudaStream_t s) {
+                    unsigned long long *lookback, const CSink &sink, int32_t spin_limit,
+                    cudaStream_t s) {
   const int64_t tiles = extend_tiles(wa, wb, block);
   if (tiles <= 0) return;
   // the staged work offsets, later the survivor pairs (2 ints per item)
@@ -168,19 +171,19 @@ void launch_cextend(const GraphDev &g, const LevelDesc &d, const CFrontier &f, i
   switch (sink.mode) {
     case kCSinkPairs:
       k_cextend<kCSinkPairs><<<(unsigned)tiles, block, smem, s>>>(
-          g, d, f, i, pstart, pslot, woff, tile_row, wa, W, T, lookback, sink);
+          g, d, f, i, pstart, pslot, woff, tile_row, wa, W, T, lookback, sink, spin_limit);
       break;
     case kCSinkRows:
       k_cextend<kCSinkRows><<<(unsigned)tiles, block, smem, s>>>(
-          g, d, f, i, pstart, pslot, woff, tile_row, wa, W, T, lookback, sink);
+          g, d, f, i, pstart, pslot, woff, tile_row, wa, W, T, lookback, sink, spin_limit);
       break;
     case kCSinkKeys:
       k_cextend<kCSinkKeys><<<(unsigned)tiles, block, smem, s>>>(
-          g, d, f, i, pstart, pslot, woff, tile_row, wa, W, T, lookback, sink);
+          g, d, f, i, pstart, pslot, woff, tile_row, wa, W, T, lookback, sink, spin_limit);
       break;
     default:
       k_cextend<kCSinkCount><<<(unsigned)tiles, block, smem, s>>>(
-          g, d, f, i, pstart, pslot, woff, tile_row, wa, W, T, lookback, sink);
+          g, d, f, i, pstart, pslot, woff, tile_row, wa, W, T, lookback, sink, spin_limit);
       break;
   }
 }

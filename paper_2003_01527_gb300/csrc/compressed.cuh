@@ -41,11 +41,13 @@ struct CSink {
 // One single-pass level over candidates [wa, wb) of the width-i rows of f
 // (the same tiles, check, ranking and look-back as launch_extend_fused):
 // lookback needs extend_tiles(wa, wb, block) + kLbExtra zeroed words (word
-// tiles + 1 receives the survivor count, tiles + 2 an error flag; the count
-// mode only uses the ticket word).  The output needs room for wb - wa rows.
+// tiles + 1 receives the survivor count, tiles + 2 an error flag set after a
+// wait of more than spin_limit polls; the count mode only uses the ticket
+// word).  The output needs room for wb - wa rows.
 void launch_cextend(const GraphDev &g, const LevelDesc &d, const CFrontier &f, int32_t i,
                     const int32_t *pstart, const uint8_t *pslot, const int64_t *woff,
                     const int32_t *tile_row, int64_t wa, int64_t wb, int32_t block,
-                    unsigned long long *lookback, const CSink &sink, cudaStream_t s);
+                    unsigned long long *lookback, const CSink &sink, int32_t spin_limit,
+                    cudaStream_t s);
 
 }  // namespace gsm

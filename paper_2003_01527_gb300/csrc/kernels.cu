@@ -11,6 +11,7 @@
 //   k_scan_*            the compaction scan
 //   k_extend_write      Write_to_Partial: survivors to consecutive rows
 #include <algorithm>
+#include <climits>
 #include <cstdio>
 
 #include "filter_body.cuh"
@@ -425,7 +426,9 @@ __global__ void __launch_bounds__(1024) k_extend_count(
         slot = pslot[r];
       }
       const int32_t w = __ldg(g.lcol + pst + (x - rs));
-      if (check_candidate(g, d, ColumnRow{F, ld, r}, w, slot)) bits |= 1u << j;
+      if (check_candidate(g, d, ColumnRow{F, ld, r}, w, slot) &&
+          (!d.la || lookahead_ok(g, d, ColumnRow{F, ld, r}, w)))
+        bits |= 1u << j;
     }
   }
   uint32_t word = bits << (4 * (lane & 7));
@@ -522,111 +525,205 @@ __global__ void __launch_bounds__(1024) k_extend_write(
   }
 }
 
-// Count and write in one pass (single-pass compaction): a tile takes its
-// index from a ticket counter, so every tile it may wait for has started;
-// it verifies its candidates as k_extend_count does, ranks its survivors
-// with a block scan, publishes its survivor count, and finds the number of
-// survivors of all earlier tiles by looking back over their published words
-// (decoupled look-back: a word holds either a tile's own count or its
-// inclusive prefix).  Survivors are then written directly at their final
-// rows, in candidate order, as the two-pass form would write them.
+// Count and write in one pass (single-pass compaction), persistent: every CTA
+// takes tiles (1,024 candidates at 256 threads) from a ticket counter until
+// none is left.  For each tile it verifies the candidates, ranks the
+// survivors with a block scan, keeps them (row, vertex) in one of two
+// shared-memory buffers and publishes its survivor count (decoupled
+// look-back).  The tile's own look-back and writes wait until the CTA has
+// verified its next tile: by then the earlier tiles have published, so the
+// look-back rarely waits and the SM is not idle at the barrier.  Survivors
+// are written directly at their final rows, in candidate order, as the
+// two-pass form would write them.
+//
+// Within a tile a warp takes 128 consecutive candidates, four per lane.
+// When all of them come from one frontier row (the usual case: rows have
+// many candidates), lane 0 finds that row once for the warp, and the
+// candidates -- one contiguous run of the pivot's label segment -- are
+// staged in shared memory with aligned int4 loads; otherwise every lane
+// finds the rows of its own four candidates.  Non-tree edges to hubs are
+// checked on the hubs' adjacency bitmaps (one probe), the others by binary
+// search of the (short) row (row_contains_l).
+//
 // lookback: tiles words, then the ticket, the survivor total and an error
-// word, all zero at launch.  A wait that exceeds kLbSpinLimit polls sets the
-// error word and goes on with the prefix found so far (rows stay in bounds;
-// the host reports the error).
+// word, all zero at launch.  A look-back that polls more than spin_limit
+// times sets the error word and goes on with the prefix found so far (rows
+// stay in bounds; the host reports the error).  stall_tile >= 0 is fault
+// injection for tests: that tile never publishes its word, so the waits of
+// the tiles after it run out.
+constexpr int32_t kStage = 136;  // ints a warp stages its 128 candidates in (+ alignment)
+constexpr size_t kFusedSmemAttr = 200 * 1024;  // dynamic shared memory a CTA may use
+constexpr size_t kFusedStageMax = 96 * 1024;   // ... with the tile's result rows staged
+
 template <int kMode>
-__global__ void __launch_bounds__(1024) k_extend_fused(
+__global__ void __launch_bounds__(1024, 1) k_extend_fused(
     GraphDev g, LevelDesc d, const int32_t *__restrict__ F, int32_t ld,
     const int32_t *__restrict__ pstart, const uint8_t *__restrict__ pslot,
     const int64_t *__restrict__ woff, const int32_t *__restrict__ tile_row, int64_t wa,
     int32_t W, int32_t tiles, unsigned long long *__restrict__ lookback, RowSink sink,
-    bool stage_out) {
+    bool stage_out, int32_t spin_limit, int32_t stall_tile) {
   static_assert(kItemsPerThread == 4, "four candidates per thread");
-  extern __shared__ int32_t s_woff[];
+  constexpr unsigned kAll = 0xffffffffu;
+  extern __shared__ int32_t smem[];
   __shared__ int32_t s_tile;
   __shared__ int32_t s_warp[33];
   __shared__ long long s_prefix;
-  if (threadIdx.x == 0) s_tile = (int32_t)atomicAdd(lookback + tiles, 1ull);
-  __syncthreads();
-  const int32_t tile = s_tile;
   const int32_t B = blockDim.x;
   const int32_t tile_items = B * kItemsPerThread;
-  const int32_t x0 = tile * tile_items;
-  const int32_t x1 = min(x0 + tile_items, W);
-  const TileRows t = stage_rows(woff, tile_row, wa, tile_items, s_woff, tile);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int32_t xb = x0 + warp * 128 + lane * kItemsPerThread;
-  uint32_t bits = 0;
-  int32_t rj[kItemsPerThread], wj[kItemsPerThread];
-  if (xb < x1) {
-    int32_t rs;
-    int32_t r = item_row(t, s_woff, woff, wa, xb, &rs);
-    int32_t rr = r - t.r0;
-    int32_t re = t.staged ? s_woff[rr + 1] : (int32_t)(woff[r + 1] - wa);
-    int32_t pst = pstart[r], slot = pslot[r];
-#pragma unroll
-    for (int j = 0; j < kItemsPerThread; ++j) {
-      rj[j] = r;
-      wj[j] = 0;
-      const int32_t x = xb + j;
-      if (x >= x1) continue;
-      while (x >= re) {  // next row (rows without work are skipped)
-        ++rr;
-        ++r;
-        rs = re;
-        re = t.staged ? s_woff[rr + 1] : (int32_t)(woff[r + 1] - wa);
-        pst = pstart[r];
-        slot = pslot[r];
-      }
-      const int32_t w = __ldg(g.lcol + pst + (x - rs));
-      rj[j] = r;
-      wj[j] = w;
-      if (check_candidate(g, d, ColumnRow{F, ld, r}, w, slot)) bits |= 1u << j;
-    }
-  }
-  // rank of this thread's survivors in the tile (thread order is candidate
-  // order)
-  const int32_t c = __popc(bits);
-  int32_t T;
-  const int32_t rank = block_rank(c, s_warp, &T);
-  // every thread is past the verification: the staged work offsets are no
-  // longer needed, and the survivors (row, vertex) go there in rank order
-  {
-    int32_t *s_pair = s_woff;
-    int32_t q = rank;
-#pragma unroll
-    for (int j = 0; j < kItemsPerThread; ++j)
-      if ((bits >> j) & 1u) {
-        s_pair[2 * q] = rj[j];
-        s_pair[2 * q + 1] = wj[j];
-        ++q;
-      }
-  }
-  if (warp == 0) {
-    const unsigned long long prefix = lookback_prefix(lookback, tile, tiles, T, lane);
-    if (lane == 0) s_prefix = (long long)prefix;
-  }
-  __syncthreads();
-  const int64_t base = sink.row0 + s_prefix;
-  if (kMode == kSinkRows && stage_out) {
-    // the tile's result rows are one contiguous block of T*k ints: assemble
-    // them in shared memory, then store the block with contiguous stores
-    const int32_t k = sink.k;
-    int32_t *s_out = s_woff + 2 * tile_items;
-    for (int32_t q = threadIdx.x; q < T; q += B) {
-      const int32_t r = s_woff[2 * q];
-      for (int cc = 0; cc < d.i; ++cc) s_out[q * k + d.out_col[cc]] = F[cc * ld + r];
-      s_out[q * k + d.out_col[d.i]] = s_woff[2 * q + 1];
+  // shared memory: staged work offsets | survivor pairs x 2 | per-warp
+  // candidate stage | assembled result rows (stage_out only)
+  int32_t *s_woff = smem;
+  int32_t *s_pairs = s_woff + tile_items + 4;
+  int32_t *s_win = s_pairs + 4 * tile_items + warp * kStage;
+  int32_t *s_out = s_pairs + 4 * tile_items + (B >> 5) * kStage;
+  int32_t pend = -1, pend_T = 0, pend_buf = 0, buf = 0;
+
+  // lookback + write of a verified tile whose survivors are in buffer pb
+  auto finish = [&](int32_t tile, int32_t T, int32_t pb) {
+    if (warp == 0) {
+      const unsigned long long prefix =
+          lookback_resolve(lookback, tile, tiles, (unsigned long long)T, lane, spin_limit,
+                           tile != stall_tile);
+      if (lane == 0) s_prefix = (long long)prefix;
     }
     __syncthreads();
-    int32_t *dst = (int32_t *)sink.out + base * k;
-    for (int32_t e = threadIdx.x; e < T * k; e += B) dst[e] = s_out[e];
-    return;
+    const int32_t *pairs = s_pairs + pb * 2 * tile_items;
+    const int64_t base = sink.row0 + s_prefix;
+    if (kMode == kSinkRows && stage_out) {
+      // the tile's result rows are one contiguous block of T*k ints:
+      // assemble them in shared memory, then store them contiguously
+      const int32_t k = sink.k;
+      for (int32_t q = threadIdx.x; q < T; q += B) {
+        const int32_t r = pairs[2 * q];
+        for (int cc = 0; cc < d.i; ++cc) s_out[q * k + d.out_col[cc]] = F[cc * ld + r];
+        s_out[q * k + d.out_col[d.i]] = pairs[2 * q + 1];
+      }
+      __syncthreads();
+      int32_t *dst = (int32_t *)sink.out + base * k;
+      for (int32_t e = threadIdx.x; e < T * k; e += B) dst[e] = s_out[e];
+    } else {
+      // survivor q is written by thread q (q, q + B, ...): each store of a
+      // warp covers 32 consecutive output rows
+      for (int32_t q = threadIdx.x; q < T; q += B)
+        put_row<kMode>(sink, d, ColumnRow{F, ld, pairs[2 * q]}, pairs[2 * q + 1], base + q);
+    }
+  };
+
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = (int32_t)atomicAdd(lookback + tiles, 1ull);
+    __syncthreads();
+    const int32_t tile = s_tile;
+    if (tile >= tiles) break;  // uniform across the block
+    const int32_t x0 = tile * tile_items;
+    const int32_t x1 = min(x0 + tile_items, W);
+    const TileRows t = stage_rows(woff, tile_row, wa, tile_items, s_woff, tile);
+    const int32_t xw = x0 + warp * 128;  // the warp's first candidate
+    const int32_t xb = xw + lane * kItemsPerThread;
+    uint32_t bits = 0;
+    int32_t rj[kItemsPerThread], wj[kItemsPerThread];
+    // one row for the whole warp?  (its first and last candidate share it)
+    int32_t r_lo = -1, r_hi = -2, rs0 = 0;
+    if (lane == 0 && xw < x1) {
+      int32_t rs1;
+      r_lo = item_row(t, s_woff, woff, wa, xw, &rs0);
+      r_hi = item_row(t, s_woff, woff, wa, min(xw + 127, x1 - 1), &rs1);
+    }
+    r_lo = __shfl_sync(kAll, r_lo, 0);
+    r_hi = __shfl_sync(kAll, r_hi, 0);
+    rs0 = __shfl_sync(kAll, rs0, 0);
+    if (r_lo == r_hi) {  // warp-uniform (r_lo = -1 < r_hi = -2 never matches)
+      const int32_t slot = pslot[r_lo];
+      // stage the warp's candidates, lcol[e0, e0 + n), with aligned int4 loads
+      const int32_t n = min(128, x1 - xw);
+      const int32_t e0 = pstart[r_lo] + (xw - rs0);
+      const int32_t a0 = e0 & ~3;
+      const int32_t nv = (e0 + n - a0 + 3) >> 2;
+      for (int32_t v = lane; v < nv; v += 32) {
+        const int32_t e = a0 + 4 * v;
+        if (e + 3 < g.nnz) {
+          const int4 q4 = __ldg(reinterpret_cast<const int4 *>(g.lcol + e));
+          s_win[4 * v] = q4.x;
+          s_win[4 * v + 1] = q4.y;
+          s_win[4 * v + 2] = q4.z;
+          s_win[4 * v + 3] = q4.w;
+        } else {
+          for (int c = 0; c < 4; ++c)
+            if (e + c < g.nnz) s_win[4 * v + c] = __ldg(g.lcol + e + c);
+        }
+      }
+      __syncwarp();
+      const ColumnRow row{F, ld, r_lo};
+#pragma unroll
+      for (int j = 0; j < kItemsPerThread; ++j) {
+        rj[j] = r_lo;
+        wj[j] = 0;
+        const int32_t x = xb + j;
+        if (x >= x1) continue;
+        const int32_t w = s_win[e0 - a0 + lane * kItemsPerThread + j];
+        wj[j] = w;
+        if (check_candidate(g, d, row, w, slot) && (!d.la || lookahead_ok(g, d, row, w)))
+          bits |= 1u << j;
+      }
+      __syncwarp();  // s_win is read before the next tile restages it
+    } else if (xb < x1) {
+      int32_t rs;
+      int32_t r = item_row(t, s_woff, woff, wa, xb, &rs);
+      int32_t rr = r - t.r0;
+      int32_t re = t.staged ? s_woff[rr + 1] : (int32_t)(woff[r + 1] - wa);
+      int32_t pst = pstart[r], slot = pslot[r];
+#pragma unroll
+      for (int j = 0; j < kItemsPerThread; ++j) {
+        rj[j] = r;
+        wj[j] = 0;
+        const int32_t x = xb + j;
+        if (x >= x1) continue;
+        while (x >= re) {  // next row (rows without work are skipped)
+          ++rr;
+          ++r;
+          rs = re;
+          re = t.staged ? s_woff[rr + 1] : (int32_t)(woff[r + 1] - wa);
+          pst = pstart[r];
+          slot = pslot[r];
+        }
+        const int32_t w = __ldg(g.lcol + pst + (x - rs));
+        rj[j] = r;
+        wj[j] = w;
+        if (check_candidate(g, d, ColumnRow{F, ld, r}, w, slot) &&
+            (!d.la || lookahead_ok(g, d, ColumnRow{F, ld, r}, w)))
+          bits |= 1u << j;
+      }
+    }
+    // rank of this thread's survivors in the tile (thread order is
+    // candidate order); the survivors go to the free pair buffer
+    const int32_t c = __popc(bits);
+    int32_t T;
+    const int32_t rank = block_rank(c, s_warp, &T);
+    {
+      int32_t *s_pair = s_pairs + buf * 2 * tile_items;
+      int32_t q = rank;
+#pragma unroll
+      for (int j = 0; j < kItemsPerThread; ++j)
+        if ((bits >> j) & 1u) {
+          s_pair[2 * q] = rj[j];
+          s_pair[2 * q + 1] = wj[j];
+          ++q;
+        }
+    }
+    if (threadIdx.x == 0) {
+      if (tile != stall_tile)
+        lookback_publish(lookback, tile, tiles, (unsigned long long)T);
+      else if (T)
+        atomicAdd(lookback + tiles + 1, (unsigned long long)T);  // the total stays right
+    }
+    __syncthreads();
+    if (pend >= 0) finish(pend, pend_T, pend_buf);
+    pend = tile;
+    pend_T = T;
+    pend_buf = buf;
+    buf ^= 1;
   }
-  // survivor q of the tile is written by thread q (q, q + B, ...): each store
-  // of a warp covers 32 consecutive output rows
-  for (int32_t q = threadIdx.x; q < T; q += B)
-    put_row<kMode>(sink, d, ColumnRow{F, ld, s_woff[2 * q]}, s_woff[2 * q + 1], base + q);
+  if (pend >= 0) finish(pend, pend_T, pend_buf);
 }
 
 __global__ void k_split_points(const int64_t *__restrict__ woff, int64_t R, int64_t step,
@@ -657,6 +754,21 @@ __global__ void k_fetch_level(const unsigned long long *__restrict__ words,
     dst[0] = S;
     dst[1] = (long long)words[1];
     dst[2] = (long long)woff[S];
+  }
+}
+
+// One warp per hub: every neighbour's bit of the hub's bitmap.
+__global__ void k_hub_bits(GraphDev g, const int32_t *__restrict__ hubs, int32_t H,
+                           int32_t words, uint32_t *__restrict__ bits) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t h = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; h < H; h += warps) {
+    const int32_t v = hubs[h];
+    uint32_t *b = bits + h * words;
+    for (int32_t e = g.rp[v] + lane; e < g.rp[v + 1]; e += 32) {
+      const int32_t w = g.col[e];
+      atomicOr(b + (w >> 5), 1u << (w & 31));
+    }
   }
 }
 
@@ -735,6 +847,13 @@ void launch_validate(const GraphDev &g, int32_t *err, cudaStream_t s) {
 
 void launch_validate_rows(const GraphDev &g, int32_t *err, cudaStream_t s) {
   k_validate_rows<<<grid_for((int64_t)g.n * 32, 256, 152 * 8), 256, 0, s>>>(g.n, g.rp, g.col, err);
+}
+
+void launch_hub_bitmaps(const GraphDev &g, const int32_t *hubs, int32_t H, int32_t words,
+                        uint32_t *bits, cudaStream_t s) {
+  if (H <= 0) return;
+  cudaMemsetAsync(bits, 0, sizeof(uint32_t) * (size_t)H * words, s);
+  k_hub_bits<<<grid_for((int64_t)H * 32, 256, 152 * 8), 256, 0, s>>>(g, hubs, H, words, bits);
 }
 
 void launch_filter(const GraphDev &g, const FilterDesc &d, uint32_t *bitmaps,
@@ -855,30 +974,73 @@ void launch_extend_write(const GraphDev &g, const LevelDesc &d, const int32_t *F
         g, d, F, (int32_t)ld, pstart, woff, tile_row, wa, W, masks, tile_off, sink);
 }
 
+namespace {
+// One persistent launch of k_extend_fused<kMode>: as many CTAs as fit on the
+// device at once (at most one per tile).  The dynamic shared-memory limit is
+// raised once per device for this instance.
+template <int kMode>
+void launch_fused_mode(const GraphDev &g, const LevelDesc &d, const int32_t *F, int64_t ld,
+                       const int32_t *pstart, const uint8_t *pslot, const int64_t *woff,
+                       const int32_t *tile_row, int64_t wa, int32_t W, int32_t tiles,
+                       int32_t block, size_t smem, unsigned long long *lookback,
+                       const RowSink &sink, bool stage, int32_t spin_limit, int32_t stall_tile,
+                       cudaStream_t s) {
+  static unsigned long long attr_set = 0;  // bit per device
+  static int per_sm_cache[64][2] = {};     // (block, smem) of the last occupancy query
+  static size_t smem_cache[64] = {};
+  static int blocks_cache[64] = {};
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int di = dev & 63;
+  if (!((attr_set >> di) & 1ull)) {
+    cudaFuncSetAttribute(k_extend_fused<kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kFusedSmemAttr);
+    attr_set |= 1ull << di;
+  }
+  int per_sm = 0;
+  if (blocks_cache[di] == block && smem_cache[di] == smem && per_sm_cache[di][0]) {
+    per_sm = per_sm_cache[di][1];
+  } else {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_extend_fused<kMode>, block, smem);
+    blocks_cache[di] = block;
+    smem_cache[di] = smem;
+    per_sm_cache[di][0] = 1;
+    per_sm_cache[di][1] = per_sm;
+  }
+  const int64_t grid = std::min<int64_t>(tiles, (int64_t)std::max(per_sm, 1) * sms);
+  k_extend_fused<kMode><<<(unsigned)grid, block, smem, s>>>(g, d, F, (int32_t)ld, pstart, pslot,
+                                                            woff, tile_row, wa, W, tiles,
+                                                            lookback, sink, stage, spin_limit,
+                                                            stall_tile);
+}
+}  // namespace
+
 void launch_extend_fused(const GraphDev &g, const LevelDesc &d, const int32_t *F, int64_t ld,
                          const int32_t *pstart, const uint8_t *pslot, const int64_t *woff,
                          const int32_t *tile_row, int64_t wa, int64_t wb, int32_t block,
-                         unsigned long long *lookback, const RowSink &sink, cudaStream_t s) {
+                         unsigned long long *lookback, const RowSink &sink, int32_t spin_limit,
+                         int32_t stall_tile, cudaStream_t s) {
   const int64_t tiles = extend_tiles(wa, wb, block);
   if (tiles <= 0) return;
   const int32_t W = (int32_t)(wb - wa), T = (int32_t)tiles;
-  // the staged work offsets (tile items + 1 ints), later the survivor pairs
-  // (2 ints per item): at most 32 KB for 1,024 threads; result rows are
-  // assembled after them when k ints per item also fit in 48 KB
+  // staged work offsets, two survivor-pair buffers, the warps' windows, and
+  // (kSinkRows) the assembled result rows of one tile when they fit
   const int64_t items = (int64_t)block * kItemsPerThread;
-  size_t smem = (size_t)(items * 2 + 1) * sizeof(int32_t);
-  const size_t smem_rows = (size_t)(items * (2 + sink.k) + 1) * sizeof(int32_t);
-  const bool stage = sink.mode == kSinkRows && smem_rows <= 48 * 1024;
+  const size_t base_ints = (size_t)(items + 4 + 4 * items + (block / 32) * kStage);
+  size_t smem = base_ints * sizeof(int32_t);
+  const size_t smem_rows = (base_ints + (size_t)items * sink.k) * sizeof(int32_t);
+  const bool stage = sink.mode == kSinkRows && smem_rows <= kFusedStageMax;
   if (stage) smem = smem_rows;
   if (sink.mode == kSinkRows)
-    k_extend_fused<kSinkRows><<<(unsigned)tiles, block, smem, s>>>(
-        g, d, F, (int32_t)ld, pstart, pslot, woff, tile_row, wa, W, T, lookback, sink, stage);
+    launch_fused_mode<kSinkRows>(g, d, F, ld, pstart, pslot, woff, tile_row, wa, W, T, block,
+                                 smem, lookback, sink, stage, spin_limit, stall_tile, s);
   else if (sink.mode == kSinkKeys)
-    k_extend_fused<kSinkKeys><<<(unsigned)tiles, block, smem, s>>>(
-        g, d, F, (int32_t)ld, pstart, pslot, woff, tile_row, wa, W, T, lookback, sink, false);
+    launch_fused_mode<kSinkKeys>(g, d, F, ld, pstart, pslot, woff, tile_row, wa, W, T, block,
+                                 smem, lookback, sink, false, spin_limit, stall_tile, s);
   else
-    k_extend_fused<kSinkColumns><<<(unsigned)tiles, block, smem, s>>>(
-        g, d, F, (int32_t)ld, pstart, pslot, woff, tile_row, wa, W, T, lookback, sink, false);
+    launch_fused_mode<kSinkColumns>(g, d, F, ld, pstart, pslot, woff, tile_row, wa, W, T, block,
+                                    smem, lookback, sink, false, spin_limit, stall_tile, s);
 }
 
 void launch_split_points(const int64_t *woff, int64_t R, int64_t step, int64_t J,

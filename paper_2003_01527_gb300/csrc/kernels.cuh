@@ -42,6 +42,18 @@ struct LevelDesc {
   int32_t nlt, lt[kMaxK];     // symmetry breaking: the new vertex must be < row[lt[t]]
   int32_t ngt, gt[kMaxK];     //                     and > row[gt[t]]
   int32_t lab;                // dense label of pi_i: only that segment of a row is traversed
+  // k-look-ahead (Sec. 3.2; la = 0 off, 1 or 2): the query neighbours of
+  // pi_i placed after it, grouped by label.  Group t: label la_lab[t],
+  // la_need[t] such neighbours, la_known[t] mapped neighbours of pi_i with
+  // that label (adjacent to a candidate by the level's own checks), la_pos[t]
+  // = positions of the other placed vertices with that label (bit j), la_uq[t]
+  // = the group's query vertices (bit u; their candidate bitmaps are
+  // cand + u * n_words).
+  int32_t la, nla;
+  int32_t la_lab[kMaxK], la_need[kMaxK], la_known[kMaxK];
+  uint32_t la_pos[kMaxK], la_uq[kMaxK];
+  const uint32_t *cand;
+  int32_t n_words;
 };
 
 struct GraphDev {
@@ -53,6 +65,12 @@ struct GraphDev {
   const int32_t *lcol;  // the same rows ordered by (label, id): label segments
   const int32_t *llab;  // dense label of lcol[e]
   int32_t num_labels;   // 1: every row is one segment and lcol equals col
+  // adjacency bitmaps of the high-degree vertices ("hubs"): hub[v] = index h
+  // of v's bitmap or -1, bit w of hub_bits[h * hub_words ..] set iff w is a
+  // neighbour of v.  hub = null: no bitmaps, every test searches the row.
+  const int32_t *hub;
+  const uint32_t *hub_bits;
+  int32_t hub_words;
 };
 
 // ---- launchers (all asynchronous on `s`) ----
@@ -71,6 +89,11 @@ int launch_label_segments(const GraphDev &g, int32_t num_labels, int32_t *edge_c
                           uint64_t *keys, int32_t *rows_out, int32_t *hist, int64_t *hist_off,
                           int64_t *tmp, int32_t *out_col, int32_t *out_lab, cudaStream_t s);
 int32_t label_segment_bits(int32_t n, int32_t num_labels);
+
+// Adjacency bitmaps of the H hubs (vertex ids hubs[0..H)): bitmap h (words
+// bits[h * words ..], zeroed here) gets bit w for every neighbour w.
+void launch_hub_bitmaps(const GraphDev &g, const int32_t *hubs, int32_t H, int32_t words,
+                        uint32_t *bits, cudaStream_t s);
 
 // Writes k bitmaps of n_words words and adds |C(u)| into sizes[u].
 void launch_filter(const GraphDev &g, const FilterDesc &d, uint32_t *bitmaps,
@@ -168,16 +191,20 @@ void launch_extend_write(const GraphDev &g, const LevelDesc &d, const int32_t *F
 // ... in candidate order, exactly where the two passes put them.  lookback
 // needs extend_tiles(wa, wb, block) + kLbExtra words, zeroed (launch_tile_rows
 // does it); afterwards word tiles + 1 holds the survivor count and word
-// tiles + 2 is non-zero if a tile gave up waiting for its predecessors.  The
-// sink needs room for wb - wa rows.
+// tiles + 2 is non-zero if a tile gave up waiting for its predecessors (after
+// spin_limit polls).  The sink needs room for wb - wa rows.  The grid is
+// persistent (at most the CTAs that fit on the device at once).  stall_tile
+// (-1 = none) is fault injection for tests: that tile never publishes its
+// look-back word, so later tiles' waits run out.
 constexpr int kLbExtra = 3;
 constexpr unsigned long long kLbAggregate = 1ull << 62, kLbInclusive = 2ull << 62;
 constexpr unsigned long long kLbValue = (1ull << 62) - 1;
-constexpr int32_t kLbSpinLimit = 1 << 20;
+constexpr int32_t kLbSpinLimit = 1 << 20;  // default bound of a look-back wait (polls)
 void launch_extend_fused(const GraphDev &g, const LevelDesc &d, const int32_t *F, int64_t ld,
                          const int32_t *pstart, const uint8_t *pslot, const int64_t *woff,
                          const int32_t *tile_row, int64_t wa, int64_t wb, int32_t block,
-                         unsigned long long *lookback, const RowSink &sink, cudaStream_t s);
+                         unsigned long long *lookback, const RowSink &sink, int32_t spin_limit,
+                         int32_t stall_tile, cudaStream_t s);
 
 // Row boundaries for work-bounded sub-chunks: bounds[j] = the row r with
 // woff[r] <= j*step < woff[r+1] (clamped to [0, R]); bounds[J] = R.
@@ -212,6 +239,10 @@ int64_t sort_hist_elems(int64_t N);
 // scan_tmp_elems(sort_hist_elems(N)) int64.  Returns the number of kernels
 // launched.
 int32_t packed_words(int32_t k, int32_t bits);
+// Packed sort keys (word w of row r at keys[w*ld + r]) of N row-major rows of
+// k int32 (values < 2^bits), ready for launch_sort_rows_packed with a = null.
+void launch_pack_rows(const int32_t *rows, int64_t N, int32_t k, int32_t bits, uint64_t *keys,
+                      int64_t ld, cudaStream_t s);
 int launch_sort_rows_packed(const int32_t *a, int64_t lda, int64_t N, int32_t k, int32_t bits,
                             int32_t sort_cols, uint64_t *keys_a, uint64_t *keys_b, int64_t ld,
                             int32_t *out, int32_t *hist, int64_t *hist_off, int64_t *tmp,

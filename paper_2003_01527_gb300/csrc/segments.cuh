@@ -36,10 +36,15 @@ __device__ __forceinline__ int2 label_segment(const GraphDev &g, int32_t x, int3
   return make_int2(lo, hi);
 }
 
-// Is w (label l) a neighbour of x?  One binary search on the (label, id)
-// order of x's row.
+// Is w (label l) a neighbour of x?  One bit of x's adjacency bitmap when x
+// is a hub, else one binary search on the (label, id) order of x's row.
 __device__ __forceinline__ bool row_contains_l(const GraphDev &g, int32_t x, int32_t l,
                                                int32_t w) {
+  if (g.hub) {
+    const int32_t h = __ldg(g.hub + x);
+    if (h >= 0)
+      return (__ldg(g.hub_bits + (size_t)h * g.hub_words + (w >> 5)) >> (w & 31)) & 1u;
+  }
   const int32_t e = __ldg(g.rp + x + 1);
   int32_t lo = __ldg(g.rp + x), len = e - lo;
   if (g.num_labels == 1) {  // one label: a plain search of the id-sorted row

@@ -25,16 +25,19 @@ constexpr int kBins = 256;
 
 constexpr int kMaxWords = kMaxKeyWords;
 
-__global__ void __launch_bounds__(256) k_pack_keys(const int32_t *__restrict__ in, int64_t ld,
-                                                   int64_t N, int32_t k, int32_t b, int32_t nw,
-                                                   uint64_t *__restrict__ keys, int64_t kld) {
+// Column j of row r is in[j * cs + r * rs] (column-major: cs = ld, rs = 1;
+// row-major: cs = 1, rs = k).
+__global__ void __launch_bounds__(256) k_pack_keys(const int32_t *__restrict__ in, int64_t cs,
+                                                   int64_t rs, int64_t N, int32_t k, int32_t b,
+                                                   int32_t nw, uint64_t *__restrict__ keys,
+                                                   int64_t kld) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= N) return;
   // word t collects the columns that overlap bits [64t, 64t+64)
   for (int32_t t = 0; t < nw; ++t) {
     uint64_t w = 0;
     for (int32_t j = 0; j < k; ++j) {
-      const uint64_t v = (uint32_t)in[(int64_t)j * ld + r];
+      const uint64_t v = (uint32_t)in[(int64_t)j * cs + r * rs];
       const int32_t lo = (k - 1 - j) * b - 64 * t;
       if (lo >= 0 && lo < 64)
         w |= v << lo;
@@ -231,6 +234,13 @@ namespace gsm {
 
 int32_t packed_words(int32_t k, int32_t bits) { return (k * bits + 63) / 64; }
 
+void launch_pack_rows(const int32_t *rows, int64_t N, int32_t k, int32_t bits, uint64_t *keys,
+                      int64_t ld, cudaStream_t s) {
+  if (N <= 0) return;
+  k_pack_keys<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(rows, 1, k, N, k, bits,
+                                                          packed_words(k, bits), keys, ld);
+}
+
 int launch_sort_rows_packed(const int32_t *a, int64_t lda, int64_t N, int32_t k, int32_t bits,
                             int32_t sort_cols, uint64_t *keys_a, uint64_t *keys_b, int64_t ld,
                             int32_t *out, int32_t *hist, int64_t *hist_off, int64_t *tmp,
@@ -239,7 +249,8 @@ int launch_sort_rows_packed(const int32_t *a, int64_t lda, int64_t N, int32_t k,
   int launches = 0;
   const int32_t nw = packed_words(k, bits);
   if (a) {
-    k_pack_keys<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(a, lda, N, k, bits, nw, keys_a, ld);
+    k_pack_keys<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(a, lda, 1, N, k, bits, nw, keys_a,
+                                                            ld);
     ++launches;
   }
   const int64_t nb = (N + kSortTile - 1) / kSortTile;

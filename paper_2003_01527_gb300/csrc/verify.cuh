@@ -69,15 +69,14 @@ struct ColumnRow {
   __device__ __forceinline__ int32_t operator()(int c) const { return F[c * ld + r]; }
 };
 
-// The one-step check of Sec. 3.2 verification for candidate w of a partial
-// embedding (row(c) = the image of pi_c): label + signature (bitmap of
-// C(pi_i)), injectivity against same-label, non-adjacent positions, the
-// ordering constraints, and presence of every query edge to a mapped
-// neighbour other than the pivot (binary search in that neighbour's label
-// segment).
-template <typename Row>
-__device__ __forceinline__ bool check_candidate(const GraphDev &g, const LevelDesc &d,
-                                                const Row &row, int32_t w, int slot) {
+// The checks of Sec. 3.2 verification that need no adjacency search, for
+// candidate w of a partial embedding (row(c) = the image of pi_c): label +
+// signature (bitmap of C(pi_i)), injectivity against same-label, non-adjacent
+// positions, and the ordering constraints of distinct counting.  Desc is a
+// level description with the fields of LevelDesc used here (the single-query
+// LevelDesc or the batched form's BatchLevel).
+template <typename Desc, typename Row>
+__device__ __forceinline__ bool check_local(const Desc &d, const Row &row, int32_t w) {
   if (!bitmap_has(d.bitmap, w)) return false;
   for (int t = 0; t < d.ninj; ++t)
     if (row(d.inj[t]) == w) return false;
@@ -85,9 +84,78 @@ __device__ __forceinline__ bool check_candidate(const GraphDev &g, const LevelDe
     if (!(w < row(d.lt[t]))) return false;
   for (int t = 0; t < d.ngt; ++t)
     if (!(w > row(d.gt[t]))) return false;
+  return true;
+}
+
+// The whole one-step check: check_local plus the presence of every query
+// edge to a mapped neighbour other than the pivot (binary search in that
+// neighbour's label segment).
+template <typename Desc, typename Row>
+__device__ __forceinline__ bool check_candidate(const GraphDev &g, const Desc &d,
+                                                const Row &row, int32_t w, int slot) {
+  if (!check_local(d, row, w)) return false;
   for (int b = 0; b < d.nb; ++b) {
     if (b == slot) continue;
     if (!row_contains_l(g, row(d.bpos[b]), d.lab, w)) return false;
+  }
+  return true;
+}
+
+// Entries of w's (label, id)-ordered row scanned at most per group by the
+// 2-look-ahead before it gives up (and keeps the candidate).
+constexpr int32_t kLaScan = 64;
+
+// The k-look-ahead of Sec. 3.2 for a candidate w of pi_i that passed the
+// level's checks: does the partial embedding extended by w still leave room
+// for the query neighbours of pi_i placed later?  For every label group t of
+// those neighbours:
+//   1-look-ahead: w keeps at least la_need[t] neighbours with the label that
+//   are not in the row (its label segment, minus the mapped neighbours of
+//   pi_i, which are adjacent to w, minus the other same-label row vertices
+//   adjacent to w), since an embedding maps the group to distinct unused
+//   neighbours of w;
+//   2-look-ahead: at least la_need[t] of those unused neighbours are
+//   candidates of some query vertex of the group (checked over the first
+//   kLaScan entries of the segment; a longer segment is not pruned).
+// Both conditions hold for every embedding that extends the row, so pruning
+// on them never changes the result.
+template <typename Row>
+__device__ __forceinline__ bool lookahead_ok(const GraphDev &g, const LevelDesc &d,
+                                             const Row &row, int32_t w) {
+  for (int t = 0; t < d.nla; ++t) {
+    const int2 seg = label_segment(g, w, d.la_lab[t]);
+    int32_t avail = seg.y - seg.x - d.la_known[t];
+    for (uint32_t m = d.la_pos[t]; m; m &= m - 1) {
+      const int32_t x = row(__ffs(m) - 1);
+      // x carries the label, so it is in w's row iff it is in the segment
+      int32_t lo = seg.x, len = seg.y - seg.x;
+      while (len > 0) {
+        const int32_t half = len >> 1;
+        if (__ldg(g.lcol + lo + half) < x) {
+          lo += half + 1;
+          len -= half + 1;
+        } else {
+          len = half;
+        }
+      }
+      if (lo < seg.y && __ldg(g.lcol + lo) == x) --avail;
+    }
+    if (avail < d.la_need[t]) return false;
+    if (d.la >= 2) {
+      const int32_t end = min(seg.y, seg.x + kLaScan);
+      int32_t found = 0;
+      for (int32_t e = seg.x; e < end && found < d.la_need[t]; ++e) {
+        const int32_t x = __ldg(g.lcol + e);
+        bool cand = false;
+        for (uint32_t u = d.la_uq[t]; u && !cand; u &= u - 1)
+          cand = bitmap_has(d.cand + (size_t)(__ffs(u) - 1) * d.n_words, x);
+        if (!cand) continue;
+        bool used = false;  // a row vertex (only same-label positions can be)
+        for (int c = 0; c < d.i && !used; ++c) used = row(c) == x;
+        if (!used) ++found;
+      }
+      if (found < d.la_need[t] && end == seg.y) return false;
+    }
   }
   return true;
 }
@@ -163,60 +231,77 @@ __device__ __forceinline__ int32_t block_rank(int32_t c, int32_t *s_warp, int32_
   return incl - c + s_warp[warp];
 }
 
-// Decoupled look-back for tile `tile` of a level with T survivors, run by
-// one whole warp: publishes the tile's count, reads the published words of
-// the 32 preceding tiles at a time (lane l: tile window_end - l) until one
-// holds an inclusive prefix, publishes the tile's own inclusive prefix and
-// adds T to the level total (word tiles + 1).  Returns the number of
-// survivors of all earlier tiles in every lane.  A wait longer than
-// kLbSpinLimit polls sets word tiles + 2 and returns the (smaller) sum found
-// so far.
+// Decoupled look-back, in two halves so that a CTA can verify its next tile
+// between them.  lookback_publish: tile `tile` has T survivors; tile 0
+// publishes its inclusive prefix, every other tile its own count, and the
+// level total (word tiles + 1) gains T.  Any thread may call it.
+__device__ __forceinline__ void lookback_publish(unsigned long long *lookback, int32_t tile,
+                                                 int32_t tiles, unsigned long long T) {
+  atomicExch(lookback + tile, (tile == 0 ? kLbInclusive : kLbAggregate) | T);
+  if (T) atomicAdd(lookback + tiles + 1, T);
+}
+
+// lookback_resolve, run by one whole warp after lookback_publish: reads the
+// published words of the 32 preceding tiles at a time (lane l: tile
+// window_end - l) until one holds an inclusive prefix, publishes the tile's
+// own inclusive prefix, and returns the number of survivors of all earlier
+// tiles in every lane.  A wait longer than spin_limit polls sets word
+// tiles + 2 and returns the (smaller) sum found so far, so every row the
+// caller writes stays inside the level's reserved output.  publish = false
+// keeps the tile's word unwritten (fault injection: later tiles wait on it).
+__device__ __forceinline__ unsigned long long lookback_resolve(unsigned long long *lookback,
+                                                               int32_t tile, int32_t tiles,
+                                                               unsigned long long T, int lane,
+                                                               int32_t spin_limit,
+                                                               bool publish = true) {
+  constexpr unsigned kAll = 0xffffffffu;
+  if (tile == 0) return 0;
+  unsigned long long prefix = 0;
+  int32_t window_end = tile - 1;
+  int32_t polls = 0;
+  bool gave_up = false;
+  while (true) {
+    const int32_t j = window_end - lane;
+    unsigned long long st = j >= 0 ? load_relaxed(lookback + j) : kLbInclusive;
+    unsigned long long flag = st & ~kLbValue;
+    // wait until every tile of the window has published
+    while (__any_sync(kAll, flag == 0)) {
+      if (++polls > spin_limit) {
+        gave_up = true;
+        break;
+      }
+      __nanosleep(32);
+      if (flag == 0) {
+        st = load_relaxed(lookback + j);
+        flag = st & ~kLbValue;
+      }
+    }
+    if (gave_up) break;
+    const uint32_t has_prefix = __ballot_sync(kAll, flag == kLbInclusive);
+    // tiles up to the nearest inclusive prefix (the lowest such lane)
+    const int32_t stop = has_prefix ? __ffs(has_prefix) - 1 : 31;
+    unsigned long long v = lane <= stop ? (st & kLbValue) : 0;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kAll, v, o);
+    prefix += v;
+    if (has_prefix) break;
+    window_end -= 32;
+  }
+  if (lane == 0) {
+    if (gave_up) atomicExch(lookback + tiles + 2, 1ull);
+    if (publish) atomicExch(lookback + tile, kLbInclusive | (prefix + T));
+  }
+  return prefix;
+}
+
+// Both halves at once (the tile waits for its prefix right after counting).
 __device__ __forceinline__ unsigned long long lookback_prefix(unsigned long long *lookback,
                                                               int32_t tile, int32_t tiles,
-                                                              unsigned long long T, int lane) {
-  constexpr unsigned kAll = 0xffffffffu;
-  unsigned long long prefix = 0;
-  if (tile == 0) {
-    if (lane == 0) atomicExch(lookback, kLbInclusive | T);
-  } else {
-    if (lane == 0) atomicExch(lookback + tile, kLbAggregate | T);
-    int32_t window_end = tile - 1;
-    int32_t polls = 0;
-    bool gave_up = false;
-    while (true) {
-      const int32_t j = window_end - lane;
-      unsigned long long st = j >= 0 ? load_relaxed(lookback + j) : kLbInclusive;
-      unsigned long long flag = st & ~kLbValue;
-      // wait until every tile of the window has published
-      while (__any_sync(kAll, flag == 0)) {
-        if (++polls > kLbSpinLimit) {
-          gave_up = true;
-          break;
-        }
-        __nanosleep(32);
-        if (flag == 0) {
-          st = load_relaxed(lookback + j);
-          flag = st & ~kLbValue;
-        }
-      }
-      if (gave_up) break;
-      const uint32_t has_prefix = __ballot_sync(kAll, flag == kLbInclusive);
-      // tiles up to the nearest inclusive prefix (the lowest such lane)
-      const int32_t stop = has_prefix ? __ffs(has_prefix) - 1 : 31;
-      unsigned long long v = lane <= stop ? (st & kLbValue) : 0;
-#pragma unroll
-      for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kAll, v, o);
-      prefix += v;
-      if (has_prefix) break;
-      window_end -= 32;
-    }
-    if (lane == 0) {
-      if (gave_up) atomicExch(lookback + tiles + 2, 1ull);
-      atomicExch(lookback + tile, kLbInclusive | (prefix + T));
-    }
-  }
-  if (lane == 0 && T) atomicAdd(lookback + tiles + 1, T);
-  return prefix;
+                                                              unsigned long long T, int lane,
+                                                              int32_t spin_limit) {
+  if (lane == 0) lookback_publish(lookback, tile, tiles, T);
+  __syncwarp();
+  return lookback_resolve(lookback, tile, tiles, T, lane, spin_limit);
 }
 
 }  // namespace gsm

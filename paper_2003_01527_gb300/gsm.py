@@ -39,6 +39,7 @@ GSM_OUT_DEVICE = 1
 GSM_OPT_TIME_KERNELS = 1
 GSM_OPT_TWO_PASS = 2
 GSM_OPT_COMPRESSED_FRONTIERS = 4
+GSM_OPT_INJECT_LOOKBACK_STALL = 8
 
 MAX_K = 16
 
@@ -51,8 +52,11 @@ EXPORTED = [
     "gsm_plan_order", "gsm_query_symmetry", "gsm_kernel_stats", "gsm_last_run_stats",
     "gsm_candidates_static", "gsm_run_batch", "gsm_batch_get_stats", "gsm_batch_configure",
     "gsm_count_distinct", "gsm_server_start", "gsm_submit", "gsm_poll", "gsm_server_stop",
+    "gsm_result_free",
 ]
 GSM_BATCH_AUTOTUNE = 1
+GSM_MODE_COUNT = 0
+GSM_MODE_ENUMERATE = 1
 GSM_STATIC_SCRATCH_BITMAP_BYTES = 8 << 20
 
 _alloc_fn = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -65,7 +69,8 @@ class gsm_options(ctypes.Structure):
                 ("alloc", _alloc_fn), ("free", _free_fn), ("alloc_ctx", ctypes.c_void_p),
                 ("block_size", ctypes.c_int32), ("chunk_rows", ctypes.c_int64),
                 ("filter_rounds", ctypes.c_int32), ("flags", ctypes.c_int32),
-                ("copy_slots", ctypes.c_int32)]
+                ("copy_slots", ctypes.c_int32), ("lookback_spin_limit", ctypes.c_int32),
+                ("lookahead", ctypes.c_int32), ("hub_bitmap_bytes", ctypes.c_int64)]
 
 
 class gsm_kernel_stat(ctypes.Structure):
@@ -85,7 +90,8 @@ class gsm_batch_stats(ctypes.Structure):
 class gsm_result(ctypes.Structure):
     _fields_ = [("count", ctypes.c_uint64), ("status", ctypes.c_int32),
                 ("t_submit_ns", ctypes.c_int64), ("t_admit_ns", ctypes.c_int64),
-                ("t_done_ns", ctypes.c_int64)]
+                ("t_done_ns", ctypes.c_int64), ("k", ctypes.c_int32),
+                ("on_device", ctypes.c_int32), ("rows", ctypes.POINTER(ctypes.c_int32))]
 
 
 class gsm_run_stats(ctypes.Structure):
@@ -120,11 +126,12 @@ def _load():
         "gsm_plan_order": (i32, [i32, i32, vp, vp, vp, vp]),
         "gsm_query_symmetry": (i32, [i32, i32, vp, vp, vp, vp, i32, vp]),
         "gsm_candidates_static": (i32, [i32, i64, vp, vp, vp, vp, vp, vp, i32, vp]),
-        "gsm_run_batch": (i32, [vp, vp, i32, vp, i32]),
+        "gsm_run_batch": (i32, [vp, vp, i32, vp, vp, i32]),
+        "gsm_result_free": (None, [vp, ctypes.POINTER(gsm_result)]),
         "gsm_batch_get_stats": (i32, [vp, ctypes.POINTER(gsm_batch_stats)]),
-        "gsm_batch_configure": (i32, [vp, u64, u64, u64]),
+        "gsm_batch_configure": (i32, [vp, u64, u64, u64, u64]),
         "gsm_server_start": (i32, [vp, i32, i32]),
-        "gsm_submit": (i32, [vp, vp, ctypes.POINTER(u64)]),
+        "gsm_submit": (i32, [vp, vp, i32, ctypes.POINTER(u64)]),
         "gsm_poll": (i32, [vp, u64, ctypes.POINTER(gsm_result)]),
         "gsm_server_stop": (i32, [vp]),
         "gsm_kernel_stats": (i32, [vp, ctypes.POINTER(gsm_kernel_stat), i32,
@@ -270,13 +277,53 @@ def gsm_candidates_static(n: int, nnz: int, row_ptr, col, labels, q: int, bitmap
         raise GsmError(st, "gsm_candidates_static")
 
 
-def gsm_run_batch(ctx: int, queries, flags: int = 0) -> np.ndarray:
-    """queries: sequence of gsm_query handles; returns uint64 counts."""
+def _take_rows(ctx: int, r: gsm_result):
+    """Copies the rows of a result into a numpy array (host rows) or a CUDA
+    tensor (device rows), then releases the library's buffer."""
+    k, c = int(r.k), int(r.count)
+    if not r.rows or c == 0:
+        on_device = bool(r.on_device)
+        _lib.gsm_result_free(ctx, ctypes.byref(r))
+        if on_device:
+            import torch
+            return torch.zeros((0, max(k, 1)), dtype=torch.int32, device="cuda")
+        return np.zeros((0, max(k, 1)), dtype=np.int32)
+    if r.on_device:
+        import torch
+        ptr = ctypes.cast(r.rows, ctypes.c_void_p).value
+        out = torch.as_tensor(_DevicePtr(ptr, c * k), device="cuda").clone().view(c, k)
+        torch.cuda.synchronize()  # the copy is done before the buffer is released
+    else:
+        out = np.ctypeslib.as_array(r.rows, shape=(c * k,)).reshape(c, k).copy()
+    _lib.gsm_result_free(ctx, ctypes.byref(r))
+    return out
+
+
+class _DevicePtr:
+    """A CUDA array interface over a raw device pointer (int32 elements)."""
+
+    def __init__(self, ptr: int, n: int):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<i4",
+                                         "data": (ptr, False), "version": 2}
+
+
+def gsm_run_batch(ctx: int, queries, flags: int = 0, enumerate: bool = False):
+    """queries: sequence of gsm_query handles.  Returns uint64 counts, or with
+    enumerate=True (counts, rows): rows[j] = the sorted rows of query j, a
+    numpy array (host) or, with flags & GSM_OUT_DEVICE, a CUDA tensor."""
     nq = len(queries)
     arr = (ctypes.c_void_p * max(nq, 1))(*queries)
     counts = np.zeros(max(nq, 1), dtype=np.uint64)
-    _check(ctx, _lib.gsm_run_batch(ctx, arr, nq, _ptr(counts), flags))
-    return counts[:nq]
+    res = (gsm_result * max(nq, 1))() if enumerate else None
+    _check(ctx, _lib.gsm_run_batch(ctx, arr, nq, _ptr(counts), res, flags))
+    if not enumerate:
+        return counts[:nq]
+    rows = [_take_rows(ctx, res[j]) for j in range(nq)]
+    return counts[:nq], rows
+
+
+def gsm_result_free(ctx: int, r: gsm_result) -> None:
+    _lib.gsm_result_free(ctx, ctypes.byref(r))
 
 
 def gsm_batch_get_stats(ctx: int) -> dict:
@@ -285,29 +332,35 @@ def gsm_batch_get_stats(ctx: int) -> dict:
     return {name: getattr(s, name) for name, _ in gsm_batch_stats._fields_}
 
 
-def gsm_batch_configure(ctx: int, cap_rows: int = 0, cap_elems: int = 0, cap_items: int = 0):
-    _check(ctx, _lib.gsm_batch_configure(ctx, cap_rows, cap_elems, cap_items))
+def gsm_batch_configure(ctx: int, cap_rows: int = 0, cap_elems: int = 0, cap_items: int = 0,
+                        cap_result_elems: int = 0):
+    _check(ctx, _lib.gsm_batch_configure(ctx, cap_rows, cap_elems, cap_items, cap_result_elems))
 
 
 def gsm_server_start(ctx: int, lanes: int = 2, max_batch: int = 256) -> None:
     _check(ctx, _lib.gsm_server_start(ctx, lanes, max_batch))
 
 
-def gsm_submit(ctx: int, q: int) -> int:
+def gsm_submit(ctx: int, q: int, mode: int = GSM_MODE_COUNT) -> int:
     t = ctypes.c_uint64()
-    _check(ctx, _lib.gsm_submit(ctx, q, ctypes.byref(t)))
+    _check(ctx, _lib.gsm_submit(ctx, q, mode, ctypes.byref(t)))
     return t.value
 
 
 def gsm_poll(ctx: int, ticket: int):
-    """None while pending, else a dict with count, status and timestamps (ns)."""
+    """None while pending, else a dict with count, status and timestamps (ns),
+    and in enumerate mode "rows" (numpy int32 [count, k], sorted; the
+    library's buffer is released)."""
     r = gsm_result()
     st = _lib.gsm_poll(ctx, ticket, ctypes.byref(r))
     if st == GSM_PENDING:
         return None
     _check(ctx, st)
-    return {"count": r.count, "status": r.status, "t_submit_ns": r.t_submit_ns,
-            "t_admit_ns": r.t_admit_ns, "t_done_ns": r.t_done_ns}
+    out = {"count": r.count, "status": r.status, "t_submit_ns": r.t_submit_ns,
+           "t_admit_ns": r.t_admit_ns, "t_done_ns": r.t_done_ns}
+    if r.rows:
+        out["rows"] = _take_rows(ctx, r)
+    return out
 
 
 def gsm_server_stop(ctx: int) -> None:
@@ -398,7 +451,9 @@ class Matcher:
     def __init__(self, device: int = 0, mem_budget_bytes: int = 0, stream=None,
                  block_size: int = 0, chunk_rows: int = 0, time_kernels: bool = False,
                  torch_allocator: bool = True, filter_rounds: int = 0, copy_slots: int = 0,
-                 two_pass: bool = False, compressed: bool = False):
+                 two_pass: bool = False, compressed: bool = False, lookback_spin_limit: int = 0,
+                 inject_lookback_stall: bool = False, alloc_hook=None, lookahead: int = 0,
+                 hub_bitmap_bytes: int = 0):
         import torch
         self.device = device
         opt = gsm_default_options()
@@ -414,13 +469,20 @@ class Matcher:
         opt.chunk_rows = chunk_rows
         opt.filter_rounds = filter_rounds
         opt.copy_slots = copy_slots
+        opt.lookback_spin_limit = lookback_spin_limit
+        opt.lookahead = lookahead
+        opt.hub_bitmap_bytes = hub_bitmap_bytes
         opt.flags = (GSM_OPT_TIME_KERNELS if time_kernels else 0) | \
             (GSM_OPT_TWO_PASS if two_pass else 0) | \
-            (GSM_OPT_COMPRESSED_FRONTIERS if compressed else 0)
+            (GSM_OPT_COMPRESSED_FRONTIERS if compressed else 0) | \
+            (GSM_OPT_INJECT_LOOKBACK_STALL if inject_lookback_stall else 0)
         if torch_allocator:
             dev = device
 
             def _alloc(_ctx, nbytes, stream_ptr):
+                # alloc_hook(nbytes) -> False makes this allocation fail (tests)
+                if alloc_hook is not None and not alloc_hook(int(nbytes)):
+                    return None
                 try:
                     return torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream_ptr)
                 except Exception:
@@ -505,10 +567,16 @@ class Matcher:
         gsm_candidates(self.ctx, q.handle, bm, sizes)
         return bm[:, :nw], sizes
 
-    def run_batch(self, queries, autotune: bool = False) -> list[int]:
-        """Counts of every Query in `queries`, computed as one batch."""
-        flags = GSM_BATCH_AUTOTUNE if autotune else 0
-        return [int(c) for c in gsm_run_batch(self.ctx, [q.handle for q in queries], flags)]
+    def run_batch(self, queries, autotune: bool = False, enumerate: bool = False,
+                  device: bool = False):
+        """Counts of every Query in `queries`, computed as one batch; with
+        enumerate=True, (counts, rows) with each query's sorted rows (numpy,
+        or CUDA tensors with device=True)."""
+        flags = (GSM_BATCH_AUTOTUNE if autotune else 0) | (GSM_OUT_DEVICE if device else 0)
+        r = gsm_run_batch(self.ctx, [q.handle for q in queries], flags, enumerate)
+        if not enumerate:
+            return [int(c) for c in r]
+        return [int(c) for c in r[0]], r[1]
 
     def batch_stats(self) -> dict:
         return gsm_batch_get_stats(self.ctx)

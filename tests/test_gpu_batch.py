@@ -66,6 +66,60 @@ def test_batch_counts_match_oracle_and_single_query(gsm_lib, cuda, rmat12b):
     m.close()
 
 
+def test_batch_enumerate_rows_match_oracle(gsm_lib, cuda, rmat12b):
+    """The batched form in enumerate mode: every query's rows equal the
+    oracle's sorted rows and gsm_enumerate's, in host and in device memory,
+    for uneven query sizes (including one-vertex queries, an absent label
+    and an empty restriction)."""
+    g = rmat12b
+    m = gsm_lib.Matcher(device=0)
+    m.load_graph(g.row_ptr, g.col, g.labels)
+    items = mixed_queries(g, 30, seed=57)
+    extra = [(I.query_from_edges(1, [], [2]), g.n),
+             (I.query_from_edges(2, [(0, 1)], [0, 1]), g.n),
+             (I.query_from_edges(3, [(0, 1), (1, 2)], [0, 99, 0]), g.n),
+             (I.query_from_edges(3, [(0, 1), (1, 2)], [0, 0, 0]), 0)]
+    for q, hi in extra:
+        c, _, _ = oracle.match(g, q, enumerate=False, root_range=(0, hi))
+        items.append((q, hi, c))
+    Qs = [m.query(q.k, q.edges, q.labels).restrict(0, 0, hi) for q, hi, _ in items]
+    want = [oracle.match(g, q, root_range=(0, hi))[1] for q, hi, _ in items]
+    counts, rows = m.run_batch(Qs, enumerate=True)
+    assert counts == [c for _, _, c in items]
+    for w, r, (q, _, _) in zip(want, rows, items):
+        assert np.array_equal(r.reshape(-1, q.k), w)
+    # rows on the device, and a second (reordered) batch of the same shape
+    perm = np.random.default_rng(2).permutation(len(Qs))
+    counts2, rows2 = m.run_batch([Qs[i] for i in perm], enumerate=True, device=True)
+    assert counts2 == [counts[i] for i in perm]
+    for i, r in zip(perm, rows2):
+        assert np.array_equal(r.cpu().numpy().reshape(-1, items[i][0].k), want[i])
+    # counts only after listing: the count graph is another shape
+    assert m.run_batch(Qs) == counts
+    # the rows equal the single-query path's
+    for Q, w in zip(Qs[:10], want[:10]):
+        alone, _ = m.enumerate(Q)
+        assert np.array_equal(alone, w)
+    assert m.batch_stats()["overflowed"] == 0
+    m.close()
+
+
+def test_batch_enumerate_arena_overflow_falls_back(gsm_lib, cuda, rmat12b):
+    g = rmat12b
+    m = gsm_lib.Matcher(device=0)
+    m.load_graph(g.row_ptr, g.col, g.labels)
+    gsm_lib.gsm_batch_configure(m.ctx, 0, 0, 0, 1024)  # a tiny result arena
+    items = [it for it in mixed_queries(g, 12, seed=58) if it[2] > 0]
+    Qs = [m.query(q.k, q.edges, q.labels).restrict(0, 0, hi) for q, hi, _ in items]
+    want = [oracle.match(g, q, root_range=(0, hi))[1] for q, hi, _ in items]
+    counts, rows = m.run_batch(Qs, enumerate=True)
+    assert counts == [c for _, _, c in items]
+    assert m.batch_stats()["overflowed"] == (1 if sum(c * q.k for q, _, c in items) > 1024 else 0)
+    for w, r, (q, _, _) in zip(want, rows, items):
+        assert np.array_equal(r.reshape(-1, q.k), w)
+    m.close()
+
+
 def test_batch_autotune_and_configurations(gsm_lib, cuda, rmat12b):
     m = gsm_lib.Matcher(device=0)
     m.load_graph(rmat12b.row_ptr, rmat12b.col, rmat12b.labels)
@@ -132,4 +186,11 @@ def test_batched_workload_full_size(gsm_lib, cuda):
             assert count == q["count"]
             digest = hashlib.sha256(np.ascontiguousarray(rows, dtype="<i4").tobytes()).hexdigest()
             assert digest == q["rows_sha256"]
+    # the whole batch in enumerate mode: every query's rows against the digests
+    counts, rows = m.run_batch(Qs, enumerate=True, device=True)
+    assert counts == [q["count"] for q in gold["queries"]]
+    assert m.batch_stats()["overflowed"] == 0
+    for q, r in zip(gold["queries"], rows):
+        got = np.ascontiguousarray(r.cpu().numpy(), dtype="<i4").reshape(-1)
+        assert hashlib.sha256(got.tobytes()).hexdigest() == q["rows_sha256"]
     m.close()

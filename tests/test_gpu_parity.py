@@ -171,6 +171,27 @@ def test_results_do_not_depend_on_chunking_or_block_size(gsm_lib, rmat12):
                 assert ca == cb and np.array_equal(a, b), opts
 
 
+@pytest.mark.parametrize("hub_bytes", [-1, 64 << 10, 0])
+def test_results_do_not_depend_on_hub_bitmaps(gsm_lib, rmat12, rmat10u, hub_bytes):
+    """Non-tree edges checked on hub adjacency bitmaps (all hubs, a budget for
+    a few, or none: every check a binary search) give the oracle's rows."""
+    m = gsm_lib.Matcher(device=0, hub_bitmap_bytes=hub_bytes)
+    walks = [(q, rmat12.n, None) for q in
+             selective_walk_queries(rmat12, 10, 3, 8, seed=41, non_tree=(2, 4))]
+    for g, items in ((rmat12, walks),
+                     (rmat10u, [(q, hi, None) for q, hi in
+                                ((I.unlabelled_shapes()["clique4"], rmat10u.n),
+                                 (I.unlabelled_shapes()["cycle5"], 48),
+                                 (I.query_from_edges(4, [(0, 1), (1, 2), (2, 3), (3, 0),
+                                                         (0, 2)]), rmat10u.n))])):
+        m.load_graph(g.row_ptr, g.col, g.labels)
+        for q, hi, _ in items:
+            want_count, want_rows, _ = oracle.match(g, q, root_range=(0, hi))
+            rows, count = m.enumerate(m.query(q.k, q.edges, q.labels).restrict(0, 0, hi))
+            assert count == want_count and np.array_equal(rows, want_rows)
+    m.close()
+
+
 def test_chunking_exercised_under_small_budget(gsm_lib, rmat10u):
     m = gsm_lib.Matcher(device=0, mem_budget_bytes=1 << 20, chunk_rows=500)
     load(m, rmat10u, validate=False)

@@ -97,3 +97,51 @@ def test_server_rejects_misuse(gsm_lib, served_setup):
     assert r is not None and r["count"] == c
     gsm_lib.gsm_server_stop(m.ctx)
     m.close()
+
+
+def test_served_enumerate_mode_rows(gsm_lib, served_setup):
+    """Requests in enumerate mode, mixed with count-mode requests under Poisson
+    arrivals: every listed result equals the oracle's sorted rows and the rows
+    the query gets alone (gsm_enumerate); count-mode results carry no rows."""
+    g, items = served_setup
+    items = [it for it in items if it[2] <= 200_000][:30]
+    m = gsm_lib.Matcher(device=0)
+    m.load_graph(g.row_ptr, g.col, g.labels)
+    Qs = [m.query(q.k, q.edges, q.labels).restrict(0, 0, hi) for q, hi, _ in items]
+    want = []
+    for (q, hi, c), Q in zip(items, Qs):
+        cnt, rows, _ = oracle.match(g, q, root_range=(0, hi))
+        alone, count = m.enumerate(Q)
+        assert count == cnt == c and np.array_equal(alone, rows)
+        want.append(rows)
+    gsm_lib.gsm_server_start(m.ctx, 2, 16)
+    rng = np.random.default_rng(65)
+    tickets = {}
+    for rep in range(2):
+        for j in rng.permutation(len(Qs)):
+            time.sleep(float(rng.exponential(1 / 2000)))
+            mode = gsm_lib.GSM_MODE_ENUMERATE if (rep + j) % 2 == 0 else gsm_lib.GSM_MODE_COUNT
+            tickets[gsm_lib.gsm_submit(m.ctx, Qs[j].handle, mode)] = (int(j), mode)
+    results = {}
+    deadline = time.time() + 120
+    while len(results) < len(tickets) and time.time() < deadline:
+        for t in tickets:
+            if t not in results:
+                r = gsm_lib.gsm_poll(m.ctx, t)
+                if r is not None:
+                    results[t] = r
+        time.sleep(0.001)
+    gsm_lib.gsm_server_stop(m.ctx)
+    assert len(results) == len(tickets)
+    listed = 0
+    for t, r in results.items():
+        j, mode = tickets[t]
+        assert r["status"] == 0 and r["count"] == items[j][2]
+        if mode == gsm_lib.GSM_MODE_ENUMERATE:
+            rows = r.get("rows", np.zeros((0, items[j][0].k), np.int32))
+            assert np.array_equal(rows.reshape(-1, items[j][0].k), want[j])
+            listed += 1
+        else:
+            assert "rows" not in r
+    assert listed >= len(Qs) // 2
+    m.close()
