@@ -10,34 +10,40 @@ row digest of every slice were written by the CPU oracle
 (tests/golden/make_workloads.py).
 
 A step = all 20 query slices through the whole path (filter, order, every
-verification level with its count and write passes, sorting into canonical
-order), listed by one gsm_enumerate_many call into device buffers.  The graph
-is resident; L2 is flushed before each timed step (the graph is smaller than
-L2).  The end-to-end figure (`e2e`) uploads the graph from pinned host memory
-and lists every slice into pinned host buffers through the same call.
+verification level, sorting into canonical order), listed by one
+gsm_enumerate_many call into device buffers.  The graph is resident; L2 is
+flushed before each timed step (the graph is smaller than L2).  The headline
+pass records no per-kernel events; a second pass of the same steps on a
+context that does gives the per-kernel split and the roofline of the
+dominant kernel.  The end-to-end figure (`e2e`) uploads the graph from pinned
+host memory and lists every slice into pinned host buffers through the same
+call.
 
-`compressed_frontiers` (same line): the same slices with frontier rows kept
-as (parent row, new vertex) instead of full tuples, against the default
-layout: time per step and peak budgeted frontier memory, rows checked.
-
-`unlabelled_counts` (same line): on unlabelled R-MAT scale 20, the 3-path count
-(checked against sum d(d-1)), the ordered and distinct (symmetry-broken)
-triangle and 4-clique counts (checked against k! x the oracle's clique count,
-tests/golden/rmat20_unlabelled.json), and the 5-cycle and 6-path on the
-stored root slices (checked against the oracle's counts).
-
-`batched_vs_plain` (same line): the R-MAT scale-18 workload (16 Zipf(1.2)
-labels, 256 random-walk queries of 3-10 vertices with 2-4 non-tree edges, on
-oracle-sized root slices) counted one query per call versus as one batch (one
-CUDA graph), then served under Poisson arrivals at 50-2,000 queries/s (the
-configured range) and at 5,000 and 10,000 queries/s (around and beyond the
-plain form's serial capacity) with p50/p99 latency; every count is checked
-against the oracle's.
+Further legs on the same line:
+  `compressed_frontiers`: the slices with frontier rows kept as (parent row,
+      new vertex), time and peak frontier memory against the default layout.
+  `lookahead`: the slices with the k-look-ahead off, at 1 and at 2:
+      candidates checked, partial embeddings kept, time per step.
+  `batched_vs_plain`: R-MAT scale 18 (16 Zipf(1.2) labels, 256 random-walk
+      queries of 3-10 vertices with 2-4 non-tree edges, oracle-sized root
+      slices) counted one query per call versus as one batch (one CUDA graph),
+      the same in enumerate mode (sorted rows in device memory), then served
+      under Poisson arrivals at 50-10,000 queries/s.
+  `unlabelled_counts`: unlabelled R-MAT scale 20: the 3-path count (checked
+      against sum d(d-1)), ordered and distinct triangle and 4-clique counts
+      (checked against k! x the oracle's clique count), and the 5-cycle and
+      6-path on stored root slices (checked against the oracle's counts).
+  `served_rmat22`: the served form on resident R-MAT scale 22 with 32
+      Zipf(1.0) labels, 2,000 Poisson arrivals per rate at 50-2,000 queries/s
+      (and 5,000 and 10,000 beyond the configured range) from a pool of
+      random-walk queries of 3-12 vertices, against the plain form run
+      serially on the same arrival stream.
+Every count and row digest is checked against the oracle's stored values.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-One JSON line on rank 0.  `--impl reference` times the CPU oracle on a
-bounded sample of the same workload.
+One JSON line on rank 0.  `--impl reference` times the CPU oracle on a fixed
+sample of the same workload.
 """
 from __future__ import annotations
 
@@ -60,7 +66,7 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "rmat16_labelled_slices.json")
 GOLDEN_BATCH = os.path.join(ROOT, "tests", "golden", "rmat18_batched_slices.json")
 GOLDEN_RMAT20 = os.path.join(ROOT, "tests", "golden", "rmat20_unlabelled.json")
 GOLDEN_SERVED = os.path.join(ROOT, "tests", "golden", "rmat22_served_slices.json")
-SERVED22_RATES = (50, 100, 200, 500, 1000, 2000)
+SERVED22_RATES = (50, 100, 200, 500, 1000, 2000, 5000, 10000)
 SERVE_RATES = (50, 100, 200, 500, 1000, 2000, 5000, 10000)
 METRIC = "embeddings/sec & queries/sec at 1 GB300 (batched vs plain, bit-exact); p50/p99"
 UNIT = "embeddings/s"
@@ -255,9 +261,10 @@ def load_served_workload():
 
 def served_rmat22(gsm, torch, device, requests_per_rate, rates=SERVED22_RATES):
     """The served form on the resident R-MAT scale-22 graph (4,194,304
-    vertices, 32 Zipf(1.0) labels): Poisson arrivals at each rate of the
-    configured range, requests drawn from a pool of random-walk queries of
-    3-12 vertices on oracle-sized root slices, against the plain form (one
+    vertices, 32 Zipf(1.0) labels): Poisson arrivals at each rate (the
+    configured 50-2,000 queries/s, then 5,000 and 10,000 to find where each
+    form saturates), requests drawn from a pool of random-walk queries of
+    3-12 vertices on oracle-sized slices, against the plain form (one
     gsm_count per request, run serially on a second context) fed the same
     arrival stream.  Every count is checked against the oracle's."""
     g, queries = load_served_workload()

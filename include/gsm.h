@@ -126,6 +126,12 @@ typedef struct gsm_options {
    * search of its row.  0 = 512 MiB; negative = no bitmaps.  Built by
    * gsm_load_graph, outside the memory budget; results do not depend on it. */
   int64_t hub_bitmap_bytes;
+  /* Host threads gsm_enumerate_many lists its queries with (0 = 2, at most
+   * 16): each thread has a worker context of its own (stream, workspace with
+   * an equal share of the memory budget, result slots) on the shared
+   * resident graph, so one query's kernels run while another waits for a
+   * read-back.  1 = one query after the other on the context itself. */
+  int32_t host_workers;
 } gsm_options;
 
 /* Fills *opt with the defaults described above. */
@@ -211,21 +217,26 @@ gsm_status gsm_count_distinct(gsm_ctx *ctx, const gsm_query *q, uint64_t *count,
 gsm_status gsm_enumerate(gsm_ctx *ctx, const gsm_query *q, int32_t *out, uint64_t cap_rows,
                          uint64_t *count, int32_t flags);
 
-/* gsm_enumerate for nq queries in order: queries[j] lists into outs[j]
- * (capacity cap_rows[j] rows), counts[j] receives its total.  Same row layout
- * and order as gsm_enumerate; all outs[] are host pointers, or all device
- * pointers with GSM_OUT_DEVICE.  The paper has no counterpart: it is the
- * serving form of the listing.  The copy of query j's rows runs on a second
- * stream while the next queries compute, so the result staging buffers of
- * gsm_enumerate exist once per slot (gsm_options.copy_slots; they stay with
- * the context for later calls).  The call returns after every copy has
- * finished (also on error); host buffers should be pinned for the copies to
- * overlap.  gsm_last_rows then refers to the last query; gsm_last_run_stats
- * counts the kernel launches of the whole call and the peak budgeted bytes
- * over its queries, and its other fields describe the last query.  Errors: as gsm_enumerate (GSM_ERR_TRUNCATED if
- * any query overflowed its capacity: every count is still set, every output
- * holds its first cap_rows[j] rows); on another error the counts of queries
- * not yet run are unspecified. */
+/* gsm_enumerate for nq queries: queries[j] lists into outs[j] (capacity
+ * cap_rows[j] rows), counts[j] receives its total.  Same row layout and order
+ * as gsm_enumerate; all outs[] are host pointers, or all device pointers with
+ * GSM_OUT_DEVICE.  The paper has no counterpart: it is the serving form of
+ * the listing.  The candidate filter of all queries runs as one launch (when
+ * filter_rounds is 0), then gsm_options.host_workers host threads take the
+ * queries in turn, each on a worker context of its own (stream, workspace,
+ * result slots; created on first use, kept with the context, sharing its
+ * graph), so one query's kernels overlap another's waits.  Each worker copies
+ * a query's rows out on a copy stream while its next queries compute, so the
+ * result staging buffers of gsm_enumerate exist once per slot and worker
+ * (gsm_options.copy_slots).  The call returns after every copy has finished
+ * (also on error); host buffers should be pinned for the copies to overlap.
+ * gsm_last_rows then refers to the last query; gsm_last_run_stats counts the
+ * kernel launches of the whole call and the peak budgeted bytes over its
+ * queries (per worker), and its other fields describe the last query;
+ * gsm_kernel_stats adds up every worker's kernels.  Errors: as gsm_enumerate
+ * (GSM_ERR_TRUNCATED if any query overflowed its capacity: every count is
+ * still set, every output holds its first cap_rows[j] rows); on another error
+ * the counts of queries not yet run are unspecified. */
 gsm_status gsm_enumerate_many(gsm_ctx *ctx, int32_t nq, const gsm_query *const *queries,
                               int32_t *const *outs, const uint64_t *cap_rows, uint64_t *counts,
                               int32_t flags);

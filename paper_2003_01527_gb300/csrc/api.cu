@@ -4,6 +4,8 @@
 // frontier chunks so intermediate results stay inside a fixed budget.
 #include <algorithm>
 #include <array>
+#include <atomic>
+#include <climits>
 #include <functional>
 #include <cstdarg>
 #include <cstdio>
@@ -77,6 +79,8 @@ struct gsm_ctx {
 
   // graph
   bool has_graph = false;
+  bool borrowed_graph = false;  // a worker context: the graph belongs to its parent
+  std::vector<gsm_ctx *> workers;  // gsm_enumerate_many's parallel listing contexts
   int32_t n = 0;
   int64_t nnz = 0;
   int32_t max_deg = 0;
@@ -84,6 +88,8 @@ struct gsm_ctx {
   int32_t *d_lcol = nullptr, *d_llab = nullptr;  // rows ordered by (label, id)
   int32_t *d_hub = nullptr;        // hub index of every vertex, -1 = none
   uint32_t *d_hub_bits = nullptr;  // adjacency bitmaps of the hubs
+  int32_t *d_hub_seg = nullptr;    // label segment starts of the hubs' rows
+  size_t hub_seg_bytes = 0;
   int32_t hub_count = 0, hub_min_deg = 0;
   size_t hub_bits_bytes = 0;
   std::vector<int32_t> label_values;  // sorted distinct labels; dense id = index
@@ -93,6 +99,8 @@ struct gsm_ctx {
   size_t bitmaps_cap = 0;
   void *bitmaps2 = nullptr;  // second buffer of the refinement rounds
   size_t bitmaps2_cap = 0;
+  void *mfilter = nullptr;  // gsm_enumerate_many: descriptors, sizes and bitmaps of all queries
+  size_t mfilter_cap = 0;
   unsigned long long *d_small = nullptr;  // [0..15] sizes, [16] total, [17] err
   void *acc[2] = {nullptr, nullptr};
   size_t acc_cap[2] = {0, 0};
@@ -210,7 +218,8 @@ GraphDev graph_dev(const gsm_ctx *ctx) {
                   (int32_t)std::max<size_t>(1, ctx->label_values.size()),
                   ctx->hub_count ? ctx->d_hub : nullptr,
                   ctx->hub_count ? ctx->d_hub_bits : nullptr,
-                  (ctx->n + 31) / 32};
+                  (ctx->n + 31) / 32,
+                  ctx->hub_count ? ctx->d_hub_seg : nullptr};
 }
 
 void set_err(gsm_ctx *c, const char *fmt, ...) {
@@ -1121,10 +1130,17 @@ void run_filter(gsm_ctx *ctx, const gsm_query *q, const int32_t *dense, uint64_t
 }
 
 // The whole matcher for one query.  out == nullptr and !enumerate: count only.
+// pre (optional): the query's candidate bitmaps and sizes, already computed
+// by a batched filter launch (gsm_enumerate_many).
+struct Prefiltered {
+  const uint32_t *bitmaps;
+  const uint64_t *sizes;
+};
+
 void run_query(gsm_ctx *ctx, const gsm_query *q, bool enumerate, int32_t *out, uint64_t cap_rows,
                int32_t flags, uint64_t *count_out, bool *truncated,
                const std::vector<std::pair<int32_t, int32_t>> *less = nullptr,
-               bool copy_async = false) {
+               bool copy_async = false, const Prefiltered *pre = nullptr) {
   if (!ctx->has_graph) FAIL(GSM_ERR_NO_GRAPH, "no data graph loaded");
   std::memset(&ctx->run, 0, sizeof(ctx->run));
   // nothing is live between calls (an earlier call may have failed mid-way)
@@ -1157,7 +1173,10 @@ void run_query(gsm_ctx *ctx, const gsm_query *q, bool enumerate, int32_t *out, u
   int32_t dense[kMaxK];
   uint64_t sizes[kMaxK] = {};
   if (!dense_labels(ctx, q, dense)) return;  // a query label absent from G: no embedding
-  run_filter(ctx, q, dense, sizes);
+  if (pre)
+    std::memcpy(sizes, pre->sizes, sizeof(uint64_t) * q->k);
+  else
+    run_filter(ctx, q, dense, sizes);
   for (int32_t u = 0; u < q->k; ++u) ctx->run.cand_size[u] = sizes[u];
   for (int32_t u = 0; u < q->k; ++u)
     if (sizes[u] == 0) return;
@@ -1181,7 +1200,7 @@ void run_query(gsm_ctx *ctx, const gsm_query *q, bool enumerate, int32_t *out, u
   R.key_nw = packed_words(q->k, key_bits);
 
   const int32_t nw = (ctx->n + 31) / 32;
-  const uint32_t *bm = (const uint32_t *)ctx->bitmaps;
+  const uint32_t *bm = pre ? pre->bitmaps : (const uint32_t *)ctx->bitmaps;
   for (int32_t i = 1; i < q->k; ++i) {
     LevelDesc &d = R.lv[i];
     std::memset(&d, 0, sizeof(d));
@@ -1383,6 +1402,15 @@ void build_hubs(gsm_ctx *ctx, const std::vector<int32_t> &h_rp) {
   GraphDev g = graph_dev(ctx);
   launch_hub_bitmaps(g, d_list, H, words, ctx->d_hub_bits, ctx->stream);
   CU(cudaGetLastError());
+  // label segment table of the hubs (labelled graphs, up to 4,096 labels)
+  const int64_t L = (int64_t)ctx->label_values.size();
+  if (L > 1 && L <= 4096) {
+    ctx->hub_seg_bytes = sizeof(int32_t) * (size_t)H * (size_t)(L + 1);
+    ctx->d_hub_seg = (int32_t *)dev_alloc(ctx, ctx->hub_seg_bytes);
+    g.num_labels = (int32_t)L;
+    launch_hub_segments(g, d_list, H, ctx->d_hub_seg, ctx->stream);
+    CU(cudaGetLastError());
+  }
   CU(cudaStreamSynchronize(ctx->stream));
   dev_free(ctx, d_list, sizeof(int32_t) * H);
   ctx->hub_count = H;
@@ -1392,7 +1420,19 @@ void build_hubs(gsm_ctx *ctx, const std::vector<int32_t> &h_rp) {
 void clear_all_graphs(gsm_ctx *ctx);
 
 void free_graph(gsm_ctx *ctx) {
+  for (gsm_ctx *w : ctx->workers) gsm_destroy(w);  // they share the graph
+  ctx->workers.clear();
   clear_all_graphs(ctx);
+  if (ctx->borrowed_graph) {
+    ctx->d_rp = ctx->d_col = ctx->d_lab = ctx->d_lcol = ctx->d_llab = ctx->d_hub = nullptr;
+    ctx->d_hub_bits = nullptr;
+    ctx->d_hub_seg = nullptr;
+    ctx->hub_count = 0;
+    ctx->has_graph = false;
+    ctx->borrowed_graph = false;
+    ctx->label_values.clear();
+    return;
+  }
   if (ctx->d_rp) dev_free(ctx, ctx->d_rp, sizeof(int32_t) * (ctx->n + 1));
   if (ctx->d_col) dev_free(ctx, ctx->d_col, sizeof(int32_t) * std::max<int64_t>(ctx->nnz, 1));
   if (ctx->d_lab) dev_free(ctx, ctx->d_lab, sizeof(int32_t) * std::max<int32_t>(ctx->n, 1));
@@ -1400,8 +1440,11 @@ void free_graph(gsm_ctx *ctx) {
   if (ctx->d_llab) dev_free(ctx, ctx->d_llab, sizeof(int32_t) * std::max<int64_t>(ctx->nnz, 1));
   if (ctx->d_hub) dev_free(ctx, ctx->d_hub, sizeof(int32_t) * std::max<int32_t>(ctx->n, 1));
   if (ctx->d_hub_bits) dev_free(ctx, ctx->d_hub_bits, ctx->hub_bits_bytes);
+  if (ctx->d_hub_seg) dev_free(ctx, ctx->d_hub_seg, ctx->hub_seg_bytes);
   ctx->d_hub = nullptr;
   ctx->d_hub_bits = nullptr;
+  ctx->d_hub_seg = nullptr;
+  ctx->hub_seg_bytes = 0;
   ctx->hub_count = 0;
   ctx->hub_bits_bytes = 0;
   ctx->d_rp = ctx->d_col = ctx->d_lab = nullptr;
@@ -2227,7 +2270,8 @@ gsm_status gsm_create(gsm_ctx **out, int32_t device, const gsm_options *opt) {
     return GSM_ERR_INVALID_ARG;
   if (opt && (opt->chunk_rows < 0 || opt->filter_rounds < 0 || opt->filter_rounds > 64 ||
               opt->copy_slots < 0 || opt->copy_slots > 64 || opt->lookback_spin_limit < 0 ||
-              opt->lookahead < 0 || opt->lookahead > 2))
+              opt->lookahead < 0 || opt->lookahead > 2 || opt->host_workers < 0 ||
+              opt->host_workers > 16))
     return GSM_ERR_INVALID_ARG;
   gsm_ctx *ctx = new gsm_ctx();
   if (opt) ctx->opt = *opt;
@@ -2271,6 +2315,7 @@ void gsm_destroy(gsm_ctx *ctx) {
     dev_free(ctx, ctx->scratch, ctx->scratch_cap);
     dev_free(ctx, ctx->bitmaps, ctx->bitmaps_cap);
     dev_free(ctx, ctx->bitmaps2, ctx->bitmaps2_cap);
+    dev_free(ctx, ctx->mfilter, ctx->mfilter_cap);
     dev_free(ctx, ctx->acc[0], ctx->acc_cap[0]);
     dev_free(ctx, ctx->acc[1], ctx->acc_cap[1]);
     dev_free(ctx, ctx->sort_tmp, ctx->sort_tmp_cap);
@@ -2493,6 +2538,62 @@ gsm_status gsm_count(gsm_ctx *ctx, const gsm_query *q, uint64_t *count) {
 }
 
 namespace {
+// The candidate filter of every query of a gsm_enumerate_many call in one
+// launch (no refinement rounds), with one read-back of all candidate-set
+// sizes; pre[j].bitmaps stays null for a query with a label absent from G.
+void prefilter_many(gsm_ctx *ctx, int32_t nq, const gsm_query *const *queries,
+                    std::vector<Prefiltered> &pre, std::vector<uint64_t> &sizes) {
+  const int32_t nw = (ctx->n + 31) / 32;
+  std::vector<FilterDesc> fds;
+  std::vector<int32_t> sel;
+  std::vector<size_t> bm_off;
+  size_t bm_words = 0;
+  for (int32_t j = 0; j < nq; ++j) {
+    int32_t dense[kMaxK];
+    if (!dense_labels(ctx, queries[j], dense)) continue;
+    FilterDesc fd;
+    fill_filter(ctx, queries[j], dense, fd);
+    fds.push_back(fd);
+    sel.push_back(j);
+    bm_off.push_back(bm_words);
+    bm_words += (size_t)queries[j]->k * nw;
+  }
+  pre.assign(nq, Prefiltered{nullptr, nullptr});
+  sizes.assign((size_t)nq * kMaxK, 0);
+  const int32_t m = (int32_t)sel.size();
+  if (m == 0) return;
+  Carve cv;
+  const size_t o_fd = cv.add<FilterDesc>(m), o_ptr = cv.add<uint32_t *>(m),
+               o_sz = cv.add<unsigned long long>((int64_t)m * kMaxK),
+               o_bm = cv.add<uint32_t>((int64_t)bm_words);
+  ensure_buf(ctx, &ctx->mfilter, &ctx->mfilter_cap, cv.off, false, 0);
+  char *base = (char *)ctx->mfilter;
+  uint32_t *bm = (uint32_t *)(base + o_bm);
+  std::vector<uint32_t *> ptrs(m);
+  for (int32_t t = 0; t < m; ++t) ptrs[t] = bm + bm_off[t];
+  CU(cudaMemcpyAsync(base + o_fd, fds.data(), sizeof(FilterDesc) * m, cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CU(cudaMemcpyAsync(base + o_ptr, ptrs.data(), sizeof(uint32_t *) * m, cudaMemcpyHostToDevice,
+                     ctx->stream));
+  unsigned long long *d_sizes = (unsigned long long *)(base + o_sz);
+  GraphDev g = graph_dev(ctx);
+  timed(ctx, K_FILTER, 12.0 * ctx->n * m + 4.0 * (double)bm_words, (uint64_t)ctx->n * m, 1, [&] {
+    launch_filter_many(g, (const FilterDesc *)(base + o_fd), (uint32_t *const *)(base + o_ptr),
+                       d_sizes, m, nw, ctx->stream);
+  });
+  std::vector<uint64_t> h((size_t)m * kMaxK);
+  CU(cudaMemcpyAsync(h.data(), d_sizes, sizeof(uint64_t) * h.size(), cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  for (int32_t t = 0; t < m; ++t) {
+    const int32_t j = sel[t];
+    std::memcpy(&sizes[(size_t)j * kMaxK], &h[(size_t)t * kMaxK], sizeof(uint64_t) * kMaxK);
+    pre[j] = Prefiltered{ptrs[t], &sizes[(size_t)j * kMaxK]};
+  }
+}
+}  // namespace
+
+namespace {
 // Parks the active result buffers and takes the oldest parked slot (creating
 // slots until there are `slots` of them); what the compute stream does next
 // waits until that slot's last copy out has finished.
@@ -2527,6 +2628,88 @@ void next_result_slot(gsm_ctx *ctx, int32_t slots) {
 }
 }  // namespace
 
+namespace {
+
+// A worker context of gsm_enumerate_many: its own stream, workspace, result
+// slots and small-read buffer, a share of the parent's memory budget, and
+// the parent's resident graph (borrowed, never freed by the worker).
+gsm_ctx *make_worker(gsm_ctx *ctx, int32_t nworkers) {
+  gsm_options o = ctx->opt;
+  o.stream = nullptr;
+  o.mem_budget_bytes = std::max<size_t>(ctx->budget / (size_t)nworkers, size_t(1) << 20);
+  gsm_ctx *w = nullptr;
+  const gsm_status st = gsm_create(&w, ctx->device, &o);
+  if (st != GSM_OK) FAIL(st, "creating a listing worker failed");
+  w->n = ctx->n;
+  w->nnz = ctx->nnz;
+  w->max_deg = ctx->max_deg;
+  w->d_rp = ctx->d_rp;
+  w->d_col = ctx->d_col;
+  w->d_lab = ctx->d_lab;
+  w->d_lcol = ctx->d_lcol;
+  w->d_llab = ctx->d_llab;
+  w->d_hub = ctx->d_hub;
+  w->d_hub_bits = ctx->d_hub_bits;
+  w->d_hub_seg = ctx->d_hub_seg;
+  w->hub_count = ctx->hub_count;
+  w->label_values = ctx->label_values;
+  w->has_graph = ctx->has_graph;
+  w->borrowed_graph = true;
+  return w;
+}
+
+// The listing loop of gsm_enumerate_many on one context: takes query indices
+// from `next` until none is left (or another worker failed), lists each into
+// its output through the context's result slots and copy stream.
+struct ManyState {
+  int32_t nq;
+  const gsm_query *const *queries;
+  int32_t *const *outs;
+  const uint64_t *cap_rows;
+  uint64_t *counts;
+  int32_t flags;
+  const std::vector<Prefiltered> *pre = nullptr;
+  std::atomic<int32_t> next{0};
+  std::atomic<int32_t> failed{0};
+  std::atomic<int32_t> first_trunc{INT32_MAX};
+};
+
+void list_many(gsm_ctx *ctx, ManyState &M, uint64_t *launches, uint64_t *peak, bool *had_last,
+               gsm_run_stats *last_run) {
+  gsm_ctx *c = ctx;
+  if (!c->copy_stream) {
+    CU(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+    CU(cudaEventCreateWithFlags(&c->rows_ready, cudaEventDisableTiming));
+  }
+  const int32_t slots = c->opt.copy_slots > 0 ? c->opt.copy_slots : 8;
+  for (;;) {
+    if (M.failed.load()) break;
+    const int32_t j = M.next.fetch_add(1);
+    if (j >= M.nq) break;
+    next_result_slot(c, slots);
+    bool trunc = false;
+    const Prefiltered *p = (M.pre && (*M.pre)[j].bitmaps) ? &(*M.pre)[j] : nullptr;
+    run_query(c, M.queries[j], true, M.outs[j], M.cap_rows[j], M.flags, &M.counts[j], &trunc,
+              nullptr, true, p);
+    *launches += c->run.kernel_launches;
+    *peak = std::max<uint64_t>(*peak, c->peak_bytes);
+    if (trunc) {
+      int32_t cur = M.first_trunc.load();
+      while (j < cur && !M.first_trunc.compare_exchange_weak(cur, j)) {
+      }
+    }
+    if (j == M.nq - 1) {
+      *had_last = true;
+      *last_run = c->run;
+    }
+  }
+  CU(cudaStreamSynchronize(c->copy_stream));
+  CU(cudaStreamSynchronize(c->stream));
+  resolve_timings(c);
+}
+
+}  // namespace
+
 gsm_status gsm_enumerate_many(gsm_ctx *ctx, int32_t nq, const gsm_query *const *queries,
                               int32_t *const *outs, const uint64_t *cap_rows, uint64_t *counts,
                               int32_t flags) {
@@ -2534,27 +2717,87 @@ gsm_status gsm_enumerate_many(gsm_ctx *ctx, int32_t nq, const gsm_query *const *
   if (nq > 0 && (!queries || !outs || !cap_rows || !counts)) return GSM_ERR_INVALID_ARG;
   for (int32_t j = 0; j < nq; ++j)
     if (!queries[j] || (cap_rows[j] > 0 && !outs[j])) return GSM_ERR_INVALID_ARG;
-  int32_t first_trunc = -1;
+  ManyState M;
+  M.nq = nq;
+  M.queries = queries;
+  M.outs = outs;
+  M.cap_rows = cap_rows;
+  M.counts = counts;
+  M.flags = flags;
+  const int32_t nworkers =
+      std::min<int32_t>(ctx->opt.host_workers > 0 ? ctx->opt.host_workers : 2, std::max(nq, 1));
   gsm_status st = guarded(ctx, [&] {
     CU(cudaSetDevice(ctx->device));
-    if (!ctx->copy_stream) {
-      CU(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
-      CU(cudaEventCreateWithFlags(&ctx->rows_ready, cudaEventDisableTiming));
-    }
-    const int32_t slots = ctx->opt.copy_slots > 0 ? ctx->opt.copy_slots : 8;
+    if (!ctx->has_graph) FAIL(GSM_ERR_NO_GRAPH, "no data graph loaded");
     uint64_t launches = 0, peak = 0;
-    for (int32_t j = 0; j < nq; ++j) {
-      next_result_slot(ctx, slots);
-      bool trunc = false;
-      run_query(ctx, queries[j], true, outs[j], cap_rows[j], flags, &counts[j], &trunc, nullptr,
-                true);
-      launches += ctx->run.kernel_launches;
-      peak = std::max<uint64_t>(peak, ctx->peak_bytes);
-      if (trunc && first_trunc < 0) first_trunc = j;
+    // without refinement rounds the filter of every query runs as one launch
+    std::vector<Prefiltered> pre;
+    std::vector<uint64_t> pre_sizes;
+    if (ctx->opt.filter_rounds == 0 && nq > 1) {
+      prefilter_many(ctx, nq, queries, pre, pre_sizes);
+      M.pre = &pre;
+      launches += 1;
     }
-    CU(cudaStreamSynchronize(ctx->copy_stream));
-    CU(cudaStreamSynchronize(ctx->stream));
+    gsm_run_stats last{};
+    if (nworkers <= 1) {
+      bool had_last = false;
+      list_many(ctx, M, &launches, &peak, &had_last, &last);
+    } else {
+      // several host threads, each on a worker context of its own, so one
+      // query's kernels fill another's waits on the host
+      while ((int32_t)ctx->workers.size() < nworkers)
+        ctx->workers.push_back(make_worker(ctx, nworkers));
+      std::vector<gsm_status> wst(nworkers, GSM_OK);
+      std::vector<uint64_t> wl(nworkers, 0), wp(nworkers, 0);
+      std::vector<char> wlast(nworkers, 0);
+      std::vector<gsm_run_stats> wrun(nworkers);
+      std::vector<std::thread> th;
+      for (int32_t w = 0; w < nworkers; ++w)
+        th.emplace_back([&, w] {
+          gsm_ctx *c = ctx->workers[w];
+          wst[w] = guarded(c, [&] {
+            CU(cudaSetDevice(c->device));
+            bool had = false;
+            list_many(c, M, &wl[w], &wp[w], &had, &wrun[w]);
+            wlast[w] = had ? 1 : 0;
+          });
+          if (wst[w] != GSM_OK) M.failed.store(1);
+        });
+      for (auto &t : th) t.join();
+      for (int32_t w = 0; w < nworkers; ++w) {
+        gsm_ctx *c = ctx->workers[w];
+        if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
+        c->active_pending = false;
+        for (auto &p : c->parked) p.pending = false;
+      }
+      for (int32_t w = 0; w < nworkers; ++w)
+        if (wst[w] != GSM_OK) {
+          ctx->err = ctx->workers[w]->err;
+          throw Fail{wst[w]};
+        }
+      for (int32_t w = 0; w < nworkers; ++w) {
+        gsm_ctx *c = ctx->workers[w];
+        launches += wl[w];
+        peak = std::max(peak, wp[w]);
+        for (int k = 0; k < K_NUM; ++k) {  // per-kernel figures of the whole call
+          ctx->kstats[k].launches += c->kstats[k].launches;
+          ctx->kstats[k].total_ms += c->kstats[k].total_ms;
+          ctx->kstats[k].algo_bytes += c->kstats[k].algo_bytes;
+          ctx->kstats[k].items += c->kstats[k].items;
+          const char *nm = c->kstats[k].name;
+          c->kstats[k] = KStat();
+          c->kstats[k].name = nm;
+        }
+        if (wlast[w]) {
+          last = wrun[w];
+          ctx->last_rows = c->last_rows;  // the rows of the call's last query
+          ctx->last_count = c->last_count;
+          ctx->last_k = c->last_k;
+        }
+      }
+    }
     resolve_timings(ctx);
+    if (nworkers > 1) ctx->run = last;
     ctx->run.kernel_launches = launches;
     ctx->run.peak_bytes = peak;
   });
@@ -2562,7 +2805,8 @@ gsm_status gsm_enumerate_many(gsm_ctx *ctx, int32_t nq, const gsm_query *const *
   if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
   ctx->active_pending = false;
   for (auto &p : ctx->parked) p.pending = false;
-  if (st == GSM_OK && first_trunc >= 0) {
+  const int32_t first_trunc = M.first_trunc.load();
+  if (st == GSM_OK && first_trunc < nq) {
     set_err(ctx, "query %d: %llu embeddings, capacity %llu rows", first_trunc,
             (unsigned long long)counts[first_trunc], (unsigned long long)cap_rows[first_trunc]);
     return GSM_ERR_TRUNCATED;

@@ -587,6 +587,15 @@ void pscan(const T *in, const int64_t *n_ptr, int64_t *out, int64_t *partials, i
 
 }  // namespace
 
+void launch_filter_many(const GraphDev &g, const FilterDesc *fds, uint32_t *const *bm_out,
+                        unsigned long long *sizes, int32_t nq, int32_t n_words,
+                        cudaStream_t s) {
+  if (nq <= 0) return;
+  cudaMemsetAsync(sizes, 0, sizeof(unsigned long long) * nq * kMaxK, s);
+  const int gx = (int)std::min<int64_t>((n_words + 7) / 8, 128);
+  k_b_filter<<<dim3(std::max(gx, 1), nq), 256, 0, s>>>(g, fds, bm_out, sizes);
+}
+
 int batch_enqueue(const GraphDev &g, const BatchArgs &a, cudaStream_t s) {
   const int32_t B = a.block, G = a.grid;
   const int32_t tile_items = B * kItemsPerThread;

@@ -71,6 +71,13 @@ struct BatchArgs {
   int64_t *ftile_off;             // [cap_items / 128 + 3]
 };
 
+// The candidate filter of nq queries in one launch: query j's FilterDesc is
+// fds[j], its k bitmaps go to bm_out[j], |C(u)| to sizes[j * kMaxK + u]
+// (zeroed here).  fds and bm_out are device arrays.
+void launch_filter_many(const GraphDev &g, const FilterDesc *fds, uint32_t *const *bm_out,
+                        unsigned long long *sizes, int32_t nq, int32_t n_words,
+                        cudaStream_t s);
+
 // Issues the whole batch on stream s (no host synchronisation, fixed launch
 // shapes, so the sequence can be captured as a CUDA graph).  Returns the
 // number of kernels launched.

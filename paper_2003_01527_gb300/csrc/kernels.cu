@@ -11,8 +11,10 @@
 //   k_scan_*            the compaction scan
 //   k_extend_write      Write_to_Partial: survivors to consecutive rows
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cstdio>
+#include <type_traits>
 
 #include "filter_body.cuh"
 #include "segments.cuh"
@@ -536,14 +538,12 @@ __global__ void __launch_bounds__(1024) k_extend_write(
 // are written directly at their final rows, in candidate order, as the
 // two-pass form would write them.
 //
-// Within a tile a warp takes 128 consecutive candidates, four per lane.
-// When all of them come from one frontier row (the usual case: rows have
-// many candidates), lane 0 finds that row once for the warp, and the
-// candidates -- one contiguous run of the pivot's label segment -- are
-// staged in shared memory with aligned int4 loads; otherwise every lane
-// finds the rows of its own four candidates.  Non-tree edges to hubs are
-// checked on the hubs' adjacency bitmaps (one probe), the others by binary
-// search of the (short) row (row_contains_l).
+// Thread t of a tile takes the 4 consecutive candidates 4t .. 4t+3 (one row
+// search for all four, in the tile's staged work offsets).  Non-tree edges
+// to hubs are checked on the hubs' adjacency bitmaps (one probe), the others
+// by binary search of the row (row_contains_l).  Result rows of an even width
+// are stored by their own thread with 16- or 8-byte stores; the others are
+// assembled in shared memory and stored contiguously.
 //
 // lookback: tiles words, then the ticket, the survivor total and an error
 // word, all zero at launch.  A look-back that polls more than spin_limit
@@ -551,12 +551,13 @@ __global__ void __launch_bounds__(1024) k_extend_write(
 // stay in bounds; the host reports the error).  stall_tile >= 0 is fault
 // injection for tests: that tile never publishes its word, so the waits of
 // the tiles after it run out.
-constexpr int32_t kStage = 136;  // ints a warp stages its 128 candidates in (+ alignment)
 constexpr size_t kFusedSmemAttr = 200 * 1024;  // dynamic shared memory a CTA may use
 constexpr size_t kFusedStageMax = 96 * 1024;   // ... with the tile's result rows staged
 
-template <int kMode>
-__global__ void __launch_bounds__(1024, 1) k_extend_fused(
+// kMaxThreads = 256: up to 256 threads per CTA, registers capped so that six
+// CTAs fit on an SM; 1024: any block size.
+template <int kMode, int kMaxThreads>
+__global__ void __launch_bounds__(kMaxThreads, kMaxThreads == 256 ? 6 : 1) k_extend_fused(
     GraphDev g, LevelDesc d, const int32_t *__restrict__ F, int32_t ld,
     const int32_t *__restrict__ pstart, const uint8_t *__restrict__ pslot,
     const int64_t *__restrict__ woff, const int32_t *__restrict__ tile_row, int64_t wa,
@@ -571,12 +572,11 @@ __global__ void __launch_bounds__(1024, 1) k_extend_fused(
   const int32_t B = blockDim.x;
   const int32_t tile_items = B * kItemsPerThread;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // shared memory: staged work offsets | survivor pairs x 2 | per-warp
-  // candidate stage | assembled result rows (stage_out only)
+  // shared memory: staged work offsets | survivor pairs x 2 | assembled
+  // result rows (stage_out only)
   int32_t *s_woff = smem;
   int32_t *s_pairs = s_woff + tile_items + 4;
-  int32_t *s_win = s_pairs + 4 * tile_items + warp * kStage;
-  int32_t *s_out = s_pairs + 4 * tile_items + (B >> 5) * kStage;
+  int32_t *s_out = s_pairs + 4 * tile_items;
   int32_t pend = -1, pend_T = 0, pend_buf = 0, buf = 0;
 
   // lookback + write of a verified tile whose survivors are in buffer pb
@@ -590,7 +590,25 @@ __global__ void __launch_bounds__(1024, 1) k_extend_fused(
     __syncthreads();
     const int32_t *pairs = s_pairs + pb * 2 * tile_items;
     const int64_t base = sink.row0 + s_prefix;
-    if (kMode == kSinkRows && stage_out) {
+    if (kMode == kSinkRows && (sink.k & 1) == 0) {
+      // result rows in the matching order (the identity here: rows are only
+      // written directly when it is canonical); an even row width is stored
+      // with 16- or 8-byte stores, so each warp store covers 32 whole rows
+      const int32_t k = sink.k, i = d.i;
+      for (int32_t q = threadIdx.x; q < T; q += B) {
+        const int32_t r = pairs[2 * q], w = pairs[2 * q + 1];
+        int32_t *dst = (int32_t *)sink.out + (base + q) * k;
+        auto col = [&](int c) { return c < i ? F[c * ld + r] : w; };
+        if ((k & 3) == 0) {
+          for (int c = 0; c < k; c += 4)
+            *reinterpret_cast<int4 *>(dst + c) = make_int4(col(c), col(c + 1), col(c + 2),
+                                                           col(c + 3));
+        } else {
+          for (int c = 0; c < k; c += 2)
+            *reinterpret_cast<int2 *>(dst + c) = make_int2(col(c), col(c + 1));
+        }
+      }
+    } else if (kMode == kSinkRows && stage_out) {
       // the tile's result rows are one contiguous block of T*k ints:
       // assemble them in shared memory, then store them contiguously
       const int32_t k = sink.k;
@@ -618,55 +636,10 @@ __global__ void __launch_bounds__(1024, 1) k_extend_fused(
     const int32_t x0 = tile * tile_items;
     const int32_t x1 = min(x0 + tile_items, W);
     const TileRows t = stage_rows(woff, tile_row, wa, tile_items, s_woff, tile);
-    const int32_t xw = x0 + warp * 128;  // the warp's first candidate
-    const int32_t xb = xw + lane * kItemsPerThread;
+    const int32_t xb = x0 + warp * 128 + lane * kItemsPerThread;
     uint32_t bits = 0;
     int32_t rj[kItemsPerThread], wj[kItemsPerThread];
-    // one row for the whole warp?  (its first and last candidate share it)
-    int32_t r_lo = -1, r_hi = -2, rs0 = 0;
-    if (lane == 0 && xw < x1) {
-      int32_t rs1;
-      r_lo = item_row(t, s_woff, woff, wa, xw, &rs0);
-      r_hi = item_row(t, s_woff, woff, wa, min(xw + 127, x1 - 1), &rs1);
-    }
-    r_lo = __shfl_sync(kAll, r_lo, 0);
-    r_hi = __shfl_sync(kAll, r_hi, 0);
-    rs0 = __shfl_sync(kAll, rs0, 0);
-    if (r_lo == r_hi) {  // warp-uniform (r_lo = -1 < r_hi = -2 never matches)
-      const int32_t slot = pslot[r_lo];
-      // stage the warp's candidates, lcol[e0, e0 + n), with aligned int4 loads
-      const int32_t n = min(128, x1 - xw);
-      const int32_t e0 = pstart[r_lo] + (xw - rs0);
-      const int32_t a0 = e0 & ~3;
-      const int32_t nv = (e0 + n - a0 + 3) >> 2;
-      for (int32_t v = lane; v < nv; v += 32) {
-        const int32_t e = a0 + 4 * v;
-        if (e + 3 < g.nnz) {
-          const int4 q4 = __ldg(reinterpret_cast<const int4 *>(g.lcol + e));
-          s_win[4 * v] = q4.x;
-          s_win[4 * v + 1] = q4.y;
-          s_win[4 * v + 2] = q4.z;
-          s_win[4 * v + 3] = q4.w;
-        } else {
-          for (int c = 0; c < 4; ++c)
-            if (e + c < g.nnz) s_win[4 * v + c] = __ldg(g.lcol + e + c);
-        }
-      }
-      __syncwarp();
-      const ColumnRow row{F, ld, r_lo};
-#pragma unroll
-      for (int j = 0; j < kItemsPerThread; ++j) {
-        rj[j] = r_lo;
-        wj[j] = 0;
-        const int32_t x = xb + j;
-        if (x >= x1) continue;
-        const int32_t w = s_win[e0 - a0 + lane * kItemsPerThread + j];
-        wj[j] = w;
-        if (check_candidate(g, d, row, w, slot) && (!d.la || lookahead_ok(g, d, row, w)))
-          bits |= 1u << j;
-      }
-      __syncwarp();  // s_win is read before the next tile restages it
-    } else if (xb < x1) {
+    if (xb < x1) {
       int32_t rs;
       int32_t r = item_row(t, s_woff, woff, wa, xb, &rs);
       int32_t rr = r - t.r0;
@@ -772,6 +745,32 @@ __global__ void k_hub_bits(GraphDev g, const int32_t *__restrict__ hubs, int32_t
   }
 }
 
+// One warp per hub: lane l finds where labels l, l + 32, ... start in the
+// hub's (label, id)-ordered row (lower bound of the label).
+__global__ void k_hub_segments(GraphDev g, const int32_t *__restrict__ hubs, int32_t H,
+                               int32_t *__restrict__ seg) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int32_t L = g.num_labels;
+  for (int64_t h = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; h < H; h += warps) {
+    const int32_t v = hubs[h];
+    const int32_t b = g.rp[v], e = g.rp[v + 1];
+    for (int32_t l = lane; l <= L; l += 32) {
+      int32_t lo = b, len = e - b;
+      while (len > 0) {
+        const int32_t half = len >> 1;
+        if (g.llab[lo + half] < l) {
+          lo += half + 1;
+          len -= half + 1;
+        } else {
+          len = half;
+        }
+      }
+      seg[h * (L + 1) + l] = lo;
+    }
+  }
+}
+
 inline int grid_for(int64_t n, int threads, int cap = 152 * 32) {
   int64_t b = (n + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -854,6 +853,12 @@ void launch_hub_bitmaps(const GraphDev &g, const int32_t *hubs, int32_t H, int32
   if (H <= 0) return;
   cudaMemsetAsync(bits, 0, sizeof(uint32_t) * (size_t)H * words, s);
   k_hub_bits<<<grid_for((int64_t)H * 32, 256, 152 * 8), 256, 0, s>>>(g, hubs, H, words, bits);
+}
+
+void launch_hub_segments(const GraphDev &g, const int32_t *hubs, int32_t H, int32_t *seg,
+                         cudaStream_t s) {
+  if (H <= 0) return;
+  k_hub_segments<<<grid_for((int64_t)H * 32, 256, 152 * 8), 256, 0, s>>>(g, hubs, H, seg);
 }
 
 void launch_filter(const GraphDev &g, const FilterDesc &d, uint32_t *bitmaps,
@@ -978,41 +983,42 @@ namespace {
 // One persistent launch of k_extend_fused<kMode>: as many CTAs as fit on the
 // device at once (at most one per tile).  The dynamic shared-memory limit is
 // raised once per device for this instance.
-template <int kMode>
+template <int kMode, int kMaxThreads>
 void launch_fused_mode(const GraphDev &g, const LevelDesc &d, const int32_t *F, int64_t ld,
                        const int32_t *pstart, const uint8_t *pslot, const int64_t *woff,
                        const int32_t *tile_row, int64_t wa, int32_t W, int32_t tiles,
                        int32_t block, size_t smem, unsigned long long *lookback,
                        const RowSink &sink, bool stage, int32_t spin_limit, int32_t stall_tile,
                        cudaStream_t s) {
-  static unsigned long long attr_set = 0;  // bit per device
-  static int per_sm_cache[64][2] = {};     // (block, smem) of the last occupancy query
-  static size_t smem_cache[64] = {};
-  static int blocks_cache[64] = {};
+  static std::atomic<unsigned long long> attr_set{0};  // bit per device
+  // occupancy of the last (block, smem) this host thread launched with
+  static thread_local int per_sm_cache[64][2] = {};
+  static thread_local size_t smem_cache[64] = {};
+  static thread_local int blocks_cache[64] = {};
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int di = dev & 63;
-  if (!((attr_set >> di) & 1ull)) {
-    cudaFuncSetAttribute(k_extend_fused<kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)kFusedSmemAttr);
-    attr_set |= 1ull << di;
+  if (!((attr_set.load() >> di) & 1ull)) {
+    cudaFuncSetAttribute(k_extend_fused<kMode, kMaxThreads>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmemAttr);
+    attr_set.fetch_or(1ull << di);
   }
   int per_sm = 0;
   if (blocks_cache[di] == block && smem_cache[di] == smem && per_sm_cache[di][0]) {
     per_sm = per_sm_cache[di][1];
   } else {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_extend_fused<kMode>, block, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_extend_fused<kMode, kMaxThreads>,
+                                                  block, smem);
     blocks_cache[di] = block;
     smem_cache[di] = smem;
     per_sm_cache[di][0] = 1;
     per_sm_cache[di][1] = per_sm;
   }
   const int64_t grid = std::min<int64_t>(tiles, (int64_t)std::max(per_sm, 1) * sms);
-  k_extend_fused<kMode><<<(unsigned)grid, block, smem, s>>>(g, d, F, (int32_t)ld, pstart, pslot,
-                                                            woff, tile_row, wa, W, tiles,
-                                                            lookback, sink, stage, spin_limit,
-                                                            stall_tile);
+  k_extend_fused<kMode, kMaxThreads><<<(unsigned)grid, block, smem, s>>>(
+      g, d, F, (int32_t)ld, pstart, pslot, woff, tile_row, wa, W, tiles, lookback, sink, stage,
+      spin_limit, stall_tile);
 }
 }  // namespace
 
@@ -1027,20 +1033,32 @@ void launch_extend_fused(const GraphDev &g, const LevelDesc &d, const int32_t *F
   // staged work offsets, two survivor-pair buffers, the warps' windows, and
   // (kSinkRows) the assembled result rows of one tile when they fit
   const int64_t items = (int64_t)block * kItemsPerThread;
-  const size_t base_ints = (size_t)(items + 4 + 4 * items + (block / 32) * kStage);
+  const size_t base_ints = (size_t)(items + 4 + 4 * items);
   size_t smem = base_ints * sizeof(int32_t);
+  // odd result widths are assembled in shared memory (even ones are stored
+  // directly)
   const size_t smem_rows = (base_ints + (size_t)items * sink.k) * sizeof(int32_t);
-  const bool stage = sink.mode == kSinkRows && smem_rows <= kFusedStageMax;
+  const bool stage = sink.mode == kSinkRows && (sink.k & 1) && smem_rows <= kFusedStageMax;
   if (stage) smem = smem_rows;
-  if (sink.mode == kSinkRows)
-    launch_fused_mode<kSinkRows>(g, d, F, ld, pstart, pslot, woff, tile_row, wa, W, T, block,
-                                 smem, lookback, sink, stage, spin_limit, stall_tile, s);
-  else if (sink.mode == kSinkKeys)
-    launch_fused_mode<kSinkKeys>(g, d, F, ld, pstart, pslot, woff, tile_row, wa, W, T, block,
-                                 smem, lookback, sink, false, spin_limit, stall_tile, s);
+  auto go = [&](auto small) {
+    constexpr int kMax = decltype(small)::value ? 256 : 1024;
+    if (sink.mode == kSinkRows)
+      launch_fused_mode<kSinkRows, kMax>(g, d, F, ld, pstart, pslot, woff, tile_row, wa, W, T,
+                                         block, smem, lookback, sink, stage, spin_limit,
+                                         stall_tile, s);
+    else if (sink.mode == kSinkKeys)
+      launch_fused_mode<kSinkKeys, kMax>(g, d, F, ld, pstart, pslot, woff, tile_row, wa, W, T,
+                                         block, smem, lookback, sink, false, spin_limit,
+                                         stall_tile, s);
+    else
+      launch_fused_mode<kSinkColumns, kMax>(g, d, F, ld, pstart, pslot, woff, tile_row, wa, W,
+                                            T, block, smem, lookback, sink, false, spin_limit,
+                                            stall_tile, s);
+  };
+  if (block <= 256)
+    go(std::true_type{});
   else
-    launch_fused_mode<kSinkColumns>(g, d, F, ld, pstart, pslot, woff, tile_row, wa, W, T, block,
-                                    smem, lookback, sink, false, spin_limit, stall_tile, s);
+    go(std::false_type{});
 }
 
 void launch_split_points(const int64_t *woff, int64_t R, int64_t step, int64_t J,

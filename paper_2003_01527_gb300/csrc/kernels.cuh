@@ -71,6 +71,9 @@ struct GraphDev {
   const int32_t *hub;
   const uint32_t *hub_bits;
   int32_t hub_words;
+  // label segments of the hubs' rows (null: none): the neighbours of hub h
+  // with label l are lcol[hub_seg[h * (num_labels + 1) + l] .. the next entry)
+  const int32_t *hub_seg;
 };
 
 // ---- launchers (all asynchronous on `s`) ----
@@ -94,6 +97,10 @@ int32_t label_segment_bits(int32_t n, int32_t num_labels);
 // bits[h * words ..], zeroed here) gets bit w for every neighbour w.
 void launch_hub_bitmaps(const GraphDev &g, const int32_t *hubs, int32_t H, int32_t words,
                         uint32_t *bits, cudaStream_t s);
+// seg[h * (g.num_labels + 1) + l] = start of label l's segment in the
+// (label, id)-ordered row of hub hubs[h] (l = num_labels: the row's end).
+void launch_hub_segments(const GraphDev &g, const int32_t *hubs, int32_t H, int32_t *seg,
+                         cudaStream_t s);
 
 // Writes k bitmaps of n_words words and adds |C(u)| into sizes[u].
 void launch_filter(const GraphDev &g, const FilterDesc &d, uint32_t *bitmaps,

@@ -10,6 +10,13 @@ namespace gsm {
 // [first, second) = the neighbours of x with label l (rows of lcol are
 // ordered by (label, id), so they are one contiguous, id-sorted segment).
 __device__ __forceinline__ int2 label_segment(const GraphDev &g, int32_t x, int32_t l) {
+  if (g.num_labels > 1 && g.hub_seg) {  // a hub: its segment table
+    const int32_t h = __ldg(g.hub + x);
+    if (h >= 0) {
+      const int32_t *t = g.hub_seg + (size_t)h * (g.num_labels + 1) + l;
+      return make_int2(__ldg(t), __ldg(t + 1));
+    }
+  }
   const int32_t b = __ldg(g.rp + x), e = __ldg(g.rp + x + 1);
   if (g.num_labels == 1) return make_int2(b, e);
   int32_t lo = b, len = e - b;  // first entry with label >= l

@@ -70,7 +70,8 @@ class gsm_options(ctypes.Structure):
                 ("block_size", ctypes.c_int32), ("chunk_rows", ctypes.c_int64),
                 ("filter_rounds", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("copy_slots", ctypes.c_int32), ("lookback_spin_limit", ctypes.c_int32),
-                ("lookahead", ctypes.c_int32), ("hub_bitmap_bytes", ctypes.c_int64)]
+                ("lookahead", ctypes.c_int32), ("hub_bitmap_bytes", ctypes.c_int64),
+                ("host_workers", ctypes.c_int32)]
 
 
 class gsm_kernel_stat(ctypes.Structure):
@@ -453,7 +454,7 @@ class Matcher:
                  torch_allocator: bool = True, filter_rounds: int = 0, copy_slots: int = 0,
                  two_pass: bool = False, compressed: bool = False, lookback_spin_limit: int = 0,
                  inject_lookback_stall: bool = False, alloc_hook=None, lookahead: int = 0,
-                 hub_bitmap_bytes: int = 0):
+                 hub_bitmap_bytes: int = 0, host_workers: int = 0):
         import torch
         self.device = device
         opt = gsm_default_options()
@@ -472,6 +473,7 @@ class Matcher:
         opt.lookback_spin_limit = lookback_spin_limit
         opt.lookahead = lookahead
         opt.hub_bitmap_bytes = hub_bitmap_bytes
+        opt.host_workers = host_workers
         opt.flags = (GSM_OPT_TIME_KERNELS if time_kernels else 0) | \
             (GSM_OPT_TWO_PASS if two_pass else 0) | \
             (GSM_OPT_COMPRESSED_FRONTIERS if compressed else 0) | \

@@ -70,14 +70,18 @@ def test_lookahead_results_equal_oracle(gsm_lib, cuda, labelled, opts):
 def test_lookahead_unlabelled_shapes(gsm_lib, cuda, unlabelled):
     g = unlabelled
     s = I.unlabelled_shapes()
-    cases = [(s["cycle5"], 64), (s["path6"], 4), (s["clique4"], g.n),
-             (I.query_from_edges(5, [(0, 1), (1, 2), (2, 3), (3, 4), (1, 3)]), 32)]
+    window = {u: (0, 512) for u in range(1, 6)}
+    cases = [(s["cycle5"], 16, None), (s["path6"], 4, window), (s["clique4"], g.n, None),
+             (I.query_from_edges(5, [(0, 1), (1, 2), (2, 3), (3, 4), (1, 3)]), 4, None)]
+    want = [oracle.match(g, q, root_range=(0, hi), ranges=rg)[:2] for q, hi, rg in cases]
     for la in (1, 2):
         m = gsm_lib.Matcher(device=0, lookahead=la)
         m.load_graph(g.row_ptr, g.col, g.labels)
-        for q, hi in cases:
-            want_count, want_rows, _ = oracle.match(g, q, root_range=(0, hi))
-            rows, count = m.enumerate(m.query(q.k, q.edges).restrict(0, 0, hi))
+        for (q, hi, rg), (want_count, want_rows) in zip(cases, want):
+            Q = m.query(q.k, q.edges).restrict(0, 0, hi)
+            for u, (a, b) in (rg or {}).items():
+                Q.restrict(u, a, b)
+            rows, count = m.enumerate(Q)
             assert count == want_count and np.array_equal(rows, want_rows)
         m.close()
 

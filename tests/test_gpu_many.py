@@ -29,7 +29,9 @@ def workload(g, num, seed):
 
 
 @pytest.mark.parametrize("opts", [{}, {"copy_slots": 1}, {"two_pass": True},
-                                  {"copy_slots": 2, "mem_budget_bytes": 1 << 21, "chunk_rows": 300}])
+                                  {"copy_slots": 2, "mem_budget_bytes": 1 << 21, "chunk_rows": 300},
+                                  {"host_workers": 1}, {"host_workers": 4, "copy_slots": 1},
+                                  {"host_workers": 3, "filter_rounds": 1}])
 def test_many_host_and_device_match_oracle(gsm_lib, cuda, rmat12, opts):
     g = rmat12
     items = workload(g, 12, seed=41)
@@ -65,7 +67,7 @@ def test_many_truncation_keeps_counts_and_prefixes(gsm_lib, cuda, rmat12):
     g = rmat12
     items = [it for it in workload(g, 6, seed=43) if it[1] >= 4][:3]
     assert items
-    m = gsm_lib.Matcher(device=0)
+    m = gsm_lib.Matcher(device=0, host_workers=2)
     m.load_graph(g.row_ptr, g.col, g.labels)
     Qs = [m.query(q.k, q.edges, q.labels) for q, _, _ in items]
     caps = [c // 2 for _, c, _ in items]
@@ -75,6 +77,30 @@ def test_many_truncation_keeps_counts_and_prefixes(gsm_lib, cuda, rmat12):
     assert counts.tolist() == [c for _, c, _ in items]
     for (q, c, rows), o, cap in zip(items, outs, caps):
         assert np.array_equal(o[:cap * q.k].reshape(cap, q.k), rows[:cap])
+    m.close()
+
+
+def test_many_workers_follow_graph_reloads(gsm_lib, cuda, rmat12):
+    """The listing workers share the resident graph: after the graph is
+    replaced they list against the new one."""
+    g = rmat12
+    items = workload(g, 6, seed=45)
+    tg, (tq,) = I.tiny_er_workload()
+    want_count, want_rows, _ = oracle.match(tg, tq)
+    m = gsm_lib.Matcher(device=0, host_workers=2)
+    for _ in range(2):
+        m.load_graph(g.row_ptr, g.col, g.labels)
+        Qs = [m.query(q.k, q.edges, q.labels) for q, _, _ in items]
+        outs = [np.zeros(max(c, 1) * q.k, np.int32) for q, c, _ in items]
+        assert m.enumerate_many(Qs, outs) == [c for _, c, _ in items]
+        for (q, c, rows), o in zip(items, outs):
+            assert np.array_equal(o[:c * q.k].reshape(c, q.k), rows)
+        m.load_graph(tg.row_ptr, tg.col, tg.labels)
+        Q = m.query(tq.k, tq.edges, tq.labels)
+        outs = [np.zeros(max(want_count, 1) * tq.k, np.int32) for _ in range(3)]
+        assert m.enumerate_many([Q, Q, Q], outs) == [want_count] * 3
+        for o in outs:
+            assert np.array_equal(o[:want_count * tq.k].reshape(-1, tq.k), want_rows)
     m.close()
 
 
