@@ -6,6 +6,8 @@ synchronisation of cudaMalloc/cudaFree) use this entry point with a graph
 they keep on the device.  Its bitmaps and sizes must equal those of
 gsm_candidates, call after call: the fixed device array it works in keeps the
 previous call's contents, so the second call checks that nothing stale leaks.
+They are also checked against the oracle's candidate predicate, with and
+without a restriction range on a query vertex.
 
 This file is collected last on purpose, and also passes alone in a fresh
 process.
@@ -13,6 +15,7 @@ process.
 import numpy as np
 import pytest
 
+import oracle
 from paper_2003_01527_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -54,6 +57,38 @@ def test_static_candidates_match_gsm_candidates_twice(gsm_lib, cuda):
                              out_bm, out_sizes, gl.GSM_OUT_DEVICE, s)
     assert np.array_equal(out_bm.cpu().numpy().view(np.uint32).reshape(q.k, -1), want_bm)
     assert np.array_equal(out_sizes.cpu().numpy().view(np.uint64), want_sizes)
+    m.close()
+
+
+def test_static_candidates_match_oracle_with_restrictions(gsm_lib, cuda, oracle_lib):
+    """The allocation-free filter against the oracle's candidate predicate
+    (bit for bit), unrestricted and with query vertices restricted to id
+    ranges, two calls in a row each."""
+    torch = cuda
+    gl = gsm_lib
+    n, rp, col = I.rmat(12, 16, *I.RMAT_ABC, seed=44)
+    g = I.make_graph(n, rp, col, I.zipf_labels(n, 4, 1.0, seed=45))
+    d = {k: torch.from_numpy(getattr(g, k)).cuda() for k in ("row_ptr", "col", "labels")}
+    m = gl.Matcher(device=0)
+    rng = np.random.default_rng(46)
+    nw = (g.n + 31) // 32
+    for rep in range(2):
+        q = I.random_walk_query(g, int(rng.integers(3, 8)), rng)
+        want = oracle.candidates(g, q).astype(bool)
+        for ranges in ({}, {0: (100, 1500), q.k - 1: (0, 2048)}):
+            Q = m.query(q.k, q.edges, q.labels)
+            w = want.copy()
+            for u, (lo, hi) in ranges.items():
+                Q.restrict(u, lo, hi)
+                w[u, :lo] = False
+                w[u, hi:] = False
+            got_bm = np.zeros((q.k, nw), dtype=np.uint32)
+            got_sizes = np.zeros(q.k, dtype=np.uint64)
+            torch.cuda.synchronize()
+            gl.gsm_candidates_static(g.n, g.nnz, d["row_ptr"], d["col"], d["labels"], Q.handle,
+                                     got_bm, got_sizes)
+            assert np.array_equal(gl.unpack_bitmaps(got_bm, g.n).astype(bool), w)
+            assert got_sizes.tolist() == w.sum(axis=1).tolist()
     m.close()
 
 
