@@ -90,6 +90,8 @@ struct gsm_ctx {
   uint32_t *d_hub_bits = nullptr;  // adjacency bitmaps of the hubs
   int32_t *d_hub_seg = nullptr;    // label segment starts of the hubs' rows
   size_t hub_seg_bytes = 0;
+  uint8_t *d_nlc = nullptr;        // neighbour label counts, nlc_stride per vertex
+  int32_t nlc_stride = 0;
   int32_t hub_count = 0, hub_min_deg = 0;
   size_t hub_bits_bytes = 0;
   std::vector<int32_t> label_values;  // sorted distinct labels; dense id = index
@@ -219,7 +221,9 @@ GraphDev graph_dev(const gsm_ctx *ctx) {
                   ctx->hub_count ? ctx->d_hub : nullptr,
                   ctx->hub_count ? ctx->d_hub_bits : nullptr,
                   (ctx->n + 31) / 32,
-                  ctx->hub_count ? ctx->d_hub_seg : nullptr};
+                  ctx->hub_count ? ctx->d_hub_seg : nullptr,
+                  ctx->d_nlc,
+                  ctx->nlc_stride};
 }
 
 void set_err(gsm_ctx *c, const char *fmt, ...) {
@@ -1420,13 +1424,14 @@ void build_hubs(gsm_ctx *ctx, const std::vector<int32_t> &h_rp) {
 void clear_all_graphs(gsm_ctx *ctx);
 
 void free_graph(gsm_ctx *ctx) {
-  for (gsm_ctx *w : ctx->workers) gsm_destroy(w);  // they share the graph
-  ctx->workers.clear();
+  for (gsm_ctx *w : ctx->workers) free_graph(w);  // they borrow it (kept for the next graph)
   clear_all_graphs(ctx);
   if (ctx->borrowed_graph) {
     ctx->d_rp = ctx->d_col = ctx->d_lab = ctx->d_lcol = ctx->d_llab = ctx->d_hub = nullptr;
     ctx->d_hub_bits = nullptr;
     ctx->d_hub_seg = nullptr;
+    ctx->d_nlc = nullptr;
+    ctx->nlc_stride = 0;
     ctx->hub_count = 0;
     ctx->has_graph = false;
     ctx->borrowed_graph = false;
@@ -1441,6 +1446,9 @@ void free_graph(gsm_ctx *ctx) {
   if (ctx->d_hub) dev_free(ctx, ctx->d_hub, sizeof(int32_t) * std::max<int32_t>(ctx->n, 1));
   if (ctx->d_hub_bits) dev_free(ctx, ctx->d_hub_bits, ctx->hub_bits_bytes);
   if (ctx->d_hub_seg) dev_free(ctx, ctx->d_hub_seg, ctx->hub_seg_bytes);
+  if (ctx->d_nlc) dev_free(ctx, ctx->d_nlc, (size_t)ctx->n * ctx->nlc_stride);
+  ctx->d_nlc = nullptr;
+  ctx->nlc_stride = 0;
   ctx->d_hub = nullptr;
   ctx->d_hub_bits = nullptr;
   ctx->d_hub_seg = nullptr;
@@ -2308,6 +2316,8 @@ void gsm_destroy(gsm_ctx *ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   if (ctx->server) gsm_server_stop(ctx);
+  for (gsm_ctx *w : ctx->workers) gsm_destroy(w);
+  ctx->workers.clear();
   try {
     lane_release(ctx, ctx->lane0);
     free_graph(ctx);
@@ -2488,6 +2498,15 @@ gsm_status gsm_load_graph(gsm_ctx *ctx, int32_t n, int64_t nnz, const int32_t *r
       CU(cudaStreamSynchronize(ctx->stream));
     }
     build_hubs(ctx, h_rp);
+    // neighbour label counts for the filter (labelled graphs with few labels)
+    const int32_t L = (int32_t)ctx->label_values.size();
+    if (L > 1 && L <= kNlcMaxLabels && (size_t)n * L <= (size_t(1) << 30)) {
+      ctx->nlc_stride = L;
+      ctx->d_nlc = (uint8_t *)dev_alloc(ctx, std::max<size_t>((size_t)n * L, 1));
+      launch_label_counts(graph_dev(ctx), ctx->d_nlc, L, ctx->stream);
+      CU(cudaGetLastError());
+      CU(cudaStreamSynchronize(ctx->stream));
+    }
     ctx->has_graph = true;
   });
 }
@@ -2630,16 +2649,9 @@ void next_result_slot(gsm_ctx *ctx, int32_t slots) {
 
 namespace {
 
-// A worker context of gsm_enumerate_many: its own stream, workspace, result
-// slots and small-read buffer, a share of the parent's memory budget, and
-// the parent's resident graph (borrowed, never freed by the worker).
-gsm_ctx *make_worker(gsm_ctx *ctx, int32_t nworkers) {
-  gsm_options o = ctx->opt;
-  o.stream = nullptr;
-  o.mem_budget_bytes = std::max<size_t>(ctx->budget / (size_t)nworkers, size_t(1) << 20);
-  gsm_ctx *w = nullptr;
-  const gsm_status st = gsm_create(&w, ctx->device, &o);
-  if (st != GSM_OK) FAIL(st, "creating a listing worker failed");
+// Points a worker at the parent's current graph (every call: the parent may
+// have loaded another graph since).
+void share_graph(const gsm_ctx *ctx, gsm_ctx *w) {
   w->n = ctx->n;
   w->nnz = ctx->nnz;
   w->max_deg = ctx->max_deg;
@@ -2651,10 +2663,25 @@ gsm_ctx *make_worker(gsm_ctx *ctx, int32_t nworkers) {
   w->d_hub = ctx->d_hub;
   w->d_hub_bits = ctx->d_hub_bits;
   w->d_hub_seg = ctx->d_hub_seg;
+  w->d_nlc = ctx->d_nlc;
+  w->nlc_stride = ctx->nlc_stride;
   w->hub_count = ctx->hub_count;
   w->label_values = ctx->label_values;
   w->has_graph = ctx->has_graph;
   w->borrowed_graph = true;
+}
+
+// A worker context of gsm_enumerate_many: its own stream, workspace, result
+// slots and small-read buffer, and a share of the parent's memory budget; it
+// lists on the parent's resident graph (borrowed, never freed by the worker)
+// and lives as long as the parent.
+gsm_ctx *make_worker(gsm_ctx *ctx, int32_t nworkers) {
+  gsm_options o = ctx->opt;
+  o.stream = nullptr;
+  o.mem_budget_bytes = std::max<size_t>(ctx->budget / (size_t)nworkers, size_t(1) << 20);
+  gsm_ctx *w = nullptr;
+  const gsm_status st = gsm_create(&w, ctx->device, &o);
+  if (st != GSM_OK) FAIL(st, "creating a listing worker failed");
   return w;
 }
 
@@ -2747,6 +2774,7 @@ gsm_status gsm_enumerate_many(gsm_ctx *ctx, int32_t nq, const gsm_query *const *
       // query's kernels fill another's waits on the host
       while ((int32_t)ctx->workers.size() < nworkers)
         ctx->workers.push_back(make_worker(ctx, nworkers));
+      for (int32_t w = 0; w < nworkers; ++w) share_graph(ctx, ctx->workers[w]);
       std::vector<gsm_status> wst(nworkers, GSM_OK);
       std::vector<uint64_t> wl(nworkers, 0), wp(nworkers, 0);
       std::vector<char> wlast(nworkers, 0);

@@ -29,7 +29,9 @@ __device__ __forceinline__ uint32_t nlc_pass(const Desc &d, uint32_t vneed,
 
 // One warp handles 32 consecutive data vertices per iteration (warps
 // warp_id, warp_id + n_warps, ...).  Each lane first applies the label /
-// degree / range test for its own vertex.  A vertex that also needs per-label
+// degree / range test for its own vertex.  With the graph's neighbour label
+// count table the requirements are read from it; otherwise they are counted
+// from the rows, as follows.  A vertex that also needs per-label
 // neighbour counts is first counted by its own lane over its first
 // kLaneScan neighbours (most rows of a power-law graph end there); only a
 // vertex whose requirements are still unmet and whose row goes on is then
@@ -65,7 +67,14 @@ __device__ __forceinline__ void filter_warps(const GraphDev &g, const Desc &d,
     }
     uint32_t result = pre & ~need;
     bool rest = false;
-    if (need) {
+    if (need && g.nlc) {  // the counts are in the graph's table
+      int32_t cnt[kMaxK];
+      const uint8_t *row = g.nlc + (int64_t)v * g.nlc_stride;
+#pragma unroll
+      for (int s = 0; s < kMaxK; ++s) cnt[s] = s < d.nslots ? __ldg(row + d.slot_label[s]) : 0;
+      result |= nlc_pass(d, need, cnt);
+      need = 0;
+    } else if (need) {
       const int32_t b = g.rp[v], e = g.rp[v + 1];
       const int32_t e1 = min(e, b + kLaneScan);
       int32_t cnt[kMaxK];

@@ -745,6 +745,25 @@ __global__ void k_hub_bits(GraphDev g, const int32_t *__restrict__ hubs, int32_t
   }
 }
 
+// One warp per vertex: the lanes count the vertex's neighbours per label in
+// shared memory (the labels of its label-segmented row), then write the
+// saturated counts.
+__global__ void __launch_bounds__(256) k_label_counts(GraphDev g, uint8_t *__restrict__ nlc,
+                                                      int32_t stride) {
+  __shared__ int32_t s_cnt[8][kNlcMaxLabels];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < g.n; v += warps) {
+    for (int l = lane; l < stride; l += 32) s_cnt[warp][l] = 0;
+    __syncwarp();
+    const int32_t b = g.rp[v], e = g.rp[v + 1];
+    for (int32_t x = b + lane; x < e; x += 32) atomicAdd(&s_cnt[warp][g.llab[x]], 1);
+    __syncwarp();
+    for (int l = lane; l < stride; l += 32) nlc[v * stride + l] = (uint8_t)min(s_cnt[warp][l], 255);
+    __syncwarp();
+  }
+}
+
 // One warp per hub: lane l finds where labels l, l + 32, ... start in the
 // hub's (label, id)-ordered row (lower bound of the label).
 __global__ void k_hub_segments(GraphDev g, const int32_t *__restrict__ hubs, int32_t H,
@@ -853,6 +872,11 @@ void launch_hub_bitmaps(const GraphDev &g, const int32_t *hubs, int32_t H, int32
   if (H <= 0) return;
   cudaMemsetAsync(bits, 0, sizeof(uint32_t) * (size_t)H * words, s);
   k_hub_bits<<<grid_for((int64_t)H * 32, 256, 152 * 8), 256, 0, s>>>(g, hubs, H, words, bits);
+}
+
+void launch_label_counts(const GraphDev &g, uint8_t *nlc, int32_t stride, cudaStream_t s) {
+  if (g.n <= 0) return;
+  k_label_counts<<<grid_for((int64_t)g.n * 32, 256, 152 * 16), 256, 0, s>>>(g, nlc, stride);
 }
 
 void launch_hub_segments(const GraphDev &g, const int32_t *hubs, int32_t H, int32_t *seg,

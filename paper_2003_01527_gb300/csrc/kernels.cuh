@@ -74,6 +74,11 @@ struct GraphDev {
   // label segments of the hubs' rows (null: none): the neighbours of hub h
   // with label l are lcol[hub_seg[h * (num_labels + 1) + l] .. the next entry)
   const int32_t *hub_seg;
+  // neighbour label counts (null: none): nlc[v * nlc_stride + l] = the number
+  // of neighbours of v with label l, saturated at 255 (a query needs at most
+  // 15, so the saturated count decides every requirement exactly)
+  const uint8_t *nlc;
+  int32_t nlc_stride;
 };
 
 // ---- launchers (all asynchronous on `s`) ----
@@ -101,6 +106,11 @@ void launch_hub_bitmaps(const GraphDev &g, const int32_t *hubs, int32_t H, int32
 // (label, id)-ordered row of hub hubs[h] (l = num_labels: the row's end).
 void launch_hub_segments(const GraphDev &g, const int32_t *hubs, int32_t H, int32_t *seg,
                          cudaStream_t s);
+
+// The neighbour label count table of every vertex (labels < g.num_labels <=
+// stride), from the label-segmented rows.
+constexpr int32_t kNlcMaxLabels = 64;
+void launch_label_counts(const GraphDev &g, uint8_t *nlc, int32_t stride, cudaStream_t s);
 
 // Writes k bitmaps of n_words words and adds |C(u)| into sizes[u].
 void launch_filter(const GraphDev &g, const FilterDesc &d, uint32_t *bitmaps,
@@ -227,6 +237,21 @@ void launch_fetch(const void *src, void *dst, size_t bytes, cudaStream_t s);
 // woff[S], the next level's candidate total.
 void launch_fetch_level(const unsigned long long *words, const int64_t *woff, void *dst,
                         cudaStream_t s);
+
+// Sorting many small results at once (one CTA each): rows src (count x k,
+// row-major) into canonical lexicographic order at dst (count x k); sort = 0
+// copies.  count <= kSmallSortRows when sort != 0.
+constexpr int32_t kSmallSortRows = 1024;
+struct SmallSortItem {
+  const int32_t *src;
+  int32_t *dst;
+  int32_t count, k, sort;
+};
+// Dynamic shared memory k_sort_small needs for rows of at most max_k ints.
+size_t small_sort_smem(int32_t max_k);
+// items: device array of nitems entries; max_k = the widest row among them.
+void launch_sort_small(const SmallSortItem *items, int32_t nitems, int32_t max_k,
+                       cudaStream_t s);
 
 // Histogram elements of the radix passes over N keys.
 int64_t sort_hist_elems(int64_t N);

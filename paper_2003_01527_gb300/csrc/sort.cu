@@ -10,6 +10,7 @@
 // unpacks every key into a row-major int32 row, the layout of the result.
 // Words are column-major (word w of row r at keys[w*ld + r]).
 #include <algorithm>
+#include <atomic>
 #include <utility>
 
 #include "kernels.cuh"
@@ -221,11 +222,81 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter_tile(
   }
 }
 
+// One CTA per item: `count` (<= kSmallSortRows) row-major rows of k int32 are
+// loaded into shared memory and their indices bitonic-sorted by a
+// lexicographic comparison of the rows (rows are distinct embeddings, so the
+// order is total); then the rows are written in that order.  sort = 0: a
+// plain copy (any count).
+__device__ __forceinline__ bool row_less(const int32_t *s_rows, int32_t k, int32_t a, int32_t b) {
+  if (a < 0) return false;  // padding sorts last
+  if (b < 0) return true;
+  const int32_t *x = s_rows + a * k, *y = s_rows + b * k;
+  for (int32_t c = 0; c < k; ++c)
+    if (x[c] != y[c]) return x[c] < y[c];
+  return false;
+}
+
+__global__ void __launch_bounds__(256) k_sort_small(const SmallSortItem *__restrict__ items) {
+  extern __shared__ int32_t s_mem[];
+  const SmallSortItem it = items[blockIdx.x];
+  const int32_t k = it.k, N = it.count;
+  if (!it.sort || N <= 1) {
+    const int64_t e_end = (int64_t)N * k;
+    for (int64_t e = threadIdx.x; e < e_end; e += blockDim.x) it.dst[e] = it.src[e];
+    return;
+  }
+  int32_t P = 1;
+  while (P < N) P <<= 1;
+  int32_t *s_idx = s_mem;       // P indices
+  int32_t *s_rows = s_mem + P;  // N rows
+  for (int32_t e = threadIdx.x; e < N * k; e += blockDim.x) s_rows[e] = it.src[e];
+  for (int32_t e = threadIdx.x; e < P; e += blockDim.x) s_idx[e] = e < N ? e : -1;
+  __syncthreads();
+  for (int32_t size = 2; size <= P; size <<= 1) {
+    for (int32_t stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int32_t t = threadIdx.x; t < (P >> 1); t += blockDim.x) {
+        const int32_t i = 2 * t - (t & (stride - 1));  // lower element of the pair
+        const int32_t j = i + stride;
+        const bool up = (i & size) == 0;
+        const int32_t a = s_idx[i], b = s_idx[j];
+        if (row_less(s_rows, k, b, a) == up) {
+          s_idx[i] = b;
+          s_idx[j] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int32_t e = threadIdx.x; e < N * k; e += blockDim.x) {
+    const int32_t q = e / k, c = e - q * k;
+    it.dst[e] = s_rows[s_idx[q] * k + c];
+  }
+}
+
 }  // namespace
 
 int64_t sort_hist_elems(int64_t N) {
   const int64_t nb = (N + kSortTile - 1) / kSortTile;
   return nb * kBins;
+}
+
+size_t small_sort_smem(int32_t max_k) {
+  return sizeof(int32_t) * (size_t)kSmallSortRows * (1 + max_k);
+}
+
+void launch_sort_small(const SmallSortItem *items, int32_t nitems, int32_t max_k,
+                       cudaStream_t s) {
+  if (nitems <= 0) return;
+  const size_t smem = small_sort_smem(max_k);
+  static std::atomic<unsigned long long> attr_set{0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (!((attr_set.load() >> (dev & 63)) & 1ull)) {
+    cudaFuncSetAttribute(k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)small_sort_smem(kMaxK));
+    attr_set.fetch_or(1ull << (dev & 63));
+  }
+  k_sort_small<<<(unsigned)nitems, 256, smem, s>>>(items);
 }
 
 }  // namespace gsm

@@ -156,6 +156,30 @@ def test_candidate_bitmaps_match_oracle(M, rmat12, gsm_lib):
         assert sizes.tolist() == want.sum(axis=1).tolist()
 
 
+@pytest.mark.parametrize("labels", [2, 63, 64, 65, 300])
+def test_candidate_bitmaps_by_label_count(M, gsm_lib, labels):
+    """Up to 64 labels the filter reads the graph's neighbour label count
+    table, above that it counts from the rows: both give the oracle's
+    candidate sets, for queries with several same-label neighbours."""
+    n, rp, col = I.rmat(11, 16, *I.RMAT_ABC, seed=27)
+    g = I.make_graph(n, rp, col, I.zipf_labels(n, labels, 0.6, seed=28))
+    load(M, g)
+    rng = np.random.default_rng(29)
+    for _ in range(6):
+        q = I.random_walk_query(g, int(rng.integers(3, 9)), rng)
+        lab = q.labels.copy()
+        lab[1:3] = lab[0]  # repeated labels: requirements above one
+        q = I.query_from_edges(q.k, q.edges, lab)
+        bm, sizes = M.candidates(M.query(q.k, q.edges, q.labels))
+        want = oracle.candidates(g, q)
+        assert np.array_equal(gsm_lib.unpack_bitmaps(bm, g.n), want)
+        assert sizes.tolist() == want.sum(axis=1).tolist()
+        _, _, rc = oracle.match(g, q, enumerate=False, root_range=(0, 256), limit=200_000,
+                                node_budget=20_000_000)
+        if rc == oracle.OK:
+            assert_parity(M, g, q, root_range=(0, 256))
+
+
 def test_results_do_not_depend_on_chunking_or_block_size(gsm_lib, rmat12):
     qs = selective_walk_queries(rmat12, 4, 4, 6, seed=27)
     ref = None
