@@ -80,6 +80,10 @@ typedef void (*gsm_free_fn)(void *alloc_ctx, void *ptr, size_t bytes, void *stre
  * (lookback_spin_limit) and the call returns GSM_ERR_TIMEOUT.  Nothing hangs
  * and every row stays inside its buffer; the context stays usable. */
 #define GSM_OPT_INJECT_LOOKBACK_STALL 8
+/* The same for the final sort of listing calls: in every single-sweep pass
+ * of the canonical row sort the second tile never publishes its digit
+ * counts; the call returns GSM_ERR_TIMEOUT and the context stays usable. */
+#define GSM_OPT_INJECT_SORT_STALL 16
 
 typedef struct gsm_options {
   /* Cap on device memory for intermediate frontiers and scratch, in bytes.

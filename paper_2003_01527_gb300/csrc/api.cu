@@ -147,6 +147,9 @@ struct gsm_ctx {
   // (the copy engines stay free for result copies in flight)
   int64_t *h_stage = nullptr;
   void *d_stage = nullptr;  // device view of h_stage
+  // mapped flag words after the 4 KB of h_stage: [0] = a sort's look-back
+  // wait ran out (set by the sort kernels, read and cleared by the host)
+  uint32_t *h_flags = nullptr, *d_flags = nullptr;
   int32_t num_sms = 0;
 
   // batched form: per-label sorted degrees (order estimates without the
@@ -180,8 +183,12 @@ struct gsm_ctx {
     BatchStep *h_state = nullptr;
     std::vector<std::array<int32_t, kMaxK>> orders;
     std::vector<int32_t> lists;
+    // device buffers of the canonical sorts: keys (2), sort scratch, the
+    // small-sort items, the staged rows of host results
     void *srt[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     size_t srt_cap[5] = {0, 0, 0, 0, 0};
+    gsm::SmallSortItem *h_items = nullptr;  // pinned staging of the items
+    size_t h_items_cap = 0;
     std::map<std::tuple<int32_t, int32_t, int32_t, int32_t, int32_t, int32_t>, cudaGraphExec_t>
         graphs;
     // a batch in flight (server): which requests, how many queries
@@ -404,6 +411,23 @@ void fetch(gsm_ctx *ctx, const void *dptr, size_t bytes) {
   ctx->run.kernel_launches += 1;
   CU(cudaGetLastError());
   CU(cudaStreamSynchronize(ctx->stream));
+}
+
+// GSM_OPT_INJECT_SORT_STALL: the tile of every sort pass that withholds its
+// counts (-1: none).
+int32_t sort_stall_tile(const gsm_ctx *ctx) {
+  return (ctx->opt.flags & GSM_OPT_INJECT_SORT_STALL) ? 1 : -1;
+}
+
+// Raises GSM_ERR_TIMEOUT if a sort's look-back wait ran out since the last
+// check (and clears the flag); call once the sort's stream has been
+// synchronised.
+void check_sort_flag(gsm_ctx *ctx) {
+  volatile uint32_t *f = ctx->h_flags;
+  if (f && f[0]) {
+    f[0] = 0;
+    FAIL(GSM_ERR_TIMEOUT, "a sort tile waited too long for its predecessors");
+  }
 }
 
 int64_t read_i64(gsm_ctx *ctx, const int64_t *dptr) {
@@ -1312,21 +1336,17 @@ void run_query(gsm_ctx *ctx, const gsm_query *q, bool enumerate, int32_t *out, u
     const size_t key_bytes = (size_t)R.acc_ld * nw * sizeof(uint64_t);
     ensure_buf(ctx, &ctx->sort_keys, &ctx->sort_keys_cap, key_bytes, false, 0);
     ensure_buf(ctx, &ctx->acc[1], &ctx->acc_cap[1], bytes, false, 0);
-    const int64_t H = sort_hist_elems((int64_t)total);
-    Carve cv;
-    const size_t o_h = cv.add<int32_t>(H), o_ho = cv.add<int64_t>(H + 1),
-                 o_t = cv.add<int64_t>(scan_tmp_elems(H));
     // outside the budget, like the result buffers it serves
-    ensure_buf(ctx, &ctx->sort_tmp, &ctx->sort_tmp_cap, cv.off, false, 0);
-    char *sc = (char *)ctx->sort_tmp;
+    ensure_buf(ctx, &ctx->sort_tmp, &ctx->sort_tmp_cap,
+               sort_scratch_bytes((int64_t)total, q->k, R.key_bits, sort_cols), false, 0);
     const int digits = (sort_cols * R.key_bits + 7) / 8;
     const double moved = 2.0 * (double)total * nw * sizeof(uint64_t) * digits;
     int launches = 0;
     timed(ctx, K_SORT, moved + (double)bytes, total, 0, [&] {
       launches = launch_sort_rows_packed(nullptr, 0, (int64_t)total, q->k, R.key_bits, sort_cols,
                                          (uint64_t *)ctx->acc[0], (uint64_t *)ctx->sort_keys,
-                                         R.acc_ld, (int32_t *)ctx->acc[1], (int32_t *)(sc + o_h),
-                                         (int64_t *)(sc + o_ho), (int64_t *)(sc + o_t),
+                                         R.acc_ld, (int32_t *)ctx->acc[1], ctx->sort_tmp,
+                                         R.spin_limit, ctx->d_flags, sort_stall_tile(ctx),
                                          ctx->stream);
     });
     ctx->run.kernel_launches += launches;
@@ -1352,6 +1372,7 @@ void run_query(gsm_ctx *ctx, const gsm_query *q, bool enumerate, int32_t *out, u
     if (ncopy)
       CU(cudaMemcpyAsync(out, rows, (size_t)ncopy * q->k * sizeof(int32_t), kind, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
+    check_sort_flag(ctx);
   }
   *truncated = total > cap_rows;
 }
@@ -1507,6 +1528,9 @@ void lane_release(gsm_ctx *ctx, Lane &L) {
   if (L.h_counts) cudaFreeHost(L.h_counts);
   if (L.h_overflow) cudaFreeHost(L.h_overflow);
   if (L.h_state) cudaFreeHost(L.h_state);
+  if (L.h_items) cudaFreeHost(L.h_items);
+  L.h_items = nullptr;
+  L.h_items_cap = 0;
   for (int j = 0; j < 5; ++j)
     if (L.srt[j]) dev_free(ctx, L.srt[j], L.srt_cap[j]);
   if (L.bitmaps) dev_free(ctx, L.bitmaps, L.bitmaps_cap);
@@ -1639,15 +1663,13 @@ void canonical_rows(gsm_ctx *ctx, Lane &L, const int32_t *src, int64_t N, int32_
   int32_t bits = 1;
   while (bits < 31 && (int64_t(1) << bits) < ctx->n) ++bits;
   const int32_t nw = packed_words(k, bits);
-  const int64_t H = sort_hist_elems(N);
   uint64_t *ka = (uint64_t *)lane_srt(ctx, L, 0, (size_t)N * nw * sizeof(uint64_t));
   uint64_t *kb = (uint64_t *)lane_srt(ctx, L, 1, (size_t)N * nw * sizeof(uint64_t));
-  int32_t *hist = (int32_t *)lane_srt(ctx, L, 2, (size_t)H * sizeof(int32_t));
-  int64_t *hoff = (int64_t *)lane_srt(
-      ctx, L, 3, (size_t)(H + 1 + scan_tmp_elems(H) + 1) * sizeof(int64_t));
+  void *scratch = lane_srt(ctx, L, 2, sort_scratch_bytes(N, k, bits, sort_cols));
   launch_pack_rows(src, N, k, bits, ka, N, L.stream);
-  launch_sort_rows_packed(nullptr, 0, N, k, bits, sort_cols, ka, kb, N, dst, hist, hoff,
-                          hoff + H + 1, L.stream);
+  launch_sort_rows_packed(nullptr, 0, N, k, bits, sort_cols, ka, kb, N, dst, scratch,
+                          ctx->opt.lookback_spin_limit, ctx->d_flags, sort_stall_tile(ctx),
+                          L.stream);
   CU(cudaGetLastError());
 }
 
@@ -1899,36 +1921,138 @@ void single_query_rows(gsm_ctx *ctx, const gsm_query *q, bool on_device, gsm_res
   CU(cudaStreamSynchronize(ctx->stream));
 }
 
+// Result rows of a listing batch share one allocation (host, or device
+// memory from the context's allocator): every result's rows pointer points
+// into the block, which is released with the last of them.  Keyed by the
+// rows pointer; process-wide, so host rows can be released without a
+// context.
+struct RowBlock {
+  void *base;
+  size_t bytes;
+  bool on_device;
+  int32_t refs;
+};
+std::mutex g_blocks_mu;
+std::unordered_map<const void *, RowBlock *> g_block_of;
+
+// Drops one reference to the block holding p.  Returns false if p is not in
+// a block; otherwise *last = the block to free (null while others remain).
+bool block_unref(const void *p, RowBlock **last) {
+  std::lock_guard<std::mutex> lk(g_blocks_mu);
+  auto it = g_block_of.find(p);
+  if (it == g_block_of.end()) return false;
+  RowBlock *b = it->second;
+  g_block_of.erase(it);
+  *last = --b->refs == 0 ? b : nullptr;
+  return true;
+}
+
+// Host rows handed out by the library (a block member or a malloc'd array).
+void release_host_rows(int32_t *p) {
+  if (!p) return;
+  RowBlock *b = nullptr;
+  if (!block_unref(p, &b)) {
+    std::free(p);
+    return;
+  }
+  if (b) {
+    std::free(b->base);
+    delete b;
+  }
+}
+
 void release_rows(gsm_ctx *ctx, gsm_result *r) {
   if (!r->rows) return;
-  if (r->on_device)
+  RowBlock *b = nullptr;
+  if (block_unref(r->rows, &b)) {
+    if (b) {
+      if (b->on_device)
+        dev_free(ctx, b->base, b->bytes);
+      else
+        std::free(b->base);
+      delete b;
+    }
+  } else if (r->on_device) {
     dev_free(ctx, r->rows, (size_t)r->count * r->k * sizeof(int32_t));
-  else
+  } else {
     std::free(r->rows);
+  }
   r->rows = nullptr;
 }
 
-// Rows of selected query t of a finished listing batch on lane L (its
-// arena rows canonicalised) into r: host memory, or device memory.
-void lane_query_rows(gsm_ctx *ctx, Lane &L, int32_t t, int64_t arena_off, uint64_t count,
-                     int32_t k, bool on_device, gsm_result *r) {
-  r->count = count;
-  r->k = k;
-  r->on_device = on_device ? 1 : 0;
-  r->rows = nullptr;
-  if (count == 0) return;
-  const size_t bytes = (size_t)count * k * sizeof(int32_t);
-  const int32_t *src = L.a.final_rows + arena_off;
-  if (on_device) {
-    r->rows = (int32_t *)dev_alloc(ctx, bytes);
-    canonical_rows(ctx, L, src, (int64_t)count, k, L.orders[t].data(), r->rows);
-  } else {
-    int32_t *stage = (int32_t *)lane_srt(ctx, L, 4, bytes);
-    canonical_rows(ctx, L, src, (int64_t)count, k, L.orders[t].data(), stage);
-    r->rows = (int32_t *)std::malloc(bytes);
-    if (!r->rows) FAIL(GSM_ERR_OOM, "host allocation of %zu bytes failed", bytes);
-    CU(cudaMemcpyAsync(r->rows, stage, bytes, cudaMemcpyDeviceToHost, L.stream));
+// Rows of the selected queries t of a finished listing batch on lane L with
+// want[t] (k >= 2), canonicalised into results[L.sel[t]]: all in one block
+// (host, or device memory from the context's allocator), each result at a
+// 16-byte aligned offset.  Results of at most kSmallSortRows rows are sorted
+// together by one launch (a CTA each), larger ones by the radix sort.  Host
+// results are staged on the device and copied back in one transfer; the
+// caller synchronises the lane's stream.
+void lane_batch_rows(gsm_ctx *ctx, Lane &L, const std::vector<int64_t> &off,
+                     const std::vector<char> &want, bool on_device, gsm_result *results) {
+  std::vector<int32_t> ts;
+  std::vector<size_t> pos;
+  size_t total = 0;
+  for (int32_t t = 0; t < L.m; ++t) {
+    const int32_t k = L.h_qs[t].k;
+    if (!want[t] || k < 2) continue;
+    gsm_result &r = results[L.sel[t]];
+    r.count = L.h_counts[t];
+    r.k = k;
+    r.on_device = on_device ? 1 : 0;
+    r.rows = nullptr;
+    if (r.count == 0) continue;
+    ts.push_back(t);
+    pos.push_back(total);
+    total += ((size_t)r.count * k + 3) & ~size_t(3);
   }
+  if (ts.empty()) return;
+  const size_t bytes = total * sizeof(int32_t);
+  void *base = on_device ? dev_alloc(ctx, bytes) : std::malloc(bytes);
+  if (!base) FAIL(GSM_ERR_OOM, "host allocation of %zu bytes failed", bytes);
+  {
+    RowBlock *b = new RowBlock{base, bytes, on_device, (int32_t)ts.size()};
+    std::lock_guard<std::mutex> lk(g_blocks_mu);
+    for (size_t i = 0; i < ts.size(); ++i) {
+      int32_t *p = (int32_t *)base + pos[i];
+      results[L.sel[ts[i]]].rows = p;
+      g_block_of[p] = b;
+    }
+  }
+  int32_t *dst = on_device ? (int32_t *)base : (int32_t *)lane_srt(ctx, L, 4, bytes);
+  std::vector<SmallSortItem> items;
+  int32_t max_k = 2;
+  for (size_t i = 0; i < ts.size(); ++i) {
+    const int32_t t = ts[i], k = L.h_qs[t].k;
+    const int64_t N = (int64_t)L.h_counts[t];
+    const int32_t *src = L.a.final_rows + off[t];
+    const int32_t sort_cols = unsorted_columns(k, L.orders[t].data());
+    if (N <= kSmallSortRows) {
+      items.push_back({src, dst + pos[i], (int32_t)N, k, sort_cols > 0 ? 1 : 0});
+      max_k = std::max(max_k, k);
+    } else if (sort_cols == 0) {
+      CU(cudaMemcpyAsync(dst + pos[i], src, (size_t)N * k * sizeof(int32_t),
+                         cudaMemcpyDeviceToDevice, L.stream));
+    } else {
+      canonical_rows(ctx, L, src, N, k, L.orders[t].data(), dst + pos[i]);
+    }
+  }
+  if (!items.empty()) {
+    const size_t ib = items.size() * sizeof(SmallSortItem);
+    if (L.h_items_cap < ib) {
+      CU(cudaStreamSynchronize(L.stream));  // an earlier upload may still read it
+      if (L.h_items) cudaFreeHost(L.h_items);
+      L.h_items = nullptr;
+      L.h_items_cap = 0;
+      CU(cudaHostAlloc(&L.h_items, std::max(ib, size_t(4096)), cudaHostAllocDefault));
+      L.h_items_cap = std::max(ib, size_t(4096));
+    }
+    std::memcpy(L.h_items, items.data(), ib);
+    void *d_items = lane_srt(ctx, L, 3, ib);
+    CU(cudaMemcpyAsync(d_items, L.h_items, ib, cudaMemcpyHostToDevice, L.stream));
+    launch_sort_small((const SmallSortItem *)d_items, (int32_t)items.size(), max_k, L.stream);
+    CU(cudaGetLastError());
+  }
+  if (!on_device) CU(cudaMemcpyAsync(base, dst, bytes, cudaMemcpyDeviceToHost, L.stream));
 }
 
 void run_batch(gsm_ctx *ctx, const gsm_query *const *qs, int32_t nq, uint64_t *counts,
@@ -2007,10 +2131,10 @@ void run_batch(gsm_ctx *ctx, const gsm_query *const *qs, int32_t nq, uint64_t *c
           const int32_t j = L.sel[t];
           if (qs[j]->k == 1)  // one-vertex queries: their candidate list
             single_query_rows(ctx, qs[j], on_device, &results[j]);
-          else
-            lane_query_rows(ctx, L, t, off[t], L.h_counts[t], qs[j]->k, on_device, &results[j]);
         }
+        lane_batch_rows(ctx, L, off, std::vector<char>(L.m, 1), on_device, results);
         CU(cudaStreamSynchronize(L.stream));
+        check_sort_flag(ctx);
       }
     }
   } catch (...) {
@@ -2103,15 +2227,18 @@ void server_complete(gsm_ctx *ctx, gsm_ctx::Server &S, Lane &L) {
         for (int32_t t = 0; t < L.m; ++t) counts[L.sel[t]] = L.h_counts[t];
         if (L.enumerate || std::count(modes.begin(), modes.end(), GSM_MODE_ENUMERATE)) {
           const std::vector<int64_t> off = lane_row_offsets(L, L.h_counts);
+          std::vector<char> want(L.m, 0);
           for (int32_t t = 0; t < L.m; ++t) {
             const int32_t j = L.sel[t];
             if (modes[j] != GSM_MODE_ENUMERATE) continue;
             if (qs[j]->k == 1)
               single_query_rows(ctx, qs[j], false, &res[j]);
             else
-              lane_query_rows(ctx, L, t, off[t], L.h_counts[t], qs[j]->k, false, &res[j]);
+              want[t] = 1;
           }
+          lane_batch_rows(ctx, L, off, want, false, res.data());
           CU(cudaStreamSynchronize(L.stream));
+          check_sort_flag(ctx);
         }
       }
     } catch (...) {
@@ -2298,8 +2425,11 @@ gsm_status gsm_create(gsm_ctx **out, int32_t device, const gsm_options *opt) {
     ctx->budget = ctx->opt.mem_budget_bytes ? ctx->opt.mem_budget_bytes : free_b / 10 * 9;
     ctx->scratch_limit = ctx->budget / 4;
     ctx->stack_limit = ctx->budget - ctx->scratch_limit;
-    CU(cudaHostAlloc(&ctx->h_stage, 4096, cudaHostAllocMapped));
+    CU(cudaHostAlloc(&ctx->h_stage, 4096 + 64, cudaHostAllocMapped));
     CU(cudaHostGetDevicePointer(&ctx->d_stage, ctx->h_stage, 0));
+    ctx->h_flags = (uint32_t *)((char *)ctx->h_stage + 4096);
+    ctx->d_flags = (uint32_t *)((char *)ctx->d_stage + 4096);
+    std::memset(ctx->h_flags, 0, 64);
     CU(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device));
     ctx->d_small = (unsigned long long *)dev_alloc(ctx, 256);
   });
@@ -2480,20 +2610,19 @@ gsm_status gsm_load_graph(gsm_ctx *ctx, int32_t n, int64_t nnz, const int32_t *r
       } else {
         const int32_t bits = label_segment_bits(n, (int32_t)ctx->label_values.size());
         const int32_t nw = packed_words(3, bits);
-        const int64_t H = sort_hist_elems(nnz);
         Carve cv;
         const size_t o_cols = cv.add<int32_t>(3 * nnz), o_rows = cv.add<int32_t>(3 * nnz),
-                     o_keys = cv.add<uint64_t>(2 * nnz * nw), o_h = cv.add<int32_t>(H),
-                     o_ho = cv.add<int64_t>(H + 1), o_t = cv.add<int64_t>(scan_tmp_elems(H));
+                     o_keys = cv.add<uint64_t>(2 * nnz * nw),
+                     o_s = cv.add<char>((int64_t)sort_scratch_bytes(nnz, 3, bits, 2));
         char *tmpbuf = (char *)dev_alloc(ctx, cv.off);
         GraphDev g = graph_dev(ctx);
         launch_label_segments(g, (int32_t)ctx->label_values.size(), (int32_t *)(tmpbuf + o_cols),
                               (uint64_t *)(tmpbuf + o_keys), (int32_t *)(tmpbuf + o_rows),
-                              (int32_t *)(tmpbuf + o_h), (int64_t *)(tmpbuf + o_ho),
-                              (int64_t *)(tmpbuf + o_t), ctx->d_lcol, ctx->d_llab, ctx->stream);
+                              tmpbuf + o_s, ctx->d_flags, ctx->d_lcol, ctx->d_llab, ctx->stream);
         CU(cudaGetLastError());
         CU(cudaStreamSynchronize(ctx->stream));
         dev_free(ctx, tmpbuf, cv.off);
+        check_sort_flag(ctx);
       }
       CU(cudaStreamSynchronize(ctx->stream));
     }
@@ -2733,6 +2862,7 @@ void list_many(gsm_ctx *ctx, ManyState &M, uint64_t *launches, uint64_t *peak, b
   CU(cudaStreamSynchronize(c->copy_stream));
   CU(cudaStreamSynchronize(c->stream));
   resolve_timings(c);
+  check_sort_flag(c);
 }
 
 }  // namespace
@@ -3094,7 +3224,7 @@ gsm_status gsm_server_stop(gsm_ctx *ctx) {
     }
     if (L->own_stream && L->stream) cudaStreamDestroy(L->stream);
   }
-  for (auto &kv : S->finished) std::free(kv.second.rows);  // never polled
+  for (auto &kv : S->finished) release_host_rows(kv.second.rows);  // never polled
   ctx->server = nullptr;
   delete S;
   return GSM_OK;

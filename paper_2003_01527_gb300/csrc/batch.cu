@@ -359,11 +359,21 @@ __global__ void __launch_bounds__(1024) k_b_count(
       }
     }
     // last-level survivors: one atomic per query per warp and item slot
+    // (a warp's rows mostly belong to one query: ballots settle that case,
+    // match_any only a warp that straddles queries)
 #pragma unroll
     for (int j = 0; j < kItemsPerThread; ++j) {
-      const uint32_t peers = __match_any_sync(kFull, qj[j]);
-      if (qj[j] >= 0 && lane == __ffs(peers) - 1)
-        atomicAdd(counts + qj[j], (unsigned long long)__popc(peers));
+      const uint32_t has = __ballot_sync(kFull, qj[j] >= 0);
+      if (!has) continue;
+      const int first = __ffs(has) - 1;
+      const int32_t qa = __shfl_sync(kFull, qj[j], first);
+      if (__ballot_sync(kFull, qj[j] == qa) == has) {
+        if (lane == first) atomicAdd(counts + qa, (unsigned long long)__popc(has));
+      } else {
+        const uint32_t peers = __match_any_sync(kFull, qj[j]);
+        if (qj[j] >= 0 && lane == __ffs(peers) - 1)
+          atomicAdd(counts + qj[j], (unsigned long long)__popc(peers));
+      }
     }
     uint32_t word = bits << (4 * (lane & 7));
     word |= __shfl_xor_sync(kFull, word, 1);

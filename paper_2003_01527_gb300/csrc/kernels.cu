@@ -834,16 +834,16 @@ int32_t label_segment_bits(int32_t n, int32_t num_labels) {
 }
 
 int launch_label_segments(const GraphDev &g, int32_t num_labels, int32_t *edge_cols,
-                          uint64_t *keys, int32_t *rows_out, int32_t *hist, int64_t *hist_off,
-                          int64_t *tmp, int32_t *out_col, int32_t *out_lab, cudaStream_t s) {
+                          uint64_t *keys, int32_t *rows_out, void *sort_scratch, uint32_t *err,
+                          int32_t *out_col, int32_t *out_lab, cudaStream_t s) {
   if (g.nnz == 0) return 0;
   k_edge_rows<<<grid_for((int64_t)g.n * 32, 256, 152 * 8), 256, 0, s>>>(g, edge_cols);
   const int32_t bits = label_segment_bits(g.n, num_labels);
   const int32_t nw = packed_words(3, bits);
   // CSR rows are already ordered by (row, id): sorting on (row, label) is enough
   int launches = 1 + launch_sort_rows_packed(edge_cols, g.nnz, g.nnz, 3, bits, 2, keys,
-                                             keys + (size_t)g.nnz * nw, g.nnz, rows_out, hist,
-                                             hist_off, tmp, s);
+                                             keys + (size_t)g.nnz * nw, g.nnz, rows_out,
+                                             sort_scratch, 0, err, -1, s);
   k_split_segments<<<grid_for(g.nnz, 256), 256, 0, s>>>(rows_out, g.nnz, out_col, out_lab);
   return launches + 1;
 }

@@ -91,11 +91,13 @@ void launch_validate_rows(const GraphDev &g, int32_t *err, cudaStream_t s);
 
 // Label-segmented rows: out_col/out_lab = every row of g ordered by (label
 // of the neighbour, neighbour id).  Uses the packed row sort on the edges as
-// 3-column rows (row, label, id); tmp needs 3*nnz int32 (+ its keys).
-// Returns kernels launched.  keys: 2 * nnz * packed_words(3, bits) uint64.
+// 3-column rows (row, label, id); edge_cols and rows_out need 3*nnz int32,
+// keys 2 * nnz * packed_words(3, bits) uint64, sort_scratch
+// sort_scratch_bytes(nnz, 3, bits, 2) bytes (bits = label_segment_bits);
+// err as for launch_sort_rows_packed.  Returns kernels launched.
 int launch_label_segments(const GraphDev &g, int32_t num_labels, int32_t *edge_cols,
-                          uint64_t *keys, int32_t *rows_out, int32_t *hist, int64_t *hist_off,
-                          int64_t *tmp, int32_t *out_col, int32_t *out_lab, cudaStream_t s);
+                          uint64_t *keys, int32_t *rows_out, void *sort_scratch, uint32_t *err,
+                          int32_t *out_col, int32_t *out_lab, cudaStream_t s);
 int32_t label_segment_bits(int32_t n, int32_t num_labels);
 
 // Adjacency bitmaps of the H hubs (vertex ids hubs[0..H)): bitmap h (words
@@ -253,9 +255,6 @@ size_t small_sort_smem(int32_t max_k);
 void launch_sort_small(const SmallSortItem *items, int32_t nitems, int32_t max_k,
                        cudaStream_t s);
 
-// Histogram elements of the radix passes over N keys.
-int64_t sort_hist_elems(int64_t N);
-
 // Lexicographic sort of N rows of k int32 (values < 2^bits) by column 0,
 // then 1, ...  Each row is a k*bits-bit integer, sum_j c_j << ((k-1-j)*bits),
 // held as packed_words(k, bits) little-endian 64-bit words (word w of row r at
@@ -266,18 +265,25 @@ int64_t sort_hist_elems(int64_t N);
 // `out` (N x k, must not overlap keys_a / keys_b; it may alias `a`).  Only
 // columns 0 .. sort_cols-1 are sorted on (1 <= sort_cols <= k): the caller
 // guarantees that rows with equal values there already stand in order of
-// the remaining columns, which the stable passes keep.  hist needs
-// sort_hist_elems(N) int32, hist_off sort_hist_elems(N)+1 int64, tmp
-// scan_tmp_elems(sort_hist_elems(N)) int64.  Returns the number of kernels
-// launched.
+// the remaining columns, which the stable passes keep.  Keys of one or two
+// words (N < 2^30) take single-sweep passes (one histogram launch, then one
+// launch per digit whose tiles find their offsets by a decoupled look-back);
+// wider keys take per-tile histograms and a scan per digit.  scratch:
+// sort_scratch_bytes(N, k, bits, sort_cols) bytes of device memory, 256-byte
+// aligned, contents not kept.  A look-back wait longer than spin_limit polls
+// (<= 0: the library default) sets *err to 1 (err may be null) and leaves the
+// rows out of order, every write still inside `out`.  stall_tile >= 0 (fault
+// injection for tests): that tile of every single-sweep pass never publishes
+// its counts.  Returns the number of kernels launched.
 int32_t packed_words(int32_t k, int32_t bits);
+size_t sort_scratch_bytes(int64_t N, int32_t k, int32_t bits, int32_t sort_cols);
 // Packed sort keys (word w of row r at keys[w*ld + r]) of N row-major rows of
 // k int32 (values < 2^bits), ready for launch_sort_rows_packed with a = null.
 void launch_pack_rows(const int32_t *rows, int64_t N, int32_t k, int32_t bits, uint64_t *keys,
                       int64_t ld, cudaStream_t s);
 int launch_sort_rows_packed(const int32_t *a, int64_t lda, int64_t N, int32_t k, int32_t bits,
                             int32_t sort_cols, uint64_t *keys_a, uint64_t *keys_b, int64_t ld,
-                            int32_t *out, int32_t *hist, int64_t *hist_off, int64_t *tmp,
-                            cudaStream_t s);
+                            int32_t *out, void *scratch, int32_t spin_limit, uint32_t *err,
+                            int32_t stall_tile, cudaStream_t s);
 
 }  // namespace gsm

@@ -59,6 +59,21 @@ __device__ __forceinline__ uint32_t key_digit(const uint64_t *__restrict__ in, i
   return (uint32_t)(v & 0xffu);
 }
 
+// Lanes of the warp whose value v (kBits bits) equals this lane's: the
+// intersection, over the bits, of the lanes that agree on the bit.  kBits
+// ballots; cheaper here than __match_any_sync for byte digits.
+template <int kBits>
+__device__ __forceinline__ uint32_t equal_lanes(uint32_t v) {
+  uint32_t peers = kFull;
+#pragma unroll
+  for (int i = 0; i < kBits; ++i) {
+    const bool bit = (v >> i) & 1u;
+    const uint32_t on = __ballot_sync(kFull, bit);
+    peers &= bit ? on : ~on;
+  }
+  return peers;
+}
+
 __global__ void __launch_bounds__(kSortThreads) k_hist_keys(const uint64_t *__restrict__ in,
                                                             int64_t ld, int64_t N, int32_t nw,
                                                             int32_t p,
@@ -97,7 +112,7 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter_keys(
     const int64_t idx = base + c * kSortThreads + threadIdx.x;
     const bool valid = idx < N;
     const uint32_t dgt = valid ? key_digit(in, ld, idx, nw, p) : kBins;
-    const uint32_t peers = __match_any_sync(kFull, dgt);
+    const uint32_t peers = equal_lanes<9>(dgt);
     const int rank = __popc(peers & lt);
     if (valid && rank == 0) s_wcnt[warp][dgt] = __popc(peers);
     __syncthreads();
@@ -132,12 +147,7 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter_keys(
   }
 }
 
-// The same pass for keys of NW <= 2 words, a tile at a time: every thread
-// first loads all its keys (item c*256 + t of the tile for chunk c), so the
-// loads of a tile are in flight together; each warp then counts its digits
-// per chunk with match_any into s_cnt[(chunk, warp)][digit], one exclusive
-// scan per digit over the 64 (chunk, warp) entries turns the counts into tile
-// offsets, and every key goes straight to hist_off + offset + rank.
+// Byte digit at bit (64 wi + sh) of a key of NW <= 2 words held in registers.
 template <int NW>
 __device__ __forceinline__ uint32_t tile_digit(const uint64_t (&kk)[NW], int32_t wi, int32_t sh) {
   uint64_t lo = kk[0], hi = 0;
@@ -153,71 +163,277 @@ __device__ __forceinline__ uint32_t tile_digit(const uint64_t (&kk)[NW], int32_t
   return (uint32_t)(v & 0xffu);
 }
 
-template <int NW, bool kUnpack>
-__global__ void __launch_bounds__(kSortThreads) k_scatter_tile(
-    const uint64_t *__restrict__ in, uint64_t *__restrict__ out_keys,
-    int32_t *__restrict__ out_rows, int64_t ld, int64_t N, int32_t k, int32_t b, int32_t p,
-    const int64_t *__restrict__ hist_off, int64_t nblocks) {
+// ---- single-sweep passes (keys of at most two words, N < 2^30) ----
+//
+// One histogram launch counts the digits of every pass in one read of the
+// keys; then each pass is one launch.  A CTA takes the next tile by ticket,
+// counts its digits, publishes the per-digit counts, and finds the count of
+// each digit in all earlier tiles by a decoupled look-back over the
+// published words of the tiles before it (per digit a 32-bit word: flag in
+// the top two bits, count or inclusive prefix below).  The tile's keys are
+// then staged in shared memory in their sorted order, so that consecutive
+// threads write consecutive positions of a digit's run.  Tiles only wait on
+// tiles with smaller tickets, which are already running, so the waits end;
+// each is still bounded (spin_limit polls, then *err = 1 and the sum found so
+// far, which keeps every write inside the output).
+constexpr uint32_t kSwAggregate = 1u << 30;
+constexpr uint32_t kSwInclusive = 2u << 30;
+constexpr uint32_t kSwFlags = 3u << 30;
+constexpr uint32_t kSwValue = kSwAggregate - 1u;
+constexpr int kMaxDigits = 16;  // two words of key
+constexpr int kLookWin = 8;     // look-back words read at once
+
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_relaxed_u32(uint32_t *p, uint32_t v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Exclusive scan of one value per thread over the 256 threads of the CTA.
+__device__ __forceinline__ uint32_t cta_excl_scan(uint32_t v, uint32_t *s_warp) {
   constexpr int kWarps = kSortThreads / 32;
-  constexpr int kSlots = kSortChunks * kWarps;
-  __shared__ __align__(16) uint16_t s_cnt[kSlots][kBins];
-  __shared__ int64_t s_base[kBins];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t base = (int64_t)blockIdx.x * kSortTile;
-  uint64_t key[kSortChunks][NW];
+  uint32_t x = v;
 #pragma unroll
-  for (int c = 0; c < kSortChunks; ++c) {
-    const int64_t idx = base + c * kSortThreads + threadIdx.x;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) key[c][w] = idx < N ? in[(int64_t)w * ld + idx] : 0;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += y;
   }
-  s_base[threadIdx.x] = hist_off[(int64_t)threadIdx.x * nblocks + blockIdx.x];
-  {
-    uint4 *z = reinterpret_cast<uint4 *>(&s_cnt[0][0]);
-    constexpr int kVec = kSlots * kBins * 2 / 16;
-    for (int e = threadIdx.x; e < kVec; e += kSortThreads) z[e] = make_uint4(0, 0, 0, 0);
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t w = lane < kWarps ? s_warp[lane] : 0;
+    uint32_t wi = w;
+#pragma unroll
+    for (int o = 1; o < kWarps; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, wi, o);
+      if (lane >= o) wi += y;
+    }
+    if (lane < kWarps) s_warp[lane] = wi - w;
   }
   __syncthreads();
-  const int32_t wi = p >> 6, sh = p & 63;
-  const uint32_t lt = (1u << lane) - 1u;
-  uint32_t dg[kSortChunks];
-  int32_t rk[kSortChunks];
-#pragma unroll
-  for (int c = 0; c < kSortChunks; ++c) {
-    const bool valid = base + c * kSortThreads + threadIdx.x < N;
-    dg[c] = valid ? tile_digit<NW>(key[c], wi, sh) : kBins;
-    const uint32_t peers = __match_any_sync(kFull, dg[c]);
-    rk[c] = __popc(peers & lt);
-    if (valid && rk[c] == 0) s_cnt[c * kWarps + warp][dg[c]] = (uint16_t)__popc(peers);
-  }
+  const uint32_t r = x - v + s_warp[warp];
   __syncthreads();
-  {
-    int32_t run = 0;
-    for (int e = 0; e < kSlots; ++e) {
-      const int32_t v = s_cnt[e][threadIdx.x];
-      s_cnt[e][threadIdx.x] = (uint16_t)run;
-      run += v;
+  return r;
+}
+
+// Column j of the packed key kk (k columns of b bits, column 0 highest).
+template <int NW>
+__device__ __forceinline__ int32_t key_column(const uint64_t (&kk)[NW], int32_t k, int32_t b,
+                                              int32_t j) {
+  const int32_t bp = (k - 1 - j) * b;
+  const int32_t wi = bp >> 6, sh = bp & 63;
+  uint64_t v = (NW > 1 && wi == 1) ? kk[NW - 1] : kk[0];
+  v >>= sh;
+  if (NW > 1 && wi == 0 && sh + b > 64) v |= kk[NW - 1] << (64 - sh);
+  return (int32_t)(v & ((1ull << b) - 1ull));
+}
+
+// Histograms of `digits` byte digits (from bit p0 up) of all N keys, added
+// into ghist[d * 256 + digit]; the last CTA to finish then writes their
+// exclusive scans, gexcl[d * 256 + digit] = the number of keys whose digit d
+// is smaller (done: a zeroed counter).  Grid-stride over tiles of kSortTile
+// keys; shared-memory atomics into two copies of the counts (even and odd
+// warps) to halve the contention of skewed digits.
+template <int NW>
+__global__ void __launch_bounds__(kSortThreads) k_digit_hist(const uint64_t *__restrict__ in,
+                                                             int64_t ld, int64_t N, int32_t p0,
+                                                             int32_t digits, uint32_t *ghist,
+                                                             uint32_t *__restrict__ gexcl,
+                                                             uint32_t *done) {
+  __shared__ uint32_t s_h[2][kMaxDigits * kBins];
+  __shared__ uint32_t s_warp[kSortThreads / 32];
+  __shared__ bool s_last;
+  uint32_t *h = s_h[(threadIdx.x >> 5) & 1];
+  for (int e = threadIdx.x; e < 2 * kMaxDigits * kBins; e += kSortThreads) (&s_h[0][0])[e] = 0;
+  __syncthreads();
+  const int64_t tiles = (N + kSortTile - 1) / kSortTile;
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int64_t base = tile * kSortTile;
+    uint64_t key[kSortChunks][NW];
+#pragma unroll
+    for (int c = 0; c < kSortChunks; ++c) {
+      const int64_t idx = base + c * kSortThreads + threadIdx.x;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) key[c][w] = idx < N ? __ldg(in + (int64_t)w * ld + idx) : 0;
+    }
+#pragma unroll
+    for (int c = 0; c < kSortChunks; ++c) {
+      if (base + c * kSortThreads + threadIdx.x >= N) continue;
+      for (int32_t d = 0; d < digits; ++d) {
+        const int32_t p = p0 + 8 * d;
+        atomicAdd(&h[d * kBins + tile_digit<NW>(key[c], p >> 6, p & 63)], 1u);
+      }
     }
   }
   __syncthreads();
-  const uint64_t mask_b = (1ull << b) - 1ull;
+  for (int e = threadIdx.x; e < digits * kBins; e += kSortThreads) {
+    const uint32_t v = s_h[0][e] + s_h[1][e];
+    if (v) atomicAdd(&ghist[e], v);
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int32_t d = 0; d < digits; ++d) {
+    const uint32_t v = ld_relaxed_u32(ghist + d * kBins + threadIdx.x);
+    gexcl[d * kBins + threadIdx.x] = cta_excl_scan(v, s_warp);
+  }
+}
+
+// One stable pass on the byte digit at bit p.  gexcl: the 256 exclusive
+// digit offsets over all keys; status: tiles * 256 look-back words, zero
+// before the pass; ticket: zero before the pass.  Warp w of a tile holds keys
+// w*256 + c*32 + lane (c = 0..7), so (warp, chunk, lane) is key order: the
+// warps first count their digits (early counts), thread t then turns the
+// counts of digit t into tile-local starts per warp and publishes the tile's
+// count; the warps rank their chunks in order (ballots; one leader per digit
+// advances the warp's running start) and stage the keys in shared memory in
+// sorted order; only then does thread t look back for the earlier tiles'
+// counts of digit t (they have had the ranking's time to publish), and
+// consecutive threads write consecutive positions of a digit's run.  The
+// last pass (kUnpack) writes each key as a row-major int32 row of out_rows
+// instead of moving the key.
+template <int NW, bool kUnpack>
+__global__ void __launch_bounds__(kSortThreads, NW == 1 ? 4 : 3) k_onesweep(
+    const uint64_t *__restrict__ in, uint64_t *__restrict__ out_keys,
+    int32_t *__restrict__ out_rows, int64_t ld, int64_t N, int32_t k, int32_t b, int32_t p,
+    const uint32_t *__restrict__ gexcl, uint32_t *status, uint32_t *ticket, int32_t spin_limit,
+    uint32_t *err, int64_t stall_tile) {
+  constexpr int kWarps = kSortThreads / 32;
+  extern __shared__ __align__(16) uint64_t s_keys[];  // NW * kSortTile: word w of key i at w*tile + i
+  __shared__ uint32_t s_wc[kWarps][kBins];
+  __shared__ int64_t s_off[kBins];
+  __shared__ uint32_t s_warp[kWarps];
+  __shared__ int64_t s_tile;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  for (int e = t; e < kWarps * kBins; e += kSortThreads) (&s_wc[0][0])[e] = 0;
+  if (t == 0) s_tile = (int64_t)atomicAdd(ticket, 1u);
+  __syncthreads();
+  const int64_t tile = s_tile;
+  const int64_t base = tile * kSortTile;
+  const int64_t wbase = base + warp * (kSortTile / kWarps);
+  uint64_t key[kSortChunks][NW];
 #pragma unroll
   for (int c = 0; c < kSortChunks; ++c) {
-    if (dg[c] == kBins) continue;
-    const int64_t pos = s_base[dg[c]] + s_cnt[c * kWarps + warp][dg[c]] + rk[c];
+    const int64_t idx = wbase + c * 32 + lane;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) key[c][w] = idx < N ? __ldg(in + (int64_t)w * ld + idx) : 0;
+  }
+  const int32_t wi = p >> 6, sh = p & 63;
+  uint32_t dg[kSortChunks];
+#pragma unroll
+  for (int c = 0; c < kSortChunks; ++c) {
+    dg[c] = wbase + c * 32 + lane < N ? tile_digit<NW>(key[c], wi, sh) : kBins;
+    if (dg[c] < kBins) atomicAdd(&s_wc[warp][dg[c]], 1u);
+  }
+  __syncthreads();
+  // thread t owns digit t
+  uint32_t wc[kWarps];
+  uint32_t cnt = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    wc[w] = s_wc[w][t];
+    cnt += wc[w];
+  }
+  uint32_t *mine = status + tile * kBins + t;
+  const bool publish = tile != stall_tile;  // fault injection: never publish
+  if (publish) st_relaxed_u32(mine, (tile == 0 ? kSwInclusive : kSwAggregate) | cnt);
+  const uint32_t lx = cta_excl_scan(cnt, s_warp);  // before digit t in this tile
+  {
+    uint32_t run = lx;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+      s_wc[w][t] = run;
+      run += wc[w];
+    }
+  }
+  __syncthreads();
+  // rank the warp's chunks in order and stage the keys (a lane without a
+  // key, only in the last tile, has digit kBins: a ninth bit)
+  const uint32_t lt = (1u << lane) - 1u;
+  const bool full = base + kSortTile <= N;
+#pragma unroll
+  for (int c = 0; c < kSortChunks; ++c) {
+    const uint32_t peers = full ? equal_lanes<8>(dg[c]) : equal_lanes<9>(dg[c]);
+    const int leader = __ffs(peers) - 1;
+    uint32_t start = 0;
+    if (lane == leader && dg[c] < kBins) {
+      start = s_wc[warp][dg[c]];
+      s_wc[warp][dg[c]] = start + __popc(peers);
+    }
+    start = __shfl_sync(kFull, start, leader);
+    if (dg[c] < kBins) {
+      const uint32_t li = start + __popc(peers & lt);
+#pragma unroll
+      for (int w = 0; w < NW; ++w) s_keys[w * kSortTile + li] = key[c][w];
+    }
+    __syncwarp();
+  }
+  // look back kLookWin tiles at a time (independent loads), summing counts
+  // up to the nearest inclusive prefix; a tile not yet published stops the
+  // window there and is polled again (a poll that makes no progress counts
+  // against spin_limit)
+  uint32_t excl = 0;
+  if (tile > 0) {
+    int64_t j = tile - 1;
+    int32_t polls = 0;
+    uint32_t nap = 32;  // ns, doubled per fruitless poll up to 1 us
+    bool done = false;
+    while (!done) {
+      uint32_t st[kLookWin];
+#pragma unroll
+      for (int w = 0; w < kLookWin; ++w)
+        st[w] = j - w >= 0 ? ld_relaxed_u32(status + (j - w) * kBins + t) : kSwInclusive;
+      int used = 0;
+#pragma unroll
+      for (int w = 0; w < kLookWin; ++w) {
+        if (done || used != w) continue;  // stopped earlier in the window
+        const uint32_t f = st[w] & kSwFlags;
+        if (f == 0) continue;
+        excl += st[w] & kSwValue;
+        used = w + 1;
+        if (f == kSwInclusive) done = true;
+      }
+      if (done) break;
+      j -= used;
+      if (used == 0) {
+        if (++polls > spin_limit) {
+          if (err) *(volatile uint32_t *)err = 1u;
+          break;
+        }
+        __nanosleep(nap);
+        nap = nap < 1024 ? 2 * nap : nap;
+      }
+    }
+    if (publish) st_relaxed_u32(mine, kSwInclusive | (excl + cnt));
+  }
+  s_off[t] = (int64_t)__ldg(gexcl + t) + excl - lx;
+  __syncthreads();
+  const int32_t n_tile = (int32_t)(N - base < kSortTile ? N - base : kSortTile);
+  for (int32_t i = t; i < n_tile; i += kSortThreads) {
+    uint64_t kk[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) kk[w] = s_keys[w * kSortTile + i];
+    const int64_t pos = s_off[tile_digit<NW>(kk, wi, sh)] + i;
     if (kUnpack) {
       int32_t *dst = out_rows + pos * k;
-      for (int32_t j = 0; j < k; ++j) {
-        const int32_t bp = (k - 1 - j) * b;
-        const int32_t bw = bp >> 6, bs = bp & 63;
-        uint64_t v = (NW > 1 && bw == 1) ? key[c][NW - 1] : key[c][0];
-        v >>= bs;
-        if (NW > 1 && bw == 0 && bs + b > 64) v |= key[c][NW - 1] << (64 - bs);
-        dst[j] = (int32_t)(v & mask_b);
+      if ((k & 1) == 0) {
+        for (int32_t j = 0; j < k; j += 2)
+          *reinterpret_cast<int2 *>(dst + j) =
+              make_int2(key_column<NW>(kk, k, b, j), key_column<NW>(kk, k, b, j + 1));
+      } else {
+        for (int32_t j = 0; j < k; ++j) dst[j] = key_column<NW>(kk, k, b, j);
       }
     } else {
 #pragma unroll
-      for (int w = 0; w < NW; ++w) out_keys[(int64_t)w * ld + pos] = key[c][w];
+      for (int w = 0; w < NW; ++w) out_keys[(int64_t)w * ld + pos] = kk[w];
     }
   }
 }
@@ -275,11 +491,6 @@ __global__ void __launch_bounds__(256) k_sort_small(const SmallSortItem *__restr
 
 }  // namespace
 
-int64_t sort_hist_elems(int64_t N) {
-  const int64_t nb = (N + kSortTile - 1) / kSortTile;
-  return nb * kBins;
-}
-
 size_t small_sort_smem(int32_t max_k) {
   return sizeof(int32_t) * (size_t)kSmallSortRows * (1 + max_k);
 }
@@ -312,43 +523,153 @@ void launch_pack_rows(const int32_t *rows, int64_t N, int32_t k, int32_t bits, u
                                                           packed_words(k, bits), keys, ld);
 }
 
+namespace {
+
+// Where the pieces of a sort's scratch go: the single-sweep passes (keys of
+// at most two words, N < 2^30) need the digit histograms, one ticket and
+// tiles * 256 look-back words per pass; the general passes a histogram per
+// tile and its scan.
+struct SortLayout {
+  bool sweep;
+  int32_t nw, digits, lo_bit;
+  int64_t tiles;
+  size_t o_ghist, o_gexcl, o_ticket, o_status, o_hist, o_hoff, o_tmp, bytes;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+SortLayout sort_layout(int64_t N, int32_t k, int32_t bits, int32_t sort_cols) {
+  SortLayout L{};
+  L.nw = packed_words(k, bits);
+  sort_cols = std::min(std::max(sort_cols, 1), k);
+  L.lo_bit = (k - sort_cols) * bits;
+  L.digits = (sort_cols * bits + 7) / 8;
+  L.tiles = (N + kSortTile - 1) / kSortTile;
+  L.sweep = L.nw <= 2 && N < (int64_t(1) << 30) && L.digits <= kMaxDigits;
+  size_t off = 0;
+  if (L.sweep) {
+    L.o_ghist = off;
+    off = align256(off + sizeof(uint32_t) * (size_t)L.digits * kBins);
+    L.o_gexcl = off;
+    off = align256(off + sizeof(uint32_t) * (size_t)L.digits * kBins);
+    L.o_ticket = off;  // one per pass, then the histogram's done counter
+    off = align256(off + sizeof(uint32_t) * (size_t)(L.digits + 1));
+    L.o_status = off;
+    off = align256(off + sizeof(uint32_t) * (size_t)L.digits * (size_t)L.tiles * kBins);
+  } else {
+    const int64_t H = L.tiles * kBins;
+    L.o_hist = off;
+    off = align256(off + sizeof(int32_t) * (size_t)H);
+    L.o_hoff = off;
+    off = align256(off + sizeof(int64_t) * (size_t)(H + 1));
+    L.o_tmp = off;
+    off = align256(off + sizeof(int64_t) * (size_t)scan_tmp_elems(H));
+  }
+  L.bytes = std::max<size_t>(off, 256);
+  return L;
+}
+
+int sm_count() {
+  static std::atomic<int> cached[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int v = cached[dev & 63].load();
+  if (!v) {
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    if (v <= 0) v = 1;
+    cached[dev & 63].store(v);
+  }
+  return v;
+}
+
+template <int NW>
+void sweep_pass(bool last, const uint64_t *src, uint64_t *dst, int32_t *out, int64_t ld,
+                int64_t N, int32_t k, int32_t bits, int32_t p, const uint32_t *gexcl,
+                uint32_t *status, uint32_t *ticket, int32_t spin_limit, uint32_t *err,
+                int64_t stall_tile, int64_t tiles, cudaStream_t s) {
+  // the staged tile lives in dynamic shared memory (two-word keys take the
+  // CTA past the 48 KB of static shared memory)
+  constexpr size_t kDyn = sizeof(uint64_t) * NW * kSortTile;
+  static std::atomic<unsigned long long> attr_set{0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (!((attr_set.load() >> (dev & 63)) & 1ull)) {
+    cudaFuncSetAttribute(k_onesweep<NW, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kDyn);
+    cudaFuncSetAttribute(k_onesweep<NW, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kDyn);
+    attr_set.fetch_or(1ull << (dev & 63));
+  }
+  if (last)
+    k_onesweep<NW, true><<<(unsigned)tiles, kSortThreads, kDyn, s>>>(
+        src, dst, out, ld, N, k, bits, p, gexcl, status, ticket, spin_limit, err, stall_tile);
+  else
+    k_onesweep<NW, false><<<(unsigned)tiles, kSortThreads, kDyn, s>>>(
+        src, dst, out, ld, N, k, bits, p, gexcl, status, ticket, spin_limit, err, stall_tile);
+}
+
+}  // namespace
+
+size_t sort_scratch_bytes(int64_t N, int32_t k, int32_t bits, int32_t sort_cols) {
+  return sort_layout(std::max<int64_t>(N, 1), k, bits, sort_cols).bytes;
+}
+
 int launch_sort_rows_packed(const int32_t *a, int64_t lda, int64_t N, int32_t k, int32_t bits,
                             int32_t sort_cols, uint64_t *keys_a, uint64_t *keys_b, int64_t ld,
-                            int32_t *out, int32_t *hist, int64_t *hist_off, int64_t *tmp,
-                            cudaStream_t s) {
+                            int32_t *out, void *scratch, int32_t spin_limit, uint32_t *err,
+                            int32_t stall_tile, cudaStream_t s) {
   if (N <= 0) return 0;
   int launches = 0;
-  const int32_t nw = packed_words(k, bits);
+  const SortLayout L = sort_layout(N, k, bits, sort_cols);
+  const int32_t nw = L.nw;
   if (a) {
     k_pack_keys<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(a, lda, 1, N, k, bits, nw, keys_a,
                                                             ld);
     ++launches;
   }
-  const int64_t nb = (N + kSortTile - 1) / kSortTile;
-  // only the bits of columns 0 .. sort_cols-1 are digits; the rest of the key
-  // is carried along (its order is already right among equal prefixes)
-  sort_cols = std::min(std::max(sort_cols, 1), k);
-  const int32_t lo_bit = (k - sort_cols) * bits;
-  const int32_t digits = (sort_cols * bits + 7) / 8;
+  char *sc = (char *)scratch;
   uint64_t *src = keys_a, *dst = keys_b;
-  for (int32_t dg = 0; dg < digits; ++dg) {
-    const int32_t p = lo_bit + 8 * dg;
+  if (L.sweep) {
+    if (spin_limit <= 0) spin_limit = kLbSpinLimit;
+    cudaMemsetAsync(sc, 0, L.bytes, s);
+    uint32_t *ghist = (uint32_t *)(sc + L.o_ghist);
+    uint32_t *gexcl = (uint32_t *)(sc + L.o_gexcl);
+    uint32_t *ticket = (uint32_t *)(sc + L.o_ticket);
+    uint32_t *status = (uint32_t *)(sc + L.o_status);
+    const unsigned grid = (unsigned)std::min<int64_t>(L.tiles, (int64_t)sm_count() * 4);
+    if (nw == 1)
+      k_digit_hist<1><<<grid, kSortThreads, 0, s>>>(keys_a, ld, N, L.lo_bit, L.digits, ghist,
+                                                    gexcl, ticket + L.digits);
+    else
+      k_digit_hist<2><<<grid, kSortThreads, 0, s>>>(keys_a, ld, N, L.lo_bit, L.digits, ghist,
+                                                    gexcl, ticket + L.digits);
+    ++launches;
+    for (int32_t dg = 0; dg < L.digits; ++dg) {
+      const int32_t p = L.lo_bit + 8 * dg;
+      const bool last = dg == L.digits - 1;
+      uint32_t *st = status + (size_t)dg * (size_t)L.tiles * kBins;
+      if (nw == 1)
+        sweep_pass<1>(last, src, dst, out, ld, N, k, bits, p, gexcl + dg * kBins, st, ticket + dg,
+                      spin_limit, err, stall_tile, L.tiles, s);
+      else
+        sweep_pass<2>(last, src, dst, out, ld, N, k, bits, p, gexcl + dg * kBins, st, ticket + dg,
+                      spin_limit, err, stall_tile, L.tiles, s);
+      ++launches;
+      std::swap(src, dst);
+    }
+    return launches;
+  }
+  // general passes: a histogram per tile, its scan, then the scatter
+  int32_t *hist = (int32_t *)(sc + L.o_hist);
+  int64_t *hist_off = (int64_t *)(sc + L.o_hoff);
+  int64_t *tmp = (int64_t *)(sc + L.o_tmp);
+  const int64_t nb = L.tiles;
+  for (int32_t dg = 0; dg < L.digits; ++dg) {
+    const int32_t p = L.lo_bit + 8 * dg;
     k_hist_keys<<<(unsigned)nb, kSortThreads, 0, s>>>(src, ld, N, nw, p, hist, nb);
     launch_scan_i32(hist, hist_off, nb * kBins, tmp, s);
-    const bool last = dg == digits - 1;
-    if (nw == 1 && last)
-      k_scatter_tile<1, true><<<(unsigned)nb, kSortThreads, 0, s>>>(src, dst, out, ld, N, k,
-                                                                    bits, p, hist_off, nb);
-    else if (nw == 1)
-      k_scatter_tile<1, false><<<(unsigned)nb, kSortThreads, 0, s>>>(src, dst, out, ld, N, k,
-                                                                     bits, p, hist_off, nb);
-    else if (nw == 2 && last)
-      k_scatter_tile<2, true><<<(unsigned)nb, kSortThreads, 0, s>>>(src, dst, out, ld, N, k,
-                                                                    bits, p, hist_off, nb);
-    else if (nw == 2)
-      k_scatter_tile<2, false><<<(unsigned)nb, kSortThreads, 0, s>>>(src, dst, out, ld, N, k,
-                                                                     bits, p, hist_off, nb);
-    else if (last)
+    const bool last = dg == L.digits - 1;
+    if (last)
       k_scatter_keys<true><<<(unsigned)nb, kSortThreads, 0, s>>>(src, dst, out, ld, N, nw, k,
                                                                  bits, p, hist_off, nb);
     else

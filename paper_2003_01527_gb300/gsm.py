@@ -40,6 +40,7 @@ GSM_OPT_TIME_KERNELS = 1
 GSM_OPT_TWO_PASS = 2
 GSM_OPT_COMPRESSED_FRONTIERS = 4
 GSM_OPT_INJECT_LOOKBACK_STALL = 8
+GSM_OPT_INJECT_SORT_STALL = 16
 
 MAX_K = 16
 
@@ -278,25 +279,37 @@ def gsm_candidates_static(n: int, nnz: int, row_ptr, col, labels, q: int, bitmap
         raise GsmError(st, "gsm_candidates_static")
 
 
-def _take_rows(ctx: int, r: gsm_result):
-    """Copies the rows of a result into a numpy array (host rows) or a CUDA
-    tensor (device rows), then releases the library's buffer."""
+def _copy_rows(r: gsm_result):
+    """A copy of the rows of a result: a numpy array (host rows) or a CUDA
+    tensor (device rows; the device copy may still be running)."""
     k, c = int(r.k), int(r.count)
     if not r.rows or c == 0:
-        on_device = bool(r.on_device)
-        _lib.gsm_result_free(ctx, ctypes.byref(r))
-        if on_device:
+        if r.on_device:
             import torch
             return torch.zeros((0, max(k, 1)), dtype=torch.int32, device="cuda")
         return np.zeros((0, max(k, 1)), dtype=np.int32)
     if r.on_device:
         import torch
         ptr = ctypes.cast(r.rows, ctypes.c_void_p).value
-        out = torch.as_tensor(_DevicePtr(ptr, c * k), device="cuda").clone().view(c, k)
-        torch.cuda.synchronize()  # the copy is done before the buffer is released
-    else:
-        out = np.ctypeslib.as_array(r.rows, shape=(c * k,)).reshape(c, k).copy()
-    _lib.gsm_result_free(ctx, ctypes.byref(r))
+        return torch.as_tensor(_DevicePtr(ptr, c * k), device="cuda").clone().view(c, k)
+    return np.ctypeslib.as_array(r.rows, shape=(c * k,)).reshape(c, k).copy()
+
+
+def _take_rows(ctx: int, r: gsm_result):
+    """Copies the rows of a result (see _copy_rows), then releases the
+    library's buffer."""
+    return _take_all(ctx, [r])[0]
+
+
+def _take_all(ctx: int, results):
+    """_copy_rows of every result, one device synchronisation, then every
+    library buffer released."""
+    out = [_copy_rows(r) for r in results]
+    if any(bool(r.on_device) and r.rows and r.count for r in results):
+        import torch
+        torch.cuda.synchronize()  # the copies are done before the buffers go
+    for r in results:
+        _lib.gsm_result_free(ctx, ctypes.byref(r))
     return out
 
 
@@ -319,7 +332,7 @@ def gsm_run_batch(ctx: int, queries, flags: int = 0, enumerate: bool = False):
     _check(ctx, _lib.gsm_run_batch(ctx, arr, nq, _ptr(counts), res, flags))
     if not enumerate:
         return counts[:nq]
-    rows = [_take_rows(ctx, res[j]) for j in range(nq)]
+    rows = _take_all(ctx, [res[j] for j in range(nq)])
     return counts[:nq], rows
 
 
@@ -454,7 +467,8 @@ class Matcher:
                  torch_allocator: bool = True, filter_rounds: int = 0, copy_slots: int = 0,
                  two_pass: bool = False, compressed: bool = False, lookback_spin_limit: int = 0,
                  inject_lookback_stall: bool = False, alloc_hook=None, lookahead: int = 0,
-                 hub_bitmap_bytes: int = 0, host_workers: int = 0):
+                 hub_bitmap_bytes: int = 0, host_workers: int = 0,
+                 inject_sort_stall: bool = False):
         import torch
         self.device = device
         opt = gsm_default_options()
@@ -477,7 +491,8 @@ class Matcher:
         opt.flags = (GSM_OPT_TIME_KERNELS if time_kernels else 0) | \
             (GSM_OPT_TWO_PASS if two_pass else 0) | \
             (GSM_OPT_COMPRESSED_FRONTIERS if compressed else 0) | \
-            (GSM_OPT_INJECT_LOOKBACK_STALL if inject_lookback_stall else 0)
+            (GSM_OPT_INJECT_LOOKBACK_STALL if inject_lookback_stall else 0) | \
+            (GSM_OPT_INJECT_SORT_STALL if inject_sort_stall else 0)
         if torch_allocator:
             dev = device
 

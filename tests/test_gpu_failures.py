@@ -8,8 +8,13 @@ waits -- no GPU fault and no hang:
   survivor count (GSM_OPT_INJECT_LOOKBACK_STALL), the tiles after it give up
   after lookback_spin_limit polls, the call returns GSM_ERR_TIMEOUT, the
   caller's buffer is left untouched, and the same context then counts
-  exactly.
+  exactly;
+* a look-back wait of the final row sort runs out (GSM_OPT_INJECT_SORT_STALL:
+  one tile of every sort pass withholds its digit counts): GSM_ERR_TIMEOUT,
+  nothing written past the rows, and the context then lists exactly.
 """
+import hashlib
+
 import numpy as np
 import pytest
 
@@ -101,6 +106,34 @@ def test_lookback_wait_runs_out(gsm_lib, cuda):
     m.load_graph(g.row_ptr, g.col, g.labels)
     Q = m.query(sl["k"], sl["edges"], sl["labels"]).restrict(0, 0, sl["root_hi"])
     assert m.count(Q) == sl["count"]
+    m.close()
+
+
+def test_sort_wait_runs_out(gsm_lib, cuda):
+    import bench
+    g, queries = bench.load_workload()
+    sl = queries[13]  # its matching order is not canonical: the rows are sorted
+    torch = cuda
+    m = gsm_lib.Matcher(device=0, lookback_spin_limit=64, inject_sort_stall=True)
+    m.load_graph(g.row_ptr, g.col, g.labels)
+    Q = m.query(sl["k"], sl["edges"], sl["labels"]).restrict(0, 0, sl["root_hi"])
+    n = sl["count"] * sl["k"]
+    out = torch.full((n + 1024,), -7, dtype=torch.int32, device="cuda")
+    with pytest.raises(gsm_lib.GsmError) as e:
+        m.enumerate(Q, out=out)
+    assert e.value.status == gsm_lib.GSM_ERR_TIMEOUT
+    assert "sort" in str(e.value)
+    assert bool((out[n:] == -7).all())  # no write past the rows
+    # counting needs no sort: exact on the same context
+    assert m.count(Q) == sl["count"]
+    m.close()
+    m = gsm_lib.Matcher(device=0, lookback_spin_limit=64)
+    m.load_graph(g.row_ptr, g.col, g.labels)
+    Q = m.query(sl["k"], sl["edges"], sl["labels"]).restrict(0, 0, sl["root_hi"])
+    _, c = m.enumerate(Q, out=out)
+    rows = out[:n].cpu().numpy().astype("<i4")
+    assert c == sl["count"]
+    assert hashlib.sha256(rows.tobytes()).hexdigest() == sl["rows_sha256"]
     m.close()
 
 
