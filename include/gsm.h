@@ -84,6 +84,11 @@ typedef void (*gsm_free_fn)(void *alloc_ctx, void *ptr, size_t bytes, void *stre
  * of the canonical row sort the second tile never publishes its digit
  * counts; the call returns GSM_ERR_TIMEOUT and the context stays usable. */
 #define GSM_OPT_INJECT_SORT_STALL 16
+/* Count the algorithmic bytes of the non-tree edge checks of single-pass
+ * levels, 4 * ceil(log2 deg) per check made (the binary-search probes of the
+ * byte model), into gsm_kernel_stat.probe_bytes (and algo_bytes).  Costs two
+ * row-pointer loads per check; results are unchanged. */
+#define GSM_OPT_COUNT_PROBES 32
 
 typedef struct gsm_options {
   /* Cap on device memory for intermediate frontiers and scratch, in bytes.
@@ -453,6 +458,9 @@ typedef struct gsm_kernel_stat {
   double total_ms;       /* sum of CUDA-event durations on the context's stream */
   double algo_bytes;     /* algorithmic bytes moved by those launches */
   uint64_t items;        /* work items (candidates checked, rows written, ...) */
+  double probe_bytes;    /* part of algo_bytes: the non-tree edge checks' binary-search
+                            probes, 4 * ceil(log2 deg) per check made (single-pass levels,
+                            with GSM_OPT_COUNT_PROBES) */
 } gsm_kernel_stat;
 
 /* Copies up to max entries into out, returns the number of kernels tracked

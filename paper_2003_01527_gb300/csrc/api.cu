@@ -41,6 +41,7 @@ struct KStat {
   uint64_t launches = 0;
   double total_ms = 0, algo_bytes = 0;
   uint64_t items = 0;
+  double probe_bytes = 0;  // part of algo_bytes
 };
 
 enum KernelId { K_FILTER, K_LIST, K_PIVOT, K_COUNT, K_WRITE, K_SORT, K_FUSED, K_NUM };
@@ -843,11 +844,13 @@ void process_fused(Run &R, int32_t i, const int32_t *F, int64_t ld, const int32_
   });
   const int64_t *S_dev = (const int64_t *)(lb + tiles + 1);
   if (last) {
-    fetch(ctx, S_dev, 2 * sizeof(unsigned long long));
+    fetch(ctx, S_dev, 3 * sizeof(unsigned long long));
     const int64_t S = ((volatile int64_t *)ctx->h_stage)[0];
     if (((volatile int64_t *)ctx->h_stage)[1])
       FAIL(GSM_ERR_TIMEOUT, "a verification tile waited too long for its predecessors");
-    ctx->kstats[K_FUSED].algo_bytes += (double)S * (double)R.acc_row_bytes();
+    const double probes = (double)((volatile int64_t *)ctx->h_stage)[2];
+    ctx->kstats[K_FUSED].algo_bytes += (double)S * (double)R.acc_row_bytes() + probes;
+    ctx->kstats[K_FUSED].probe_bytes += probes;
     R.acc_rows += (uint64_t)S;
     return;
   }
@@ -870,7 +873,9 @@ void process_fused(Run &R, int32_t i, const int32_t *F, int64_t ld, const int32_
   if (((volatile int64_t *)ctx->h_stage)[1])
     FAIL(GSM_ERR_TIMEOUT, "a verification tile waited too long for its predecessors");
   const int64_t W2 = ((volatile int64_t *)ctx->h_stage)[2];
-  ctx->kstats[K_FUSED].algo_bytes += (double)S * 4.0 * w_out;
+  const double probes = (double)((volatile int64_t *)ctx->h_stage)[3];
+  ctx->kstats[K_FUSED].algo_bytes += (double)S * 4.0 * w_out + probes;
+  ctx->kstats[K_FUSED].probe_bytes += probes;
   ctx->kstats[K_PIVOT].algo_bytes += (double)S * (4.0 * dn.nb + 8.0 * dn.nb + 13.0 + 16.0);
   ctx->kstats[K_PIVOT].items += (uint64_t)S;
   if (S > 0) recurse_rest(R, i + 1, Fn, W, S, pstart2, pslot2, woff2, W2);
@@ -1247,6 +1252,7 @@ void run_query(gsm_ctx *ctx, const gsm_query *q, bool enumerate, int32_t *out, u
     d.la = std::max<int32_t>(0, ctx->opt.lookahead);
     d.cand = bm;
     d.n_words = nw;
+    d.count_probes = (ctx->opt.flags & GSM_OPT_COUNT_PROBES) ? 1 : 0;
     if (d.la) {
       // query neighbours of pi_i placed after it, grouped by label
       uint32_t placed = 0;
@@ -2942,6 +2948,7 @@ gsm_status gsm_enumerate_many(gsm_ctx *ctx, int32_t nq, const gsm_query *const *
           ctx->kstats[k].total_ms += c->kstats[k].total_ms;
           ctx->kstats[k].algo_bytes += c->kstats[k].algo_bytes;
           ctx->kstats[k].items += c->kstats[k].items;
+          ctx->kstats[k].probe_bytes += c->kstats[k].probe_bytes;
           const char *nm = c->kstats[k].name;
           c->kstats[k] = KStat();
           c->kstats[k].name = nm;
@@ -3277,6 +3284,7 @@ gsm_status gsm_kernel_stats(gsm_ctx *ctx, gsm_kernel_stat *out, int32_t max, int
     out[i].total_ms = ctx->kstats[i].total_ms;
     out[i].algo_bytes = ctx->kstats[i].algo_bytes;
     out[i].items = ctx->kstats[i].items;
+    out[i].probe_bytes = ctx->kstats[i].probe_bytes;
   }
   if (n) *n = K_NUM;
   if (reset)

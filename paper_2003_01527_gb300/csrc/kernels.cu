@@ -637,7 +637,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMaxThreads == 256 ? 6 : 1) k_ext
     const int32_t x1 = min(x0 + tile_items, W);
     const TileRows t = stage_rows(woff, tile_row, wa, tile_items, s_woff, tile);
     const int32_t xb = x0 + warp * 128 + lane * kItemsPerThread;
-    uint32_t bits = 0;
+    uint32_t bits = 0, probes = 0;
     int32_t rj[kItemsPerThread], wj[kItemsPerThread];
     if (xb < x1) {
       int32_t rs;
@@ -662,10 +662,16 @@ __global__ void __launch_bounds__(kMaxThreads, kMaxThreads == 256 ? 6 : 1) k_ext
         const int32_t w = __ldg(g.lcol + pst + (x - rs));
         rj[j] = r;
         wj[j] = w;
-        if (check_candidate(g, d, ColumnRow{F, ld, r}, w, slot) &&
-            (!d.la || lookahead_ok(g, d, ColumnRow{F, ld, r}, w)))
-          bits |= 1u << j;
+        const bool ok = d.count_probes
+                            ? check_candidate_probes(g, d, ColumnRow{F, ld, r}, w, slot, &probes)
+                            : check_candidate(g, d, ColumnRow{F, ld, r}, w, slot);
+        if (ok && (!d.la || lookahead_ok(g, d, ColumnRow{F, ld, r}, w))) bits |= 1u << j;
       }
+    }
+    if (d.count_probes) {
+#pragma unroll
+      for (int o = 16; o; o >>= 1) probes += __shfl_xor_sync(kAll, probes, o);
+      if (lane == 0 && probes) atomicAdd(lookback + tiles + 3, (unsigned long long)probes);
     }
     // rank of this thread's survivors in the tile (thread order is
     // candidate order); the survivors go to the free pair buffer
@@ -727,6 +733,7 @@ __global__ void k_fetch_level(const unsigned long long *__restrict__ words,
     dst[0] = S;
     dst[1] = (long long)words[1];
     dst[2] = (long long)woff[S];
+    dst[3] = (long long)words[2];
   }
 }
 

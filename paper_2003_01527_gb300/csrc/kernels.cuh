@@ -54,6 +54,10 @@ struct LevelDesc {
   uint32_t la_pos[kMaxK], la_uq[kMaxK];
   const uint32_t *cand;
   int32_t n_words;
+  // 1 (GSM_OPT_COUNT_PROBES): the single-pass level adds the algorithmic
+  // bytes of its non-tree edge checks, 4 * ceil(log2 deg) per check made
+  // (the binary-search probes of the byte model), to lookback word tiles + 3
+  int32_t count_probes;
 };
 
 struct GraphDev {
@@ -209,13 +213,14 @@ void launch_extend_write(const GraphDev &g, const LevelDesc &d, const int32_t *F
 // last level): survivors of candidates [wa, wb) go to rows sink.row0 + 0, 1,
 // ... in candidate order, exactly where the two passes put them.  lookback
 // needs extend_tiles(wa, wb, block) + kLbExtra words, zeroed (launch_tile_rows
-// does it); afterwards word tiles + 1 holds the survivor count and word
+// does it); afterwards word tiles + 1 holds the survivor count, word
 // tiles + 2 is non-zero if a tile gave up waiting for its predecessors (after
-// spin_limit polls).  The sink needs room for wb - wa rows.  The grid is
-// persistent (at most the CTAs that fit on the device at once).  stall_tile
-// (-1 = none) is fault injection for tests: that tile never publishes its
-// look-back word, so later tiles' waits run out.
-constexpr int kLbExtra = 3;
+// spin_limit polls) and word tiles + 3 holds the probe bytes (count_probes).
+// The sink needs room for wb - wa rows.  The grid is persistent (at most the
+// CTAs that fit on the device at once).  stall_tile (-1 = none) is fault
+// injection for tests: that tile never publishes its look-back word, so later
+// tiles' waits run out.
+constexpr int kLbExtra = 4;
 constexpr unsigned long long kLbAggregate = 1ull << 62, kLbInclusive = 2ull << 62;
 constexpr unsigned long long kLbValue = (1ull << 62) - 1;
 constexpr int32_t kLbSpinLimit = 1 << 20;  // default bound of a look-back wait (polls)
@@ -235,8 +240,8 @@ void launch_split_points(const int64_t *woff, int64_t R, int64_t step, int64_t J
 // so small reads back to the host do not queue behind copy-engine transfers.
 void launch_fetch(const void *src, void *dst, size_t bytes, cudaStream_t s);
 // After a single-pass level and the next level's pivot and work scan: dst
-// (3 x int64) = the survivor count S (words[0]), the error word (words[1]) and
-// woff[S], the next level's candidate total.
+// (4 x int64) = the survivor count S (words[0]), the error word (words[1]),
+// woff[S] (the next level's candidate total) and the probe bytes (words[2]).
 void launch_fetch_level(const unsigned long long *words, const int64_t *woff, void *dst,
                         cudaStream_t s);
 

@@ -101,6 +101,24 @@ __device__ __forceinline__ bool check_candidate(const GraphDev &g, const Desc &d
   return true;
 }
 
+// check_candidate that also adds to *probe_bytes 4 * ceil(log2 deg(x)) for
+// every non-tree edge check it makes against a mapped vertex x (the bytes a
+// binary search of x's row reads; the check itself may be one bitmap probe).
+template <typename Desc, typename Row>
+__device__ __forceinline__ bool check_candidate_probes(const GraphDev &g, const Desc &d,
+                                                       const Row &row, int32_t w, int slot,
+                                                       uint32_t *probe_bytes) {
+  if (!check_local(d, row, w)) return false;
+  for (int b = 0; b < d.nb; ++b) {
+    if (b == slot) continue;
+    const int32_t x = row(d.bpos[b]);
+    const int32_t deg = __ldg(g.rp + x + 1) - __ldg(g.rp + x);
+    *probe_bytes += deg > 1 ? 4u * (32u - __clz((uint32_t)(deg - 1))) : 0u;
+    if (!row_contains_l(g, x, d.lab, w)) return false;
+  }
+  return true;
+}
+
 // Entries of w's (label, id)-ordered row scanned at most per group by the
 // 2-look-ahead before it gives up (and keeps the candidate).
 constexpr int32_t kLaScan = 64;

@@ -41,6 +41,7 @@ GSM_OPT_TWO_PASS = 2
 GSM_OPT_COMPRESSED_FRONTIERS = 4
 GSM_OPT_INJECT_LOOKBACK_STALL = 8
 GSM_OPT_INJECT_SORT_STALL = 16
+GSM_OPT_COUNT_PROBES = 32
 
 MAX_K = 16
 
@@ -78,7 +79,7 @@ class gsm_options(ctypes.Structure):
 class gsm_kernel_stat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint64),
                 ("total_ms", ctypes.c_double), ("algo_bytes", ctypes.c_double),
-                ("items", ctypes.c_uint64)]
+                ("items", ctypes.c_uint64), ("probe_bytes", ctypes.c_double)]
 
 
 class gsm_batch_stats(ctypes.Structure):
@@ -415,7 +416,8 @@ def gsm_kernel_stats(ctx: int, reset: bool = False) -> list[dict]:
     _check(ctx, _lib.gsm_kernel_stats(ctx, arr, 16, ctypes.byref(n), int(reset)))
     return [{"name": arr[i].name.decode(), "launches": arr[i].launches,
              "total_ms": arr[i].total_ms, "algo_bytes": arr[i].algo_bytes,
-             "items": arr[i].items} for i in range(min(n.value, 16))]
+             "items": arr[i].items, "probe_bytes": arr[i].probe_bytes}
+            for i in range(min(n.value, 16))]
 
 
 def gsm_last_run_stats(ctx: int) -> dict:
@@ -468,7 +470,7 @@ class Matcher:
                  two_pass: bool = False, compressed: bool = False, lookback_spin_limit: int = 0,
                  inject_lookback_stall: bool = False, alloc_hook=None, lookahead: int = 0,
                  hub_bitmap_bytes: int = 0, host_workers: int = 0,
-                 inject_sort_stall: bool = False):
+                 inject_sort_stall: bool = False, count_probes: bool = False):
         import torch
         self.device = device
         opt = gsm_default_options()
@@ -492,7 +494,8 @@ class Matcher:
             (GSM_OPT_TWO_PASS if two_pass else 0) | \
             (GSM_OPT_COMPRESSED_FRONTIERS if compressed else 0) | \
             (GSM_OPT_INJECT_LOOKBACK_STALL if inject_lookback_stall else 0) | \
-            (GSM_OPT_INJECT_SORT_STALL if inject_sort_stall else 0)
+            (GSM_OPT_INJECT_SORT_STALL if inject_sort_stall else 0) | \
+            (GSM_OPT_COUNT_PROBES if count_probes else 0)
         if torch_allocator:
             dev = device
 
