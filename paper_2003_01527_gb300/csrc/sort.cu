@@ -193,9 +193,9 @@ __device__ __forceinline__ void st_relaxed_u32(uint32_t *p, uint32_t v) {
   asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Exclusive scan of one value per thread over the 256 threads of the CTA.
+// Exclusive scan of one value per thread over the kWarps warps of the CTA.
+template <int kWarps>
 __device__ __forceinline__ uint32_t cta_excl_scan(uint32_t v, uint32_t *s_warp) {
-  constexpr int kWarps = kSortThreads / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t x = v;
 #pragma unroll
@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_hist(const uint64_t *__r
   __threadfence();
   for (int32_t d = 0; d < digits; ++d) {
     const uint32_t v = ld_relaxed_u32(ghist + d * kBins + threadIdx.x);
-    gexcl[d * kBins + threadIdx.x] = cta_excl_scan(v, s_warp);
+    gexcl[d * kBins + threadIdx.x] = cta_excl_scan<kSortThreads / 32>(v, s_warp);
   }
 }
 
@@ -300,25 +300,35 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_hist(const uint64_t *__r
 // consecutive threads write consecutive positions of a digit's run.  The
 // last pass (kUnpack) writes each key as a row-major int32 row of out_rows
 // instead of moving the key.
+// Threads of a single-sweep CTA: 512 for one-word keys (tiles of 4,096 keys:
+// half the tiles to look back over), 256 for two-word keys (registers).
+template <int NW>
+__host__ __device__ constexpr int sweep_threads() {
+  return NW == 1 ? 512 : 256;
+}
+
 template <int NW, bool kUnpack>
-__global__ void __launch_bounds__(kSortThreads, NW == 1 ? 4 : 3) k_onesweep(
+__global__ void __launch_bounds__(sweep_threads<NW>(), NW == 1 ? 2 : 3) k_onesweep(
     const uint64_t *__restrict__ in, uint64_t *__restrict__ out_keys,
     int32_t *__restrict__ out_rows, int64_t ld, int64_t N, int32_t k, int32_t b, int32_t p,
     const uint32_t *__restrict__ gexcl, uint32_t *status, uint32_t *ticket, int32_t spin_limit,
     uint32_t *err, int64_t stall_tile) {
-  constexpr int kWarps = kSortThreads / 32;
-  extern __shared__ __align__(16) uint64_t s_keys[];  // NW * kSortTile: word w of key i at w*tile + i
+  constexpr int kT = sweep_threads<NW>();
+  constexpr int kTile = kT * kSortChunks;
+  constexpr int kWarps = kT / 32;
+  extern __shared__ __align__(16) uint64_t s_keys[];  // NW * kTile: word w of key i at w*kTile + i
   __shared__ uint32_t s_wc[kWarps][kBins];
   __shared__ int64_t s_off[kBins];
   __shared__ uint32_t s_warp[kWarps];
   __shared__ int64_t s_tile;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  for (int e = t; e < kWarps * kBins; e += kSortThreads) (&s_wc[0][0])[e] = 0;
+  const bool owner = t < kBins;  // thread t < 256 owns digit t
+  for (int e = t; e < kWarps * kBins; e += kT) (&s_wc[0][0])[e] = 0;
   if (t == 0) s_tile = (int64_t)atomicAdd(ticket, 1u);
   __syncthreads();
   const int64_t tile = s_tile;
-  const int64_t base = tile * kSortTile;
-  const int64_t wbase = base + warp * (kSortTile / kWarps);
+  const int64_t base = tile * kTile;
+  const int64_t wbase = base + warp * (kTile / kWarps);
   uint64_t key[kSortChunks][NW];
 #pragma unroll
   for (int c = 0; c < kSortChunks; ++c) {
@@ -334,31 +344,29 @@ __global__ void __launch_bounds__(kSortThreads, NW == 1 ? 4 : 3) k_onesweep(
     if (dg[c] < kBins) atomicAdd(&s_wc[warp][dg[c]], 1u);
   }
   __syncthreads();
-  // thread t owns digit t
-  uint32_t wc[kWarps];
   uint32_t cnt = 0;
+  if (owner) {
 #pragma unroll
-  for (int w = 0; w < kWarps; ++w) {
-    wc[w] = s_wc[w][t];
-    cnt += wc[w];
+    for (int w = 0; w < kWarps; ++w) cnt += s_wc[w][t];
   }
   uint32_t *mine = status + tile * kBins + t;
-  const bool publish = tile != stall_tile;  // fault injection: never publish
+  const bool publish = owner && tile != stall_tile;  // fault injection: never publish
   if (publish) st_relaxed_u32(mine, (tile == 0 ? kSwInclusive : kSwAggregate) | cnt);
-  const uint32_t lx = cta_excl_scan(cnt, s_warp);  // before digit t in this tile
-  {
+  const uint32_t lx = cta_excl_scan<kWarps>(cnt, s_warp);  // before digit t in this tile
+  if (owner) {
     uint32_t run = lx;
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) {
+      const uint32_t v = s_wc[w][t];
       s_wc[w][t] = run;
-      run += wc[w];
+      run += v;
     }
   }
   __syncthreads();
   // rank the warp's chunks in order and stage the keys (a lane without a
   // key, only in the last tile, has digit kBins: a ninth bit)
   const uint32_t lt = (1u << lane) - 1u;
-  const bool full = base + kSortTile <= N;
+  const bool full = base + kTile <= N;
 #pragma unroll
   for (int c = 0; c < kSortChunks; ++c) {
     const uint32_t peers = full ? equal_lanes<8>(dg[c]) : equal_lanes<9>(dg[c]);
@@ -372,7 +380,7 @@ __global__ void __launch_bounds__(kSortThreads, NW == 1 ? 4 : 3) k_onesweep(
     if (dg[c] < kBins) {
       const uint32_t li = start + __popc(peers & lt);
 #pragma unroll
-      for (int w = 0; w < NW; ++w) s_keys[w * kSortTile + li] = key[c][w];
+      for (int w = 0; w < NW; ++w) s_keys[w * kTile + li] = key[c][w];
     }
     __syncwarp();
   }
@@ -381,7 +389,7 @@ __global__ void __launch_bounds__(kSortThreads, NW == 1 ? 4 : 3) k_onesweep(
   // window there and is polled again (a poll that makes no progress counts
   // against spin_limit)
   uint32_t excl = 0;
-  if (tile > 0) {
+  if (owner && tile > 0) {
     int64_t j = tile - 1;
     int32_t polls = 0;
     uint32_t nap = 32;  // ns, doubled per fruitless poll up to 1 us
@@ -414,13 +422,13 @@ __global__ void __launch_bounds__(kSortThreads, NW == 1 ? 4 : 3) k_onesweep(
     }
     if (publish) st_relaxed_u32(mine, kSwInclusive | (excl + cnt));
   }
-  s_off[t] = (int64_t)__ldg(gexcl + t) + excl - lx;
+  if (owner) s_off[t] = (int64_t)__ldg(gexcl + t) + excl - lx;
   __syncthreads();
-  const int32_t n_tile = (int32_t)(N - base < kSortTile ? N - base : kSortTile);
-  for (int32_t i = t; i < n_tile; i += kSortThreads) {
+  const int32_t n_tile = (int32_t)(N - base < kTile ? N - base : kTile);
+  for (int32_t i = t; i < n_tile; i += kT) {
     uint64_t kk[NW];
 #pragma unroll
-    for (int w = 0; w < NW; ++w) kk[w] = s_keys[w * kSortTile + i];
+    for (int w = 0; w < NW; ++w) kk[w] = s_keys[w * kTile + i];
     const int64_t pos = s_off[tile_digit<NW>(kk, wi, sh)] + i;
     if (kUnpack) {
       int32_t *dst = out_rows + pos * k;
@@ -544,8 +552,11 @@ SortLayout sort_layout(int64_t N, int32_t k, int32_t bits, int32_t sort_cols) {
   sort_cols = std::min(std::max(sort_cols, 1), k);
   L.lo_bit = (k - sort_cols) * bits;
   L.digits = (sort_cols * bits + 7) / 8;
-  L.tiles = (N + kSortTile - 1) / kSortTile;
   L.sweep = L.nw <= 2 && N < (int64_t(1) << 30) && L.digits <= kMaxDigits;
+  const int64_t tile = L.sweep ? (int64_t)(L.nw == 1 ? sweep_threads<1>() : sweep_threads<2>()) *
+                                     kSortChunks
+                               : kSortTile;
+  L.tiles = (N + tile - 1) / tile;  // tiles of the passes
   size_t off = 0;
   if (L.sweep) {
     L.o_ghist = off;
@@ -589,7 +600,8 @@ void sweep_pass(bool last, const uint64_t *src, uint64_t *dst, int32_t *out, int
                 int64_t stall_tile, int64_t tiles, cudaStream_t s) {
   // the staged tile lives in dynamic shared memory (two-word keys take the
   // CTA past the 48 KB of static shared memory)
-  constexpr size_t kDyn = sizeof(uint64_t) * NW * kSortTile;
+  constexpr int kT = sweep_threads<NW>();
+  constexpr size_t kDyn = sizeof(uint64_t) * NW * kT * kSortChunks;
   static std::atomic<unsigned long long> attr_set{0};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -601,10 +613,10 @@ void sweep_pass(bool last, const uint64_t *src, uint64_t *dst, int32_t *out, int
     attr_set.fetch_or(1ull << (dev & 63));
   }
   if (last)
-    k_onesweep<NW, true><<<(unsigned)tiles, kSortThreads, kDyn, s>>>(
+    k_onesweep<NW, true><<<(unsigned)tiles, kT, kDyn, s>>>(
         src, dst, out, ld, N, k, bits, p, gexcl, status, ticket, spin_limit, err, stall_tile);
   else
-    k_onesweep<NW, false><<<(unsigned)tiles, kSortThreads, kDyn, s>>>(
+    k_onesweep<NW, false><<<(unsigned)tiles, kT, kDyn, s>>>(
         src, dst, out, ld, N, k, bits, p, gexcl, status, ticket, spin_limit, err, stall_tile);
 }
 
