@@ -345,7 +345,10 @@ __global__ void k_bitmap_emit(const uint32_t *__restrict__ bm, int32_t n_words,
 __global__ void k_pivot(GraphDev g, LevelDesc d, const int32_t *__restrict__ F, int64_t ld,
                         int64_t R, int32_t *__restrict__ pstart, uint8_t *__restrict__ pslot,
                         int64_t *__restrict__ work, const int64_t *R_dev) {
-  if (R_dev) R = *R_dev;  // the actual row count (R is then the launch's bound)
+  // the actual row count (R is then the launch's bound); a set error word
+  // beside it means the level that wrote the rows gave up a wait, so some
+  // rows were never written: read none of them
+  if (R_dev) R = R_dev[1] ? 0 : R_dev[0];
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R; r += stride) {
     int32_t best = 0x7fffffff, best_start = 0, best_slot = 0;

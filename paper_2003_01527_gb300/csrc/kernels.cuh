@@ -160,7 +160,10 @@ void launch_bitmap_to_list(const uint32_t *bitmap, int32_t n_words, int32_t *cnt
 // pivot) and record its CSR start, its slot in bpos, and its degree as work
 // (int64, so the work array can be scanned in place into offsets).  F has
 // leading dimension ld >= R.
-// With R_dev the row count is read on the device and R is its upper bound.
+// With R_dev the row count is read on the device (R_dev[0]; R is its upper
+// bound) and R_dev[1] is the error word of the level that wrote F: when it is
+// set (a look-back wait ran out, so some rows were never written) no row is
+// read.
 void launch_pivot(const GraphDev &g, const LevelDesc &d, const int32_t *F, int64_t ld, int64_t R,
                   int32_t *pstart, uint8_t *pslot, int64_t *work, cudaStream_t s,
                   const int64_t *R_dev = nullptr);

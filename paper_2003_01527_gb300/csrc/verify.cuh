@@ -193,6 +193,24 @@ __device__ __forceinline__ void put_row(const RowSink &sink, const LevelDesc &d,
     int32_t *o = (int32_t *)sink.out + row * sink.k;
     for (int c = 0; c < i; ++c) o[d.out_col[c]] = src(c);
     o[d.out_col[i]] = w;
+  } else if (sink.nw <= 2) {
+    // packed key of one or two words: column j occupies bits
+    // [(k-1-j)*b, (k-j)*b); each column is read once and or-ed into the
+    // word(s) it overlaps
+    uint64_t *o = (uint64_t *)sink.out + row;
+    uint64_t w0 = 0, w1 = 0;
+    for (int c = 0; c <= i; ++c) {
+      const uint64_t v = (uint32_t)(c < i ? src(c) : w);
+      const int32_t p = (sink.k - 1 - d.out_col[c]) * sink.bits;
+      if (p >= 64) {
+        w1 |= v << (p - 64);
+      } else {
+        w0 |= v << p;
+        if (p + sink.bits > 64) w1 |= v >> (64 - p);
+      }
+    }
+    o[0] = w0;
+    if (sink.nw == 2) o[sink.ld] = w1;
   } else {
     // packed key: column j occupies bits [(k-1-j)*b, (k-j)*b); word t
     // collects the columns that overlap bits [64t, 64t+64)

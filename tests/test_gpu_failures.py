@@ -101,8 +101,9 @@ def test_lookback_wait_runs_out(gsm_lib, cuda):
     want = int(((g.labels[src] == 0) & (g.labels[g.col] == 0)).sum())
     assert m.count(m.query(2, [(0, 1)], [0, 0])) == want
     m.close()
-    # and without the injection the slice is exact
-    m = gsm_lib.Matcher(device=0, lookback_spin_limit=64)
+    # and without the injection the slice is exact (under a bound the
+    # levels' own waits never reach)
+    m = gsm_lib.Matcher(device=0, lookback_spin_limit=4096)
     m.load_graph(g.row_ptr, g.col, g.labels)
     Q = m.query(sl["k"], sl["edges"], sl["labels"]).restrict(0, 0, sl["root_hi"])
     assert m.count(Q) == sl["count"]
@@ -114,7 +115,8 @@ def test_sort_wait_runs_out(gsm_lib, cuda):
     g, queries = bench.load_workload()
     sl = queries[13]  # its matching order is not canonical: the rows are sorted
     torch = cuda
-    m = gsm_lib.Matcher(device=0, lookback_spin_limit=64, inject_sort_stall=True)
+    # a bound the levels' own waits never reach, short enough for the test
+    m = gsm_lib.Matcher(device=0, lookback_spin_limit=4096, inject_sort_stall=True)
     m.load_graph(g.row_ptr, g.col, g.labels)
     Q = m.query(sl["k"], sl["edges"], sl["labels"]).restrict(0, 0, sl["root_hi"])
     n = sl["count"] * sl["k"]
@@ -127,7 +129,7 @@ def test_sort_wait_runs_out(gsm_lib, cuda):
     # counting needs no sort: exact on the same context
     assert m.count(Q) == sl["count"]
     m.close()
-    m = gsm_lib.Matcher(device=0, lookback_spin_limit=64)
+    m = gsm_lib.Matcher(device=0, lookback_spin_limit=4096)
     m.load_graph(g.row_ptr, g.col, g.labels)
     Q = m.query(sl["k"], sl["edges"], sl["labels"]).restrict(0, 0, sl["root_hi"])
     _, c = m.enumerate(Q, out=out)
