@@ -51,6 +51,7 @@ typedef int32_t gsm_status;
 #define GSM_ERR_TIMEOUT (-9)       /* a bounded device wait gave up */
 #define GSM_ERR_CUDA (-10)         /* a CUDA runtime call failed */
 #define GSM_ERR_TOO_LARGE (-11)    /* nnz >= 2^31 or n >= 2^31 - 1 */
+#define GSM_ERR_INTERNAL (-12)     /* a device bounds check failed (GSM_DEBUG build only) */
 
 typedef struct gsm_ctx gsm_ctx;
 typedef struct gsm_query gsm_query;

@@ -1,7 +1,10 @@
 """Builds libgsm.so in-tree: every .cu under csrc/ compiled for sm_103a in
 parallel, linked with the static CUDA runtime, exporting only gsm_* symbols.
+build(debug=True) makes libgsm_debug.so, the same sources with GSM_DEBUG
+defined (device bounds checks that report instead of faulting), which the
+binding loads when the environment sets GSM_DEBUG=1.
 
-    python -m paper_2003_01527_gb300.build [--force]
+    python -m paper_2003_01527_gb300.build [--force] [--debug]
 """
 from __future__ import annotations
 
@@ -39,22 +42,29 @@ def _deps():
             + glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.join(CSRC, "libgsm.map"), __file__])
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+LIB_DEBUG = os.path.join(HERE, "libgsm_debug.so")
+
+
+def up_to_date(debug: bool = False) -> bool:
+    lib = LIB_DEBUG if debug else LIB
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    lib = LIB_DEBUG if debug else LIB
+    if not force and up_to_date(debug):
+        return lib
+    build_dir = BUILD + ("_debug" if debug else "")
+    os.makedirs(build_dir, exist_ok=True)
     nvcc = _nvcc()
+    flags = NVCC_FLAGS + (["-DGSM_DEBUG=1"] if debug else [])
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = [nvcc] + NVCC_FLAGS + ["-c", src, "-o", obj]
+        obj = os.path.join(build_dir, os.path.basename(src) + ".o")
+        cmd = [nvcc] + flags + ["-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -64,15 +74,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with concurrent.futures.ThreadPoolExecutor(max_workers=8) as ex:
         objs = list(ex.map(compile_one, _sources()))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc, "-shared", "-cudart", "static"] + ARCH + objs + [
-        "-o", tmp, "-Xlinker", "--version-script=" + os.path.join(CSRC, "libgsm.map")]
+        "-o", tmp, "-ldl", "-Xlinker", "--version-script=" + os.path.join(CSRC, "libgsm.map")]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, debug="--debug" in sys.argv))

@@ -24,6 +24,8 @@
 #include <tuple>
 #include <unordered_map>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "batch.h"
 #include "gsm.h"
 #include "compressed.cuh"
@@ -231,7 +233,8 @@ GraphDev graph_dev(const gsm_ctx *ctx) {
                   (ctx->n + 31) / 32,
                   ctx->hub_count ? ctx->d_hub_seg : nullptr,
                   ctx->d_nlc,
-                  ctx->nlc_stride};
+                  ctx->nlc_stride,
+                  ctx->d_flags ? ctx->d_flags + 1 : nullptr};
 }
 
 void set_err(gsm_ctx *c, const char *fmt, ...) {
@@ -421,14 +424,39 @@ int32_t sort_stall_tile(const gsm_ctx *ctx) {
 }
 
 // Raises GSM_ERR_TIMEOUT if a sort's look-back wait ran out since the last
-// check (and clears the flag); call once the sort's stream has been
+// check, or GSM_ERR_INTERNAL if a bounds check of the GSM_DEBUG build failed
+// (and clears the flags); call once the kernels' stream has been
 // synchronised.
 void check_sort_flag(gsm_ctx *ctx) {
   volatile uint32_t *f = ctx->h_flags;
+  if (f && f[1]) {
+    const uint32_t site = f[1];
+    f[1] = 0;
+    FAIL(GSM_ERR_INTERNAL, "a device bounds check failed (site %u)", site);
+  }
   if (f && f[0]) {
     f[0] = 0;
     FAIL(GSM_ERR_TIMEOUT, "a sort tile waited too long for its predecessors");
   }
+}
+
+// NVTX ranges (header-only NVTX 3: a cheap no-op unless a profiler is
+// attached) around a listing call, the filter, every verification-level
+// launch and the sort, so that a profile can be cut to one level
+// (ncu --nvtx --nvtx-include "gsm level 3/").
+struct Range {
+  explicit Range(const char *name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range &) = delete;
+  Range &operator=(const Range &) = delete;
+};
+
+const char *level_range(int32_t i) {
+  static const char *kNames[] = {"gsm level 0",  "gsm level 1",  "gsm level 2",  "gsm level 3",
+                                 "gsm level 4",  "gsm level 5",  "gsm level 6",  "gsm level 7",
+                                 "gsm level 8",  "gsm level 9",  "gsm level 10", "gsm level 11",
+                                 "gsm level 12", "gsm level 13", "gsm level 14", "gsm level 15"};
+  return (i >= 0 && i < 16) ? kNames[i] : "gsm level";
 }
 
 int64_t read_i64(gsm_ctx *ctx, const int64_t *dptr) {
@@ -708,6 +736,7 @@ void process_sub(Run &R, int32_t i, const int32_t *F, int64_t ld, const int32_t 
                  const uint8_t *pslot, const int64_t *woff, int64_t ra, int64_t rb, int64_t wa,
                  int64_t wb) {
   gsm_ctx *ctx = R.ctx;
+  const Range range(level_range(i));
   const LevelDesc &d = R.lv[i];
   const bool last = i == R.k - 1;
   const int64_t W = wb - wa, nrows = rb - ra;
@@ -810,6 +839,7 @@ void process_fused(Run &R, int32_t i, const int32_t *F, int64_t ld, const int32_
                    const uint8_t *pslot, const int64_t *woff, int64_t ra, int64_t rb, int64_t wa,
                    int64_t wb) {
   gsm_ctx *ctx = R.ctx;
+  const Range range(level_range(i));
   const LevelDesc &d = R.lv[i];
   const bool last = i == R.k - 1;
   const int64_t W = wb - wa, nrows = rb - ra;
@@ -970,6 +1000,7 @@ void recurse_c(Run &R, int32_t i, const CFrontier &f, int64_t rows);
 void process_c(Run &R, int32_t i, const CFrontier &f, const int32_t *pstart, const uint8_t *pslot,
                const int64_t *woff, int64_t ra, int64_t rb, int64_t wa, int64_t wb) {
   gsm_ctx *ctx = R.ctx;
+  const Range range(level_range(i));
   const LevelDesc &d = R.lv[i];
   const bool last = i == R.k - 1;
   const int64_t W = wb - wa, nrows = rb - ra;
@@ -1122,6 +1153,7 @@ bool dense_labels(gsm_ctx *ctx, const gsm_query *q, int32_t *dense) {
 // opt.filter_rounds refinement rounds (double-buffered, so every round reads
 // the previous round's sets only).
 void run_filter(gsm_ctx *ctx, const gsm_query *q, const int32_t *dense, uint64_t *sizes) {
+  const Range range("gsm filter");
   FilterDesc fd;
   fill_filter(ctx, q, dense, fd);
   const size_t bytes = (size_t)q->k * fd.n_words * sizeof(uint32_t);
@@ -1175,6 +1207,7 @@ void run_query(gsm_ctx *ctx, const gsm_query *q, bool enumerate, int32_t *out, u
                const std::vector<std::pair<int32_t, int32_t>> *less = nullptr,
                bool copy_async = false, const Prefiltered *pre = nullptr) {
   if (!ctx->has_graph) FAIL(GSM_ERR_NO_GRAPH, "no data graph loaded");
+  const Range range(enumerate ? "gsm query (list)" : "gsm query (count)");
   std::memset(&ctx->run, 0, sizeof(ctx->run));
   // nothing is live between calls (an earlier call may have failed mid-way)
   ctx->top_block = 0;
@@ -1345,6 +1378,7 @@ void run_query(gsm_ctx *ctx, const gsm_query *q, bool enumerate, int32_t *out, u
     // outside the budget, like the result buffers it serves
     ensure_buf(ctx, &ctx->sort_tmp, &ctx->sort_tmp_cap,
                sort_scratch_bytes((int64_t)total, q->k, R.key_bits, sort_cols), false, 0);
+    const Range sort_range("gsm sort");
     const int digits = (sort_cols * R.key_bits + 7) / 8;
     const double moved = 2.0 * (double)total * nw * sizeof(uint64_t) * digits;
     int launches = 0;
@@ -2063,6 +2097,7 @@ void lane_batch_rows(gsm_ctx *ctx, Lane &L, const std::vector<int64_t> &off,
 
 void run_batch(gsm_ctx *ctx, const gsm_query *const *qs, int32_t nq, uint64_t *counts,
                gsm_result *results, int32_t flags) {
+  const Range range("gsm batch");
   if (!ctx->has_graph) FAIL(GSM_ERR_NO_GRAPH, "no data graph loaded");
   const auto t0 = std::chrono::steady_clock::now();
   Lane &L = ctx->lane0;
@@ -2399,6 +2434,7 @@ const char *gsm_status_string(gsm_status s) {
     case GSM_ERR_TIMEOUT: return "GSM_ERR_TIMEOUT";
     case GSM_ERR_CUDA: return "GSM_ERR_CUDA";
     case GSM_ERR_TOO_LARGE: return "GSM_ERR_TOO_LARGE";
+    case GSM_ERR_INTERNAL: return "GSM_ERR_INTERNAL";
     default: return "GSM_ERR_UNKNOWN";
   }
 }
@@ -2587,6 +2623,7 @@ gsm_status gsm_load_graph(gsm_ctx *ctx, int32_t n, int64_t nnz, const int32_t *r
         FAIL(GSM_ERR_INVALID_GRAPH, "row_ptr is not a valid CSR offset array");
       }
       GraphDev g{n, nnz, ctx->d_rp, ctx->d_col, ctx->d_lab, nullptr, nullptr, 1};
+      g.dbg = ctx->d_flags ? ctx->d_flags + 1 : nullptr;
       int32_t *err = (int32_t *)(ctx->d_small + kMaxK + 1);
       CU(cudaMemsetAsync(err, 0, sizeof(int32_t), ctx->stream));
       launch_validate(g, err, ctx->stream);
@@ -2697,6 +2734,7 @@ namespace {
 // sizes; pre[j].bitmaps stays null for a query with a label absent from G.
 void prefilter_many(gsm_ctx *ctx, int32_t nq, const gsm_query *const *queries,
                     std::vector<Prefiltered> &pre, std::vector<uint64_t> &sizes) {
+  const Range range("gsm filter (all queries)");
   const int32_t nw = (ctx->n + 31) / 32;
   std::vector<FilterDesc> fds;
   std::vector<int32_t> sel;

@@ -354,6 +354,12 @@ __global__ void k_pivot(GraphDev g, LevelDesc d, const int32_t *__restrict__ F, 
     int32_t best = 0x7fffffff, best_start = 0, best_slot = 0;
     for (int b = 0; b < d.nb; ++b) {
       const int32_t x = F[(int64_t)d.bpos[b] * ld + r];
+      if (!GSM_IN_BOUNDS(g.dbg, x >= 0 && x < g.n, kDbgPivotVertex)) {
+        best = 0;  // the row gets no candidates
+        best_start = 0;
+        best_slot = b;
+        break;
+      }
       const int2 seg = label_segment(g, x, d.lab);  // only pi_i's label can match
       if (seg.y - seg.x < best) {
         best = seg.y - seg.x;
@@ -593,6 +599,8 @@ __global__ void __launch_bounds__(kMaxThreads, kMaxThreads == 256 ? 6 : 1) k_ext
     __syncthreads();
     const int32_t *pairs = s_pairs + pb * 2 * tile_items;
     const int64_t base = sink.row0 + s_prefix;
+    // (GSM_DEBUG) the level reserved W rows from sink.row0
+    if (!GSM_IN_BOUNDS(g.dbg, s_prefix >= 0 && s_prefix + T <= W, kDbgOutputRow)) return;
     if (kMode == kSinkRows && (sink.k & 1) == 0) {
       // result rows in the matching order (the identity here: rows are only
       // written directly when it is canonical); an even row width is stored
@@ -662,6 +670,9 @@ __global__ void __launch_bounds__(kMaxThreads, kMaxThreads == 256 ? 6 : 1) k_ext
           pst = pstart[r];
           slot = pslot[r];
         }
+        if (!GSM_IN_BOUNDS(g.dbg, pst + (x - rs) >= 0 && pst + (x - rs) < g.nnz, kDbgCandidate) ||
+            !GSM_IN_BOUNDS(g.dbg, r >= 0 && r < ld, kDbgRow))
+          continue;
         const int32_t w = __ldg(g.lcol + pst + (x - rs));
         rj[j] = r;
         wj[j] = w;

@@ -83,7 +83,28 @@ struct GraphDev {
   // 15, so the saturated count decides every requirement exactly)
   const uint8_t *nlc;
   int32_t nlc_stride;
+  // GSM_DEBUG builds: the mapped word a failed bounds check writes its site
+  // to (null: not reported)
+  uint32_t *dbg;
 };
+
+// Bounds checks of the GSM_DEBUG build at the hot kernels' indexed accesses:
+// GSM_IN_BOUNDS(dbg, cond, site) is true when cond holds; otherwise it
+// records `site` in *dbg and is false, and the caller skips the access (no
+// trap; the host reports GSM_ERR_INTERNAL).  In other builds it is true and
+// costs nothing.
+#ifdef GSM_DEBUG
+__device__ __forceinline__ bool gsm_in_bounds(uint32_t *dbg, bool ok, uint32_t site) {
+  if (!ok && dbg) *(volatile uint32_t *)dbg = site;
+  return ok;
+}
+#define GSM_IN_BOUNDS(dbg, cond, site) gsm_in_bounds((dbg), (cond), (site))
+#else
+#define GSM_IN_BOUNDS(dbg, cond, site) true
+#endif
+// check sites
+constexpr uint32_t kDbgPivotVertex = 1, kDbgCandidate = 2, kDbgRow = 3, kDbgNeighbour = 4,
+                   kDbgOutputRow = 5, kDbgSortPosition = 6;
 
 // ---- launchers (all asynchronous on `s`) ----
 
@@ -278,11 +299,13 @@ void launch_sort_small(const SmallSortItem *items, int32_t nitems, int32_t max_k
 // launch per digit whose tiles find their offsets by a decoupled look-back);
 // wider keys take per-tile histograms and a scan per digit.  scratch:
 // sort_scratch_bytes(N, k, bits, sort_cols) bytes of device memory, 256-byte
-// aligned, contents not kept.  A look-back wait longer than spin_limit polls
-// (<= 0: the library default) sets *err to 1 (err may be null) and leaves the
-// rows out of order, every write still inside `out`.  stall_tile >= 0 (fault
-// injection for tests): that tile of every single-sweep pass never publishes
-// its counts.  Returns the number of kernels launched.
+// aligned, contents not kept.  err: null, or two words: a look-back wait
+// longer than spin_limit polls (<= 0: the library default) sets err[0] to 1
+// and leaves the rows out of order, every write still inside `out`; a failed
+// bounds check of the GSM_DEBUG build writes its site to err[1].
+// stall_tile >= 0 (fault injection for tests): that tile of every
+// single-sweep pass never publishes its counts.  Returns the number of
+// kernels launched.
 int32_t packed_words(int32_t k, int32_t bits);
 size_t sort_scratch_bytes(int64_t N, int32_t k, int32_t bits, int32_t sort_cols);
 // Packed sort keys (word w of row r at keys[w*ld + r]) of N row-major rows of

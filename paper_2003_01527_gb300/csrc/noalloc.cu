@@ -110,6 +110,7 @@ extern "C" gsm_status gsm_candidates_static(int32_t n, int64_t nnz, const int32_
   // contents: clear them first.  (The bitmap words are all overwritten.)
   if (cudaMemsetAsync(d_sizes, 0, kCounterBytes, s) != cudaSuccess) return GSM_ERR_CUDA;
   GraphDev g{n, nnz, row_ptr, col, labels, nullptr, nullptr, 0};  // the filter reads id-sorted rows
+  g.dbg = nullptr;
   launch_filter(g, fd, d_bitmaps, d_sizes, s);
   if (cudaGetLastError() != cudaSuccess) return GSM_ERR_CUDA;
   const cudaMemcpyKind kind =

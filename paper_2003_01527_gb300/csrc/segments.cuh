@@ -47,6 +47,7 @@ __device__ __forceinline__ int2 label_segment(const GraphDev &g, int32_t x, int3
 // is a hub, else one binary search on the (label, id) order of x's row.
 __device__ __forceinline__ bool row_contains_l(const GraphDev &g, int32_t x, int32_t l,
                                                int32_t w) {
+  if (!GSM_IN_BOUNDS(g.dbg, x >= 0 && x < g.n, kDbgNeighbour)) return false;
   if (g.hub) {
     const int32_t h = __ldg(g.hub + x);
     if (h >= 0)

@@ -430,6 +430,7 @@ __global__ void __launch_bounds__(sweep_threads<NW>(), NW == 1 ? 2 : 3) k_oneswe
 #pragma unroll
     for (int w = 0; w < NW; ++w) kk[w] = s_keys[w * kTile + i];
     const int64_t pos = s_off[tile_digit<NW>(kk, wi, sh)] + i;
+    if (!GSM_IN_BOUNDS(err ? err + 1 : nullptr, pos >= 0 && pos < N, kDbgSortPosition)) continue;
     if (kUnpack) {
       int32_t *dst = out_rows + pos * k;
       if ((k & 1) == 0) {

@@ -17,7 +17,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libgsm.so")
+# GSM_DEBUG=1 in the environment: the build with device bounds checks
+DEBUG = os.environ.get("GSM_DEBUG", "") not in ("", "0")
+LIB_PATH = os.path.join(_HERE, "libgsm_debug.so" if DEBUG else "libgsm.so")
 
 GSM_OK = 0
 GSM_PENDING = 1
@@ -32,6 +34,7 @@ GSM_ERR_TRUNCATED = -8
 GSM_ERR_TIMEOUT = -9
 GSM_ERR_CUDA = -10
 GSM_ERR_TOO_LARGE = -11
+GSM_ERR_INTERNAL = -12
 
 GSM_DEVICE_PTRS = 1
 GSM_VALIDATE = 2
@@ -106,8 +109,8 @@ class gsm_run_stats(ctypes.Structure):
 
 def _load():
     if not os.path.exists(LIB_PATH):
-        raise ImportError(f"libgsm.so not built ({LIB_PATH}); run "
-                          "python -m paper_2003_01527_gb300.build")
+        raise ImportError(f"{os.path.basename(LIB_PATH)} not built ({LIB_PATH}); run "
+                          "python -m paper_2003_01527_gb300.build" + (" --debug" if DEBUG else ""))
     lib = ctypes.CDLL(LIB_PATH)
     vp, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
     sig = {
