@@ -1375,19 +1375,31 @@ void run_query(gsm_ctx *ctx, const gsm_query *q, bool enumerate, int32_t *out, u
     const size_t key_bytes = (size_t)R.acc_ld * nw * sizeof(uint64_t);
     ensure_buf(ctx, &ctx->sort_keys, &ctx->sort_keys_cap, key_bytes, false, 0);
     ensure_buf(ctx, &ctx->acc[1], &ctx->acc_cap[1], bytes, false, 0);
+    // the rows leave the levels sorted by the columns the matching order
+    // places first in id order (0, 1, ..., p-1), with at most |F_p|
+    // distinct prefixes
+    SortPrefix pre;
+    while (pre.cols < q->k && R.order[pre.cols] == pre.cols) ++pre.cols;
+    pre.groups = pre.cols > 0 ? (int64_t)ctx->run.frontier[pre.cols] : 0;
+    if (pre.cols == 0 || pre.groups <= 0) pre = SortPrefix();
     // outside the budget, like the result buffers it serves
     ensure_buf(ctx, &ctx->sort_tmp, &ctx->sort_tmp_cap,
-               sort_scratch_bytes((int64_t)total, q->k, R.key_bits, sort_cols), false, 0);
+               sort_scratch_bytes((int64_t)total, q->k, R.key_bits, sort_cols, pre), false, 0);
     const Range sort_range("gsm sort");
-    const int digits = (sort_cols * R.key_bits + 7) / 8;
-    const double moved = 2.0 * (double)total * nw * sizeof(uint64_t) * digits;
+    bool ranked = false;
+    const int digits =
+        sort_digit_passes((int64_t)total, q->k, R.key_bits, sort_cols, pre, &ranked);
+    // key bytes read + written per digit pass; the prefix rank reads the
+    // keys twice, writes the flags, scans them and rewrites the keys
+    const double moved = 2.0 * (double)total * nw * sizeof(uint64_t) * digits +
+                         (ranked ? (double)total * (3.0 * nw * 8.0 + 4.0 + 12.0) : 0.0);
     int launches = 0;
     timed(ctx, K_SORT, moved + (double)bytes, total, 0, [&] {
       launches = launch_sort_rows_packed(nullptr, 0, (int64_t)total, q->k, R.key_bits, sort_cols,
                                          (uint64_t *)ctx->acc[0], (uint64_t *)ctx->sort_keys,
                                          R.acc_ld, (int32_t *)ctx->acc[1], ctx->sort_tmp,
                                          R.spin_limit, ctx->d_flags, sort_stall_tile(ctx),
-                                         ctx->stream);
+                                         ctx->stream, pre);
     });
     ctx->run.kernel_launches += launches;
     rows = (int32_t *)ctx->acc[1];

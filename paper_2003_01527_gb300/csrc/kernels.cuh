@@ -306,8 +306,22 @@ void launch_sort_small(const SmallSortItem *items, int32_t nitems, int32_t max_k
 // stall_tile >= 0 (fault injection for tests): that tile of every
 // single-sweep pass never publishes its counts.  Returns the number of
 // kernels launched.
+// Optional knowledge of the input order: the rows already stand sorted by
+// their first `cols` columns (1 <= cols < sort_cols), with at most `groups`
+// distinct prefixes.  The sort then orders those columns by the prefix's
+// dense rank (ceil(log2 groups) bits or-ed in above the k columns, when the
+// key words have room and it saves digit passes: one flag pass, a scan and
+// one rank pass instead of the prefix's own digits); the result is the same.
+struct SortPrefix {
+  int32_t cols = 0;
+  int64_t groups = 0;
+};
 int32_t packed_words(int32_t k, int32_t bits);
-size_t sort_scratch_bytes(int64_t N, int32_t k, int32_t bits, int32_t sort_cols);
+size_t sort_scratch_bytes(int64_t N, int32_t k, int32_t bits, int32_t sort_cols,
+                          SortPrefix pre = SortPrefix());
+// Digit passes the sort makes (and whether it ranks the prefix).
+int32_t sort_digit_passes(int64_t N, int32_t k, int32_t bits, int32_t sort_cols,
+                          SortPrefix pre = SortPrefix(), bool *prefix_rank = nullptr);
 // Packed sort keys (word w of row r at keys[w*ld + r]) of N row-major rows of
 // k int32 (values < 2^bits), ready for launch_sort_rows_packed with a = null.
 void launch_pack_rows(const int32_t *rows, int64_t N, int32_t k, int32_t bits, uint64_t *keys,
@@ -315,6 +329,6 @@ void launch_pack_rows(const int32_t *rows, int64_t N, int32_t k, int32_t bits, u
 int launch_sort_rows_packed(const int32_t *a, int64_t lda, int64_t N, int32_t k, int32_t bits,
                             int32_t sort_cols, uint64_t *keys_a, uint64_t *keys_b, int64_t ld,
                             int32_t *out, void *scratch, int32_t spin_limit, uint32_t *err,
-                            int32_t stall_tile, cudaStream_t s);
+                            int32_t stall_tile, cudaStream_t s, SortPrefix pre = SortPrefix());
 
 }  // namespace gsm

@@ -233,15 +233,19 @@ __device__ __forceinline__ int32_t key_column(const uint64_t (&kk)[NW], int32_t 
   return (int32_t)(v & ((1ull << b) - 1ull));
 }
 
-// Histograms of `digits` byte digits (from bit p0 up) of all N keys, added
+// Histograms of `digits` byte digits (at bits pos.p[0..digits)) of all N keys, added
 // into ghist[d * 256 + digit]; the last CTA to finish then writes their
 // exclusive scans, gexcl[d * 256 + digit] = the number of keys whose digit d
 // is smaller (done: a zeroed counter).  Grid-stride over tiles of kSortTile
 // keys; shared-memory atomics into two copies of the counts (even and odd
 // warps) to halve the contention of skewed digits.
+struct DigitPos {
+  int32_t p[kMaxDigits];  // bit position of each digit pass, lowest first
+};
+
 template <int NW>
 __global__ void __launch_bounds__(kSortThreads) k_digit_hist(const uint64_t *__restrict__ in,
-                                                             int64_t ld, int64_t N, int32_t p0,
+                                                             int64_t ld, int64_t N, DigitPos pos,
                                                              int32_t digits, uint32_t *ghist,
                                                              uint32_t *__restrict__ gexcl,
                                                              uint32_t *done) {
@@ -265,7 +269,7 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_hist(const uint64_t *__r
     for (int c = 0; c < kSortChunks; ++c) {
       if (base + c * kSortThreads + threadIdx.x >= N) continue;
       for (int32_t d = 0; d < digits; ++d) {
-        const int32_t p = p0 + 8 * d;
+        const int32_t p = pos.p[d];
         atomicAdd(&h[d * kBins + tile_digit<NW>(key[c], p >> 6, p & 63)], 1u);
       }
     }
@@ -447,6 +451,40 @@ __global__ void __launch_bounds__(sweep_threads<NW>(), NW == 1 ? 2 : 3) k_oneswe
   }
 }
 
+// flags[i] = 1 where key i's prefix (the key bits selected by m0 in word 0
+// and m1 in word 1) differs from key i-1's; flags[0] = 0.
+template <int NW>
+__global__ void __launch_bounds__(256) k_prefix_flags(const uint64_t *__restrict__ keys,
+                                                      int64_t ld, int64_t N, uint64_t m0,
+                                                      uint64_t m1, int32_t *__restrict__ flags) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+    if (i == 0) {
+      flags[0] = 0;
+      continue;
+    }
+    uint64_t d = (__ldg(keys + i) ^ __ldg(keys + i - 1)) & m0;
+    if (NW > 1) d |= (__ldg(keys + ld + i) ^ __ldg(keys + ld + i - 1)) & m1;
+    flags[i] = d != 0;
+  }
+}
+
+// Key i gains the dense rank of its prefix, incl[i] = offs[i + 1] (the
+// prefix changes up to i), at bit rank_pos (rank_bits bits, above the k
+// columns).
+template <int NW>
+__global__ void __launch_bounds__(256) k_put_rank(uint64_t *__restrict__ keys, int64_t ld,
+                                                  int64_t N, const int64_t *__restrict__ offs,
+                                                  int32_t rank_pos, int32_t rank_bits) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int32_t w = rank_pos >> 6, sh = rank_pos & 63;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+    const uint64_t rank = (uint64_t)__ldg(offs + i + 1);
+    keys[(int64_t)w * ld + i] |= rank << sh;
+    if (NW > 1 && w == 0 && sh > 0 && sh + rank_bits > 64) keys[ld + i] |= rank >> (64 - sh);
+  }
+}
+
 // One CTA per item: `count` (<= kSmallSortRows) row-major rows of k int32 are
 // loaded into shared memory and their indices bitonic-sorted by a
 // lexicographic comparison of the rows (rows are distinct embeddings, so the
@@ -541,18 +579,38 @@ namespace {
 struct SortLayout {
   bool sweep;
   int32_t nw, digits, lo_bit;
+  DigitPos pos;                // bit position of each digit pass
+  int32_t prefix_cols, rank_bits, rank_pos;  // rank_bits = 0: no prefix rank
   int64_t tiles;
-  size_t o_ghist, o_gexcl, o_ticket, o_status, o_hist, o_hoff, o_tmp, bytes;
+  size_t o_ghist, o_gexcl, o_ticket, o_status, o_hist, o_hoff, o_tmp, o_flags, o_offs, o_rtmp,
+      bytes;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-SortLayout sort_layout(int64_t N, int32_t k, int32_t bits, int32_t sort_cols) {
+SortLayout sort_layout(int64_t N, int32_t k, int32_t bits, int32_t sort_cols, SortPrefix pre) {
   SortLayout L{};
   L.nw = packed_words(k, bits);
   sort_cols = std::min(std::max(sort_cols, 1), k);
   L.lo_bit = (k - sort_cols) * bits;
   L.digits = (sort_cols * bits + 7) / 8;
+  // prefix rank: the sorted leading columns keyed by their dense rank above
+  // the k columns, when the key words have room and it saves passes
+  if (pre.cols >= 1 && pre.cols < sort_cols && pre.groups >= 1 && L.nw <= 2) {
+    int32_t rb = 1;
+    while (rb < 62 && (int64_t(1) << rb) < pre.groups) ++rb;
+    const int32_t low = ((sort_cols - pre.cols) * bits + 7) / 8, high = (rb + 7) / 8;
+    if (k * bits + rb <= 64 * L.nw && low + high < L.digits) {
+      L.prefix_cols = pre.cols;
+      L.rank_bits = rb;
+      L.rank_pos = k * bits;
+      for (int32_t d = 0; d < low; ++d) L.pos.p[d] = L.lo_bit + 8 * d;
+      for (int32_t d = 0; d < high; ++d) L.pos.p[low + d] = L.rank_pos + 8 * d;
+      L.digits = low + high;
+    }
+  }
+  if (!L.rank_bits)
+    for (int32_t d = 0; d < std::min(L.digits, kMaxDigits); ++d) L.pos.p[d] = L.lo_bit + 8 * d;
   L.sweep = L.nw <= 2 && N < (int64_t(1) << 30) && L.digits <= kMaxDigits;
   const int64_t tile = L.sweep ? (int64_t)(L.nw == 1 ? sweep_threads<1>() : sweep_threads<2>()) *
                                      kSortChunks
@@ -576,6 +634,14 @@ SortLayout sort_layout(int64_t N, int32_t k, int32_t bits, int32_t sort_cols) {
     off = align256(off + sizeof(int64_t) * (size_t)(H + 1));
     L.o_tmp = off;
     off = align256(off + sizeof(int64_t) * (size_t)scan_tmp_elems(H));
+  }
+  if (L.rank_bits) {
+    L.o_flags = off;
+    off = align256(off + sizeof(int32_t) * (size_t)N);
+    L.o_offs = off;
+    off = align256(off + sizeof(int64_t) * (size_t)(N + 1));
+    L.o_rtmp = off;
+    off = align256(off + sizeof(int64_t) * (size_t)scan_tmp_elems(N));
   }
   L.bytes = std::max<size_t>(off, 256);
   return L;
@@ -623,17 +689,25 @@ void sweep_pass(bool last, const uint64_t *src, uint64_t *dst, int32_t *out, int
 
 }  // namespace
 
-size_t sort_scratch_bytes(int64_t N, int32_t k, int32_t bits, int32_t sort_cols) {
-  return sort_layout(std::max<int64_t>(N, 1), k, bits, sort_cols).bytes;
+size_t sort_scratch_bytes(int64_t N, int32_t k, int32_t bits, int32_t sort_cols,
+                          SortPrefix pre) {
+  return sort_layout(std::max<int64_t>(N, 1), k, bits, sort_cols, pre).bytes;
+}
+
+int32_t sort_digit_passes(int64_t N, int32_t k, int32_t bits, int32_t sort_cols,
+                          SortPrefix pre, bool *prefix_rank) {
+  const SortLayout L = sort_layout(std::max<int64_t>(N, 1), k, bits, sort_cols, pre);
+  if (prefix_rank) *prefix_rank = L.rank_bits > 0;
+  return L.digits;
 }
 
 int launch_sort_rows_packed(const int32_t *a, int64_t lda, int64_t N, int32_t k, int32_t bits,
                             int32_t sort_cols, uint64_t *keys_a, uint64_t *keys_b, int64_t ld,
                             int32_t *out, void *scratch, int32_t spin_limit, uint32_t *err,
-                            int32_t stall_tile, cudaStream_t s) {
+                            int32_t stall_tile, cudaStream_t s, SortPrefix pre) {
   if (N <= 0) return 0;
   int launches = 0;
-  const SortLayout L = sort_layout(N, k, bits, sort_cols);
+  const SortLayout L = sort_layout(N, k, bits, sort_cols, pre);
   const int32_t nw = L.nw;
   if (a) {
     k_pack_keys<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(a, lda, 1, N, k, bits, nw, keys_a,
@@ -641,24 +715,49 @@ int launch_sort_rows_packed(const int32_t *a, int64_t lda, int64_t N, int32_t k,
     ++launches;
   }
   char *sc = (char *)scratch;
+  if (L.rank_bits) {
+    // the prefix's dense rank: change flags, their scan, the rank or-ed in
+    // above the k columns (the prefix bits themselves stay, for the unpack)
+    const int32_t plo = (k - L.prefix_cols) * bits, phi = k * bits;
+    auto word_mask = [&](int32_t w) {
+      const int32_t lo = std::max(plo - 64 * w, 0), hi = std::min(phi - 64 * w, 64);
+      if (hi <= lo) return 0ull;
+      const unsigned long long top = hi >= 64 ? ~0ull : ((1ull << hi) - 1ull);
+      return top & ~((1ull << lo) - 1ull);
+    };
+    int32_t *flags = (int32_t *)(sc + L.o_flags);
+    int64_t *offs = (int64_t *)(sc + L.o_offs);
+    const unsigned g = (unsigned)std::min<int64_t>((N + 255) / 256, (int64_t)sm_count() * 8);
+    if (nw == 1) {
+      k_prefix_flags<1><<<g, 256, 0, s>>>(keys_a, ld, N, word_mask(0), 0ull, flags);
+      launch_scan_i32(flags, offs, N, (int64_t *)(sc + L.o_rtmp), s);
+      k_put_rank<1><<<g, 256, 0, s>>>(keys_a, ld, N, offs, L.rank_pos, L.rank_bits);
+    } else {
+      k_prefix_flags<2><<<g, 256, 0, s>>>(keys_a, ld, N, word_mask(0), word_mask(1), flags);
+      launch_scan_i32(flags, offs, N, (int64_t *)(sc + L.o_rtmp), s);
+      k_put_rank<2><<<g, 256, 0, s>>>(keys_a, ld, N, offs, L.rank_pos, L.rank_bits);
+    }
+    launches += 2 + scan_kernels(N);
+  }
   uint64_t *src = keys_a, *dst = keys_b;
   if (L.sweep) {
     if (spin_limit <= 0) spin_limit = kLbSpinLimit;
-    cudaMemsetAsync(sc, 0, L.bytes, s);
+    cudaMemsetAsync(sc, 0, L.o_status + sizeof(uint32_t) * (size_t)L.digits * (size_t)L.tiles * kBins,
+                    s);
     uint32_t *ghist = (uint32_t *)(sc + L.o_ghist);
     uint32_t *gexcl = (uint32_t *)(sc + L.o_gexcl);
     uint32_t *ticket = (uint32_t *)(sc + L.o_ticket);
     uint32_t *status = (uint32_t *)(sc + L.o_status);
     const unsigned grid = (unsigned)std::min<int64_t>(L.tiles, (int64_t)sm_count() * 4);
     if (nw == 1)
-      k_digit_hist<1><<<grid, kSortThreads, 0, s>>>(keys_a, ld, N, L.lo_bit, L.digits, ghist,
+      k_digit_hist<1><<<grid, kSortThreads, 0, s>>>(keys_a, ld, N, L.pos, L.digits, ghist,
                                                     gexcl, ticket + L.digits);
     else
-      k_digit_hist<2><<<grid, kSortThreads, 0, s>>>(keys_a, ld, N, L.lo_bit, L.digits, ghist,
+      k_digit_hist<2><<<grid, kSortThreads, 0, s>>>(keys_a, ld, N, L.pos, L.digits, ghist,
                                                     gexcl, ticket + L.digits);
     ++launches;
     for (int32_t dg = 0; dg < L.digits; ++dg) {
-      const int32_t p = L.lo_bit + 8 * dg;
+      const int32_t p = L.pos.p[dg];
       const bool last = dg == L.digits - 1;
       uint32_t *st = status + (size_t)dg * (size_t)L.tiles * kBins;
       if (nw == 1)
@@ -678,7 +777,7 @@ int launch_sort_rows_packed(const int32_t *a, int64_t lda, int64_t N, int32_t k,
   int64_t *tmp = (int64_t *)(sc + L.o_tmp);
   const int64_t nb = L.tiles;
   for (int32_t dg = 0; dg < L.digits; ++dg) {
-    const int32_t p = L.lo_bit + 8 * dg;
+    const int32_t p = dg < kMaxDigits ? L.pos.p[dg] : L.lo_bit + 8 * dg;
     k_hist_keys<<<(unsigned)nb, kSortThreads, 0, s>>>(src, ld, N, nw, p, hist, nb);
     launch_scan_i32(hist, hist_off, nb * kBins, tmp, s);
     const bool last = dg == L.digits - 1;
