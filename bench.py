@@ -608,7 +608,7 @@ def run_gpu(args):
     if args.queries:
         keep = [int(x) for x in args.queries.split(",")]
         queries = [queries[i] for i in keep]
-    # two contexts on the same graph: M (no per-kernel events, two host
+    # two contexts on the same graph: M (no per-kernel events, six host
     # workers) is timed for the headline; MK records CUDA events around every
     # kernel and lists the queries one after the other (so no other query's
     # kernels fall between a kernel's events), timed in a second pass for the

@@ -113,9 +113,10 @@ typedef struct gsm_options {
    * gsm_candidates returns the refined sets.  The batched form ignores it. */
   int32_t filter_rounds;
   int32_t flags;          /* GSM_OPT_* */
-  /* Result staging slots gsm_enumerate_many uses in turn (0 = 8, at most 64):
-   * each holds the staging buffers of one query's rows until they are copied
-   * out, so up to this many queries can be ahead of the copies. */
+  /* Result staging slots gsm_enumerate_many uses in turn, per worker (0 = 8
+   * with one host worker, 2 with several; at most 64): each holds the staging
+   * buffers of one query's rows until they are copied out, so up to this
+   * many of a worker's queries can be ahead of its copies. */
   int32_t copy_slots;
   /* Bound of every wait of a single-pass level on the counts of earlier
    * tiles (polls of about 32 ns; 0 = 2^20).  A wait that runs out ends the
@@ -136,11 +137,13 @@ typedef struct gsm_options {
    * search of its row.  0 = 512 MiB; negative = no bitmaps.  Built by
    * gsm_load_graph, outside the memory budget; results do not depend on it. */
   int64_t hub_bitmap_bytes;
-  /* Host threads gsm_enumerate_many lists its queries with (0 = 2, at most
+  /* Host threads gsm_enumerate_many lists its queries with (0 = 6, at most
    * 16): each thread has a worker context of its own (stream, workspace with
    * an equal share of the memory budget, result slots) on the shared
    * resident graph, so one query's kernels run while another waits for a
-   * read-back.  1 = one query after the other on the context itself. */
+   * read-back.  1 = one query after the other on the context itself.  (On
+   * the 20-slice R-MAT 16 listing, 1 / 2 / 4 / 6 / 8 workers: 6.70 / 5.93 /
+   * 5.47 / 5.39 / 5.42 ms with 2-4 slots.) */
   int32_t host_workers;
 } gsm_options;
 

@@ -2881,6 +2881,7 @@ struct ManyState {
   uint64_t *counts;
   int32_t flags;
   const std::vector<Prefiltered> *pre = nullptr;
+  int32_t nworkers = 1;
   std::atomic<int32_t> next{0};
   std::atomic<int32_t> failed{0};
   std::atomic<int32_t> first_trunc{INT32_MAX};
@@ -2893,7 +2894,7 @@ void list_many(gsm_ctx *ctx, ManyState &M, uint64_t *launches, uint64_t *peak, b
     CU(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
     CU(cudaEventCreateWithFlags(&c->rows_ready, cudaEventDisableTiming));
   }
-  const int32_t slots = c->opt.copy_slots > 0 ? c->opt.copy_slots : 8;
+  const int32_t slots = c->opt.copy_slots > 0 ? c->opt.copy_slots : (M.nworkers > 1 ? 2 : 8);
   for (;;) {
     if (M.failed.load()) break;
     const int32_t j = M.next.fetch_add(1);
@@ -2938,7 +2939,8 @@ gsm_status gsm_enumerate_many(gsm_ctx *ctx, int32_t nq, const gsm_query *const *
   M.counts = counts;
   M.flags = flags;
   const int32_t nworkers =
-      std::min<int32_t>(ctx->opt.host_workers > 0 ? ctx->opt.host_workers : 2, std::max(nq, 1));
+      std::min<int32_t>(ctx->opt.host_workers > 0 ? ctx->opt.host_workers : 6, std::max(nq, 1));
+  M.nworkers = nworkers;
   gsm_status st = guarded(ctx, [&] {
     CU(cudaSetDevice(ctx->device));
     if (!ctx->has_graph) FAIL(GSM_ERR_NO_GRAPH, "no data graph loaded");
