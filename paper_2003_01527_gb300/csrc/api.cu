@@ -187,11 +187,13 @@ struct gsm_ctx {
     std::vector<std::array<int32_t, kMaxK>> orders;
     std::vector<int32_t> lists;
     // device buffers of the canonical sorts: keys (2), sort scratch, the
-    // small-sort items, the staged rows of host results
-    void *srt[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-    size_t srt_cap[5] = {0, 0, 0, 0, 0};
+    // small-sort items, the staged rows of host results, the segment tables
+    void *srt[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    size_t srt_cap[6] = {0, 0, 0, 0, 0, 0};
     gsm::SmallSortItem *h_items = nullptr;  // pinned staging of the items
     size_t h_items_cap = 0;
+    gsm::SortSegment *h_segs = nullptr;  // pinned staging of the segment tables
+    size_t h_segs_cap = 0;
     std::map<std::tuple<int32_t, int32_t, int32_t, int32_t, int32_t, int32_t>, cudaGraphExec_t>
         graphs;
     // a batch in flight (server): which requests, how many queries
@@ -1583,7 +1585,10 @@ void lane_release(gsm_ctx *ctx, Lane &L) {
   if (L.h_items) cudaFreeHost(L.h_items);
   L.h_items = nullptr;
   L.h_items_cap = 0;
-  for (int j = 0; j < 5; ++j)
+  if (L.h_segs) cudaFreeHost(L.h_segs);
+  L.h_segs = nullptr;
+  L.h_segs_cap = 0;
+  for (int j = 0; j < 6; ++j)
     if (L.srt[j]) dev_free(ctx, L.srt[j], L.srt_cap[j]);
   if (L.bitmaps) dev_free(ctx, L.bitmaps, L.bitmaps_cap);
   for (cudaEvent_t e : {L.ev0, L.ev1, L.ev_done})
@@ -1697,32 +1702,6 @@ int32_t unsorted_columns(int32_t k, const int32_t *order) {
   int32_t sort_cols = k - 1;
   while (sort_cols > 0 && pos[sort_cols - 1] < pos[sort_cols]) --sort_cols;
   return sort_cols;
-}
-
-// N row-major result rows of k int32 in query-id column order, emitted in
-// lexicographic order of the matching order `order`, written into dst (device)
-// in canonical (lexicographic) order: a copy when the order already is
-// canonical, else a packed-key radix sort of the unsorted leading columns.
-void canonical_rows(gsm_ctx *ctx, Lane &L, const int32_t *src, int64_t N, int32_t k,
-                    const int32_t *order, int32_t *dst) {
-  if (N <= 0) return;
-  const int32_t sort_cols = unsorted_columns(k, order);
-  if (sort_cols == 0) {
-    CU(cudaMemcpyAsync(dst, src, (size_t)N * k * sizeof(int32_t), cudaMemcpyDeviceToDevice,
-                       L.stream));
-    return;
-  }
-  int32_t bits = 1;
-  while (bits < 31 && (int64_t(1) << bits) < ctx->n) ++bits;
-  const int32_t nw = packed_words(k, bits);
-  uint64_t *ka = (uint64_t *)lane_srt(ctx, L, 0, (size_t)N * nw * sizeof(uint64_t));
-  uint64_t *kb = (uint64_t *)lane_srt(ctx, L, 1, (size_t)N * nw * sizeof(uint64_t));
-  void *scratch = lane_srt(ctx, L, 2, sort_scratch_bytes(N, k, bits, sort_cols));
-  launch_pack_rows(src, N, k, bits, ka, N, L.stream);
-  launch_sort_rows_packed(nullptr, 0, N, k, bits, sort_cols, ka, kb, N, dst, scratch,
-                          ctx->opt.lookback_spin_limit, ctx->d_flags, sort_stall_tile(ctx),
-                          L.stream);
-  CU(cudaGetLastError());
 }
 
 // Element offset in the result arena of every selected query that listed
@@ -2032,18 +2011,39 @@ void release_rows(gsm_ctx *ctx, gsm_result *r) {
   r->rows = nullptr;
 }
 
+// Grows pinned host staging *p to hold `bytes` (contents not kept; the
+// lane's stream is synchronised first, as an earlier upload may read it).
+template <typename T>
+T *lane_pinned(gsm_ctx *ctx, Lane &L, T **p, size_t *cap, size_t bytes) {
+  if (*cap < bytes) {
+    CU(cudaStreamSynchronize(L.stream));
+    if (*p) cudaFreeHost(*p);
+    *p = nullptr;
+    *cap = 0;
+    const size_t want = std::max(bytes, size_t(4096));
+    CU(cudaHostAlloc((void **)p, want, cudaHostAllocDefault));
+    *cap = want;
+  }
+  return *p;
+}
+
 // Rows of the selected queries t of a finished listing batch on lane L with
-// want[t] (k >= 2), canonicalised into results[L.sel[t]]: all in one block
-// (host, or device memory from the context's allocator), each result at a
-// 16-byte aligned offset.  Results of at most kSmallSortRows rows are sorted
-// together by one launch (a CTA each), larger ones by the radix sort.  Host
-// results are staged on the device and copied back in one transfer; the
-// caller synchronises the lane's stream.
+// want[t] (k >= 2), canonicalised into results[L.sel[t]], all in one block
+// (host, or device memory from the context's allocator).  Results of at most
+// kSmallSortRows rows are sorted together by one launch (a CTA each); larger
+// ones whose matching order is not canonical are sorted together per query
+// size, as one segmented sort (the query's index within the group as the
+// key's most significant part: the arena already holds each query's rows
+// contiguously, queries in batch order), straight into their place in the
+// block; the rest are copied.  Host results are staged on the device and
+// copied back in one transfer; the caller synchronises the lane's stream.
 void lane_batch_rows(gsm_ctx *ctx, Lane &L, const std::vector<int64_t> &off,
                      const std::vector<char> &want, bool on_device, gsm_result *results) {
-  std::vector<int32_t> ts;
-  std::vector<size_t> pos;
-  size_t total = 0;
+  // the groups (per k, in batch order) take the front of the block, their
+  // rows contiguous; every other result follows at a 16-byte aligned offset
+  std::map<int32_t, std::vector<int32_t>> groups;
+  std::vector<int32_t> rest;
+  std::vector<int32_t> sort_cols(L.m, 0);
   for (int32_t t = 0; t < L.m; ++t) {
     const int32_t k = L.h_qs[t].k;
     if (!want[t] || k < 2) continue;
@@ -2053,54 +2053,106 @@ void lane_batch_rows(gsm_ctx *ctx, Lane &L, const std::vector<int64_t> &off,
     r.on_device = on_device ? 1 : 0;
     r.rows = nullptr;
     if (r.count == 0) continue;
-    ts.push_back(t);
-    pos.push_back(total);
-    total += ((size_t)r.count * k + 3) & ~size_t(3);
+    sort_cols[t] = unsorted_columns(k, L.orders[t].data());
+    if (r.count > (uint64_t)kSmallSortRows && sort_cols[t] > 0)
+      groups[k].push_back(t);
+    else
+      rest.push_back(t);
   }
-  if (ts.empty()) return;
+  if (groups.empty() && rest.empty()) return;
+  std::vector<size_t> pos(L.m, 0);
+  size_t total = 0;
+  for (const auto &kv : groups) {
+    for (int32_t t : kv.second) {
+      pos[t] = total;
+      total += (size_t)L.h_counts[t] * kv.first;
+    }
+    total = (total + 3) & ~size_t(3);
+  }
+  for (int32_t t : rest) {
+    pos[t] = total;
+    total += ((size_t)L.h_counts[t] * L.h_qs[t].k + 3) & ~size_t(3);
+  }
   const size_t bytes = total * sizeof(int32_t);
   void *base = on_device ? dev_alloc(ctx, bytes) : std::malloc(bytes);
   if (!base) FAIL(GSM_ERR_OOM, "host allocation of %zu bytes failed", bytes);
   {
-    RowBlock *b = new RowBlock{base, bytes, on_device, (int32_t)ts.size()};
+    int32_t nres = (int32_t)rest.size();
+    for (const auto &kv : groups) nres += (int32_t)kv.second.size();
+    RowBlock *b = new RowBlock{base, bytes, on_device, nres};
     std::lock_guard<std::mutex> lk(g_blocks_mu);
-    for (size_t i = 0; i < ts.size(); ++i) {
-      int32_t *p = (int32_t *)base + pos[i];
-      results[L.sel[ts[i]]].rows = p;
+    auto own = [&](int32_t t) {
+      int32_t *p = (int32_t *)base + pos[t];
+      results[L.sel[t]].rows = p;
       g_block_of[p] = b;
-    }
+    };
+    for (const auto &kv : groups)
+      for (int32_t t : kv.second) own(t);
+    for (int32_t t : rest) own(t);
   }
   int32_t *dst = on_device ? (int32_t *)base : (int32_t *)lane_srt(ctx, L, 4, bytes);
+  int32_t bits = 1;
+  while (bits < 31 && (int64_t(1) << bits) < ctx->n) ++bits;
+  // segmented sorts, one per query size
+  if (!groups.empty()) {
+    size_t nsegs = 0;
+    for (const auto &kv : groups) nsegs += kv.second.size();
+    SortSegment *h =
+        lane_pinned(ctx, L, &L.h_segs, &L.h_segs_cap, nsegs * sizeof(SortSegment));
+    SortSegment *d = (SortSegment *)lane_srt(ctx, L, 5, nsegs * sizeof(SortSegment));
+    size_t e = 0;
+    for (const auto &kv : groups) {
+      int64_t first = 0;
+      for (int32_t t : kv.second) {
+        h[e++] = SortSegment{L.a.final_rows + off[t], first, (int64_t)L.h_counts[t]};
+        first += (int64_t)L.h_counts[t];
+      }
+    }
+    CU(cudaMemcpyAsync(d, h, nsegs * sizeof(SortSegment), cudaMemcpyHostToDevice, L.stream));
+    e = 0;
+    for (const auto &kv : groups) {
+      const int32_t k = kv.first, nseg = (int32_t)kv.second.size();
+      int64_t N = 0;
+      int32_t S = 1;
+      for (int32_t t : kv.second) {
+        N += (int64_t)L.h_counts[t];
+        S = std::max(S, sort_cols[t]);
+      }
+      SortPrefix pre;
+      pre.given_bits = 1;
+      while ((int64_t(1) << pre.given_bits) < nseg) ++pre.given_bits;
+      const int32_t nw = sort_key_words(k, bits, pre);
+      uint64_t *ka = (uint64_t *)lane_srt(ctx, L, 0, (size_t)N * nw * sizeof(uint64_t));
+      uint64_t *kb = (uint64_t *)lane_srt(ctx, L, 1, (size_t)N * nw * sizeof(uint64_t));
+      void *scratch = lane_srt(ctx, L, 2, sort_scratch_bytes(N, k, bits, S, pre));
+      launch_pack_segments(d + e, nseg, N, k, bits, pre.given_bits, nw, ka, N, L.stream);
+      launch_sort_rows_packed(nullptr, 0, N, k, bits, S, ka, kb, N, dst + pos[kv.second[0]],
+                              scratch, ctx->opt.lookback_spin_limit, ctx->d_flags,
+                              sort_stall_tile(ctx), L.stream, pre);
+      CU(cudaGetLastError());
+      e += (size_t)nseg;
+    }
+  }
   std::vector<SmallSortItem> items;
   int32_t max_k = 2;
-  for (size_t i = 0; i < ts.size(); ++i) {
-    const int32_t t = ts[i], k = L.h_qs[t].k;
+  for (int32_t t : rest) {
+    const int32_t k = L.h_qs[t].k;
     const int64_t N = (int64_t)L.h_counts[t];
     const int32_t *src = L.a.final_rows + off[t];
-    const int32_t sort_cols = unsorted_columns(k, L.orders[t].data());
     if (N <= kSmallSortRows) {
-      items.push_back({src, dst + pos[i], (int32_t)N, k, sort_cols > 0 ? 1 : 0});
+      items.push_back({src, dst + pos[t], (int32_t)N, k, sort_cols[t] > 0 ? 1 : 0});
       max_k = std::max(max_k, k);
-    } else if (sort_cols == 0) {
-      CU(cudaMemcpyAsync(dst + pos[i], src, (size_t)N * k * sizeof(int32_t),
+    } else {  // canonical order already
+      CU(cudaMemcpyAsync(dst + pos[t], src, (size_t)N * k * sizeof(int32_t),
                          cudaMemcpyDeviceToDevice, L.stream));
-    } else {
-      canonical_rows(ctx, L, src, N, k, L.orders[t].data(), dst + pos[i]);
     }
   }
   if (!items.empty()) {
     const size_t ib = items.size() * sizeof(SmallSortItem);
-    if (L.h_items_cap < ib) {
-      CU(cudaStreamSynchronize(L.stream));  // an earlier upload may still read it
-      if (L.h_items) cudaFreeHost(L.h_items);
-      L.h_items = nullptr;
-      L.h_items_cap = 0;
-      CU(cudaHostAlloc(&L.h_items, std::max(ib, size_t(4096)), cudaHostAllocDefault));
-      L.h_items_cap = std::max(ib, size_t(4096));
-    }
-    std::memcpy(L.h_items, items.data(), ib);
+    SmallSortItem *h = lane_pinned(ctx, L, &L.h_items, &L.h_items_cap, ib);
+    std::memcpy(h, items.data(), ib);
     void *d_items = lane_srt(ctx, L, 3, ib);
-    CU(cudaMemcpyAsync(d_items, L.h_items, ib, cudaMemcpyHostToDevice, L.stream));
+    CU(cudaMemcpyAsync(d_items, h, ib, cudaMemcpyHostToDevice, L.stream));
     launch_sort_small((const SmallSortItem *)d_items, (int32_t)items.size(), max_k, L.stream);
     CU(cudaGetLastError());
   }

@@ -312,20 +312,36 @@ void launch_sort_small(const SmallSortItem *items, int32_t nitems, int32_t max_k
 // dense rank (ceil(log2 groups) bits or-ed in above the k columns, when the
 // key words have room and it saves digit passes: one flag pass, a scan and
 // one rank pass instead of the prefix's own digits); the result is the same.
+//
+// given_bits > 0 instead: the keys already carry a dense rank of their group
+// (rows of one group contiguous, groups in order) in given_bits bits above
+// the k columns, and the key is ceil((k*bits + given_bits)/64) words wide;
+// the sort orders the groups by it (segmented sort of many row sets at once).
 struct SortPrefix {
   int32_t cols = 0;
   int64_t groups = 0;
+  int32_t given_bits = 0;
 };
+// One segment of a segmented sort: the rows [src, src + count*k) (row-major)
+// become compact rows first .. first + count - 1, group `index`.
+struct SortSegment {
+  const int32_t *src;
+  int64_t first, count;
+};
+// Packs the segments' rows (segs: device array of nseg entries, ascending
+// `first`, N rows in all) into keys of nw words (word w of row r at
+// keys[w*ld + r]) with the segment's index in bits [k*bits, k*bits + seg_bits).
+void launch_pack_segments(const SortSegment *segs, int32_t nseg, int64_t N, int32_t k,
+                          int32_t bits, int32_t seg_bits, int32_t nw, uint64_t *keys, int64_t ld,
+                          cudaStream_t s);
 int32_t packed_words(int32_t k, int32_t bits);
 size_t sort_scratch_bytes(int64_t N, int32_t k, int32_t bits, int32_t sort_cols,
                           SortPrefix pre = SortPrefix());
+// Key words of a sort (wider with given_bits).
+int32_t sort_key_words(int32_t k, int32_t bits, SortPrefix pre = SortPrefix());
 // Digit passes the sort makes (and whether it ranks the prefix).
 int32_t sort_digit_passes(int64_t N, int32_t k, int32_t bits, int32_t sort_cols,
                           SortPrefix pre = SortPrefix(), bool *prefix_rank = nullptr);
-// Packed sort keys (word w of row r at keys[w*ld + r]) of N row-major rows of
-// k int32 (values < 2^bits), ready for launch_sort_rows_packed with a = null.
-void launch_pack_rows(const int32_t *rows, int64_t N, int32_t k, int32_t bits, uint64_t *keys,
-                      int64_t ld, cudaStream_t s);
 int launch_sort_rows_packed(const int32_t *a, int64_t lda, int64_t N, int32_t k, int32_t bits,
                             int32_t sort_cols, uint64_t *keys_a, uint64_t *keys_b, int64_t ld,
                             int32_t *out, void *scratch, int32_t spin_limit, uint32_t *err,

@@ -485,6 +485,41 @@ __global__ void __launch_bounds__(256) k_put_rank(uint64_t *__restrict__ keys, i
   }
 }
 
+// Packed keys of the segments' rows (see launch_pack_segments): compact row
+// i belongs to the last segment whose `first` is <= i (binary search).
+__global__ void __launch_bounds__(256) k_pack_segments(const SortSegment *__restrict__ segs,
+                                                       int32_t nseg, int64_t N, int32_t k,
+                                                       int32_t b, int32_t seg_bits, int32_t nw,
+                                                       uint64_t *__restrict__ keys, int64_t ld) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+    int32_t lo = 0, hi = nseg;  // largest j with segs[j].first <= i
+    while (hi - lo > 1) {
+      const int32_t mid = (lo + hi) >> 1;
+      if (segs[mid].first <= i) lo = mid; else hi = mid;
+    }
+    const int32_t *row = segs[lo].src + (i - segs[lo].first) * k;
+    for (int32_t t = 0; t < nw; ++t) {
+      uint64_t w = 0;
+      for (int32_t j = 0; j < k; ++j) {
+        const uint64_t v = (uint32_t)__ldg(row + j);
+        const int32_t p = (k - 1 - j) * b - 64 * t;
+        if (p >= 0 && p < 64)
+          w |= v << p;
+        else if (p < 0 && p + b > 0)
+          w |= v >> (-p);
+      }
+      const int32_t q = k * b - 64 * t;  // the segment index
+      const uint64_t sv = (uint64_t)lo;
+      if (q >= 0 && q < 64)
+        w |= sv << q;
+      else if (q < 0 && q + seg_bits > 0)
+        w |= sv >> (-q);
+      keys[(int64_t)t * ld + i] = w;
+    }
+  }
+}
+
 // One CTA per item: `count` (<= kSmallSortRows) row-major rows of k int32 are
 // loaded into shared memory and their indices bitonic-sorted by a
 // lexicographic comparison of the rows (rows are distinct embeddings, so the
@@ -563,12 +598,10 @@ namespace gsm {
 
 int32_t packed_words(int32_t k, int32_t bits) { return (k * bits + 63) / 64; }
 
-void launch_pack_rows(const int32_t *rows, int64_t N, int32_t k, int32_t bits, uint64_t *keys,
-                      int64_t ld, cudaStream_t s) {
-  if (N <= 0) return;
-  k_pack_keys<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(rows, 1, k, N, k, bits,
-                                                          packed_words(k, bits), keys, ld);
+int32_t sort_key_words(int32_t k, int32_t bits, SortPrefix pre) {
+  return (k * bits + std::max(pre.given_bits, 0) + 63) / 64;
 }
+
 
 namespace {
 
@@ -581,6 +614,7 @@ struct SortLayout {
   int32_t nw, digits, lo_bit;
   DigitPos pos;                // bit position of each digit pass
   int32_t prefix_cols, rank_bits, rank_pos;  // rank_bits = 0: no prefix rank
+  bool given;                                // a group rank came with the keys
   int64_t tiles;
   size_t o_ghist, o_gexcl, o_ticket, o_status, o_hist, o_hoff, o_tmp, o_flags, o_offs, o_rtmp,
       bytes;
@@ -590,10 +624,17 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 SortLayout sort_layout(int64_t N, int32_t k, int32_t bits, int32_t sort_cols, SortPrefix pre) {
   SortLayout L{};
-  L.nw = packed_words(k, bits);
+  L.nw = sort_key_words(k, bits, pre);
   sort_cols = std::min(std::max(sort_cols, 1), k);
   L.lo_bit = (k - sort_cols) * bits;
   L.digits = (sort_cols * bits + 7) / 8;
+  if (pre.given_bits > 0) {
+    // a group rank is already in the keys, right above the k columns: the
+    // sort field is the contiguous bits of the sorted columns and the rank
+    L.digits = (sort_cols * bits + pre.given_bits + 7) / 8;
+    pre = SortPrefix();  // no rank to compute
+    L.given = true;
+  }
   // prefix rank: the sorted leading columns keyed by their dense rank above
   // the k columns, when the key words have room and it saves passes
   if (pre.cols >= 1 && pre.cols < sort_cols && pre.groups >= 1 && L.nw <= 2) {
@@ -791,6 +832,14 @@ int launch_sort_rows_packed(const int32_t *a, int64_t lda, int64_t N, int32_t k,
     std::swap(src, dst);
   }
   return launches;
+}
+
+void launch_pack_segments(const SortSegment *segs, int32_t nseg, int64_t N, int32_t k,
+                          int32_t bits, int32_t seg_bits, int32_t nw, uint64_t *keys, int64_t ld,
+                          cudaStream_t s) {
+  if (N <= 0 || nseg <= 0) return;
+  const unsigned g = (unsigned)std::min<int64_t>((N + 255) / 256, (int64_t)sm_count() * 8);
+  k_pack_segments<<<g, 256, 0, s>>>(segs, nseg, N, k, bits, seg_bits, nw, keys, ld);
 }
 
 }  // namespace gsm
