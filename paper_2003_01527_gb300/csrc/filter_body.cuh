@@ -27,6 +27,23 @@ __device__ __forceinline__ uint32_t nlc_pass(const Desc &d, uint32_t vneed,
   return pass;
 }
 
+// The same test against v's row of the graph's label-count table: each
+// requirement reads its one count byte (the row is L1-resident), with no
+// register array to index.
+template <typename Desc>
+__device__ __forceinline__ uint32_t nlc_pass_row(const Desc &d, uint32_t vneed,
+                                                 const uint8_t *__restrict__ row) {
+  uint32_t pass = 0;
+  for (uint32_t m = vneed; m; m &= m - 1) {
+    const int u = __ffs(m) - 1;
+    bool ok = true;
+    for (int r = 0; r < d.nreq[u] && ok; ++r)
+      ok = (int32_t)__ldg(row + d.slot_label[d.req_slot[u][r]]) >= d.req_cnt[u][r];
+    if (ok) pass |= 1u << u;
+  }
+  return pass;
+}
+
 // One warp handles 32 consecutive data vertices per iteration (warps
 // warp_id, warp_id + n_warps, ...).  Each lane first applies the label /
 // degree / range test for its own vertex.  With the graph's neighbour label
@@ -57,22 +74,17 @@ __device__ __forceinline__ void filter_warps(const GraphDev &g, const Desc &d,
       deg = g.rp[v + 1] - g.rp[v];
     }
     uint32_t pre = 0, need = 0;
-#pragma unroll
-    for (int u = 0; u < kMaxK; ++u) {
-      if (u < d.k && valid && lv == d.qlab[u] && deg >= d.qdeg[u] && v >= d.lo[u] &&
-          v < d.hi[u]) {
-        pre |= 1u << u;
-        if (d.nreq[u] > 0) need |= 1u << u;
+    if (valid)
+      for (int u = 0; u < d.k; ++u) {
+        if (lv == d.qlab[u] && deg >= d.qdeg[u] && v >= d.lo[u] && v < d.hi[u]) {
+          pre |= 1u << u;
+          if (d.nreq[u] > 0) need |= 1u << u;
+        }
       }
-    }
     uint32_t result = pre & ~need;
     bool rest = false;
     if (need && g.nlc) {  // the counts are in the graph's table
-      int32_t cnt[kMaxK];
-      const uint8_t *row = g.nlc + (int64_t)v * g.nlc_stride;
-#pragma unroll
-      for (int s = 0; s < kMaxK; ++s) cnt[s] = s < d.nslots ? __ldg(row + d.slot_label[s]) : 0;
-      result |= nlc_pass(d, need, cnt);
+      result |= nlc_pass_row(d, need, g.nlc + (int64_t)v * g.nlc_stride);
       need = 0;
     } else if (need) {
       const int32_t b = g.rp[v], e = g.rp[v + 1];
@@ -124,14 +136,11 @@ __device__ __forceinline__ void filter_warps(const GraphDev &g, const Desc &d,
       }
       if (lane == src) result |= pass;
     }
-#pragma unroll
-    for (int u = 0; u < kMaxK; ++u) {
-      if (u < d.k) {
-        const uint32_t word = __ballot_sync(kFull, (result >> u) & 1u);
-        if (lane == u) {
-          bitmaps[(int64_t)u * d.n_words + grp] = word;
-          my_size += __popc(word);
-        }
+    for (int u = 0; u < d.k; ++u) {  // d.k is warp-uniform
+      const uint32_t word = __ballot_sync(kFull, (result >> u) & 1u);
+      if (lane == u) {
+        bitmaps[(int64_t)u * d.n_words + grp] = word;
+        my_size += __popc(word);
       }
     }
   }
