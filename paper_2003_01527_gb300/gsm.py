@@ -307,9 +307,38 @@ def _take_rows(ctx: int, r: gsm_result):
 
 def _take_all(ctx: int, results):
     """_copy_rows of every result, one device synchronisation, then every
-    library buffer released."""
-    out = [_copy_rows(r) for r in results]
-    if any(bool(r.on_device) and r.rows and r.count for r in results):
+    library buffer released.  Device results whose rows follow one another
+    in memory (a listing batch puts them in one block, at most 12 bytes
+    apart) are copied with one copy per such run and returned as views into
+    it; the copy never reads past a result's rows by more than that gap."""
+    out = [None] * len(results)
+    dev = sorted((ctypes.cast(r.rows, ctypes.c_void_p).value, 4 * int(r.count) * int(r.k), j)
+                 for j, r in enumerate(results) if r.on_device and r.rows and r.count)
+    if len(dev) > 1:
+        import torch
+        runs, cur = [], [dev[0]]
+        for e in dev[1:]:
+            p0, n0, _ = cur[-1]
+            if 0 <= e[0] - (p0 + n0) < 16:
+                cur.append(e)
+            else:
+                runs.append(cur)
+                cur = [e]
+        runs.append(cur)
+        for run in runs:
+            if len(run) < 2:
+                continue
+            lo = run[0][0]
+            hi = run[-1][0] + run[-1][1]
+            span = torch.as_tensor(_DevicePtr(lo, (hi - lo) // 4), device="cuda").clone()
+            for ptr, _, j in run:
+                c, k = int(results[j].count), int(results[j].k)
+                a = (ptr - lo) // 4
+                out[j] = span[a:a + c * k].view(c, k)
+    for j, r in enumerate(results):
+        if out[j] is None:
+            out[j] = _copy_rows(r)
+    if dev:
         import torch
         torch.cuda.synchronize()  # the copies are done before the buffers go
     for r in results:
