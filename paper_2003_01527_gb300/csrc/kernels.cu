@@ -565,7 +565,7 @@ constexpr size_t kFusedStageMax = 96 * 1024;   // ... with the tile's result row
 
 // kMaxThreads = 256: up to 256 threads per CTA, registers capped so that six
 // CTAs fit on an SM; 1024: any block size.
-template <int kMode, int kMaxThreads>
+template <int kMode, int kMaxThreads, bool kProbes>
 __global__ void __launch_bounds__(kMaxThreads, kMaxThreads == 256 ? 6 : 1) k_extend_fused(
     GraphDev g, LevelDesc d, const int32_t *__restrict__ F, int32_t ld,
     const int32_t *__restrict__ pstart, const uint8_t *__restrict__ pslot,
@@ -676,13 +676,15 @@ __global__ void __launch_bounds__(kMaxThreads, kMaxThreads == 256 ? 6 : 1) k_ext
         const int32_t w = __ldg(g.lcol + pst + (x - rs));
         rj[j] = r;
         wj[j] = w;
-        const bool ok = d.count_probes
-                            ? check_candidate_probes(g, d, ColumnRow{F, ld, r}, w, slot, &probes)
-                            : check_candidate(g, d, ColumnRow{F, ld, r}, w, slot);
+        bool ok;
+        if constexpr (kProbes)
+          ok = check_candidate_probes(g, d, ColumnRow{F, ld, r}, w, slot, &probes);
+        else
+          ok = check_candidate(g, d, ColumnRow{F, ld, r}, w, slot);
         if (ok && (!d.la || lookahead_ok(g, d, ColumnRow{F, ld, r}, w))) bits |= 1u << j;
       }
     }
-    if (d.count_probes) {
+    if constexpr (kProbes) {
 #pragma unroll
       for (int o = 16; o; o >>= 1) probes += __shfl_xor_sync(kAll, probes, o);
       if (lane == 0 && probes) atomicAdd(lookback + tiles + 3, (unsigned long long)probes);
@@ -1025,10 +1027,10 @@ void launch_extend_write(const GraphDev &g, const LevelDesc &d, const int32_t *F
 }
 
 namespace {
-// One persistent launch of k_extend_fused<kMode>: as many CTAs as fit on the
+// One persistent launch of k_extend_fused<kMode, ..., kProbes>: as many CTAs as fit on the
 // device at once (at most one per tile).  The dynamic shared-memory limit is
 // raised once per device for this instance.
-template <int kMode, int kMaxThreads>
+template <int kMode, int kMaxThreads, bool kProbes>
 void launch_fused_mode(const GraphDev &g, const LevelDesc &d, const int32_t *F, int64_t ld,
                        const int32_t *pstart, const uint8_t *pslot, const int64_t *woff,
                        const int32_t *tile_row, int64_t wa, int32_t W, int32_t tiles,
@@ -1045,7 +1047,7 @@ void launch_fused_mode(const GraphDev &g, const LevelDesc &d, const int32_t *F, 
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int di = dev & 63;
   if (!((attr_set.load() >> di) & 1ull)) {
-    cudaFuncSetAttribute(k_extend_fused<kMode, kMaxThreads>,
+    cudaFuncSetAttribute(k_extend_fused<kMode, kMaxThreads, kProbes>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmemAttr);
     attr_set.fetch_or(1ull << di);
   }
@@ -1053,7 +1055,7 @@ void launch_fused_mode(const GraphDev &g, const LevelDesc &d, const int32_t *F, 
   if (blocks_cache[di] == block && smem_cache[di] == smem && per_sm_cache[di][0]) {
     per_sm = per_sm_cache[di][1];
   } else {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_extend_fused<kMode, kMaxThreads>,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_extend_fused<kMode, kMaxThreads, kProbes>,
                                                   block, smem);
     blocks_cache[di] = block;
     smem_cache[di] = smem;
@@ -1061,7 +1063,7 @@ void launch_fused_mode(const GraphDev &g, const LevelDesc &d, const int32_t *F, 
     per_sm_cache[di][1] = per_sm;
   }
   const int64_t grid = std::min<int64_t>(tiles, (int64_t)std::max(per_sm, 1) * sms);
-  k_extend_fused<kMode, kMaxThreads><<<(unsigned)grid, block, smem, s>>>(
+  k_extend_fused<kMode, kMaxThreads, kProbes><<<(unsigned)grid, block, smem, s>>>(
       g, d, F, (int32_t)ld, pstart, pslot, woff, tile_row, wa, W, tiles, lookback, sink, stage,
       spin_limit, stall_tile);
 }
@@ -1085,25 +1087,32 @@ void launch_extend_fused(const GraphDev &g, const LevelDesc &d, const int32_t *F
   const size_t smem_rows = (base_ints + (size_t)items * sink.k) * sizeof(int32_t);
   const bool stage = sink.mode == kSinkRows && (sink.k & 1) && smem_rows <= kFusedStageMax;
   if (stage) smem = smem_rows;
-  auto go = [&](auto small) {
+  auto go = [&](auto small, auto probes) {
     constexpr int kMax = decltype(small)::value ? 256 : 1024;
+    constexpr bool kP = decltype(probes)::value;
     if (sink.mode == kSinkRows)
-      launch_fused_mode<kSinkRows, kMax>(g, d, F, ld, pstart, pslot, woff, tile_row, wa, W, T,
-                                         block, smem, lookback, sink, stage, spin_limit,
-                                         stall_tile, s);
+      launch_fused_mode<kSinkRows, kMax, kP>(g, d, F, ld, pstart, pslot, woff, tile_row, wa, W,
+                                             T, block, smem, lookback, sink, stage, spin_limit,
+                                             stall_tile, s);
     else if (sink.mode == kSinkKeys)
-      launch_fused_mode<kSinkKeys, kMax>(g, d, F, ld, pstart, pslot, woff, tile_row, wa, W, T,
-                                         block, smem, lookback, sink, false, spin_limit,
-                                         stall_tile, s);
+      launch_fused_mode<kSinkKeys, kMax, kP>(g, d, F, ld, pstart, pslot, woff, tile_row, wa, W,
+                                             T, block, smem, lookback, sink, false, spin_limit,
+                                             stall_tile, s);
     else
-      launch_fused_mode<kSinkColumns, kMax>(g, d, F, ld, pstart, pslot, woff, tile_row, wa, W,
-                                            T, block, smem, lookback, sink, false, spin_limit,
-                                            stall_tile, s);
+      launch_fused_mode<kSinkColumns, kMax, kP>(g, d, F, ld, pstart, pslot, woff, tile_row, wa,
+                                                W, T, block, smem, lookback, sink, false,
+                                                spin_limit, stall_tile, s);
   };
-  if (block <= 256)
-    go(std::true_type{});
+  // the probe-byte accounting is a separate instance, so the default one
+  // carries no trace of it
+  if (block <= 256 && !d.count_probes)
+    go(std::true_type{}, std::false_type{});
+  else if (block <= 256)
+    go(std::true_type{}, std::true_type{});
+  else if (!d.count_probes)
+    go(std::false_type{}, std::false_type{});
   else
-    go(std::false_type{});
+    go(std::false_type{}, std::true_type{});
 }
 
 void launch_split_points(const int64_t *woff, int64_t R, int64_t step, int64_t J,

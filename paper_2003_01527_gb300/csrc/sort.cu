@@ -268,7 +268,9 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_hist(const uint64_t *__r
 #pragma unroll
     for (int c = 0; c < kSortChunks; ++c) {
       if (base + c * kSortThreads + threadIdx.x >= N) continue;
-      for (int32_t d = 0; d < digits; ++d) {
+#pragma unroll
+      for (int32_t d = 0; d < kMaxDigits; ++d) {  // unrolled: pos is indexed statically
+        if (d >= digits) break;
         const int32_t p = pos.p[d];
         atomicAdd(&h[d * kBins + tile_digit<NW>(key[c], p >> 6, p & 63)], 1u);
       }
