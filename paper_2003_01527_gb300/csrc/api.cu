@@ -130,6 +130,8 @@ struct gsm_ctx {
   cudaEvent_t rows_ready = nullptr;
   void *sort_tmp = nullptr;  // radix-sort histograms (scale with the result)
   size_t sort_tmp_cap = 0;
+  void *d_prefix = nullptr;  // PrefixState of the last level's prefix ranks
+  size_t d_prefix_cap = 0;
   void *sort_keys = nullptr;  // the second buffer of the packed-key radix passes
   size_t sort_keys_cap = 0;
   const int32_t *last_rows = nullptr;  // sorted rows of the last gsm_enumerate
@@ -699,6 +701,12 @@ struct Run {
   }
   unsigned __int128 count = 0;
   unsigned long long *d_total;
+  // the last level's keys carry the dense rank of the prefix (query vertices
+  // 0..rank_p-1, placed first in that order) when rank_p > 0: ranks of the
+  // rows of the last level's input piece in `rank`, running state in prefix
+  int32_t rank_p = 0, rank_pos = 0;
+  PrefixState *prefix = nullptr;
+  const int32_t *rank = nullptr;
 };
 
 void recurse(Run &R, int32_t i, const int32_t *F, int64_t ld, int64_t rows);
@@ -799,8 +807,10 @@ void process_sub(Run &R, int32_t i, const int32_t *F, int64_t ld, const int32_t 
   if (S == 0) return;
   if (last) {
     ensure_acc(R, R.acc_rows + (uint64_t)S);
-    const RowSink sink{R.acc_mode, R.k, R.key_bits, R.key_nw, R.acc_ld, (int64_t)R.acc_rows,
-                       ctx->acc[0]};
+    RowSink sink{R.acc_mode, R.k, R.key_bits, R.key_nw, R.acc_ld, (int64_t)R.acc_rows,
+                 ctx->acc[0]};
+    sink.rank = R.rank;
+    sink.rank_pos = R.rank_pos;
     timed(ctx, K_WRITE, (double)S * R.acc_row_bytes(), (uint64_t)S, 1, [&] {
       launch_extend_write(R.g, d, F, ld, pstart, woff, tile_row, wa, wb, R.block, masks,
                           tile_off, sink, ctx->stream);
@@ -866,6 +876,8 @@ void process_fused(Run &R, int32_t i, const int32_t *F, int64_t ld, const int32_
     ensure_acc(R, R.acc_rows + (uint64_t)W);
     sink = RowSink{R.acc_mode, R.k, R.key_bits, R.key_nw, R.acc_ld, (int64_t)R.acc_rows,
                    ctx->acc[0]};
+    sink.rank = R.rank;
+    sink.rank_pos = R.rank_pos;
   } else {
     Fn = (int32_t *)stack_push(ctx, (size_t)W * w_out * sizeof(int32_t));
     sink = RowSink{kSinkColumns, w_out, 0, 0, W, 0, Fn};
@@ -987,10 +999,24 @@ void recurse_rest(Run &R, int32_t i, const int32_t *F, int64_t ld, int64_t rows,
                   const int32_t *pstart, const uint8_t *pslot, const int64_t *woff, int64_t W) {
   R.ctx->run.frontier[i] += (uint64_t)rows;
   R.ctx->run.candidates[i] += (uint64_t)W;
+  if (i == R.k - 1 && R.rank_p > 0 && rows > 0) {
+    // prefix ranks of this piece of the last level's input (the caller's
+    // stack mark releases them)
+    gsm_ctx *ctx = R.ctx;
+    int32_t *flags = (int32_t *)stack_push(ctx, sizeof(int32_t) * rows);
+    int64_t *offs = (int64_t *)stack_push(ctx, sizeof(int64_t) * (rows + 1));
+    int64_t *tmp = (int64_t *)stack_push(ctx, sizeof(int64_t) * scan_tmp_elems(rows));
+    int32_t *rank = (int32_t *)stack_push(ctx, sizeof(int32_t) * rows);
+    ctx->run.kernel_launches +=
+        launch_prefix_ranks(F, ld, rows, R.rank_p, R.prefix, flags, offs, tmp, rank, ctx->stream);
+    CU(cudaGetLastError());
+    R.rank = rank;
+  }
   std::vector<int64_t> bnd, bw;
   level_chunks(R, woff, rows, W, bnd, bw);
   for (size_t j = 0; j + 1 < bnd.size(); ++j)
     process_sub(R, i, F, ld, pstart, pslot, woff, bnd[j], bnd[j + 1], bw[j], bw[j + 1]);
+  if (i == R.k - 1) R.rank = nullptr;
 }
 
 // ---- compressed frontiers (GSM_OPT_COMPRESSED_FRONTIERS): a row of width i
@@ -1266,6 +1292,23 @@ void run_query(gsm_ctx *ctx, const gsm_query *q, bool enumerate, int32_t *out, u
   R.acc_mode = sort_cols == 0 ? kSinkRows : kSinkKeys;
   R.key_bits = key_bits;
   R.key_nw = packed_words(q->k, key_bits);
+  // rows leave the levels sorted by the columns of query vertices 0..p-1 when
+  // the matching order starts with them; the last level then writes their
+  // dense rank into the keys' spare bits (any int32 fits), so that the sort
+  // keys those columns by it
+  if (enumerate && R.acc_mode == kSinkKeys && !(ctx->opt.flags & GSM_OPT_COMPRESSED_FRONTIERS) &&
+      R.key_nw <= 2 && sort_rank_pos(q->k, key_bits, sort_cols) + 31 <= 64 * R.key_nw) {
+    int32_t p = 0;
+    while (p < q->k && R.order[p] == p) ++p;
+    if (p >= 1 && p < sort_cols) {
+      R.rank_p = p;
+      R.rank_pos = sort_rank_pos(q->k, key_bits, sort_cols);
+      ensure_buf(ctx, &ctx->d_prefix, &ctx->d_prefix_cap, sizeof(PrefixState), false, 0);
+      R.prefix = (PrefixState *)ctx->d_prefix;
+      launch_prefix_state_reset(R.prefix, ctx->stream);
+      ctx->run.kernel_launches += 1;
+    }
+  }
 
   const int32_t nw = (ctx->n + 31) / 32;
   const uint32_t *bm = pre ? pre->bitmaps : (const uint32_t *)ctx->bitmaps;
@@ -1384,6 +1427,7 @@ void run_query(gsm_ctx *ctx, const gsm_query *q, bool enumerate, int32_t *out, u
     while (pre.cols < q->k && R.order[pre.cols] == pre.cols) ++pre.cols;
     pre.groups = pre.cols > 0 ? (int64_t)ctx->run.frontier[pre.cols] : 0;
     if (pre.cols == 0 || pre.groups <= 0) pre = SortPrefix();
+    pre.ranked = R.rank_p > 0 && pre.cols == R.rank_p;  // the last level wrote the ranks
     // outside the budget, like the result buffers it serves
     ensure_buf(ctx, &ctx->sort_tmp, &ctx->sort_tmp_cap,
                sort_scratch_bytes((int64_t)total, q->k, R.key_bits, sort_cols, pre), false, 0);
@@ -2566,6 +2610,7 @@ void gsm_destroy(gsm_ctx *ctx) {
     dev_free(ctx, ctx->acc[1], ctx->acc_cap[1]);
     dev_free(ctx, ctx->sort_tmp, ctx->sort_tmp_cap);
     dev_free(ctx, ctx->sort_keys, ctx->sort_keys_cap);
+    dev_free(ctx, ctx->d_prefix, ctx->d_prefix_cap);
     for (auto &p : ctx->parked) {
       dev_free(ctx, p.acc[0], p.acc_cap[0]);
       dev_free(ctx, p.acc[1], p.acc_cap[1]);

@@ -753,6 +753,49 @@ __global__ void k_fetch_level(const unsigned long long *__restrict__ words,
   }
 }
 
+// flags[r] = 1 where row r's prefix (positions 0..p-1) differs from row
+// r-1's, or, for r = 0, from the prefix the last earlier piece ended with.
+__global__ void k_prefix_change(const int32_t *__restrict__ F, int64_t ld, int64_t rows,
+                                int32_t p, const PrefixState *__restrict__ st,
+                                int32_t *__restrict__ flags) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += stride) {
+    bool diff = false;
+    for (int32_t c = 0; c < p; ++c) {
+      const int32_t prev = r > 0 ? F[(int64_t)c * ld + r - 1] : st->prefix[c];
+      diff = diff || F[(int64_t)c * ld + r] != prev;
+    }
+    flags[r] = diff ? 1 : 0;
+  }
+}
+
+// rank[r] = the last rank of the earlier pieces + the changes up to r
+// (offs: exclusive scan of the flags, offs[rows] = their total).
+__global__ void k_prefix_rank(const int64_t *__restrict__ offs, int64_t rows,
+                              const PrefixState *__restrict__ st, int32_t *__restrict__ rank) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const long long last = st->last;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += stride)
+    rank[r] = (int32_t)(last + offs[r + 1]);
+}
+
+// After the piece: the state takes its last rank and last row's prefix.
+__global__ void k_prefix_advance(const int32_t *__restrict__ F, int64_t ld, int64_t rows,
+                                 int32_t p, const int64_t *__restrict__ offs,
+                                 PrefixState *__restrict__ st) {
+  if (threadIdx.x == 0 && blockIdx.x == 0 && rows > 0) {
+    st->last += offs[rows];
+    for (int32_t c = 0; c < p; ++c) st->prefix[c] = F[(int64_t)c * ld + rows - 1];
+  }
+}
+
+__global__ void k_prefix_reset(PrefixState *st) {
+  if (threadIdx.x == 0) {
+    st->last = -1;
+    for (int32_t c = 0; c < kMaxK; ++c) st->prefix[c] = -1;  // no vertex id: a change
+  }
+}
+
 // One warp per hub: every neighbour's bit of the hub's bitmap.
 __global__ void k_hub_bits(GraphDev g, const int32_t *__restrict__ hubs, int32_t H,
                            int32_t words, uint32_t *__restrict__ bits) {
@@ -895,6 +938,22 @@ void launch_hub_bitmaps(const GraphDev &g, const int32_t *hubs, int32_t H, int32
   if (H <= 0) return;
   cudaMemsetAsync(bits, 0, sizeof(uint32_t) * (size_t)H * words, s);
   k_hub_bits<<<grid_for((int64_t)H * 32, 256, 152 * 8), 256, 0, s>>>(g, hubs, H, words, bits);
+}
+
+void launch_prefix_state_reset(PrefixState *st, cudaStream_t s) {
+  k_prefix_reset<<<1, 32, 0, s>>>(st);
+}
+
+int launch_prefix_ranks(const int32_t *F, int64_t ld, int64_t rows, int32_t p, PrefixState *st,
+                        int32_t *flags, int64_t *offs, int64_t *tmp, int32_t *rank,
+                        cudaStream_t s) {
+  if (rows <= 0) return 0;
+  const unsigned g = grid_for(rows, 256, 152 * 8);
+  k_prefix_change<<<g, 256, 0, s>>>(F, ld, rows, p, st, flags);
+  launch_scan_i32(flags, offs, rows, tmp, s);
+  k_prefix_rank<<<g, 256, 0, s>>>(offs, rows, st, rank);
+  k_prefix_advance<<<1, 32, 0, s>>>(F, ld, rows, p, offs, st);
+  return 3 + scan_kernels(rows);
 }
 
 void launch_label_counts(const GraphDev &g, uint8_t *nlc, int32_t stride, cudaStream_t s) {

@@ -223,7 +223,29 @@ struct RowSink {
   int64_t ld;    // elements per column / per key word
   int64_t row0;  // row of the first survivor
   void *out;
+  // kSinkKeys with 1-2 words: rank[r] (the dense rank of parent row r's
+  // sorted prefix) is or-ed into every key written from row r, at bit
+  // rank_pos (above the k columns); null: none
+  const int32_t *rank = nullptr;
+  int32_t rank_pos = 0;
 };
+
+// Dense ranks of the prefix (positions 0..p-1) of the rows of a frontier
+// piece whose rows stand sorted by it, continuing the ranks of the pieces
+// before it (pieces in order): state holds the last rank given (-1 at the
+// start of a query) and the prefix it was given to.
+struct PrefixState {
+  long long last;
+  int32_t prefix[kMaxK];
+};
+// Resets *st for a new query.
+void launch_prefix_state_reset(PrefixState *st, cudaStream_t s);
+// rank[r] for rows [0, rows) of F (leading dimension ld); flags and offs
+// (rows + 1 int64) and tmp (scan_tmp_elems(rows) int64) are scratch.
+// Returns the kernels launched.
+int launch_prefix_ranks(const int32_t *F, int64_t ld, int64_t rows, int32_t p, PrefixState *st,
+                        int32_t *flags, int64_t *offs, int64_t *tmp, int32_t *rank,
+                        cudaStream_t s);
 
 // Write pass: survivor q of tile t becomes row sink.row0 + tile_off[t] + rank;
 // input position c goes to column d.out_col[c], the new vertex to column
@@ -309,7 +331,7 @@ void launch_sort_small(const SmallSortItem *items, int32_t nitems, int32_t max_k
 // Optional knowledge of the input order: the rows already stand sorted by
 // their first `cols` columns (1 <= cols < sort_cols), with at most `groups`
 // distinct prefixes.  The sort then orders those columns by the prefix's
-// dense rank (ceil(log2 groups) bits or-ed in above the k columns, when the
+// dense rank (ceil(log2 groups) bits or-ed in at sort_rank_pos, when the
 // key words have room and it saves digit passes: one flag pass, a scan and
 // one rank pass instead of the prefix's own digits); the result is the same.
 //
@@ -321,6 +343,10 @@ struct SortPrefix {
   int32_t cols = 0;
   int64_t groups = 0;
   int32_t given_bits = 0;
+  // with cols: the keys already carry the prefix's dense rank at
+  // sort_rank_pos (written by the last level, RowSink::rank): the sort
+  // computes none
+  bool ranked = false;
 };
 // One segment of a segmented sort: the rows [src, src + count*k) (row-major)
 // become compact rows first .. first + count - 1, group `index`.
@@ -337,6 +363,10 @@ void launch_pack_segments(const SortSegment *segs, int32_t nseg, int64_t N, int3
 int32_t packed_words(int32_t k, int32_t bits);
 size_t sort_scratch_bytes(int64_t N, int32_t k, int32_t bits, int32_t sort_cols,
                           SortPrefix pre = SortPrefix());
+// Bit where a prefix rank goes in the keys of a sort on sort_cols columns:
+// above the k columns and above every bit the plain digit passes read, so
+// that keys carrying a rank sort right whether or not the sort uses it.
+int32_t sort_rank_pos(int32_t k, int32_t bits, int32_t sort_cols);
 // Key words of a sort (wider with given_bits).
 int32_t sort_key_words(int32_t k, int32_t bits, SortPrefix pre = SortPrefix());
 // Digit passes the sort makes (and whether it ranks the prefix).

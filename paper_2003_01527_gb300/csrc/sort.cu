@@ -600,6 +600,12 @@ namespace gsm {
 
 int32_t packed_words(int32_t k, int32_t bits) { return (k * bits + 63) / 64; }
 
+int32_t sort_rank_pos(int32_t k, int32_t bits, int32_t sort_cols) {
+  sort_cols = std::min(std::max(sort_cols, 1), k);
+  const int32_t lo = (k - sort_cols) * bits;
+  return std::max(k * bits, lo + 8 * ((sort_cols * bits + 7) / 8));
+}
+
 int32_t sort_key_words(int32_t k, int32_t bits, SortPrefix pre) {
   return (k * bits + std::max(pre.given_bits, 0) + 63) / 64;
 }
@@ -617,6 +623,7 @@ struct SortLayout {
   DigitPos pos;                // bit position of each digit pass
   int32_t prefix_cols, rank_bits, rank_pos;  // rank_bits = 0: no prefix rank
   bool given;                                // a group rank came with the keys
+  bool ranked;                               // the prefix rank came with the keys
   int64_t tiles;
   size_t o_ghist, o_gexcl, o_ticket, o_status, o_hist, o_hoff, o_tmp, o_flags, o_offs, o_rtmp,
       bytes;
@@ -643,10 +650,12 @@ SortLayout sort_layout(int64_t N, int32_t k, int32_t bits, int32_t sort_cols, So
     int32_t rb = 1;
     while (rb < 62 && (int64_t(1) << rb) < pre.groups) ++rb;
     const int32_t low = ((sort_cols - pre.cols) * bits + 7) / 8, high = (rb + 7) / 8;
-    if (k * bits + rb <= 64 * L.nw && low + high < L.digits) {
+    const int32_t rp = sort_rank_pos(k, bits, sort_cols);
+    if (rp + rb <= 64 * L.nw && low + high < L.digits) {
       L.prefix_cols = pre.cols;
       L.rank_bits = rb;
-      L.rank_pos = k * bits;
+      L.ranked = pre.ranked;
+      L.rank_pos = rp;
       for (int32_t d = 0; d < low; ++d) L.pos.p[d] = L.lo_bit + 8 * d;
       for (int32_t d = 0; d < high; ++d) L.pos.p[low + d] = L.rank_pos + 8 * d;
       L.digits = low + high;
@@ -678,7 +687,7 @@ SortLayout sort_layout(int64_t N, int32_t k, int32_t bits, int32_t sort_cols, So
     L.o_tmp = off;
     off = align256(off + sizeof(int64_t) * (size_t)scan_tmp_elems(H));
   }
-  if (L.rank_bits) {
+  if (L.rank_bits && !L.ranked) {
     L.o_flags = off;
     off = align256(off + sizeof(int32_t) * (size_t)N);
     L.o_offs = off;
@@ -740,7 +749,7 @@ size_t sort_scratch_bytes(int64_t N, int32_t k, int32_t bits, int32_t sort_cols,
 int32_t sort_digit_passes(int64_t N, int32_t k, int32_t bits, int32_t sort_cols,
                           SortPrefix pre, bool *prefix_rank) {
   const SortLayout L = sort_layout(std::max<int64_t>(N, 1), k, bits, sort_cols, pre);
-  if (prefix_rank) *prefix_rank = L.rank_bits > 0;
+  if (prefix_rank) *prefix_rank = L.rank_bits > 0 && !L.ranked;  // ranks computed here
   return L.digits;
 }
 
@@ -758,7 +767,7 @@ int launch_sort_rows_packed(const int32_t *a, int64_t lda, int64_t N, int32_t k,
     ++launches;
   }
   char *sc = (char *)scratch;
-  if (L.rank_bits) {
+  if (L.rank_bits && !L.ranked) {
     // the prefix's dense rank: change flags, their scan, the rank or-ed in
     // above the k columns (the prefix bits themselves stay, for the unpack)
     const int32_t plo = (k - L.prefix_cols) * bits, phi = k * bits;

@@ -69,6 +69,14 @@ struct ColumnRow {
   __device__ __forceinline__ int32_t operator()(int c) const { return F[c * ld + r]; }
 };
 
+// Index of the parent row a written row comes from (for the sink's prefix
+// ranks); -1 where the row type has none.
+__device__ __forceinline__ int32_t parent_index(const ColumnRow &r) { return r.r; }
+template <typename Row>
+__device__ __forceinline__ int32_t parent_index(const Row &) {
+  return -1;
+}
+
 // The checks of Sec. 3.2 verification that need no adjacency search, for
 // candidate w of a partial embedding (row(c) = the image of pi_c): label +
 // signature (bitmap of C(pi_i)), injectivity against same-label, non-adjacent
@@ -207,6 +215,19 @@ __device__ __forceinline__ void put_row(const RowSink &sink, const LevelDesc &d,
       } else {
         w0 |= v << p;
         if (p + sink.bits > 64) w1 |= v >> (64 - p);
+      }
+    }
+    if (sink.rank) {
+      const int32_t pr = parent_index(src);
+      if (pr >= 0) {
+        const uint64_t v = (uint32_t)__ldg(sink.rank + pr);
+        const int32_t p = sink.rank_pos;
+        if (p >= 64) {
+          w1 |= v << (p - 64);
+        } else {
+          w0 |= v << p;
+          if (p > 32) w1 |= v >> (64 - p);
+        }
       }
     }
     o[0] = w0;

@@ -392,3 +392,25 @@ def test_refined_candidates_match_oracle_and_results_do_not_change(gsm_lib, rmat
             else:
                 assert count == base[j][0] and np.array_equal(rows, base[j][1])
         m.close()
+
+
+def test_sorted_prefix_ranks_across_pieces(gsm_lib):
+    """Slice q9 of the R-MAT 16 workload (matching order 0, 1, 3, 4, 2, 5):
+    the last level writes the rank of the sorted prefix (query vertices 0, 1)
+    into the sort keys, continued across the pieces its input comes in.
+    Under budgets that split the levels into more and more pieces, and with
+    small launch chunks, the rows still equal the oracle's stored digest."""
+    gold = _golden("rmat16_labelled_slices.json")
+    g, _ = I.rmat_labelled_workload(scale=16, num_labels=8, zipf_s=1.0, num_queries=0, seed=2)
+    item = gold["queries"][9]
+    for budget, chunk in ((0, 0), (96 << 20, 0), (48 << 20, 100_000)):
+        m = gsm_lib.Matcher(device=0, mem_budget_bytes=budget, chunk_rows=chunk)
+        m.load_graph(g.row_ptr, g.col, g.labels)
+        Q = m.query(item["k"], item["edges"], item["labels"]).restrict(0, 0, item["root_hi"])
+        rows, count = m.enumerate(Q)
+        st = m.last_run_stats()
+        assert st["order"][:2] == [0, 1] and st["order"] != list(range(item["k"]))
+        assert count == item["count"]
+        digest = hashlib.sha256(np.ascontiguousarray(rows, dtype="<i4").tobytes()).hexdigest()
+        assert digest == item["rows_sha256"], (budget, chunk)
+        m.close()
