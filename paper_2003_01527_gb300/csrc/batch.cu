@@ -25,10 +25,6 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kPScanThreads = 256;
 constexpr int kPScanTile = 2048;  // 8 elements per thread
 
-__device__ __forceinline__ bool bm_has(const uint32_t *__restrict__ bm, int32_t v) {
-  return (__ldg(bm + (v >> 5)) >> (v & 31)) & 1u;
-}
-
 __device__ __forceinline__ int64_t warp_incl(int64_t x, int lane) {
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
