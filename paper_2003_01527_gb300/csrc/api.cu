@@ -598,7 +598,7 @@ gsm_status validate_query_edges(int32_t k, int32_t m, const int32_t *edges, uint
 bool aut_exists(int32_t k, const uint32_t *adj, const int32_t *lab, uint32_t fixed, int32_t a,
                 int32_t b) {
   int32_t sigma[kMaxK];
-  for (int32_t u = 0; u < k; ++u) sigma[u] = -1;
+  for (int32_t u = 0; u < kMaxK; ++u) sigma[u] = -1;
   for (int32_t u = 0; u < k; ++u)
     if (fixed >> u & 1u) sigma[u] = u;
   if (sigma[a] >= 0 && sigma[a] != b) return false;
