@@ -783,7 +783,7 @@ def run_gpu(args):
         "kernel_split": {"note": "per-kernel CUDA events on every launch, from a second "
                                  "timed pass of the same steps with one host worker (the "
                                  "headline pass records no per-kernel events and lists "
-                                 "with two)",
+                                 "with the default six workers)",
                          "ms_per_step_with_events": round(ms_k / args.steps, 4)},
         "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": round(statistics.median(e2e_ms), 3)},
