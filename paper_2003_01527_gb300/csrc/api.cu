@@ -859,14 +859,16 @@ void process_fused(Run &R, int32_t i, const int32_t *F, int64_t ld, const int32_
   const int32_t w_out = i + 1;
   Carve cv;
   const size_t o_row = cv.add<int32_t>(tiles + 1);
-  const size_t o_lb = cv.add<unsigned long long>(tiles + kLbExtra);
-  // the work scan of the next level (sized for up to W rows)
-  const size_t o_tmp = last ? 0 : cv.add<int64_t>(scan_tmp_elems(W));
+  // the level's look-back words, then (not last) those of the next level's
+  // pivot choice and work scan (sized for up to W rows); k_tile_rows zeroes
+  // both
+  const int64_t pwords = last ? 0 : pivot_scan_words(W);
+  const size_t o_lb = cv.add<unsigned long long>(tiles + kLbExtra + pwords);
   char *sc = (char *)scratch_get(ctx, cv.off);
   int32_t *tile_row = (int32_t *)(sc + o_row);
   unsigned long long *lb = (unsigned long long *)(sc + o_lb);
-  timed(ctx, K_PIVOT, 8.0 * (nrows + tiles) + 8.0 * tiles, (uint64_t)tiles, 1, [&] {
-    launch_tile_rows(woff, ra, rb, wa, wb, R.block, tile_row, lb, ctx->stream);
+  timed(ctx, K_PIVOT, 8.0 * (nrows + tiles) + 8.0 * (tiles + pwords), (uint64_t)tiles, 1, [&] {
+    launch_tile_rows(woff, ra, rb, wa, wb, R.block, tile_row, lb, ctx->stream, pwords);
   });
   const double read_bytes = (double)nrows * (4.0 * i + 13.0) + 4.0 * (double)W;
   const Mark mk = stack_mark(ctx);
@@ -900,17 +902,16 @@ void process_fused(Run &R, int32_t i, const int32_t *F, int64_t ld, const int32_
   }
   // the next level's pivot choice and work scan run before the host learns
   // S (they read it on the device; their arrays were reserved for W rows),
-  // so one read-back serves both levels
+  // and their last CTA writes both levels' totals to the host stage, so one
+  // read-back serves both levels
   const LevelDesc &dn = R.lv[i + 1];
   int32_t *pstart2 = (int32_t *)stack_push(ctx, sizeof(int32_t) * W);
   uint8_t *pslot2 = (uint8_t *)stack_push(ctx, W);
   int64_t *woff2 = (int64_t *)stack_push(ctx, sizeof(int64_t) * (W + 1));
-  timed(ctx, K_PIVOT, 0.0, 0, 1 + scan_kernels(W), [&] {
-    launch_pivot(R.g, dn, Fn, W, W, pstart2, pslot2, woff2, ctx->stream, S_dev);
-    launch_scan_i64_dev(woff2, woff2, W, S_dev, (int64_t *)(sc + o_tmp), ctx->stream);
+  timed(ctx, K_PIVOT, 0.0, 0, 1, [&] {
+    launch_pivot_scan(R.g, dn, Fn, W, W, pstart2, pslot2, woff2, lb + tiles + kLbExtra,
+                      R.spin_limit, ctx->d_stage, ctx->stream, S_dev);
   });
-  launch_fetch_level(lb + tiles + 1, woff2, ctx->d_stage, ctx->stream);
-  ctx->run.kernel_launches += 1;
   CU(cudaGetLastError());
   CU(cudaStreamSynchronize(ctx->stream));
   const int64_t S = ((volatile int64_t *)ctx->h_stage)[0];
@@ -920,7 +921,7 @@ void process_fused(Run &R, int32_t i, const int32_t *F, int64_t ld, const int32_
   const double probes = (double)((volatile int64_t *)ctx->h_stage)[3];
   ctx->kstats[K_FUSED].algo_bytes += (double)S * 4.0 * w_out + probes;
   ctx->kstats[K_FUSED].probe_bytes += probes;
-  ctx->kstats[K_PIVOT].algo_bytes += (double)S * (4.0 * dn.nb + 8.0 * dn.nb + 13.0 + 16.0);
+  ctx->kstats[K_PIVOT].algo_bytes += (double)S * (4.0 * dn.nb + 8.0 * dn.nb + 13.0);
   ctx->kstats[K_PIVOT].items += (uint64_t)S;
   if (S > 0) recurse_rest(R, i + 1, Fn, W, S, pstart2, pslot2, woff2, W2);
   stack_release(ctx, mk);
@@ -983,13 +984,19 @@ void recurse(Run &R, int32_t i, const int32_t *F, int64_t ld, int64_t rows) {
   int32_t *pstart = (int32_t *)stack_push(ctx, sizeof(int32_t) * rows);
   uint8_t *pslot = (uint8_t *)stack_push(ctx, rows);
   int64_t *woff = (int64_t *)stack_push(ctx, sizeof(int64_t) * (rows + 1));
-  int64_t *tmp = (int64_t *)scratch_get(ctx, sizeof(int64_t) * scan_tmp_elems(rows));
-  timed(ctx, K_PIVOT, (double)rows * (4.0 * d.nb + 8.0 * d.nb + 13.0 + 16.0), (uint64_t)rows,
-        1 + scan_kernels(rows), [&] {
-    launch_pivot(R.g, d, F, ld, rows, pstart, pslot, woff, ctx->stream);
-    launch_scan_i64(woff, woff, rows, tmp, ctx->stream);
+  const int64_t pwords = pivot_scan_words(rows);
+  auto *plb = (unsigned long long *)scratch_get(ctx, sizeof(unsigned long long) * pwords);
+  CU(cudaMemsetAsync(plb, 0, sizeof(unsigned long long) * pwords, ctx->stream));
+  timed(ctx, K_PIVOT, (double)rows * (4.0 * d.nb + 8.0 * d.nb + 13.0), (uint64_t)rows, 1,
+        [&] {
+    launch_pivot_scan(R.g, d, F, ld, rows, pstart, pslot, woff, plb, R.spin_limit,
+                      ctx->d_stage, ctx->stream);
   });
-  const int64_t W = read_i64(ctx, woff + rows);
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(ctx->stream));
+  if (((volatile int64_t *)ctx->h_stage)[1])
+    FAIL(GSM_ERR_TIMEOUT, "a pivot-scan tile waited too long for its predecessors");
+  const int64_t W = ((volatile int64_t *)ctx->h_stage)[2];
   recurse_rest(R, i, F, ld, rows, pstart, pslot, woff, W);
   stack_release(ctx, mk);
 }

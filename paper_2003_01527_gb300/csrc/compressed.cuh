@@ -21,7 +21,7 @@ struct CFrontier {
   const int32_t *P[kMaxK + 1];
 };
 
-// Pivot choice of launch_pivot for the R rows of width i of f.
+// Pivot choice of launch_pivot_scan for the R rows of width i of f.
 void launch_cpivot(const GraphDev &g, const LevelDesc &d, const CFrontier &f, int32_t i,
                    int64_t R, int32_t *pstart, uint8_t *pslot, int64_t *work, cudaStream_t s);
 

@@ -5,7 +5,8 @@
 // Paper mapping (Sec. 3.2, Algorithm 1; Sec. 3.3):
 //   k_filter            Filter_candidate_set (label / degree / neighbourhood)
 //   k_bitmap_*          the first frontier: compaction of C(pi_0)
-//   k_pivot             Advance setup: which mapped neighbour's row to traverse
+//   k_pivot_scan        Advance setup: which mapped neighbour's row to traverse,
+//                       and the scan of the rows' work
 //   k_extend_count      Advance + Compute: check label, injectivity and every
 //                       non-tree edge of each traversed candidate in one step
 //   k_scan_*            the compaction scan
@@ -200,9 +201,7 @@ __device__ int64_t block_excl_scan(int64_t x, int64_t *s_warp, int64_t *total) {
 
 template <typename T>
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const T *in, int64_t n,
-                                                              int64_t *partial,
-                                                              const int64_t *n_dev) {
-  if (n_dev) n = *n_dev;  // the actual length (n is then the launch's bound)
+                                                              int64_t *partial) {
   __shared__ int64_t s_warp[33];
   const int64_t base = (int64_t)blockIdx.x * kScanTile;
   int64_t sum = 0;
@@ -235,9 +234,7 @@ __global__ void __launch_bounds__(1024) k_scan_partials(int64_t *partial, int64_
 template <typename T>
 __global__ void __launch_bounds__(kScanThreads) k_scan_down(const T *in, int64_t n,
                                                             const int64_t *__restrict__ partial,
-                                                            int64_t nb, int64_t *out,
-                                                            const int64_t *n_dev) {
-  if (n_dev) n = *n_dev;
+                                                            int64_t nb, int64_t *out) {
   __shared__ int64_t s_val[kScanTile];
   __shared__ int64_t s_warp[33];
   const int64_t base = (int64_t)blockIdx.x * kScanTile;
@@ -275,9 +272,7 @@ constexpr int kOneThreads = 512;
 constexpr int64_t kOneCtaMax = 4 * kOneThreads * kScanIpt;  // longest input taken
 template <typename T>
 __global__ void __launch_bounds__(kOneThreads) k_scan_one_cta(const T *in, int64_t n,
-                                                              int64_t *out,
-                                                              const int64_t *n_dev) {
-  if (n_dev) n = *n_dev;
+                                                              int64_t *out) {
   constexpr int kTile = kOneThreads * kScanIpt;
   __shared__ int64_t s_val[kTile];
   __shared__ int64_t s_warp[33];
@@ -342,48 +337,144 @@ __global__ void k_bitmap_emit(const uint32_t *__restrict__ bm, int32_t n_words,
 // consecutive rows, or writing one position of 32 consecutive survivors,
 // touches 128 contiguous bytes.
 
-__global__ void k_pivot(GraphDev g, LevelDesc d, const int32_t *__restrict__ F, int64_t ld,
-                        int64_t R, int32_t *__restrict__ pstart, uint8_t *__restrict__ pslot,
-                        int64_t *__restrict__ work, const int64_t *R_dev) {
+// Advance setup of a level in one pass: every row's pivot and the
+// exclusive scan of the rows' work into woff (woff[R] = the total).
+// Tiles of kPsRows consecutive rows are taken by ticket; a tile's offset
+// comes from the decoupled look-back of the single-pass level
+// (lookback_prefix), so the scan needs no second launch.  lookback:
+// ptiles + kLbExtra zeroed words (tile words, then the ticket, the total,
+// the error word and the count of finished CTAs).  The CTA that finishes
+// last writes woff[R] and, with stage (mapped host memory), stage[0] = the
+// row count, stage[1] = the error words (the producing level's and this
+// scan's, OR-ed), stage[2] = the total and stage[3] = the producing level's
+// probe bytes.  R_dev: as for launch_pivot_scan.
+constexpr int kPsThreads = 256, kPsIpt = 4;
+constexpr int64_t kPsRows = (int64_t)kPsThreads * kPsIpt;
+__global__ void __launch_bounds__(kPsThreads, 4) k_pivot_scan(
+    GraphDev g, LevelDesc d, const int32_t *__restrict__ F, int64_t ld, int64_t R,
+    int32_t ptiles, int32_t *__restrict__ pstart, uint8_t *__restrict__ pslot,
+    int64_t *__restrict__ woff, const int64_t *R_dev, unsigned long long *lookback,
+    int32_t spin_limit, long long *stage) {
+  __shared__ int64_t s_val[kPsRows];
+  __shared__ int64_t s_warp[33];
+  __shared__ int32_t s_tile;
+  __shared__ unsigned long long s_prefix;
   // the actual row count (R is then the launch's bound); a set error word
   // beside it means the level that wrote the rows gave up a wait, so some
   // rows were never written: read none of them
-  if (R_dev) R = R_dev[1] ? 0 : R_dev[0];
-  int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R; r += stride) {
-    int32_t best = 0x7fffffff, best_start = 0, best_slot = 0;
+  long long rows_in = R, lvl_err = 0, lvl_probes = 0;
+  if (R_dev) {
+    rows_in = R_dev[0];
+    lvl_err = R_dev[1];
+    lvl_probes = R_dev[2];
+    R = lvl_err ? 0 : min(R, (int64_t)rows_in);
+  }
+  const int32_t ntiles = (int32_t)((R + kPsRows - 1) / kPsRows);  // <= ptiles
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = (int32_t)atomicAdd(lookback + ptiles, 1ull);
+    __syncthreads();
+    const int32_t tile = s_tile;
+    if (tile >= ntiles) break;  // uniform across the block
+    const int64_t base = (int64_t)tile * kPsRows;
+    // rows base + j*kPsThreads + t: each load and store of a warp covers 32
+    // consecutive rows.  Per row, the pivot is the mapped neighbour of pi_i
+    // whose pi_i-label segment is shortest (only pi_i's label can match);
+    // its length is the row's work.  Neighbour slot b is taken for all of a
+    // thread's rows at once, so their loads are in flight together.
+    int32_t best[kPsIpt], bstart[kPsIpt], bslot[kPsIpt];
+#pragma unroll
+    for (int j = 0; j < kPsIpt; ++j) {
+      best[j] = base + j * kPsThreads + threadIdx.x < R ? 0x7fffffff : 0;
+      bstart[j] = 0;
+      bslot[j] = 0;
+    }
     for (int b = 0; b < d.nb; ++b) {
-      const int32_t x = F[(int64_t)d.bpos[b] * ld + r];
-      if (!GSM_IN_BOUNDS(g.dbg, x >= 0 && x < g.n, kDbgPivotVertex)) {
-        best = 0;  // the row gets no candidates
-        best_start = 0;
-        best_slot = b;
-        break;
-      }
-      const int2 seg = label_segment(g, x, d.lab);  // only pi_i's label can match
-      if (seg.y - seg.x < best) {
-        best = seg.y - seg.x;
-        best_start = seg.x;
-        best_slot = b;
+      int32_t x[kPsIpt];
+#pragma unroll
+      for (int j = 0; j < kPsIpt; ++j)  // rows past R, or with no work left, read nothing
+        x[j] = best[j] ? F[(int64_t)d.bpos[b] * ld + base + j * kPsThreads + threadIdx.x] : 0;
+#pragma unroll
+      for (int j = 0; j < kPsIpt; ++j) {
+        if (!best[j]) continue;
+        if (!GSM_IN_BOUNDS(g.dbg, x[j] >= 0 && x[j] < g.n, kDbgPivotVertex)) {
+          best[j] = 0;  // the row gets no candidates
+          bstart[j] = 0;
+          bslot[j] = b;
+          continue;
+        }
+        const int2 seg = label_segment(g, x[j], d.lab);
+        if (seg.y - seg.x < best[j]) {
+          best[j] = seg.y - seg.x;
+          bstart[j] = seg.x;
+          bslot[j] = b;
+        }
       }
     }
-    pstart[r] = best_start;
-    pslot[r] = (uint8_t)best_slot;
-    work[r] = best;
+#pragma unroll
+    for (int j = 0; j < kPsIpt; ++j) {
+      const int64_t r = base + j * kPsThreads + threadIdx.x;
+      if (r < R) {
+        pstart[r] = bstart[j];
+        pslot[r] = (uint8_t)bslot[j];
+      }
+      s_val[j * kPsThreads + threadIdx.x] = r < R ? best[j] : 0;
+    }
+    __syncthreads();
+    // thread t scans rows base + t*kPsIpt .. + kPsIpt - 1
+    int64_t loc[kPsIpt];
+    int64_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < kPsIpt; ++j) {
+      loc[j] = sum;
+      sum += s_val[threadIdx.x * kPsIpt + j];
+    }
+    int64_t total;
+    const int64_t ex = block_excl_scan(sum, s_warp, &total);
+    if (warp == 0) {
+      const unsigned long long p =
+          lookback_prefix(lookback, tile, ptiles, (unsigned long long)total, lane, spin_limit);
+      if (lane == 0) s_prefix = p;
+    }
+    __syncthreads();
+    const int64_t off = (int64_t)s_prefix + ex;
+#pragma unroll
+    for (int j = 0; j < kPsIpt; ++j) s_val[threadIdx.x * kPsIpt + j] = off + loc[j];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kPsIpt; ++j) {
+      const int64_t r = base + j * kPsThreads + threadIdx.x;
+      if (r < R) woff[r] = s_val[j * kPsThreads + threadIdx.x];
+    }
+    __syncthreads();  // s_val and s_tile are reused by the next tile
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();  // this CTA's offsets and look-back words before its count
+    const unsigned long long done = atomicAdd(lookback + ptiles + 3, 1ull);
+    if (done == gridDim.x - 1) {  // every other CTA has finished
+      __threadfence();
+      const long long W = (long long)atomicAdd(lookback + ptiles + 1, 0ull);
+      const long long err = (long long)atomicAdd(lookback + ptiles + 2, 0ull);
+      woff[R] = W;
+      if (stage) {
+        stage[0] = rows_in;
+        stage[1] = lvl_err | err;
+        stage[2] = W;
+        stage[3] = lvl_probes;
+      }
+    }
   }
 }
 
 // tile_row[t] = the row whose candidates include local item t*tile_items
 // (rows partition the items, so exactly one row writes each entry);
-// tile_row[tiles] = rb - 1.  Rows < 2^31.
+// tile_row[tiles] = rb - 1.  Rows < 2^31.  Also zeroes lookback[0, lb_words).
 __global__ void k_tile_rows(const int64_t *__restrict__ woff, int64_t ra, int64_t rb, int64_t wa,
                             int64_t tile_items, int64_t tiles, int32_t *__restrict__ tile_row,
-                            unsigned long long *__restrict__ lookback) {
+                            unsigned long long *__restrict__ lookback, int64_t lb_words) {
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  if (lookback)
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tiles + kLbExtra;
-         t += stride)
-      lookback[t] = 0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < lb_words; t += stride)
+    lookback[t] = 0;
   for (int64_t r = ra + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rb; r += stride) {
     const int64_t s = woff[r] - wa, e = woff[r + 1] - wa;
     if (e <= s) continue;
@@ -741,18 +832,6 @@ __global__ void k_fetch(const uint32_t *__restrict__ src, uint32_t *__restrict__
   for (int32_t i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
 }
 
-// dst[0] = S (survivor count), dst[1] = the error word, dst[2] = woff[S].
-__global__ void k_fetch_level(const unsigned long long *__restrict__ words,
-                              const int64_t *__restrict__ woff, long long *__restrict__ dst) {
-  if (threadIdx.x == 0) {
-    const long long S = (long long)words[0];
-    dst[0] = S;
-    dst[1] = (long long)words[1];
-    dst[2] = (long long)woff[S];
-    dst[3] = (long long)words[2];
-  }
-}
-
 // flags[r] = 1 where row r's prefix (positions 0..p-1) differs from row
 // r-1's, or, for r = 0, from the prefix the last earlier piece ended with.
 __global__ void k_prefix_change(const int32_t *__restrict__ F, int64_t ld, int64_t rows,
@@ -914,11 +993,6 @@ int launch_label_segments(const GraphDev &g, int32_t num_labels, int32_t *edge_c
   return launches + 1;
 }
 
-void launch_fetch_level(const unsigned long long *words, const int64_t *woff, void *dst,
-                        cudaStream_t s) {
-  k_fetch_level<<<1, 32, 0, s>>>(words, woff, (long long *)dst);
-}
-
 void launch_fetch(const void *src, void *dst, size_t bytes, cudaStream_t s) {
   const int32_t n = (int32_t)(std::min<size_t>(bytes, 4096) / 4);
   if (n > 0) k_fetch<<<1, 128, 0, s>>>((const uint32_t *)src, (uint32_t *)dst, n);
@@ -984,22 +1058,19 @@ void launch_refine(const GraphDev &g, const RefineDesc &d, const uint32_t *bm_in
 int64_t scan_tmp_elems(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
 
 template <typename T>
-// n_dev (optional): the length is read on the device, n is its upper bound
-// (the grids are sized by n; tiles past the length contribute zero).
-void scan_impl(const T *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t s,
-               const int64_t *n_dev = nullptr) {
+void scan_impl(const T *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t s) {
   const int64_t nb = (n + kScanTile - 1) / kScanTile;
   if (nb == 0) {
     cudaMemsetAsync(out, 0, sizeof(int64_t), s);
     return;
   }
   if (n <= kOneCtaMax) {
-    k_scan_one_cta<T><<<1, kOneThreads, 0, s>>>(in, n, out, n_dev);
+    k_scan_one_cta<T><<<1, kOneThreads, 0, s>>>(in, n, out);
     return;
   }
-  k_scan_reduce<T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, tmp, n_dev);
+  k_scan_reduce<T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, tmp);
   k_scan_partials<<<1, 1024, 0, s>>>(tmp, nb);
-  k_scan_down<T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, tmp, nb, out, n_dev);
+  k_scan_down<T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, tmp, nb, out);
 }
 
 int scan_kernels(int64_t n) {
@@ -1015,11 +1086,6 @@ void launch_scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *tmp, c
   scan_impl<int64_t>(in, out, n, tmp, s);
 }
 
-void launch_scan_i64_dev(const int64_t *in, int64_t *out, int64_t n_max, const int64_t *n_dev,
-                         int64_t *tmp, cudaStream_t s) {
-  scan_impl<int64_t>(in, out, n_max, tmp, s, n_dev);
-}
-
 void launch_bitmap_to_list(const uint32_t *bitmap, int32_t n_words, int32_t *cnt, int64_t *off,
                            int64_t *tmp, int32_t *out, cudaStream_t s) {
   k_bitmap_popc<<<grid_for(n_words, 256), 256, 0, s>>>(bitmap, n_words, cnt);
@@ -1027,10 +1093,18 @@ void launch_bitmap_to_list(const uint32_t *bitmap, int32_t n_words, int32_t *cnt
   k_bitmap_emit<<<grid_for(n_words, 256), 256, 0, s>>>(bitmap, n_words, off, out);
 }
 
-void launch_pivot(const GraphDev &g, const LevelDesc &d, const int32_t *F, int64_t ld, int64_t R,
-                  int32_t *pstart, uint8_t *pslot, int64_t *work, cudaStream_t s,
-                  const int64_t *R_dev) {
-  k_pivot<<<grid_for(R, 256, 152 * 64), 256, 0, s>>>(g, d, F, ld, R, pstart, pslot, work, R_dev);
+int64_t pivot_scan_words(int64_t R) {
+  return std::max<int64_t>(1, (R + kPsRows - 1) / kPsRows) + kLbExtra;
+}
+
+void launch_pivot_scan(const GraphDev &g, const LevelDesc &d, const int32_t *F, int64_t ld,
+                       int64_t R, int32_t *pstart, uint8_t *pslot, int64_t *woff,
+                       unsigned long long *lookback, int32_t spin_limit, void *stage,
+                       cudaStream_t s, const int64_t *R_dev) {
+  const int64_t ptiles = pivot_scan_words(R) - kLbExtra;
+  const int grid = (int)std::min<int64_t>(ptiles, 152 * 4);  // the CTAs resident at once
+  k_pivot_scan<<<grid, kPsThreads, 0, s>>>(g, d, F, ld, R, (int32_t)ptiles, pstart, pslot, woff,
+                                           R_dev, lookback, spin_limit, (long long *)stage);
 }
 
 int64_t extend_tiles(int64_t wa, int64_t wb, int32_t block) {
@@ -1040,12 +1114,13 @@ int64_t extend_tiles(int64_t wa, int64_t wb, int32_t block) {
 
 void launch_tile_rows(const int64_t *woff, int64_t ra, int64_t rb, int64_t wa, int64_t wb,
                       int32_t block, int32_t *tile_row, unsigned long long *lookback,
-                      cudaStream_t s) {
+                      cudaStream_t s, int64_t extra_words) {
   const int64_t tiles = extend_tiles(wa, wb, block);
-  if (tiles <= 0) return;
-  const int64_t n = std::max<int64_t>(rb - ra, lookback ? tiles + kLbExtra : 0);
+  if (tiles <= 0 && extra_words <= 0) return;
+  const int64_t lb_words = lookback ? tiles + kLbExtra + extra_words : 0;
+  const int64_t n = std::max<int64_t>(rb - ra, lb_words);
   k_tile_rows<<<grid_for(n, 256, 152 * 64), 256, 0, s>>>(
-      woff, ra, rb, wa, (int64_t)block * kItemsPerThread, tiles, tile_row, lookback);
+      woff, ra, rb, wa, (int64_t)block * kItemsPerThread, tiles, tile_row, lookback, lb_words);
 }
 
 void launch_extend_count(const GraphDev &g, const LevelDesc &d, const int32_t *F, int64_t ld,

@@ -165,10 +165,6 @@ int64_t scan_tmp_elems(int64_t n);
 int scan_kernels(int64_t n);
 void launch_scan_i32(const int32_t *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t s);
 void launch_scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t s);
-// The same with the length read on the device (*n_dev <= n_max; tmp sized
-// for n_max; out needs n_max + 1 elements).
-void launch_scan_i64_dev(const int64_t *in, int64_t *out, int64_t n_max, const int64_t *n_dev,
-                         int64_t *tmp, cudaStream_t s);
 
 // Bitmap -> ascending vertex list.  cnt: int32[n_words], off: int64[n_words+1]
 // (scratch), tmp: scan_tmp_elems(n_words).
@@ -177,17 +173,27 @@ void launch_bitmap_to_list(const uint32_t *bitmap, int32_t n_words, int32_t *cnt
 
 // Frontiers are column-major: position c of row r is F[c*ld + r].
 
-// Per row: pick the mapped neighbour of pi_i with the fewest neighbours (the
-// pivot) and record its CSR start, its slot in bpos, and its degree as work
-// (int64, so the work array can be scanned in place into offsets).  F has
-// leading dimension ld >= R.
+// Advance setup of a level (Sec. 3.3): per row, pick the mapped neighbour of
+// pi_i whose pi_i-label segment is shortest (the pivot) and record that
+// segment's CSR start and the neighbour's slot in d.bpos (pstart, pslot: R
+// entries); woff (R + 1 entries) receives the exclusive scan of the segment
+// lengths, woff[R] = the level's candidate total.  One launch: the scan uses
+// a decoupled look-back over tiles of rows.  F has leading dimension ld >= R.
+// lookback: pivot_scan_words(R) words, zeroed before the launch (a memset,
+// or launch_tile_rows' extra words); a look-back wait longer than spin_limit
+// polls sets the error word.  stage (optional, device view of mapped host
+// memory, 4 words) receives, once the kernel is done: [0] the row count,
+// [1] non-zero if a wait ran out (this scan's or, with R_dev, the producing
+// level's), [2] woff[R], [3] R_dev[2] (0 without R_dev).
 // With R_dev the row count is read on the device (R_dev[0]; R is its upper
-// bound) and R_dev[1] is the error word of the level that wrote F: when it is
-// set (a look-back wait ran out, so some rows were never written) no row is
-// read.
-void launch_pivot(const GraphDev &g, const LevelDesc &d, const int32_t *F, int64_t ld, int64_t R,
-                  int32_t *pstart, uint8_t *pslot, int64_t *work, cudaStream_t s,
-                  const int64_t *R_dev = nullptr);
+// bound), R_dev[1] is the error word of the level that wrote F (when it is
+// set, some rows were never written and no row is read) and R_dev[2] its
+// probe bytes: the words a single-pass level leaves after its total.
+int64_t pivot_scan_words(int64_t R);
+void launch_pivot_scan(const GraphDev &g, const LevelDesc &d, const int32_t *F, int64_t ld,
+                       int64_t R, int32_t *pstart, uint8_t *pslot, int64_t *woff,
+                       unsigned long long *lookback, int32_t spin_limit, void *stage,
+                       cudaStream_t s, const int64_t *R_dev = nullptr);
 
 // Number of extend tiles for candidates [wa, wb).
 int64_t extend_tiles(int64_t wa, int64_t wb, int32_t block);
@@ -195,10 +201,11 @@ int64_t extend_tiles(int64_t wa, int64_t wb, int32_t block);
 // tile_row[0..tiles]: first row of every tile of candidates [wa, wb) of rows
 // [ra, rb) (woff = exclusive work offsets of the level).
 // Limits of one extend launch: wb - wa < 2^30, rows < 2^31, ld * (i+1) < 2^31.
-// Also zeroes lookback[0 .. tiles + kLbExtra) when lookback is non-null.
+// Also zeroes lookback[0 .. tiles + kLbExtra + extra_words) when lookback is
+// non-null (the extra words: a following launch_pivot_scan's look-back).
 void launch_tile_rows(const int64_t *woff, int64_t ra, int64_t rb, int64_t wa, int64_t wb,
                       int32_t block, int32_t *tile_row, unsigned long long *lookback,
-                      cudaStream_t s);
+                      cudaStream_t s, int64_t extra_words = 0);
 
 // Verification pass over candidates [wa, wb): writes one survivor bit per
 // candidate into masks (if non-null), one survivor count per tile into
@@ -285,11 +292,6 @@ void launch_split_points(const int64_t *woff, int64_t R, int64_t step, int64_t J
 // small kernel; dst is typically the device view of mapped pinned host memory,
 // so small reads back to the host do not queue behind copy-engine transfers.
 void launch_fetch(const void *src, void *dst, size_t bytes, cudaStream_t s);
-// After a single-pass level and the next level's pivot and work scan: dst
-// (4 x int64) = the survivor count S (words[0]), the error word (words[1]),
-// woff[S] (the next level's candidate total) and the probe bytes (words[2]).
-void launch_fetch_level(const unsigned long long *words, const int64_t *woff, void *dst,
-                        cudaStream_t s);
 
 // Sorting many small results at once (one CTA each): rows src (count x k,
 // row-major) into canonical lexicographic order at dst (count x k); sort = 0
