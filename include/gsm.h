@@ -90,6 +90,13 @@ typedef void (*gsm_free_fn)(void *alloc_ctx, void *ptr, size_t bytes, void *stre
  * byte model), into gsm_kernel_stat.probe_bytes (and algo_bytes).  Costs two
  * row-pointer loads per check; results are unchanged. */
 #define GSM_OPT_COUNT_PROBES 32
+/* The same for the work scan of the advance setup (the pivot choice and the
+ * scan of every row's candidate count, one kernel per level): its second
+ * tile never publishes its work total, so the waits of the tiles after it
+ * run out; the call returns GSM_ERR_TIMEOUT, no offset is used, and the
+ * context stays usable.  Only levels of more than 1,024 rows have a second
+ * tile. */
+#define GSM_OPT_INJECT_SCAN_STALL 64
 
 typedef struct gsm_options {
   /* Cap on device memory for intermediate frontiers and scratch, in bytes.

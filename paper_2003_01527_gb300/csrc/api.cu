@@ -688,6 +688,7 @@ struct Run {
   int32_t block;
   int32_t spin_limit;  // polls a look-back wait may take
   int32_t stall_tile;  // GSM_OPT_INJECT_LOOKBACK_STALL: the tile that withholds its count
+  int32_t scan_stall_tile;  // GSM_OPT_INJECT_SCAN_STALL: the same for the work scan
   int64_t wcap;        // max candidates per extend launch
   int64_t chunk_rows;  // max rows per extend launch (0 = unbounded)
   uint64_t acc_rows = 0;  // final rows so far, in ctx->acc[0]
@@ -910,13 +911,14 @@ void process_fused(Run &R, int32_t i, const int32_t *F, int64_t ld, const int32_
   int64_t *woff2 = (int64_t *)stack_push(ctx, sizeof(int64_t) * (W + 1));
   timed(ctx, K_PIVOT, 0.0, 0, 1, [&] {
     launch_pivot_scan(R.g, dn, Fn, W, W, pstart2, pslot2, woff2, lb + tiles + kLbExtra,
-                      R.spin_limit, ctx->d_stage, ctx->stream, S_dev);
+                      R.spin_limit, ctx->d_stage, R.scan_stall_tile, ctx->stream, S_dev);
   });
   CU(cudaGetLastError());
   CU(cudaStreamSynchronize(ctx->stream));
   const int64_t S = ((volatile int64_t *)ctx->h_stage)[0];
   if (((volatile int64_t *)ctx->h_stage)[1])
-    FAIL(GSM_ERR_TIMEOUT, "a verification tile waited too long for its predecessors");
+    FAIL(GSM_ERR_TIMEOUT,
+         "a verification or work-scan tile waited too long for its predecessors");
   const int64_t W2 = ((volatile int64_t *)ctx->h_stage)[2];
   const double probes = (double)((volatile int64_t *)ctx->h_stage)[3];
   ctx->kstats[K_FUSED].algo_bytes += (double)S * 4.0 * w_out + probes;
@@ -990,12 +992,12 @@ void recurse(Run &R, int32_t i, const int32_t *F, int64_t ld, int64_t rows) {
   timed(ctx, K_PIVOT, (double)rows * (4.0 * d.nb + 8.0 * d.nb + 13.0), (uint64_t)rows, 1,
         [&] {
     launch_pivot_scan(R.g, d, F, ld, rows, pstart, pslot, woff, plb, R.spin_limit,
-                      ctx->d_stage, ctx->stream);
+                      ctx->d_stage, R.scan_stall_tile, ctx->stream);
   });
   CU(cudaGetLastError());
   CU(cudaStreamSynchronize(ctx->stream));
   if (((volatile int64_t *)ctx->h_stage)[1])
-    FAIL(GSM_ERR_TIMEOUT, "a pivot-scan tile waited too long for its predecessors");
+    FAIL(GSM_ERR_TIMEOUT, "a work-scan tile waited too long for its predecessors");
   const int64_t W = ((volatile int64_t *)ctx->h_stage)[2];
   recurse_rest(R, i, F, ld, rows, pstart, pslot, woff, W);
   stack_release(ctx, mk);
@@ -1261,6 +1263,7 @@ void run_query(gsm_ctx *ctx, const gsm_query *q, bool enumerate, int32_t *out, u
   R.block = ctx->opt.block_size > 0 ? ctx->opt.block_size : 256;
   R.spin_limit = ctx->opt.lookback_spin_limit > 0 ? ctx->opt.lookback_spin_limit : kLbSpinLimit;
   R.stall_tile = (ctx->opt.flags & GSM_OPT_INJECT_LOOKBACK_STALL) ? 1 : -1;
+  R.scan_stall_tile = (ctx->opt.flags & GSM_OPT_INJECT_SCAN_STALL) ? 1 : -1;
   R.chunk_rows = ctx->opt.chunk_rows;
   // masks take W/8 bytes and tile arrays 12 bytes per tile of scratch
   R.wcap = std::max<int64_t>((int64_t)ctx->max_deg + 1,

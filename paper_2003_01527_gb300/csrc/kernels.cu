@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(kPsThreads, 4) k_pivot_scan(
     GraphDev g, LevelDesc d, const int32_t *__restrict__ F, int64_t ld, int64_t R,
     int32_t ptiles, int32_t *__restrict__ pstart, uint8_t *__restrict__ pslot,
     int64_t *__restrict__ woff, const int64_t *R_dev, unsigned long long *lookback,
-    int32_t spin_limit, long long *stage) {
+    int32_t spin_limit, long long *stage, int32_t stall_tile) {
   __shared__ int64_t s_val[kPsRows];
   __shared__ int64_t s_warp[33];
   __shared__ int32_t s_tile;
@@ -432,8 +432,18 @@ __global__ void __launch_bounds__(kPsThreads, 4) k_pivot_scan(
     int64_t total;
     const int64_t ex = block_excl_scan(sum, s_warp, &total);
     if (warp == 0) {
-      const unsigned long long p =
-          lookback_prefix(lookback, tile, ptiles, (unsigned long long)total, lane, spin_limit);
+      // stall_tile (fault injection) adds its work to the total but never
+      // publishes its tile word, so the waits of the tiles after it run out
+      if (lane == 0) {
+        if (tile != stall_tile)
+          lookback_publish(lookback, tile, ptiles, (unsigned long long)total);
+        else if (total)
+          atomicAdd(lookback + ptiles + 1, (unsigned long long)total);
+      }
+      __syncwarp();
+      const unsigned long long p = lookback_resolve(lookback, tile, ptiles,
+                                                    (unsigned long long)total, lane, spin_limit,
+                                                    tile != stall_tile);
       if (lane == 0) s_prefix = p;
     }
     __syncthreads();
@@ -1100,11 +1110,12 @@ int64_t pivot_scan_words(int64_t R) {
 void launch_pivot_scan(const GraphDev &g, const LevelDesc &d, const int32_t *F, int64_t ld,
                        int64_t R, int32_t *pstart, uint8_t *pslot, int64_t *woff,
                        unsigned long long *lookback, int32_t spin_limit, void *stage,
-                       cudaStream_t s, const int64_t *R_dev) {
+                       int32_t stall_tile, cudaStream_t s, const int64_t *R_dev) {
   const int64_t ptiles = pivot_scan_words(R) - kLbExtra;
   const int grid = (int)std::min<int64_t>(ptiles, 152 * 4);  // the CTAs resident at once
   k_pivot_scan<<<grid, kPsThreads, 0, s>>>(g, d, F, ld, R, (int32_t)ptiles, pstart, pslot, woff,
-                                           R_dev, lookback, spin_limit, (long long *)stage);
+                                           R_dev, lookback, spin_limit, (long long *)stage,
+                                           stall_tile);
 }
 
 int64_t extend_tiles(int64_t wa, int64_t wb, int32_t block) {

@@ -184,7 +184,9 @@ void launch_bitmap_to_list(const uint32_t *bitmap, int32_t n_words, int32_t *cnt
 // polls sets the error word.  stage (optional, device view of mapped host
 // memory, 4 words) receives, once the kernel is done: [0] the row count,
 // [1] non-zero if a wait ran out (this scan's or, with R_dev, the producing
-// level's), [2] woff[R], [3] R_dev[2] (0 without R_dev).
+// level's), [2] woff[R], [3] R_dev[2] (0 without R_dev).  stall_tile (-1 =
+// none) is fault injection for tests: that tile never publishes its
+// look-back word, so the waits of the tiles after it run out.
 // With R_dev the row count is read on the device (R_dev[0]; R is its upper
 // bound), R_dev[1] is the error word of the level that wrote F (when it is
 // set, some rows were never written and no row is read) and R_dev[2] its
@@ -193,7 +195,7 @@ int64_t pivot_scan_words(int64_t R);
 void launch_pivot_scan(const GraphDev &g, const LevelDesc &d, const int32_t *F, int64_t ld,
                        int64_t R, int32_t *pstart, uint8_t *pslot, int64_t *woff,
                        unsigned long long *lookback, int32_t spin_limit, void *stage,
-                       cudaStream_t s, const int64_t *R_dev = nullptr);
+                       int32_t stall_tile, cudaStream_t s, const int64_t *R_dev = nullptr);
 
 // Number of extend tiles for candidates [wa, wb).
 int64_t extend_tiles(int64_t wa, int64_t wb, int32_t block);

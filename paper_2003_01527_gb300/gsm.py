@@ -45,6 +45,7 @@ GSM_OPT_COMPRESSED_FRONTIERS = 4
 GSM_OPT_INJECT_LOOKBACK_STALL = 8
 GSM_OPT_INJECT_SORT_STALL = 16
 GSM_OPT_COUNT_PROBES = 32
+GSM_OPT_INJECT_SCAN_STALL = 64
 
 MAX_K = 16
 
@@ -502,7 +503,8 @@ class Matcher:
                  two_pass: bool = False, compressed: bool = False, lookback_spin_limit: int = 0,
                  inject_lookback_stall: bool = False, alloc_hook=None, lookahead: int = 0,
                  hub_bitmap_bytes: int = 0, host_workers: int = 0,
-                 inject_sort_stall: bool = False, count_probes: bool = False):
+                 inject_sort_stall: bool = False, count_probes: bool = False,
+                 inject_scan_stall: bool = False):
         import torch
         self.device = device
         opt = gsm_default_options()
@@ -527,7 +529,8 @@ class Matcher:
             (GSM_OPT_COMPRESSED_FRONTIERS if compressed else 0) | \
             (GSM_OPT_INJECT_LOOKBACK_STALL if inject_lookback_stall else 0) | \
             (GSM_OPT_INJECT_SORT_STALL if inject_sort_stall else 0) | \
-            (GSM_OPT_COUNT_PROBES if count_probes else 0)
+            (GSM_OPT_COUNT_PROBES if count_probes else 0) | \
+            (GSM_OPT_INJECT_SCAN_STALL if inject_scan_stall else 0)
         if torch_allocator:
             dev = device
 

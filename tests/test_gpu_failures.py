@@ -11,7 +11,11 @@ waits -- no GPU fault and no hang:
   exactly;
 * a look-back wait of the final row sort runs out (GSM_OPT_INJECT_SORT_STALL:
   one tile of every sort pass withholds its digit counts): GSM_ERR_TIMEOUT,
-  nothing written past the rows, and the context then lists exactly.
+  nothing written past the rows, and the context then lists exactly;
+* a look-back wait of a level's work scan runs out (GSM_OPT_INJECT_SCAN_STALL:
+  one tile of every pivot-and-scan launch withholds its work total):
+  GSM_ERR_TIMEOUT, the caller's buffer untouched, and the context still
+  counts exactly.
 """
 import hashlib
 
@@ -136,6 +140,35 @@ def test_sort_wait_runs_out(gsm_lib, cuda):
     rows = out[:n].cpu().numpy().astype("<i4")
     assert c == sl["count"]
     assert hashlib.sha256(rows.tobytes()).hexdigest() == sl["rows_sha256"]
+    m.close()
+
+
+def test_work_scan_wait_runs_out(gsm_lib, cuda):
+    import bench
+    g, queries = bench.load_workload()
+    sl = queries[0]
+    torch = cuda
+    m = gsm_lib.Matcher(device=0)
+    m.load_graph(g.row_ptr, g.col, g.labels)
+    Q = m.query(sl["k"], sl["edges"], sl["labels"]).restrict(0, 0, sl["root_hi"])
+    assert m.count(Q) == sl["count"]
+    # a level after the first has more rows than one scan tile (1,024)
+    assert max(m.last_run_stats()["frontier"][1:]) > 2048
+    m.close()
+    # a bound the levels' own waits never reach, short enough for the test
+    m = gsm_lib.Matcher(device=0, lookback_spin_limit=4096, inject_scan_stall=True)
+    m.load_graph(g.row_ptr, g.col, g.labels)
+    Q = m.query(sl["k"], sl["edges"], sl["labels"]).restrict(0, 0, sl["root_hi"])
+    out = torch.full((sl["count"] * sl["k"] + 1024,), -7, dtype=torch.int32, device="cuda")
+    for call in (lambda: m.enumerate(Q, out=out), lambda: m.count(Q)):
+        with pytest.raises(gsm_lib.GsmError) as e:
+            call()
+        assert e.value.status == gsm_lib.GSM_ERR_TIMEOUT
+        assert "work-scan" in str(e.value)
+    assert bool((out == -7).all())  # nothing was copied out
+    # the same context still runs kernels and counts exactly: a one-vertex
+    # query has no level and so no work scan
+    assert m.count(m.query(1, [], [0])) == int((g.labels == 0).sum())
     m.close()
 
 
