@@ -31,10 +31,38 @@ def test_library_exports_every_declared_symbol(gsm_lib):
     assert declared == set(gsm_lib.EXPORTED)
 
 
+def header_constants():
+    """Every integer #define of include/gsm.h, evaluated (plain literals,
+    parenthesised negatives, unsigned shifts)."""
+    out = {}
+    src = open(os.path.join(ROOT, "include", "gsm.h")).read()
+    for name, expr in re.findall(r"^#define\s+(GSM_\w+)\s+([^/\n]+)", src, flags=re.M):
+        expr = re.sub(r"(\d+)u\b", r"\1", expr.strip())
+        if re.fullmatch(r"[\d\s()<\-+]+", expr):
+            out[name] = eval(expr)  # integer literal arithmetic only (checked above)
+    return out
+
+
+def test_binding_constants_match_the_header(gsm_lib):
+    consts = header_constants()
+    assert {"GSM_OK", "GSM_ERR_TIMEOUT", "GSM_OPT_INJECT_SCAN_STALL",
+            "GSM_STATIC_SCRATCH_BITMAP_BYTES"} <= set(consts)
+    for name, value in consts.items():
+        assert getattr(gsm_lib, name) == value, name
+    # the option flags are distinct bits
+    flags = [v for n, v in consts.items() if n.startswith("GSM_OPT_")]
+    assert all(f > 0 and f & (f - 1) == 0 for f in flags)
+    assert len(set(flags)) == len(flags)
+
+
 def test_status_strings(gsm_lib):
     assert gsm_lib.gsm_status_string(0) == "GSM_OK"
     assert gsm_lib.gsm_status_string(-6) == "GSM_ERR_BUDGET"
     assert gsm_lib.gsm_status_string(-99) == "GSM_ERR_UNKNOWN"
+    # every status the header defines has its own name
+    for name, value in header_constants().items():
+        if name == "GSM_OK" or name == "GSM_PENDING" or name.startswith("GSM_ERR_"):
+            assert gsm_lib.gsm_status_string(value) == name, name
 
 
 def test_query_validation_without_device(gsm_lib):
