@@ -525,8 +525,11 @@ class ClockSampler:
         self.dev = device_index
         self.proc = None
         self.lines = []
+        self.mark = 0
 
-    def start(self):
+    def start(self, settle_s: float = 5.0):
+        """Starts nvidia-smi and returns once its first sample is in (at most
+        settle_s), so that its start-up does not overlap the timed steps."""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
@@ -536,14 +539,26 @@ class ClockSampler:
             self.thread.start()
         except Exception:
             self.proc = None
+            return
+        t0 = time.time()
+        while not self.lines and self.proc.poll() is None and time.time() - t0 < settle_s:
+            time.sleep(0.005)
+        self.mark = len(self.lines)  # samples from here on belong to the timed region
 
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
-    def stop(self):
+    def stop(self, wait_s: float = 0.5):
+        """Ends sampling; the record is the samples taken since start()
+        returned (waiting up to wait_s for one when the timed region was
+        shorter than the sampling interval)."""
         if not self.proc:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        t0 = time.time()
+        while len(self.lines) <= self.mark and self.proc.poll() is None and \
+                time.time() - t0 < wait_s:
+            time.sleep(0.005)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -551,7 +566,7 @@ class ClockSampler:
             self.proc.kill()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in self.lines[self.mark:]:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
