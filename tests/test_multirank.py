@@ -34,7 +34,9 @@ def _rank(rank, world, port, out):
 def test_two_rank_aggregation():
     world = 2
     port = _free_port()
-    with mp.Manager() as mgr:
+    # the manager's server process is spawned too: earlier tests leave this
+    # process multi-threaded, and a fork of it may deadlock
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.spawn(_rank, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
