@@ -1,9 +1,10 @@
 """The stored workload files under tests/golden/ against what wrote them
-(tests/golden/make_workloads.py): the seeded generators rebuild the same
-graphs (SHA-256 of the CSR and labels) and the same queries, and the
-oracle, re-run on the stored slices it finishes quickly, gives the stored
-counts and row digests.  So no stored value can have drifted from the
-oracle's.  No GPU."""
+(tests/golden/make_workloads.py, make_rmat20_counts.py): the seeded
+generators rebuild the same graphs (SHA-256 of the CSR and labels) and the
+same queries, and the oracle, re-run on the stored slices it finishes
+quickly, gives the stored counts and row digests (for the R-MAT 20 file:
+its graph and its listed slice).  So no stored value can have drifted from
+the oracle's.  No GPU."""
 import hashlib
 import json
 import os
@@ -65,3 +66,20 @@ def test_rmat18_batched_slices(oracle_lib):
     g, qs = I.rmat_labelled_workload(scale=18, num_labels=16, zipf_s=1.2, num_queries=256,
                                      kmin=3, kmax=10, non_tree=(2, 4), seed=4)
     check(gold, g, qs, max_count=300_000, min_checked=256)  # every slice
+
+
+def test_rmat20_unlabelled_graph_and_listed_slice(oracle_lib):
+    with open(os.path.join(GOLDEN, "rmat20_unlabelled.json")) as f:
+        gold = json.load(f)
+    g = I.rmat_unlabelled_graph(scale=20, seed=3)
+    assert graph_digest(g) == gold["graph"]["sha256"]
+    assert (g.n, g.nnz) == (gold["graph"]["n"], gold["graph"]["nnz"])
+    shapes = I.unlabelled_shapes()
+    listed = [s for s in gold["slices"] if s["rows_sha256"] and s["window"] is None]
+    assert listed
+    for s in listed:
+        count, rows, rc = oracle.match(g, shapes[s["shape"]],
+                                       root_range=(s["root_lo"], s["root_hi"]))
+        assert rc == oracle.OK
+        assert count == s["count"]
+        assert rows_digest(rows) == s["rows_sha256"]
